@@ -1,0 +1,304 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused D2Q9 MRTLB-VANSE stream + collide step.
+
+Workload (one GPU): the porous channel, 4096 x 4096 cells, FP32 populations,
+half-way bounce-back walls at the bottom and top, periodic in x, body force
+F^B = phi (1e-6, 0), tau = 0.6, kappa = 0.5, void fraction a seeded Gaussian
+random field (correlation length 32) mapped to [0.35, 1.0] with an embedded
+sharp block (1.0 -> 0.4 over two cells). One step = one time step of the whole
+lattice. Metric: MLUPS (million lattice-cell updates per second), with the
+achieved fraction of the measured HBM bandwidth for the step kernel.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on
+the host cores instead, on bounded row bands of the same channel.
+Multi-GPU runs (torchrun) are independent replicas, one lattice per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MRT-VANSE MLUPS & % HBM roofline; FP16-store vs FP32 at equal MMS L2 error"
+WORKLOAD = ("porous channel 4096x4096, D2Q9 MRT-VANSE, bounce-back walls top/bottom, periodic x, "
+            "g_x=1e-6, tau=0.6, kappa=0.5, GRF void fraction [0.35,1] (l=32, seed 2409) with a sharp block")
+TAU, G = 0.6, 1e-6
+DTYPE = {"fp32": "f32", "fp16": "f32", "bf16": "f32", "fp64": "f64"}
+SBYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        pass
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            try:
+                sm.append(float(r[0]))
+                smax = float(r[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        loaded = sorted(sm)[len(sm) // 2:] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_channel(n: int, storage: str, strip_rows: int = 0):
+    import paper_2409_02964_gb300 as P
+    from synth import fields
+    phi = fields.channel_phi(n, n)
+    lat = P.Lattice(n, n, TAU, bc_y="bounceback", storage=storage, strip_rows=strip_rows)
+    lat.set_void_fraction(phi)
+    lat.set_body_force(G, 0.0)
+    rho, ux, uy = fields.rest_fields(n, n)
+    lat.init_fields(rho, ux, uy)
+    return lat, phi
+
+
+def time_steps(lat, steps: int, warmup: int):
+    """Device time of `steps` step kernels on the library's stream (CUDA events)."""
+    import torch
+    lat.step(warmup)
+    lat.sync()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(lat.stream)
+    lat.step(steps)
+    ev1.record(lat.stream)
+    ev1.synchronize()
+    lat.sync()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def e2e_run(lat, phi: np.ndarray, steps: int):
+    """The per-step user sequence through the public API with host buffers: upload
+    phi(x, t) from pinned host memory, advance one step, read the FP64 mass back."""
+    import torch
+    host_phi = torch.from_numpy(np.ascontiguousarray(phi, dtype=np.float64)).pin_memory()
+    lat.set_void_fraction(host_phi)
+    lat.step(1)
+    lat.reduce()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        lat.set_void_fraction(host_phi)
+        lat.step(1)
+        lat.reduce()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dt, host_phi.numel() * 8, 3 * 8
+
+
+def oracle_rate(n_rows: int, nx: int, steps: int, threads: int):
+    """FP64 oracle on a band of the channel: returns (MLUPS, seconds, cells)."""
+    import oracle as O
+    from synth import fields
+    phi = fields.channel_phi(nx, n_rows)
+    prm = O.Params(nx=nx, ny=n_rows, **O.rates_from_tau(TAU), kappa=0.5, bc_y=1, nthreads=threads)
+    fb = np.stack([phi * G, np.zeros_like(phi)])
+    f = O.init(prm, np.ones((n_rows, nx)), np.zeros((n_rows, nx)), np.zeros((n_rows, nx)), phi, fb)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = O.step(prm, f, phi, None, fb)
+    dt = time.perf_counter() - t0
+    return nx * n_rows * steps / dt / 1e6, dt, nx * n_rows
+
+
+def cpu_baseline(nx: int, budget_s: float = 15.0):
+    import oracle as O
+    threads = O.max_threads()
+    rate, dt, _ = oracle_rate(16, nx, 1, threads)          # calibration
+    rows = int(max(8, min(1024, budget_s * rate * 1e6 / (2 * nx))))
+    rate, dt, cells = oracle_rate(rows, nx, 2, threads)
+    return {"value": round(rate, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"FP64 oracle, 2 steps of a {nx}x{rows} band of the channel (same recipe), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    nx = args.n
+    threads = O.max_threads()
+    rate, _, _ = oracle_rate(16, nx, 1, threads)
+    # each step: one oracle step of a row band sized so warmup + steps stay within ~90 s
+    per_step_s = 90.0 / max(1, args.steps + args.warmup)
+    rows = int(max(3, min(args.n, per_step_s * rate * 1e6 / nx)))
+    from synth import fields
+    phi = fields.channel_phi(nx, rows)
+    prm = O.Params(nx=nx, ny=rows, **O.rates_from_tau(TAU), kappa=0.5, bc_y=1, nthreads=threads)
+    fb = np.stack([phi * G, np.zeros_like(phi)])
+    f = O.init(prm, np.ones((rows, nx)), np.zeros((rows, nx)), np.zeros((rows, nx)), phi, fb)
+    for _ in range(args.warmup):
+        f = O.step(prm, f, phi, None, fb)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = O.step(prm, f, phi, None, fb)
+    dt = time.perf_counter() - t0
+    value = nx * rows * args.steps / dt / 1e6
+    sample = f"FP64 oracle, each step a {nx}x{rows} row band of the channel"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": nx, "ny": args.n, "storage": "fp64 (oracle)"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["fp32", "fp16", "bf16", "fp64"], default="fp32")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--strip-rows", type=int, default=0)
+    ap.add_argument("--quick", action="store_true", help="timed steps only (no e2e / variants / CPU baseline)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    lat, phi = build_channel(args.n, args.storage, args.strip_rows)
+    cells = args.n * args.n
+    m0 = lat.reduce()[0]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local).__enter__() if rank == 0 else None
+    secs = time_steps(lat, args.steps, args.warmup)
+    clocks = sampler.stop() if sampler else None
+    m1 = lat.reduce()[0]
+    if dist:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+        dist.barrier()
+    value = world * cells * args.steps / secs / 1e6
+    bpc = lat.bytes_per_cell
+    step_s = secs / args.steps
+    achieved = bpc * cells / step_s / 1e9
+    peak, peak_kind = _peaks()
+    shape = lat.launch_shape()
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.storage], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "storage": args.storage,
+                       "bytes_per_cell": bpc, "l2": "inputs larger than L2 (two population buffers of "
+                       f"{2 * 9 * cells * SBYTES[args.storage] / 1e9:.2f} GB, L2 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single", "launch": shape},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_source": f"{peak_kind} hbm_gbs", "kernel": "vanse_step_kernel"},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "mass_drift": (m1 - m0) / m0,
+        }
+    if not args.quick and rank == 0:
+        e2e_steps = 30
+        dt, h2d, d2h = e2e_run(lat, phi, e2e_steps)
+        out["e2e"] = {"value": round(world * cells * e2e_steps / dt / 1e6, 1), "unit": "MLUPS",
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "sequence": "set_void_fraction(host phi) + step(1) + reduce() per step"}
+    lat.close()
+    if not args.quick and rank == 0:
+        variants = {}
+        for st in ("fp16", "bf16", "fp64"):
+            if st == args.storage:
+                continue
+            lv, _ = build_channel(args.n, st)
+            ns = 2000 if st != "fp64" else 200
+            s = time_steps(lv, ns, 5)
+            variants[st] = {"MLUPS": round(cells * ns / s / 1e6, 1),
+                            "GB_s": round(lv.bytes_per_cell * cells * ns / s / 1e9, 1),
+                            "bytes_per_cell": lv.bytes_per_cell, "steps": ns}
+            lv.close()
+        out["variants"] = variants
+        out["cpu_baseline"] = cpu_baseline(args.n)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

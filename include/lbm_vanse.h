@@ -1,0 +1,157 @@
+/*
+ * lbm_vanse.h -- C ABI of the GB300 (sm_103a) library for the consistent
+ * multiple-relaxation-time lattice Boltzmann method for the volume-averaged
+ * Navier-Stokes equations (MRTLB-VANSE; Liu, Zhang, Min, Wu, arXiv:2409.02964),
+ * D2Q9, lattice units (dx = dt = c = 1, cs^2 = 1/3).
+ *
+ * One handle = one lattice resident on the current CUDA device. Every call is
+ * issued on the CUDA stream given at creation; calls that hand results back to
+ * host memory synchronise that stream. No C++ exception crosses this boundary:
+ * every entry point returns an lbm_status and keeps a message per handle
+ * (lbm_vanse_last_error).
+ *
+ * Layouts seen by callers: scalar fields are row-major [ny][nx] doubles (cell
+ * (x, y) at y*nx + x); population arrays are [9][ny][nx] doubles with the D2Q9
+ * order of Eq. (5): e_0 = (0,0), e_1..e_4 = E, N, W, S, e_5..e_8 = NE, NW, SW, SE.
+ * "on_device" = 1 means the pointer is a device pointer on the handle's device,
+ * 0 means host memory. Caller memory is only read or written during the call.
+ * Internally the library stores populations as SoA planes with a padded row
+ * pitch, in the precision chosen at creation; callers never see that layout.
+ */
+#ifndef LBM_VANSE_H
+#define LBM_VANSE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,       /* invalid argument (sizes, rates, pointers, unsupported option) */
+    LBM_ERR_CUDA = -2,      /* a CUDA runtime call failed; see lbm_vanse_last_error */
+    LBM_ERR_OOM = -3,       /* device allocation failed */
+    LBM_ERR_DIVERGED = -4,  /* a reduction found NaN/Inf in the populations */
+    LBM_ERR_STATE = -5,     /* call out of order (e.g. step before init_fields) */
+    LBM_ERR_TIMEOUT = -6    /* a kernel's bounded wait on its copy engine gave up */
+} lbm_status;
+
+/* Storage precision of the populations. FP64 computes in FP64; the others
+ * compute in FP32. FP16 and BF16 store deviations from the rest state,
+ * (f_i - f_i^rest) * 2^storage_scale_log2, with f_i^rest = w_i kappa rho0 for
+ * i >= 1 and (phi - 5 kappa / 9) rho0 for i = 0 (the rest equilibrium of Eq. 14). */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3 } lbm_storage;
+
+/* Boundary type of an axis pair: periodic (Sec. 3, default) or half-way
+ * bounce-back no-slip walls at both ends (Sec. 3.1). Walls are supported on y. */
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 } lbm_bc;
+
+/*
+ * Problem statement (Sec. 2.3 and 3): lattice size; relaxation TIME tau_nu of the
+ * shear moments (rate s_nu = 1/tau_nu, viscosity nu = (tau_nu - 1/2)/3, Eq. 3-4);
+ * the other diagonal entries of Gamma as RATES (s_e <= 0 derives s_e from the bulk
+ * viscosity nu_e = nu/3 that Eq. (A12) requires); kappa of the provisional
+ * equation of state (Eq. 13-14, default 0.5, Sec. 3); reference density rho0;
+ * boundary types; storage precision; model_b = 1 selects the model-B variant
+ * (kappa - phi -> kappa - 1 in Eq. 13 and 20, Sec. 2.3).
+ */
+typedef struct {
+    int nx, ny;
+    double tau_nu;
+    double s_e, s_eps, s_q, s_c;
+    double kappa;
+    double rho0;
+    int bc_x, bc_y;              /* lbm_bc */
+    int storage;                 /* lbm_storage */
+    int model_b;
+    int storage_scale_log2;      /* FP16/BF16 deviation scale exponent (default 16 / 0) */
+    int strip_rows;              /* rows per CTA strip of the step kernel; 0 = automatic */
+} lbm_vanse_params;
+
+typedef struct lbm_vanse* lbm_vanse_t;
+
+/* Fill *p with the paper's defaults: tau_nu = 0.8 (nu = 0.1), s_e derived,
+ * s_eps = 1.2, s_q = 1.4, s_c = 1 (Sec. 2.3), kappa = 0.5, rho0 = 1 (Sec. 3),
+ * periodic, FP32 storage. nx, ny are left at 0. */
+void lbm_vanse_default_params(lbm_vanse_params* p);
+
+/* Create a lattice on the current device. cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream). Allocates the two population buffers, the void-fraction
+ * and body-force buffers. Errors: LBM_ERR_ARG (sizes < 1, tau_nu <= 1/2, rates
+ * outside (0, 2), kappa outside [0, 1], bc_x = bounce-back), LBM_ERR_OOM. */
+lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_vanse_t* out);
+
+/* Void fraction phi(x, t) of the next step and phi(x, t+1) (Eq. 7, 13, 14, 20;
+ * d_t phi = phi(t+1) - phi(t), Sec. 2.3). phi_next = NULL means steady. After a
+ * step, phi(t) takes the value of phi(t+1) and the field is steady until the next
+ * call. Values must lie in (0, 1]. Must be called before lbm_vanse_init_fields. */
+lbm_status lbm_vanse_set_void_fraction(lbm_vanse_t h, const double* phi_t, const double* phi_next,
+                                       int on_device);
+
+/* Body force F^B(x, t) = phi(x, t) * (gx, gy) + field(x) (Eq. 6; the phi G form of
+ * Sec. 3.1 plus an optional per-cell part, [2][ny][nx], x component first, e.g.
+ * the manufactured force of Eq. 25). field may be NULL. Stays in effect until the
+ * next call. */
+lbm_status lbm_vanse_set_body_force(lbm_vanse_t h, double gx, double gy, const double* field,
+                                    int on_device);
+
+/* Initial populations f = f^eq(rho, u, phi) - F_i(u, F)/2 (Eq. 14, Eq. 6 with
+ * F = F^p + F^B, F^p from grad rho by Eq. 10 and 13), so that Eq. (7) returns u.
+ * rho, ux, uy: [ny][nx]. Uses the void fraction and body force set before. */
+lbm_status lbm_vanse_init_fields(lbm_vanse_t h, const double* rho, const double* ux,
+                                 const double* uy, int on_device);
+
+/* Advance nsteps time steps: per cell the fused stream + collide of Eq. (16)
+ * (moments Eq. 17/A1, equilibrium Eq. 18, force moments Eq. 19 with F^p of Eq. 13,
+ * penalty source Eq. 20 with gradients by Eq. 10, back-transform A1), streaming
+ * with periodic wrap or half-way bounce-back. Asynchronous on the stream. */
+lbm_status lbm_vanse_step(lbm_vanse_t h, int nsteps);
+
+/* Macroscopic fields at the current time (Eq. 7): rho = sum f / phi,
+ * u = (sum e f + F/2) / sum f with F = F^p + F^B, p = rho cs^2. Any output may
+ * be NULL. Arrays [ny][nx]. */
+lbm_status lbm_vanse_macros(lbm_vanse_t h, double* rho, double* ux, double* uy, double* p,
+                            int on_device);
+
+/* Post-streaming populations f_i(x, t) as [9][ny][nx] doubles (get), or replace
+ * them (set; e.g. to restore a checkpoint). */
+lbm_status lbm_vanse_get_populations(lbm_vanse_t h, double* f, int on_device);
+lbm_status lbm_vanse_set_populations(lbm_vanse_t h, const double* f, int on_device);
+
+/* Domain sums accumulated in FP64 on the device: mass = sum_x sum_i f_i and
+ * momentum sum_x sum_i e_i f_i (= sum of j = phi rho u - F/2, Eq. 17). Results to
+ * host memory (synchronises). Returns LBM_ERR_DIVERGED if any is NaN/Inf. */
+lbm_status lbm_vanse_reduce(lbm_vanse_t h, double* mass, double* momx, double* momy);
+
+/* Velocity error of Eq. (26), accumulated in FP64:
+ * *num = sum |u - u_ref|^2, *den = sum |u_ref|^2 (E_u = sqrt(num/den)).
+ * ux_ref, uy_ref: [ny][nx]. Results to host memory. */
+lbm_status lbm_vanse_velocity_error(lbm_vanse_t h, const double* ux_ref, const double* uy_ref,
+                                    int on_device, double* num, double* den);
+
+/* Synchronise the stream and report any deferred kernel error (LBM_ERR_TIMEOUT
+ * if a bounded wait gave up, LBM_ERR_CUDA for a launch/runtime error). */
+lbm_status lbm_vanse_sync(lbm_vanse_t h);
+
+/* Steps taken since init_fields / set_populations. */
+long long lbm_vanse_step_count(lbm_vanse_t h);
+
+/* Device bytes one step reads and writes per cell as the method requires them
+ * (9 populations in and out, phi, plus phi(t+1) and the force field when set). */
+double lbm_vanse_bytes_per_cell(lbm_vanse_t h);
+
+/* Launch shape of the step kernel: threads per CTA, output columns per CTA,
+ * rows per strip, CTAs in x and y, dynamic shared memory bytes. Any may be NULL. */
+lbm_status lbm_vanse_launch_shape(lbm_vanse_t h, int* threads, int* cols, int* rows, int* grid_x,
+                                  int* grid_y, int* smem_bytes);
+
+/* Message of the last failed call on h (or of the last failed create when h is NULL). */
+const char* lbm_vanse_last_error(lbm_vanse_t h);
+
+/* Free every device buffer of h. Safe on NULL. */
+void lbm_vanse_destroy(lbm_vanse_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_VANSE_H */

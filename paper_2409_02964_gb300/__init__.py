@@ -1,0 +1,11 @@
+"""GB300 (sm_103a) implementation of the fused D2Q9 stream + collide step of the
+consistent MRT lattice Boltzmann method for the volume-averaged Navier-Stokes
+equations (MRTLB-VANSE, arXiv:2409.02964).
+
+``capi`` binds the C ABI of ``include/lbm_vanse.h``; ``Lattice`` is a thin handle
+over it. The computation runs only in the CUDA library (``liblbm_vanse.so``).
+"""
+from . import build, capi  # noqa: F401
+from .lattice import Lattice, LbmError  # noqa: F401
+
+__all__ = ["Lattice", "LbmError", "build", "capi"]

@@ -1,0 +1,92 @@
+"""ctypes binding of the C ABI in ``include/lbm_vanse.h``, same names, argument
+marshalling only. Every computation runs in the CUDA library; if the library is
+missing this module raises instead of falling back to anything else."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_STATE, LBM_ERR_TIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6)
+LBM_FP64, LBM_FP32, LBM_FP16, LBM_BF16 = 0, 1, 2, 3
+LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = 0, 1
+
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
+                -4: "LBM_ERR_DIVERGED", -5: "LBM_ERR_STATE", -6: "LBM_ERR_TIMEOUT"}
+
+# every entry point of include/lbm_vanse.h
+EXPORTS = [
+    "lbm_vanse_default_params", "lbm_vanse_create", "lbm_vanse_set_void_fraction",
+    "lbm_vanse_set_body_force", "lbm_vanse_init_fields", "lbm_vanse_step", "lbm_vanse_macros",
+    "lbm_vanse_get_populations", "lbm_vanse_set_populations", "lbm_vanse_reduce",
+    "lbm_vanse_velocity_error", "lbm_vanse_sync", "lbm_vanse_step_count",
+    "lbm_vanse_bytes_per_cell", "lbm_vanse_launch_shape", "lbm_vanse_last_error",
+    "lbm_vanse_destroy",
+]
+
+
+class lbm_vanse_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("tau_nu", ctypes.c_double),
+        ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
+        ("s_c", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+        ("storage", ctypes.c_int), ("model_b", ctypes.c_int),
+        ("storage_scale_log2", ctypes.c_int), ("strip_rows", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liblbm_vanse.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not found at {path}")
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    i = ctypes.c_int
+    d = ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    pp = ctypes.POINTER(lbm_vanse_params)
+    sig = {
+        "lbm_vanse_default_params": (None, [pp]),
+        "lbm_vanse_create": (i, [pp, vp, ctypes.POINTER(vp)]),
+        "lbm_vanse_set_void_fraction": (i, [vp, vp, vp, i]),
+        "lbm_vanse_set_body_force": (i, [vp, d, d, vp, i]),
+        "lbm_vanse_init_fields": (i, [vp, vp, vp, vp, i]),
+        "lbm_vanse_step": (i, [vp, i]),
+        "lbm_vanse_macros": (i, [vp, vp, vp, vp, vp, i]),
+        "lbm_vanse_get_populations": (i, [vp, vp, i]),
+        "lbm_vanse_set_populations": (i, [vp, vp, i]),
+        "lbm_vanse_reduce": (i, [vp, dp, dp, dp]),
+        "lbm_vanse_velocity_error": (i, [vp, vp, vp, i, dp, dp]),
+        "lbm_vanse_sync": (i, [vp]),
+        "lbm_vanse_step_count": (ctypes.c_longlong, [vp]),
+        "lbm_vanse_bytes_per_cell": (d, [vp]),
+        "lbm_vanse_launch_shape": (i, [vp, ip, ip, ip, ip, ip, ip]),
+        "lbm_vanse_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_vanse_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def default_params() -> lbm_vanse_params:
+    p = lbm_vanse_params()
+    load().lbm_vanse_default_params(ctypes.byref(p))
+    return p

@@ -1,0 +1,638 @@
+// lbm_vanse.cu -- host side of the C ABI declared in include/lbm_vanse.h.
+//
+// Owns the device buffers of one lattice (two population buffers used in
+// ping-pong, phi(t), phi(t+1), the optional body-force field, reduction scratch)
+// and launches the kernels of vanse_step.cuh / vanse_aux.cuh on the handle's
+// stream. Every entry point converts failures into an lbm_status and a message.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "lbm_vanse.h"
+#include "vanse_aux.cuh"
+#include "vanse_step.cuh"
+
+using namespace lbmv;
+
+namespace {
+
+constexpr int kThreads = 128;       // step kernel CTA size (W = kThreads - 4 columns)
+constexpr int kAuxThreads = 256;
+constexpr int kReduceBlocks = 1024;
+
+thread_local std::string g_create_error;
+
+int storage_bytes(int storage) {
+    switch (storage) {
+        case LBM_FP64: return 8;
+        case LBM_FP32: return 4;
+        default: return 2;
+    }
+}
+
+}  // namespace
+
+struct lbm_vanse {
+    lbm_vanse_params prm;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sbytes = 4, rbytes = 4;   // storage and compute element sizes
+    int P = 0;                    // padded row pitch (elements)
+    long long plane = 0;          // elements per plane
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* phi = nullptr;          // phi(t), R, padded
+    void* phin = nullptr;         // phi(t+1), R, padded
+    void* fb = nullptr;           // body-force field (2 planes), R, padded
+    bool unsteady = false, has_fb = false, phi_set = false, initialised = false;
+    double gx = 0, gy = 0;
+    double s_nu = 0, s_e = 0;
+    double scale = 1, inv_scale = 1;
+    int* err = nullptr;           // device flag set by bounded waits
+    double* partial = nullptr;    // reduction partials (kReduceBlocks * 3)
+    double* red_out = nullptr;    // reduction result (3)
+    double* scratch = nullptr;    // 3 dense double fields (macros / error norms)
+    long long steps = 0;
+    // step-kernel launch shape
+    int W = 0, H = 0, gridx = 0, gridy = 0, wwmax = 0;
+    std::string msg;
+};
+
+namespace {
+
+lbm_status fail(lbm_vanse* h, lbm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->msg = buf; else g_create_error = buf;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_vanse* h, cudaError_t e, const char* what) {
+    return fail(h, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                                      \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);         \
+    } while (0)
+
+template <typename R>
+Rest<R> make_rest(const lbm_vanse* h) {
+    Rest<R> r;
+    const double k = h->prm.kappa, r0 = h->prm.rho0;
+    r.ax = (R)(k * r0 / 9.0);
+    r.dg = (R)(k * r0 / 36.0);
+    r.k59 = (R)(5.0 * k * r0 / 9.0);
+    r.rho0 = (R)r0;
+    return r;
+}
+
+template <typename R>
+Lattice<R> make_lattice(const lbm_vanse* h) {
+    Lattice<R> L;
+    L.plane = h->plane;
+    L.nx = h->prm.nx;
+    L.ny = h->prm.ny;
+    L.P = h->P;
+    L.wall_y = h->prm.bc_y == LBM_BC_BOUNCEBACK;
+    L.model_b = h->prm.model_b;
+    L.kappa = (R)h->prm.kappa;
+    L.gx = (R)h->gx;
+    L.gy = (R)h->gy;
+    L.scale = (R)h->scale;
+    L.inv_scale = (R)h->inv_scale;
+    L.rest = make_rest<R>(h);
+    return L;
+}
+
+int aux_blocks(long long n) {
+    long long b = (n + kAuxThreads - 1) / kAuxThreads;
+    return (int)std::max<long long>(1, std::min<long long>(b, 65535LL * 8));
+}
+
+template <typename S>
+size_t step_smem_bytes(const lbm_vanse* h, int nR, int* slot_stride_out) {
+    using R = typename Prec<S>::R;
+    const int ring_off = (128 + 7 * kThreads * (int)sizeof(R) + 127) & ~127;
+    int slot = 9 * h->wwmax * (int)sizeof(S) + nR * h->wwmax * (int)sizeof(R);
+    slot = (slot + 127) & ~127;
+    if (slot_stride_out) *slot_stride_out = slot;
+    return (size_t)ring_off + (size_t)kSlots * slot;
+}
+
+template <typename S>
+lbm_status configure(lbm_vanse* h) {
+    using R = typename Prec<S>::R;
+    auto kern = vanse_step_kernel<S, R, kThreads>;
+    const size_t smax = step_smem_bytes<S>(h, 4, nullptr);
+    CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    const size_t s1 = step_smem_bytes<S>(h, 1, nullptr);
+    int per_sm = 0, nsm = 0;
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, s1));
+    CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const int resident = std::max(1, per_sm * nsm);
+    int H = h->prm.strip_rows;
+    if (H <= 0) {
+        int nstrips = std::max(1, resident / h->gridx);
+        H = (h->prm.ny + nstrips - 1) / nstrips;
+        H = std::max(H, 8);
+    }
+    h->H = std::min(H, h->prm.ny);
+    h->gridy = (h->prm.ny + h->H - 1) / h->H;
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status launch_step(lbm_vanse* h) {
+    using R = typename Prec<S>::R;
+    StepParams<R> p;
+    p.src = h->f[h->cur];
+    p.dst = h->f[1 - h->cur];
+    p.phi = (const R*)h->phi;
+    p.phin = h->unsteady ? (const R*)h->phin : (const R*)h->phi;
+    p.fb = h->has_fb ? (const R*)h->fb : nullptr;
+    p.plane = h->plane;
+    p.nx = h->prm.nx;
+    p.ny = h->prm.ny;
+    p.P = h->P;
+    p.W = h->W;
+    p.H = h->H;
+    p.wall_y = h->prm.bc_y == LBM_BC_BOUNCEBACK;
+    p.unsteady = h->unsteady;
+    p.has_fb = h->has_fb;
+    p.model_b = h->prm.model_b;
+    const int nR = 1 + (h->unsteady ? 1 : 0) + (h->has_fb ? 2 : 0);
+    int slot_stride = 0;
+    const size_t smem = step_smem_bytes<S>(h, nR, &slot_stride);
+    p.slot_stride = slot_stride;
+    p.wwmax = h->wwmax;
+    p.kappa = (R)h->prm.kappa;
+    p.gx = (R)h->gx;
+    p.gy = (R)h->gy;
+    p.s_c = (R)h->prm.s_c;
+    p.s_e = (R)h->s_e;
+    p.s_eps = (R)h->prm.s_eps;
+    p.s_q = (R)h->prm.s_q;
+    p.s_nu = (R)h->s_nu;
+    p.scale = (R)h->scale;
+    p.inv_scale = (R)h->inv_scale;
+    p.rest = make_rest<R>(h);
+    p.err = h->err;
+    dim3 grid(h->gridx, h->gridy);
+    vanse_step_kernel<S, R, kThreads><<<grid, kThreads, smem, h->stream>>>(p);
+    CK(h, cudaGetLastError());
+    h->cur = 1 - h->cur;
+    if (h->unsteady) {
+        // phi(t) <- phi(t+1); the field stays steady until the next set call
+        std::swap(h->phi, h->phin);
+        h->unsteady = false;
+    }
+    h->steps++;
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status run_init(lbm_vanse* h, const double* rho, const double* ux, const double* uy) {
+    using R = typename Prec<S>::R;
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    Lattice<R> L = make_lattice<R>(h);
+    init_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>(
+        (S*)h->f[h->cur], (const R*)h->phi, h->has_fb ? (const R*)h->fb : nullptr, rho, ux, uy, L);
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status run_get(lbm_vanse* h, double* out) {
+    using R = typename Prec<S>::R;
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    get_pop_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>((const S*)h->f[h->cur], (const R*)h->phi, out,
+                                                                       make_lattice<R>(h));
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status run_set(lbm_vanse* h, const double* in) {
+    using R = typename Prec<S>::R;
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    set_pop_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>((S*)h->f[h->cur], (const R*)h->phi, in,
+                                                                       make_lattice<R>(h));
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status run_macros(lbm_vanse* h, double* rho, double* ux, double* uy, double* p) {
+    using R = typename Prec<S>::R;
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    Lattice<R> L = make_lattice<R>(h);
+    rho_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>((const S*)h->f[h->cur], (const R*)h->phi, rho, L);
+    CK(h, cudaGetLastError());
+    if (ux || uy || p) {
+        vel_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>(
+            (const S*)h->f[h->cur], (const R*)h->phi, h->has_fb ? (const R*)h->fb : nullptr, rho, ux, uy, p, L);
+        CK(h, cudaGetLastError());
+    }
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status run_reduce(lbm_vanse* h) {
+    using R = typename Prec<S>::R;
+    moments_reduce_kernel<S, R><<<kReduceBlocks, kAuxThreads, 0, h->stream>>>((const S*)h->f[h->cur],
+                                                                               (const R*)h->phi, h->partial,
+                                                                               make_lattice<R>(h));
+    CK(h, cudaGetLastError());
+    finish_reduce_kernel<<<1, 1024, 0, h->stream>>>(h->partial, kReduceBlocks, h->red_out);
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+#define DISPATCH(h, fn, ...)                                                     \
+    ([&]() -> lbm_status {                                                       \
+        switch ((h)->prm.storage) {                                              \
+            case LBM_FP64: return fn<double>((h), ##__VA_ARGS__);                \
+            case LBM_FP32: return fn<float>((h), ##__VA_ARGS__);                 \
+            case LBM_FP16: return fn<__half>((h), ##__VA_ARGS__);                \
+            default: return fn<__nv_bfloat16>((h), ##__VA_ARGS__);               \
+        }                                                                        \
+    }())
+
+// Copy a caller array to device memory if it lives on the host; returns the
+// device pointer to use (caller's own pointer when on_device).
+lbm_status stage_in(lbm_vanse* h, const double* src, long long count, int on_device, double** dev, bool* owned) {
+    *owned = false;
+    if (on_device) { *dev = const_cast<double*>(src); return LBM_OK; }
+    CK(h, cudaMallocAsync((void**)dev, (size_t)count * sizeof(double), h->stream));
+    *owned = true;
+    CK(h, cudaMemcpyAsync(*dev, src, (size_t)count * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    return LBM_OK;
+}
+
+lbm_status pad_into(lbm_vanse* h, const double* dev_src, void* dst) {
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    if (h->rbytes == 8)
+        pad_field_kernel<double><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>(dev_src, (double*)dst, h->prm.nx,
+                                                                               h->prm.ny, h->P);
+    else
+        pad_field_kernel<float><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>(dev_src, (float*)dst, h->prm.nx,
+                                                                              h->prm.ny, h->P);
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status ensure_scratch(lbm_vanse* h) {
+    if (h->scratch) return LBM_OK;
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    CK(h, cudaMallocAsync((void**)&h->scratch, (size_t)(3 * n) * sizeof(double), h->stream));
+    return LBM_OK;
+}
+
+bool rate_ok(double s) { return s > 0.0 && s < 2.0; }
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" void lbm_vanse_default_params(lbm_vanse_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->tau_nu = 0.8;
+    p->s_e = 0.0;
+    p->s_eps = 1.2;
+    p->s_q = 1.4;
+    p->s_c = 1.0;
+    p->kappa = 0.5;
+    p->rho0 = 1.0;
+    p->bc_x = LBM_BC_PERIODIC;
+    p->bc_y = LBM_BC_PERIODIC;
+    p->storage = LBM_FP32;
+    p->model_b = 0;
+    p->storage_scale_log2 = -1000;  // sentinel: per-precision default
+    p->strip_rows = 0;
+}
+
+extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_vanse_t* out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, LBM_ERR_ARG, "params is NULL");
+    if (p->nx < 1 || p->ny < 1) return fail(nullptr, LBM_ERR_ARG, "nx, ny must be >= 1 (got %d, %d)", p->nx, p->ny);
+    if ((long long)p->nx * p->ny > (1LL << 31)) return fail(nullptr, LBM_ERR_ARG, "lattice too large");
+    if (!(p->tau_nu > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau_nu must exceed 1/2 (got %g)", p->tau_nu);
+    if (!(p->kappa >= 0.0 && p->kappa <= 1.0)) return fail(nullptr, LBM_ERR_ARG, "kappa must lie in [0, 1]");
+    if (!(p->rho0 > 0.0)) return fail(nullptr, LBM_ERR_ARG, "rho0 must be positive");
+    if (!rate_ok(p->s_eps) || !rate_ok(p->s_q) || !rate_ok(p->s_c) || (p->s_e > 0 && !rate_ok(p->s_e)))
+        return fail(nullptr, LBM_ERR_ARG, "relaxation rates must lie in (0, 2)");
+    if (p->bc_x != LBM_BC_PERIODIC) return fail(nullptr, LBM_ERR_ARG, "only periodic x boundaries are supported");
+    if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_BOUNCEBACK) return fail(nullptr, LBM_ERR_ARG, "bad bc_y");
+    if (p->storage < LBM_FP64 || p->storage > LBM_BF16) return fail(nullptr, LBM_ERR_ARG, "bad storage");
+    if (p->strip_rows < 0) return fail(nullptr, LBM_ERR_ARG, "strip_rows must be >= 0");
+
+    lbm_vanse* h = new lbm_vanse();
+    h->prm = *p;
+    h->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { delete h; return fail(nullptr, LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
+    h->sbytes = storage_bytes(p->storage);
+    h->rbytes = p->storage == LBM_FP64 ? 8 : 4;
+    h->s_nu = 1.0 / p->tau_nu;
+    if (p->s_e > 0) h->s_e = p->s_e;
+    else {
+        const double nu = (p->tau_nu - 0.5) / 3.0;  // Eq. (3)-(4): tau^-1 = nu / cs^2 + 1/2
+        const double nu_e = nu / 3.0;               // Eq. (A12)
+        h->s_e = 1.0 / (3.0 * nu_e + 0.5);
+    }
+    int k = p->storage_scale_log2;
+    if (k == -1000) k = (p->storage == LBM_FP16) ? 16 : 0;
+    if (p->storage == LBM_FP16 || p->storage == LBM_BF16) {
+        h->scale = std::ldexp(1.0, k);
+        h->inv_scale = std::ldexp(1.0, -k);
+    }
+    h->W = kThreads - 4;
+    h->gridx = (p->nx + h->W - 1) / h->W;
+    const int A = 16 / h->sbytes;
+    h->wwmax = kThreads + 2 * A;
+    h->P = ((kPadCols + h->gridx * h->W + kPadCols) + 31) / 32 * 32;
+    h->plane = (long long)p->ny * h->P;
+
+    lbm_status st = LBM_OK;
+    auto alloc = [&](void** ptr, size_t bytes) -> bool {
+        cudaError_t ee = cudaMallocAsync(ptr, bytes, h->stream);
+        if (ee != cudaSuccess) { st = cuda_fail(h, ee, "cudaMallocAsync"); return false; }
+        ee = cudaMemsetAsync(*ptr, 0, bytes, h->stream);
+        if (ee != cudaSuccess) { st = cuda_fail(h, ee, "cudaMemsetAsync"); return false; }
+        return true;
+    };
+    const size_t popb = (size_t)9 * h->plane * h->sbytes;
+    const size_t fldb = (size_t)h->plane * h->rbytes;
+    bool ok = alloc(&h->f[0], popb) && alloc(&h->f[1], popb) && alloc(&h->phi, fldb) && alloc(&h->phin, fldb) &&
+              alloc((void**)&h->err, sizeof(int)) && alloc((void**)&h->partial, kReduceBlocks * 3 * sizeof(double)) &&
+              alloc((void**)&h->red_out, 4 * sizeof(double));
+    if (ok) st = DISPATCH(h, configure);
+    if (!ok || st != LBM_OK) {
+        g_create_error = h->msg;
+        lbm_vanse_destroy(h);
+        return st == LBM_OK ? LBM_ERR_CUDA : st;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_set_void_fraction(lbm_vanse_t h, const double* phi_t, const double* phi_next,
+                                                  int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!phi_t) return fail(h, LBM_ERR_ARG, "phi_t is NULL");
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    double* d = nullptr;
+    bool owned = false;
+    lbm_status st = stage_in(h, phi_t, n, on_device, &d, &owned);
+    if (st != LBM_OK) return st;
+    st = pad_into(h, d, h->phi);
+    if (owned) cudaFreeAsync(d, h->stream);
+    if (st != LBM_OK) return st;
+    h->unsteady = false;
+    if (phi_next) {
+        st = stage_in(h, phi_next, n, on_device, &d, &owned);
+        if (st != LBM_OK) return st;
+        st = pad_into(h, d, h->phin);
+        if (owned) cudaFreeAsync(d, h->stream);
+        if (st != LBM_OK) return st;
+        h->unsteady = true;
+    }
+    h->phi_set = true;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_set_body_force(lbm_vanse_t h, double gx, double gy, const double* field,
+                                               int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!std::isfinite(gx) || !std::isfinite(gy)) return fail(h, LBM_ERR_ARG, "non-finite body force");
+    h->gx = gx;
+    h->gy = gy;
+    if (!field) { h->has_fb = false; return LBM_OK; }
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    if (!h->fb) {
+        cudaError_t e = cudaMallocAsync(&h->fb, (size_t)2 * h->plane * h->rbytes, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMallocAsync(body force)");
+        e = cudaMemsetAsync(h->fb, 0, (size_t)2 * h->plane * h->rbytes, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync(body force)");
+    }
+    double* d = nullptr;
+    bool owned = false;
+    lbm_status st = stage_in(h, field, 2 * n, on_device, &d, &owned);
+    if (st != LBM_OK) return st;
+    st = pad_into(h, d, h->fb);
+    if (st == LBM_OK) st = pad_into(h, d + n, (char*)h->fb + (size_t)h->plane * h->rbytes);
+    if (owned) cudaFreeAsync(d, h->stream);
+    if (st != LBM_OK) return st;
+    h->has_fb = true;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_init_fields(lbm_vanse_t h, const double* rho, const double* ux, const double* uy,
+                                            int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!rho || !ux || !uy) return fail(h, LBM_ERR_ARG, "rho, ux, uy must be non-NULL");
+    if (!h->phi_set) return fail(h, LBM_ERR_STATE, "set the void fraction before init_fields");
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    double *dr, *dx, *dy;
+    bool o1, o2, o3;
+    lbm_status st = stage_in(h, rho, n, on_device, &dr, &o1);
+    if (st != LBM_OK) return st;
+    st = stage_in(h, ux, n, on_device, &dx, &o2);
+    if (st != LBM_OK) return st;
+    st = stage_in(h, uy, n, on_device, &dy, &o3);
+    if (st != LBM_OK) return st;
+    h->cur = 0;
+    st = DISPATCH(h, run_init, dr, dx, dy);
+    if (o1) cudaFreeAsync(dr, h->stream);
+    if (o2) cudaFreeAsync(dx, h->stream);
+    if (o3) cudaFreeAsync(dy, h->stream);
+    if (st != LBM_OK) return st;
+    h->initialised = true;
+    h->steps = 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_step(lbm_vanse_t h, int nsteps) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps must be >= 0");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "init_fields or set_populations must come first");
+    for (int s = 0; s < nsteps; ++s) {
+        lbm_status st = DISPATCH(h, launch_step);
+        if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_macros(lbm_vanse_t h, double* rho, double* ux, double* uy, double* p, int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lattice not initialised");
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    lbm_status st = ensure_scratch(h);
+    if (st != LBM_OK) return st;
+    double* dr = (on_device && rho) ? rho : h->scratch;
+    double* dx = (on_device && ux) ? ux : (ux ? h->scratch + n : nullptr);
+    double* dy = (on_device && uy) ? uy : (uy ? h->scratch + 2 * n : nullptr);
+    double* dp = (on_device && p) ? p : nullptr;
+    st = DISPATCH(h, run_macros, dr, dx, dy, dp);
+    if (st != LBM_OK) return st;
+    if (!on_device) {
+        if (rho) CK(h, cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (ux) CK(h, cudaMemcpyAsync(ux, dx, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (uy) CK(h, cudaMemcpyAsync(uy, dy, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (p) {
+            if (rho) { for (long long k = 0; k < n; ++k) p[k] = rho[k] / 3.0; }
+            else {
+                CK(h, cudaMemcpy(p, dr, n * sizeof(double), cudaMemcpyDeviceToHost));
+                for (long long k = 0; k < n; ++k) p[k] /= 3.0;
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_get_populations(lbm_vanse_t h, double* f, int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!f) return fail(h, LBM_ERR_ARG, "f is NULL");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lattice not initialised");
+    const long long n9 = 9LL * h->prm.nx * h->prm.ny;
+    double* d = f;
+    if (!on_device) CK(h, cudaMallocAsync((void**)&d, n9 * sizeof(double), h->stream));
+    lbm_status st = DISPATCH(h, run_get, d);
+    if (st == LBM_OK && !on_device) {
+        cudaError_t e = cudaMemcpyAsync(f, d, n9 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "copy populations to host");
+    }
+    if (!on_device) cudaFreeAsync(d, h->stream);
+    return st;
+}
+
+extern "C" lbm_status lbm_vanse_set_populations(lbm_vanse_t h, const double* f, int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!f) return fail(h, LBM_ERR_ARG, "f is NULL");
+    if (!h->phi_set) return fail(h, LBM_ERR_STATE, "set the void fraction before set_populations");
+    const long long n9 = 9LL * h->prm.nx * h->prm.ny;
+    double* d = nullptr;
+    bool owned = false;
+    lbm_status st = stage_in(h, f, n9, on_device, &d, &owned);
+    if (st != LBM_OK) return st;
+    h->cur = 0;
+    st = DISPATCH(h, run_set, d);
+    if (owned) cudaFreeAsync(d, h->stream);
+    if (st != LBM_OK) return st;
+    h->initialised = true;
+    h->steps = 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_reduce(lbm_vanse_t h, double* mass, double* momx, double* momy) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lattice not initialised");
+    lbm_status st = DISPATCH(h, run_reduce);
+    if (st != LBM_OK) return st;
+    double r[3];
+    CK(h, cudaMemcpyAsync(r, h->red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (mass) *mass = r[0];
+    if (momx) *momx = r[1];
+    if (momy) *momy = r[2];
+    if (!std::isfinite(r[0]) || !std::isfinite(r[1]) || !std::isfinite(r[2]))
+        return fail(h, LBM_ERR_DIVERGED, "non-finite populations (mass %g)", r[0]);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_velocity_error(lbm_vanse_t h, const double* ux_ref, const double* uy_ref,
+                                               int on_device, double* num, double* den) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!ux_ref || !uy_ref) return fail(h, LBM_ERR_ARG, "reference velocity is NULL");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lattice not initialised");
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    lbm_status st = ensure_scratch(h);
+    if (st != LBM_OK) return st;
+    st = DISPATCH(h, run_macros, h->scratch, h->scratch + n, h->scratch + 2 * n, (double*)nullptr);
+    if (st != LBM_OK) return st;
+    double *rx, *ry;
+    bool ox, oy;
+    st = stage_in(h, ux_ref, n, on_device, &rx, &ox);
+    if (st != LBM_OK) return st;
+    st = stage_in(h, uy_ref, n, on_device, &ry, &oy);
+    if (st != LBM_OK) return st;
+    velocity_error_kernel<<<kReduceBlocks, kAuxThreads, 0, h->stream>>>(h->scratch + n, h->scratch + 2 * n, rx, ry, n,
+                                                                         h->partial);
+    CK(h, cudaGetLastError());
+    finish_reduce_kernel<<<1, 1024, 0, h->stream>>>(h->partial, kReduceBlocks, h->red_out);
+    CK(h, cudaGetLastError());
+    double r[3];
+    CK(h, cudaMemcpyAsync(r, h->red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (ox) cudaFreeAsync(rx, h->stream);
+    if (oy) cudaFreeAsync(ry, h->stream);
+    if (num) *num = r[0];
+    if (den) *den = r[1];
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_sync(lbm_vanse_t h) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    CK(h, cudaStreamSynchronize(h->stream));
+    int flag = 0;
+    CK(h, cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(h, LBM_ERR_TIMEOUT, "a step kernel gave up waiting for its staged rows");
+    return LBM_OK;
+}
+
+extern "C" long long lbm_vanse_step_count(lbm_vanse_t h) { return h ? h->steps : -1; }
+
+extern "C" double lbm_vanse_bytes_per_cell(lbm_vanse_t h) {
+    if (!h) return 0.0;
+    double b = 18.0 * h->sbytes + h->rbytes;  // 9 populations read + 9 written, phi(t)
+    if (h->unsteady) b += h->rbytes;
+    if (h->has_fb) b += 2.0 * h->rbytes;
+    return b;
+}
+
+extern "C" lbm_status lbm_vanse_launch_shape(lbm_vanse_t h, int* threads, int* cols, int* rows, int* grid_x,
+                                             int* grid_y, int* smem_bytes) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (threads) *threads = kThreads;
+    if (cols) *cols = h->W;
+    if (rows) *rows = h->H;
+    if (grid_x) *grid_x = h->gridx;
+    if (grid_y) *grid_y = h->gridy;
+    if (smem_bytes) {
+        const int nR = 1 + (h->unsteady ? 1 : 0) + (h->has_fb ? 2 : 0);
+        size_t s = 0;
+        switch (h->prm.storage) {
+            case LBM_FP64: s = step_smem_bytes<double>(h, nR, nullptr); break;
+            case LBM_FP32: s = step_smem_bytes<float>(h, nR, nullptr); break;
+            case LBM_FP16: s = step_smem_bytes<__half>(h, nR, nullptr); break;
+            default: s = step_smem_bytes<__nv_bfloat16>(h, nR, nullptr); break;
+        }
+        *smem_bytes = (int)s;
+    }
+    return LBM_OK;
+}
+
+extern "C" const char* lbm_vanse_last_error(lbm_vanse_t h) { return h ? h->msg.c_str() : g_create_error.c_str(); }
+
+extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    void* ptrs[] = {h->f[0], h->f[1], h->phi, h->phin, h->fb, h->err, h->partial, h->red_out, h->scratch};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete h;
+}

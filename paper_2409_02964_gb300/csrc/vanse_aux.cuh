@@ -1,0 +1,277 @@
+// vanse_aux.cuh -- the non-hot kernels: field padding, initial populations,
+// population get/set, macroscopic fields and FP64 reductions.
+//
+// Storage convention (shared with the step kernel): population plane i, padded
+// row pitch P, cell (x, y) at i*plane + y*P + kPadCols + x, holding f_i+(x, t-1);
+// cell x at time t pulls f_i(x, t) = f_i+(x - e_i, t-1), or, across a half-way
+// bounce-back wall, f_opp(i)+(x, t-1). Periodic x is served by kGhost ghost
+// columns on each side, rewritten whenever a cell near the edge is written.
+#pragma once
+
+#include "vanse_common.cuh"
+
+namespace lbmv {
+
+template <typename R>
+struct Lattice {
+    long long plane;   // elements per padded plane
+    int nx, ny, P;
+    int wall_y, model_b;
+    R kappa, gx, gy;
+    R scale, inv_scale;
+    Rest<R> rest;
+};
+
+__device__ __forceinline__ long long cell_off(int P, int x, int y) { return (long long)y * P + kPadCols + x; }
+
+// Write v at padded column x of row y and at every periodic ghost image of x.
+template <typename T>
+__device__ __forceinline__ void put_with_ghosts(T* plane_base, int P, int nx, int x, int y, T v) {
+    const long long ro = (long long)y * P + kPadCols;
+    plane_base[ro + x] = v;
+    for (int g = x - nx; g >= -kGhost; g -= nx) plane_base[ro + g] = v;
+    for (int g = x + nx; g < nx + kGhost; g += nx) plane_base[ro + g] = v;
+}
+
+// Copy a dense [ny][nx] double field into a padded R field (with ghosts).
+template <typename R>
+__global__ void pad_field_kernel(const double* __restrict__ src, R* __restrict__ dst, int nx, int ny, int P) {
+    const long long n = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / nx), x = (int)(k % nx);
+        put_with_ghosts<R>(dst, P, nx, x, y, (R)src[k]);
+    }
+}
+
+// Pull the post-streaming populations of cell (x, y) from the stored planes.
+template <typename S, typename R>
+__device__ __forceinline__ void pull_cell(const S* __restrict__ buf, const R* __restrict__ phi, const Lattice<R>& L,
+                                          int x, int y, R f[9]) {
+    const R ph = phi[cell_off(L.P, x, y)];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        int sx = x - ex_of(i), sy = y - ey_of(i);
+        int pi = i;
+        if (sy < 0 || sy >= L.ny) {
+            if (L.wall_y) { sx = x; sy = y; pi = opp_of(i); }
+            else sy = (sy + L.ny) % L.ny;
+        }
+        const S v = buf[pi * L.plane + cell_off(L.P, sx, sy)];
+        const R rest = (i == 0) ? L.rest.r0(ph) : L.rest.ri(i);
+        f[i] = dec(v, rest, L.inv_scale);
+    }
+}
+
+// Store post-streaming value f_i(x, y) where the next pull will find it.
+template <typename S, typename R>
+__device__ __forceinline__ void scatter_cell(S* __restrict__ buf, const Lattice<R>& L, int x, int y, int i, R fi,
+                                             R phi_cell) {
+    int tx = x - ex_of(i), ty = y - ey_of(i);
+    int pi = i;
+    if (ty < 0 || ty >= L.ny) {
+        if (L.wall_y) { tx = x; ty = y; pi = opp_of(i); }
+        else ty = (ty + L.ny) % L.ny;
+    }
+    tx = (tx + L.nx) % L.nx;
+    const R rest = (i == 0) ? L.rest.r0(phi_cell) : L.rest.ri(i);
+    put_with_ghosts<S>(buf + pi * L.plane, L.P, L.nx, tx, ty, enc<S, R>(fi, rest, L.scale));
+}
+
+// Eq. (10) on a dense [ny][nx] double field; rho-like (even) ghost rule at walls.
+template <typename R>
+__device__ __forceinline__ void grad_dense_even(const double* __restrict__ a, const Lattice<R>& L, int x, int y, R& gx,
+                                                R& gy) {
+    R sx = 0, sy = 0;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        int nx_ = (x + ex_of(i) + L.nx) % L.nx;
+        int ny_ = y + ey_of(i);
+        if (ny_ < 0 || ny_ >= L.ny) {
+            if (L.wall_y) ny_ = ny_ < 0 ? -1 - ny_ : 2 * L.ny - 1 - ny_;
+            else ny_ = (ny_ + L.ny) % L.ny;
+        }
+        const R w = (i <= 4) ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0);
+        const R v = (R)a[(long long)ny_ * L.nx + nx_];
+        sx += w * v * (R)ex_of(i);
+        sy += w * v * (R)ey_of(i);
+    }
+    gx = (R)3 * sx;
+    gy = (R)3 * sy;
+}
+
+// Initial populations f = f^eq(rho, u, phi) - F_i(u, F)/2 (Eq. 14, 6), F = F^p + F^B.
+template <typename S, typename R>
+__global__ void init_kernel(S* __restrict__ buf, const R* __restrict__ phi, const R* __restrict__ fb,
+                            const double* __restrict__ rho_in, const double* __restrict__ ux_in,
+                            const double* __restrict__ uy_in, const Lattice<R> L) {
+    const long long n = (long long)L.nx * L.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        const long long co = cell_off(L.P, x, y);
+        const R ph = phi[co];
+        const R rho = (R)rho_in[k], ux = (R)ux_in[k], uy = (R)uy_in[k];
+        R gx, gy;
+        grad_dense_even<R>(rho_in, L, x, y, gx, gy);
+        const R kp = (L.model_b ? (L.kappa - (R)1) : (L.kappa - ph)) / (R)3;
+        R Fx = kp * gx + ph * L.gx, Fy = kp * gy + ph * L.gy;
+        if (fb) { Fx += fb[co]; Fy += fb[L.plane + co]; }
+        const R X = L.kappa / ph;
+        const R pr = ph * rho;
+        const R uu = ux * ux + uy * uy;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const R exi = (R)ex_of(i), eyi = (R)ey_of(i);
+            const R eu = exi * ux + eyi * uy;
+            R feq;
+            if (i == 0) {
+                feq = pr - (R)(5.0 / 9.0) * L.kappa * rho - (R)(2.0 / 3.0) * pr * uu;
+            } else {
+                const R w = (i <= 4) ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0);
+                const R g = (i <= 4) ? ((R)3 - X) * (R)0.5 : X;   // 1 + (X-1)(3|e|^2 - 4)/2
+                feq = w * (L.kappa * rho + pr * ((R)3 * eu * g + (R)4.5 * eu * eu - (R)1.5 * uu));
+            }
+            const R w = (i == 0) ? (R)(4.0 / 9.0) : ((i <= 4) ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0));
+            const R Fi = w * (((R)3 * (exi - ux) + (R)9 * eu * exi) * Fx + ((R)3 * (eyi - uy) + (R)9 * eu * eyi) * Fy);
+            scatter_cell<S, R>(buf, L, x, y, i, feq - (R)0.5 * Fi, ph);
+        }
+    }
+}
+
+template <typename S, typename R>
+__global__ void get_pop_kernel(const S* __restrict__ buf, const R* __restrict__ phi, double* __restrict__ out,
+                               const Lattice<R> L) {
+    const long long n = (long long)L.nx * L.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        R f[9];
+        pull_cell<S, R>(buf, phi, L, x, y, f);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[i * n + k] = (double)f[i];
+    }
+}
+
+template <typename S, typename R>
+__global__ void set_pop_kernel(S* __restrict__ buf, const R* __restrict__ phi, const double* __restrict__ in,
+                               const Lattice<R> L) {
+    const long long n = (long long)L.nx * L.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        const R ph = phi[cell_off(L.P, x, y)];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) scatter_cell<S, R>(buf, L, x, y, i, (R)in[i * n + k], ph);
+    }
+}
+
+// Macroscopic pass 1: rho = sum f / phi (Eq. 7) into a dense double array.
+template <typename S, typename R>
+__global__ void rho_kernel(const S* __restrict__ buf, const R* __restrict__ phi, double* __restrict__ rho,
+                           const Lattice<R> L) {
+    const long long n = (long long)L.nx * L.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        R f[9];
+        pull_cell<S, R>(buf, phi, L, x, y, f);
+        R s = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s += f[i];
+        rho[k] = (double)(s / phi[cell_off(L.P, x, y)]);
+    }
+}
+
+// Macroscopic pass 2: F = F^p + F^B (Eq. 13), u = (sum e f + F/2) / sum f, p = rho/3.
+template <typename S, typename R>
+__global__ void vel_kernel(const S* __restrict__ buf, const R* __restrict__ phi, const R* __restrict__ fb,
+                           const double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy,
+                           double* __restrict__ pr, const Lattice<R> L) {
+    const long long n = (long long)L.nx * L.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        const long long co = cell_off(L.P, x, y);
+        R f[9];
+        pull_cell<S, R>(buf, phi, L, x, y, f);
+        R s = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) { s += f[i]; jx += (R)ex_of(i) * f[i]; jy += (R)ey_of(i) * f[i]; }
+        R gx, gy;
+        grad_dense_even<R>(rho, L, x, y, gx, gy);
+        const R ph = phi[co];
+        const R kp = (L.model_b ? (L.kappa - (R)1) : (L.kappa - ph)) / (R)3;
+        R Fx = kp * gx + ph * L.gx, Fy = kp * gy + ph * L.gy;
+        if (fb) { Fx += fb[co]; Fy += fb[L.plane + co]; }
+        if (ux) ux[k] = (double)((jx + (R)0.5 * Fx) / s);
+        if (uy) uy[k] = (double)((jy + (R)0.5 * Fy) / s);
+        if (pr) pr[k] = rho[k] / 3.0;
+    }
+}
+
+// FP64 block reduction of three sums into partial[blockIdx.x * 3 + j].
+__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* partial) {
+    __shared__ double sh[3][32];
+    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; sh[2][wid] = c; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        a = lane < nw ? sh[0][lane] : 0.0;
+        b = lane < nw ? sh[1][lane] : 0.0;
+        c = lane < nw ? sh[2][lane] : 0.0;
+        a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+        if (lane == 0) { partial[blockIdx.x * 3 + 0] = a; partial[blockIdx.x * 3 + 1] = b; partial[blockIdx.x * 3 + 2] = c; }
+    }
+}
+
+// Mass sum f and momentum sum e f per cell, FP64 partial sums per block.
+template <typename S, typename R>
+__global__ void moments_reduce_kernel(const S* __restrict__ buf, const R* __restrict__ phi, double* __restrict__ partial,
+                                      const Lattice<R> L) {
+    const long long n = (long long)L.nx * L.ny;
+    double m = 0, jx = 0, jy = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
+        R f[9];
+        pull_cell<S, R>(buf, phi, L, x, y, f);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double v = (double)f[i];
+            m += v; jx += ex_of(i) * v; jy += ey_of(i) * v;
+        }
+    }
+    block_reduce3(m, jx, jy, partial);
+}
+
+// Eq. (26) sums: sum |u - u_ref|^2 and sum |u_ref|^2 (third slot unused).
+__global__ void velocity_error_kernel(const double* __restrict__ ux, const double* __restrict__ uy,
+                                      const double* __restrict__ uxr, const double* __restrict__ uyr, long long n,
+                                      double* __restrict__ partial) {
+    double num = 0, den = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double dx = ux[k] - uxr[k], dy = uy[k] - uyr[k];
+        num += dx * dx + dy * dy;
+        den += uxr[k] * uxr[k] + uyr[k] * uyr[k];
+    }
+    block_reduce3(num, den, 0.0, partial);
+}
+
+// Sum nblocks partial triples in a fixed order (deterministic) into out[0..2].
+__global__ void finish_reduce_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+    double a = 0, b = 0, c = 0;
+    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+        a += partial[k * 3 + 0]; b += partial[k * 3 + 1]; c += partial[k * 3 + 2];
+    }
+    __shared__ double sh[3][32];
+    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; sh[2][wid] = c; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        a = lane < nw ? sh[0][lane] : 0.0;
+        b = lane < nw ? sh[1][lane] : 0.0;
+        c = lane < nw ? sh[2][lane] : 0.0;
+        a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+        if (lane == 0) { out[0] = a; out[1] = b; out[2] = c; }
+    }
+}
+
+}  // namespace lbmv

@@ -1,0 +1,179 @@
+"""Python handle for one lattice of the CUDA library (argument marshalling only).
+
+PyTorch provides device memory and the stream; every step of the method runs in
+``liblbm_vanse.so``. Inputs may be CUDA tensors (passed by device pointer) or
+host arrays (numpy / CPU tensors, copied by the library). Outputs are float64
+CUDA tensors unless stated otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import capi
+
+_STORAGE = {"fp64": capi.LBM_FP64, "fp32": capi.LBM_FP32, "fp16": capi.LBM_FP16, "bf16": capi.LBM_BF16}
+_BC = {"periodic": capi.LBM_BC_PERIODIC, "bounceback": capi.LBM_BC_BOUNCEBACK}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{capi.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int, handle) -> None:
+    if st != capi.LBM_OK:
+        msg = capi.load().lbm_vanse_last_error(handle)
+        raise LbmError(st, msg.decode() if msg else "")
+
+
+class _Arg:
+    """Holds a caller array as (pointer, on_device) for one call."""
+
+    def __init__(self, a, count: int, device: torch.device):
+        if a is None:
+            self.ptr, self.on_device, self._keep = None, 1, None
+            return
+        if isinstance(a, torch.Tensor) and a.is_cuda:
+            if a.device != device:
+                raise ValueError(f"tensor on {a.device}, lattice on {device}")
+            t = a.detach().to(torch.float64).contiguous()
+            if t.numel() != count:
+                raise ValueError(f"expected {count} elements, got {t.numel()}")
+            self.ptr, self.on_device, self._keep = t.data_ptr(), 1, t
+        else:
+            arr = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else np.asarray(a)
+            arr = np.ascontiguousarray(arr, dtype=np.float64)
+            if arr.size != count:
+                raise ValueError(f"expected {count} elements, got {arr.size}")
+            self.ptr, self.on_device, self._keep = arr.ctypes.data, 0, arr
+
+
+class Lattice:
+    """One D2Q9 MRTLB-VANSE lattice on the current CUDA device.
+
+    Parameters follow the paper's statement of the problem (Sec. 2.3, 3): ``tau``
+    is the relaxation time of the shear moments (nu = (tau - 1/2)/3); ``s_e <= 0``
+    derives the energy rate from nu_e = nu/3 (Eq. A12); ``s_eps``, ``s_q``, ``s_c``
+    are rates; ``kappa`` is the provisional equation-of-state constant.
+    """
+
+    def __init__(self, nx: int, ny: int, tau: float = 0.8, *, s_e: float = 0.0, s_eps: float = 1.2,
+                 s_q: float = 1.4, s_c: float = 1.0, kappa: float = 0.5, rho0: float = 1.0,
+                 bc_y: str = "periodic", storage: str = "fp32", model_b: bool = False,
+                 scale_log2: int | None = None, strip_rows: int = 0, stream=None):
+        L = capi.load()
+        p = capi.default_params()
+        p.nx, p.ny, p.tau_nu = int(nx), int(ny), float(tau)
+        p.s_e, p.s_eps, p.s_q, p.s_c = float(s_e), float(s_eps), float(s_q), float(s_c)
+        p.kappa, p.rho0 = float(kappa), float(rho0)
+        p.bc_x, p.bc_y = capi.LBM_BC_PERIODIC, _BC[bc_y]
+        p.storage, p.model_b = _STORAGE[storage], int(bool(model_b))
+        if scale_log2 is not None:
+            p.storage_scale_log2 = int(scale_log2)
+        p.strip_rows = int(strip_rows)
+        self.nx, self.ny, self.storage = int(nx), int(ny), storage
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = L.lbm_vanse_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != capi.LBM_OK:
+            raise LbmError(st, L.lbm_vanse_last_error(None).decode())
+        self._h = h
+        self._L = L
+
+    # -- lifetime
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._L.lbm_vanse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny
+
+    def _dense(self, k: int = 1) -> torch.Tensor:
+        shape = (self.ny, self.nx) if k == 1 else (k, self.ny, self.nx)
+        return torch.empty(shape, dtype=torch.float64, device=self.device)
+
+    # -- inputs
+    def set_void_fraction(self, phi_t, phi_next=None) -> None:
+        a, b = _Arg(phi_t, self.n, self.device), _Arg(phi_next, self.n, self.device)
+        on = a.on_device if phi_next is None else a.on_device
+        if phi_next is not None and a.on_device != b.on_device:
+            raise ValueError("phi_t and phi_next must both be on the device or both on the host")
+        _check(self._L.lbm_vanse_set_void_fraction(self._h, a.ptr, b.ptr, on), self._h)
+
+    def set_body_force(self, gx: float = 0.0, gy: float = 0.0, field=None) -> None:
+        a = _Arg(field, 2 * self.n, self.device)
+        _check(self._L.lbm_vanse_set_body_force(self._h, float(gx), float(gy), a.ptr, a.on_device), self._h)
+
+    def init_fields(self, rho, ux, uy) -> None:
+        args = [_Arg(v, self.n, self.device) for v in (rho, ux, uy)]
+        on = {a.on_device for a in args}
+        if len(on) != 1:
+            raise ValueError("rho, ux, uy must all be on the device or all on the host")
+        _check(self._L.lbm_vanse_init_fields(self._h, args[0].ptr, args[1].ptr, args[2].ptr, on.pop()), self._h)
+
+    # -- time stepping
+    def step(self, nsteps: int = 1) -> None:
+        _check(self._L.lbm_vanse_step(self._h, int(nsteps)), self._h)
+
+    def sync(self) -> None:
+        _check(self._L.lbm_vanse_sync(self._h), self._h)
+
+    @property
+    def step_count(self) -> int:
+        return int(self._L.lbm_vanse_step_count(self._h))
+
+    @property
+    def bytes_per_cell(self) -> float:
+        return float(self._L.lbm_vanse_bytes_per_cell(self._h))
+
+    def launch_shape(self) -> dict:
+        v = [ctypes.c_int() for _ in range(6)]
+        _check(self._L.lbm_vanse_launch_shape(self._h, *[ctypes.byref(x) for x in v]), self._h)
+        return dict(zip(("threads", "cols", "rows", "grid_x", "grid_y", "smem_bytes"), [x.value for x in v]))
+
+    # -- outputs
+    def macros(self) -> dict:
+        rho, ux, uy, p = (self._dense() for _ in range(4))
+        _check(self._L.lbm_vanse_macros(self._h, rho.data_ptr(), ux.data_ptr(), uy.data_ptr(), p.data_ptr(), 1),
+               self._h)
+        return {"rho": rho, "ux": ux, "uy": uy, "p": p}
+
+    def get_populations(self) -> torch.Tensor:
+        f = self._dense(9)
+        _check(self._L.lbm_vanse_get_populations(self._h, f.data_ptr(), 1), self._h)
+        return f
+
+    def set_populations(self, f) -> None:
+        a = _Arg(f, 9 * self.n, self.device)
+        _check(self._L.lbm_vanse_set_populations(self._h, a.ptr, a.on_device), self._h)
+
+    def reduce(self):
+        m, jx, jy = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self._L.lbm_vanse_reduce(self._h, ctypes.byref(m), ctypes.byref(jx), ctypes.byref(jy)), self._h)
+        return m.value, jx.value, jy.value
+
+    def velocity_error(self, ux_ref, uy_ref):
+        a, b = _Arg(ux_ref, self.n, self.device), _Arg(uy_ref, self.n, self.device)
+        num, den = ctypes.c_double(), ctypes.c_double()
+        _check(self._L.lbm_vanse_velocity_error(self._h, a.ptr, b.ptr, a.on_device, ctypes.byref(num),
+                                                ctypes.byref(den)), self._h)
+        return num.value, den.value

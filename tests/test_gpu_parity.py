@@ -1,0 +1,298 @@
+"""Parity of the CUDA library (called through its C ABI binding) with the FP64
+oracle, element by element on the same seeded inputs.
+
+Tolerances (max |f_gpu - f_oracle| relative to max |f_oracle - f_rest|, where
+f_rest is the rest state of Eq. (14)):
+  FP64  1e-12 (the stated bar; only the summation order differs).
+  FP32  per step, the FP32 compute rounds each output population with error of a
+        few tens of units of 2^-24 |f|; we allow 32 * 2^-24 * max|f| per step,
+        accumulated linearly over k steps.
+  FP16  storage rounds each deviation to 11 significant bits: 2^-11 max|f - f_rest|
+        per step (plus the FP32 term), accumulated over k steps, times 2.
+  BF16  8 significant bits: 2^-8 max|f - f_rest| per step, times 2.
+"""
+import numpy as np
+import pytest
+
+from synth import fields, mms
+
+from gpu_cases import channel_case, random_case, rest_populations, total_force
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_02964_gb300 as pkg
+    pkg.capi.load()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def O(oracle_mod):
+    return oracle_mod
+
+
+def _oracle_params(O, nx, ny, tau, wall_y, kappa=0.5, s_eps=1.2, s_q=1.4, model_b=0):
+    return O.Params(nx=nx, ny=ny, **O.rates_from_tau(tau, s_eps=s_eps, s_q=s_q), kappa=kappa,
+                    bc_y=int(wall_y), model_b=model_b)
+
+
+def _gpu_lattice(P, nx, ny, tau, wall_y, storage, case, model_b=False, strip_rows=0, s_eps=1.2, s_q=1.4):
+    lat = P.Lattice(nx, ny, tau, s_eps=s_eps, s_q=s_q, bc_y="bounceback" if wall_y else "periodic",
+                    storage=storage, model_b=model_b, strip_rows=strip_rows)
+    lat.set_void_fraction(case["phi"], case["phin"])
+    lat.set_body_force(case["g"][0], case["g"][1], case["fb"])
+    lat.init_fields(case["rho"], case["ux"], case["uy"])
+    return lat
+
+
+def _run_both(P, O, nx, ny, case, steps, storage="fp64", tau=0.8, wall_y=False, model_b=False, strip_rows=0):
+    """Run the library and the oracle from the same initial fields; returns the
+    device's initial and final populations, the oracle's initial and final
+    populations, and the case as it stands after the steps."""
+    lat = _gpu_lattice(P, nx, ny, tau, wall_y, storage, case, model_b=model_b, strip_rows=strip_rows)
+    prm = _oracle_params(O, nx, ny, tau, wall_y, model_b=int(model_b))
+    fb = total_force(case)
+    f = O.init(prm, case["rho"], case["ux"], case["uy"], case["phi"], fb)
+    f_init = f.copy()
+    f0_gpu = lat.get_populations().cpu().numpy()
+    for k in range(steps):
+        phin = case["phin"] if k == 0 else None
+        if k == 1 and case["phin"] is not None:
+            # after the first step phi(t) <- phi(t+1) and the field is steady
+            case = dict(case, phi=case["phin"], phin=None)
+            fb = total_force(case)
+        f = O.step(prm, f, case["phi"], phin, fb)
+    lat.step(steps)
+    lat.sync()
+    fg = lat.get_populations().cpu().numpy()
+    lat.close()
+    return f0_gpu, f_init, fg, f, case
+
+
+def _scale(f_ref, phi):
+    return np.abs(f_ref - rest_populations(phi)).max()
+
+
+CASES = [
+    # nx, ny, wall_y, unsteady, field, g
+    (13, 7, False, False, False, (0.0, 0.0)),
+    (130, 21, False, True, True, (0.0, 0.0)),     # two CTAs in x with a ragged tail
+    (127, 40, True, False, False, (2e-5, -1e-5)),  # channel walls, constant force
+    (250, 9, True, True, True, (1e-5, 0.0)),
+    (5, 3, False, False, True, (0.0, 0.0)),
+    (3, 4, True, False, False, (1e-4, 0.0)),
+    (1, 6, False, False, False, (0.0, 0.0)),
+]
+
+
+@pytest.mark.parametrize("nx,ny,wall_y,unsteady,field,g", CASES)
+@pytest.mark.parametrize("steps", [1, 6])
+def test_fp64_matches_oracle(P, O, nx, ny, wall_y, unsteady, field, g, steps):
+    case = random_case(nx, ny, seed=nx * 100 + ny, wall_y=wall_y, unsteady=unsteady, field=field, g=g)
+    f0g, f0o, fg, fo, case = _run_both(P, O, nx, ny, case, steps, "fp64", wall_y=wall_y)
+    assert np.abs(f0g - f0o).max() <= 1e-14 * np.abs(f0o).max()   # initial populations
+    err = np.abs(fg - fo).max() / _scale(fo, case["phi"])
+    assert err <= 1e-12, err
+
+
+def test_fp64_model_b_matches_oracle(P, O):
+    case = random_case(70, 33, seed=7, wall_y=True, unsteady=True, field=True, g=(1e-5, 0))
+    _, _, fg, fo, case = _run_both(P, O, 70, 33, case, 4, "fp64", wall_y=True, model_b=True)
+    assert np.abs(fg - fo).max() / _scale(fo, case["phi"]) <= 1e-12
+
+
+@pytest.mark.parametrize("storage,per_step", [("fp32", None), ("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_reduced_precision_matches_oracle(P, O, storage, per_step):
+    nx, ny, steps = 130, 21, 5
+    case = random_case(nx, ny, seed=11, wall_y=True, unsteady=True, field=True, g=(1e-5, 0.0))
+    _, _, fg, fo, case = _run_both(P, O, nx, ny, case, steps, storage, wall_y=True)
+    dev = _scale(fo, case["phi"])
+    tol = steps * 32 * EPS32 * np.abs(fo).max()
+    if per_step is not None:
+        tol += 2 * steps * per_step * dev
+    err = np.abs(fg - fo).max()
+    assert err <= tol, (err, tol, err / dev)
+
+
+@pytest.mark.parametrize("storage,eps", [("fp64", 2.0 ** -53), ("fp32", 2.0 ** -24)])
+def test_strip_decomposition_invariance(P, storage, eps):
+    """The strip height only changes which CTA (and which of the three unrolled
+    copies of the row body) computes a row; results agree to rounding."""
+    nx, ny = 300, 77
+    case = random_case(nx, ny, seed=3, wall_y=True, unsteady=False, field=True, g=(1e-5, 0))
+    outs = []
+    for rows in (0, 5, 13, 77):
+        lat = _gpu_lattice(P, nx, ny, 0.7, True, storage, case, strip_rows=rows)
+        lat.step(9)
+        outs.append(lat.get_populations().cpu().numpy())
+        lat.close()
+    scale = np.abs(outs[0]).max()
+    for o in outs[1:]:
+        d = np.abs(o - outs[0]).max()
+        print(f"strip invariance {storage}: max diff {d:.3e} = {d / (eps * scale):.1f} ulp(max f)")
+        assert d <= 64 * eps * scale
+
+
+def test_fp64_manufactured_1000_steps(P, O):
+    """The 64 x 64 spatiotemporal manufactured solution, 1000 steps, FP64 storage:
+    populations within 1e-12 of the oracle relative to the deviation from rest;
+    velocity and pressure fields within 1e-12 relative L2."""
+    n, T = 64, 1000
+    M = mms.Config1(n=n, T=float(T))
+    tau, nu = 0.8, 0.1
+    prm = O.Params(nx=n, ny=n, **O.rates_from_tau(tau, s_eps=1.2, s_q=1.2), kappa=0.5)
+    lat = P.Lattice(n, n, tau, s_eps=1.2, s_q=1.2, storage="fp64")
+    ux0, uy0 = M.velocity(0)
+    fb0 = M.force(0, nu)
+    lat.set_void_fraction(M.phi(0), M.phi(1))
+    lat.set_body_force(0.0, 0.0, fb0)
+    lat.init_fields(np.ones((n, n)), ux0, uy0)
+    f = O.init(prm, np.ones((n, n)), ux0, uy0, M.phi(0), fb0)
+    phi_next = M.phi(0)
+    for t in range(T):
+        phi_t, phi_next = phi_next, M.phi(t + 1)
+        fb = M.force(t, nu)
+        f = O.step(prm, f, phi_t, phi_next, fb)
+        lat.set_void_fraction(phi_t, phi_next)
+        lat.set_body_force(0.0, 0.0, fb)
+        lat.step(1)
+    fbT = M.force(T, nu)
+    lat.set_void_fraction(M.phi(T))
+    lat.set_body_force(0.0, 0.0, fbT)
+    fg = lat.get_populations().cpu().numpy()
+    mg = {k: v.cpu().numpy() for k, v in lat.macros().items()}
+    mo = O.macros(prm, f, M.phi(T), fbT)
+    lat.close()
+    assert np.abs(fg - f).max() / _scale(f, M.phi(T)) <= 1e-12
+    u_err = np.sqrt(np.sum((mg["ux"] - mo["ux"]) ** 2 + (mg["uy"] - mo["uy"]) ** 2)
+                    / np.sum(mo["ux"] ** 2 + mo["uy"] ** 2))
+    assert u_err <= 1e-12
+    pb = mo["p"] - mo["p"].mean()
+    p_err = np.sqrt(np.sum((mg["p"] - mo["p"]) ** 2) / np.sum(pb ** 2))
+    assert p_err <= 1e-12
+
+
+def test_macros_match_oracle(P, O):
+    nx, ny = 90, 31
+    case = random_case(nx, ny, seed=5, wall_y=True, field=True, g=(3e-5, 1e-5))
+    lat = _gpu_lattice(P, nx, ny, 0.9, True, "fp64", case)
+    lat.step(3)
+    f = lat.get_populations().cpu().numpy()
+    mg = {k: v.cpu().numpy() for k, v in lat.macros().items()}
+    lat.close()
+    mo = O.macros(_oracle_params(O, nx, ny, 0.9, True), f, case["phi"], total_force(case))
+    for k in ("rho", "ux", "uy", "p"):
+        assert np.abs(mg[k] - mo[k]).max() <= 1e-14 * max(1.0, np.abs(mo[k]).max()), k
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
+def test_mass_conserved_on_gpu(P, storage):
+    nx, ny = 200, 64
+    case = channel_case(nx, ny, g=1e-5)
+    lat = _gpu_lattice(P, nx, ny, 0.6, True, storage, case)
+    m0, _, _ = lat.reduce()
+    lat.step(50)
+    m1, jx, jy = lat.reduce()
+    lat.close()
+    tol = {"fp64": 1e-13, "fp32": 1e-6, "fp16": 1e-4}[storage]
+    assert abs(m1 - m0) / m0 < tol
+    assert jx > 0  # the force drives the flow along +x
+
+
+def test_populations_roundtrip(P):
+    nx, ny = 40, 17
+    case = random_case(nx, ny, seed=9)
+    lat = _gpu_lattice(P, nx, ny, 0.8, False, "fp64", case)
+    lat.step(2)
+    f = lat.get_populations().cpu().numpy()
+    lat.set_populations(f)
+    assert np.array_equal(lat.get_populations().cpu().numpy(), f)
+    assert lat.step_count == 0
+    lat.close()
+
+
+def test_velocity_error_matches_eq26(P):
+    nx, ny = 64, 48
+    case = random_case(nx, ny, seed=21)
+    lat = _gpu_lattice(P, nx, ny, 0.8, False, "fp64", case)
+    m = {k: v.cpu().numpy() for k, v in lat.macros().items()}
+    rng = np.random.default_rng(0)
+    uxr, uyr = m["ux"] + 1e-4 * rng.normal(size=m["ux"].shape), m["uy"]
+    num, den = lat.velocity_error(uxr, uyr)
+    lat.close()
+    assert abs(np.sqrt(num / den) - mms.relative_l2(m["ux"], m["uy"], uxr, uyr)) < 1e-12
+
+
+def test_full_size_channel_sampled_windows(P, O):
+    """4096 x 4096 channel (FP32, the benchmark's launch configuration): one step on
+    the device, then the oracle recomputes sampled windows from the device's own
+    input populations. An output cell depends on inputs within 3 cells, so the
+    oracle runs each 24 x 24 window as its own lattice (periodic in x, walls kept
+    where the window touches them) and the central 12 x 12 cells are compared."""
+    import torch
+    nx = ny = 4096
+    case = channel_case(nx, ny)
+    lat = _gpu_lattice(P, nx, ny, 0.6, True, "fp32", case)
+    lat.step(20)  # let the flow start
+    fin = lat.get_populations()
+    lat.step(1)
+    fout = lat.get_populations()
+    phi = case["phi"]
+    prm_kw = dict(**O.rates_from_tau(0.6), kappa=0.5)
+    W = lat.launch_shape()["cols"]
+    rows = lat.launch_shape()["rows"]
+    centres = [(5, 0), (2047, 0), (4090, 4095), (W - 1, 1000), (W, rows), (2 * W + 1, rows - 1),
+               (1700, 1650), (1638, 1638), (2000, 2457), (3000, 3000), (0, 2048), (4095, 17)]
+    for cx, cy in centres:
+        x0 = cx - 12
+        xs = np.arange(x0, x0 + 24) % nx
+        if cy < 12:
+            ys = np.arange(0, 24)
+            wall_lo, wall_hi = True, False
+        elif cy > ny - 13:
+            ys = np.arange(ny - 24, ny)
+            wall_lo, wall_hi = False, True
+        else:
+            ys = np.arange(cy - 12, cy + 12)
+            wall_lo = wall_hi = False
+        sub = np.ix_(ys, xs)
+        f_in = fin[:, torch.as_tensor(ys)[:, None], torch.as_tensor(xs)[None, :]].cpu().numpy()
+        f_out = fout[:, torch.as_tensor(ys)[:, None], torch.as_tensor(xs)[None, :]].cpu().numpy()
+        ph = phi[sub]
+        fb = np.stack([ph * 1e-6, np.zeros_like(ph)])
+        prm = O.Params(nx=24, ny=24, bc_y=1 if (wall_lo or wall_hi) else 0, **prm_kw)
+        f_ref = O.step(prm, f_in.astype(np.float64), ph, None, fb)
+        # trusted region: 4 cells from each artificial edge (the walls are real edges)
+        ylo = 0 if wall_lo else 6
+        yhi = 24 if wall_hi else 18
+        reg = (slice(None), slice(ylo, yhi), slice(6, 18))
+        tol = 32 * EPS32 * np.abs(f_ref).max()
+        assert np.abs(f_out[reg] - f_ref[reg]).max() <= tol, (cx, cy)
+    m, _, _ = lat.reduce()
+    lat.close()
+    assert np.isfinite(m)
+
+
+def test_invalid_arguments_are_reported(P):
+    with pytest.raises(P.LbmError) as e:
+        P.Lattice(0, 5)
+    assert e.value.status == P.capi.LBM_ERR_ARG
+    with pytest.raises(P.LbmError):
+        P.Lattice(8, 8, tau=0.5)
+    with pytest.raises(P.LbmError):
+        P.Lattice(8, 8, s_q=2.5)
+    lat = P.Lattice(8, 8)
+    with pytest.raises(P.LbmError) as e:
+        lat.step(1)
+    assert e.value.status == P.capi.LBM_ERR_STATE
+    with pytest.raises(P.LbmError) as e:
+        lat.init_fields(np.ones((8, 8)), np.zeros((8, 8)), np.zeros((8, 8)))
+    assert e.value.status == P.capi.LBM_ERR_STATE
+    lat.close()
