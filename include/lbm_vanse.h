@@ -65,6 +65,8 @@ typedef struct {
     int model_b;
     int storage_scale_log2;      /* FP16/BF16 deviation scale exponent (default 16 / 0) */
     int strip_rows;              /* rows per CTA strip of the step kernel; 0 = automatic */
+    int eager;                   /* 1 = launch each step on its own; 0 = replay runs of steady
+                                    steps as a captured CUDA graph (default) */
 } lbm_vanse_params;
 
 typedef struct lbm_vanse* lbm_vanse_t;
@@ -103,7 +105,9 @@ lbm_status lbm_vanse_init_fields(lbm_vanse_t h, const double* rho, const double*
 /* Advance nsteps time steps: per cell the fused stream + collide of Eq. (16)
  * (moments Eq. 17/A1, equilibrium Eq. 18, force moments Eq. 19 with F^p of Eq. 13,
  * penalty source Eq. 20 with gradients by Eq. 10, back-transform A1), streaming
- * with periodic wrap or half-way bounce-back. Asynchronous on the stream. */
+ * with periodic wrap or half-way bounce-back. Asynchronous on the stream. Unless
+ * params.eager is set, runs of steady steps are replayed as a CUDA graph captured
+ * on first use (re-captured when phi, the force or the buffer parity change). */
 lbm_status lbm_vanse_step(lbm_vanse_t h, int nsteps);
 
 /* Macroscopic fields at the current time (Eq. 7): rho = sum f / phi,

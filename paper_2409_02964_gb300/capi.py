@@ -37,6 +37,7 @@ class lbm_vanse_params(ctypes.Structure):
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
         ("storage", ctypes.c_int), ("model_b", ctypes.c_int),
         ("storage_scale_log2", ctypes.c_int), ("strip_rows", ctypes.c_int),
+        ("eager", ctypes.c_int),
     ]
 
 

@@ -24,6 +24,7 @@ namespace {
 constexpr int kThreads = 128;       // step kernel CTA size (W = kThreads - 4 columns)
 constexpr int kAuxThreads = 256;
 constexpr int kReduceBlocks = 1024;
+constexpr int kGraphSteps = 32;     // steps per replayed CUDA graph (even: ping-pong returns to its buffer)
 
 thread_local std::string g_create_error;
 
@@ -60,6 +61,16 @@ struct lbm_vanse {
     long long steps = 0;
     // step-kernel launch shape
     int W = 0, H = 0, gridx = 0, gridy = 0, wwmax = 0;
+    // replayed graph of kGraphSteps steady steps, valid while its key matches
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    struct GraphKey {
+        const void* phi; const void* fb; int has_fb; double gx, gy; int cur;
+        bool operator==(const GraphKey& o) const {
+            return phi == o.phi && fb == o.fb && has_fb == o.has_fb && gx == o.gx && gy == o.gy && cur == o.cur;
+        }
+    } gkey{};
+    bool use_graphs = true;
     std::string msg;
 };
 
@@ -152,11 +163,11 @@ lbm_status configure(lbm_vanse* h) {
 }
 
 template <typename S>
-lbm_status launch_step(lbm_vanse* h) {
+lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src) {
     using R = typename Prec<S>::R;
     StepParams<R> p;
-    p.src = h->f[h->cur];
-    p.dst = h->f[1 - h->cur];
+    p.src = h->f[src];
+    p.dst = h->f[1 - src];
     p.phi = (const R*)h->phi;
     p.phin = h->unsteady ? (const R*)h->phin : (const R*)h->phi;
     p.fb = h->has_fb ? (const R*)h->fb : nullptr;
@@ -188,8 +199,15 @@ lbm_status launch_step(lbm_vanse* h) {
     p.rest = make_rest<R>(h);
     p.err = h->err;
     dim3 grid(h->gridx, h->gridy);
-    vanse_step_kernel<S, R, kThreads><<<grid, kThreads, smem, h->stream>>>(p);
+    vanse_step_kernel<S, R, kThreads><<<grid, kThreads, smem, stream>>>(p);
     CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status launch_step(lbm_vanse* h) {
+    lbm_status st = enqueue_step<S>(h, h->stream, h->cur);
+    if (st != LBM_OK) return st;
     h->cur = 1 - h->cur;
     if (h->unsteady) {
         // phi(t) <- phi(t+1); the field stays steady until the next set call
@@ -197,6 +215,39 @@ lbm_status launch_step(lbm_vanse* h) {
         h->unsteady = false;
     }
     h->steps++;
+    return LBM_OK;
+}
+
+// Capture kGraphSteps steady steps starting from buffer h->cur into an executable
+// graph. Capture runs on a private stream (the caller's may be the legacy default
+// stream, which cannot be captured); the graph is then launched on h->stream.
+template <typename S>
+lbm_status build_graph(lbm_vanse* h) {
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status st = LBM_OK;
+    for (int k = 0; k < kGraphSteps && st == LBM_OK; ++k) st = enqueue_step<S>(h, h->cap_stream, h->cur ^ (k & 1));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (st != LBM_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+    h->gkey = {h->phi, h->fb, (int)h->has_fb, h->gx, h->gy, h->cur};
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status replay_graph(lbm_vanse* h) {
+    lbm_vanse::GraphKey key{h->phi, h->fb, (int)h->has_fb, h->gx, h->gy, h->cur};
+    if (!h->gexec || !(key == h->gkey)) {
+        lbm_status st = build_graph<S>(h);
+        if (st != LBM_OK) return st;
+    }
+    CK(h, cudaGraphLaunch(h->gexec, h->stream));
+    h->steps += kGraphSteps;   // even count: h->cur is unchanged
     return LBM_OK;
 }
 
@@ -320,6 +371,7 @@ extern "C" void lbm_vanse_default_params(lbm_vanse_params* p) {
     p->model_b = 0;
     p->storage_scale_log2 = -1000;  // sentinel: per-precision default
     p->strip_rows = 0;
+    p->eager = 0;
 }
 
 extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_vanse_t* out) {
@@ -341,6 +393,7 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
     lbm_vanse* h = new lbm_vanse();
     h->prm = *p;
     h->stream = (cudaStream_t)cuda_stream;
+    h->use_graphs = p->eager == 0;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; return fail(nullptr, LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
     h->sbytes = storage_bytes(p->storage);
@@ -468,7 +521,18 @@ extern "C" lbm_status lbm_vanse_step(lbm_vanse_t h, int nsteps) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (nsteps < 0) return fail(h, LBM_ERR_ARG, "nsteps must be >= 0");
     if (!h->initialised) return fail(h, LBM_ERR_STATE, "init_fields or set_populations must come first");
-    for (int s = 0; s < nsteps; ++s) {
+    int left = nsteps;
+    while (left > 0 && h->unsteady) {   // the step that consumes phi(t+1) runs on its own
+        lbm_status st = DISPATCH(h, launch_step);
+        if (st != LBM_OK) return st;
+        --left;
+    }
+    while (h->use_graphs && left >= kGraphSteps) {
+        lbm_status st = DISPATCH(h, replay_graph);
+        if (st != LBM_OK) return st;
+        left -= kGraphSteps;
+    }
+    while (left-- > 0) {
         lbm_status st = DISPATCH(h, launch_step);
         if (st != LBM_OK) return st;
     }
@@ -631,6 +695,8 @@ extern "C" const char* lbm_vanse_last_error(lbm_vanse_t h) { return h ? h->msg.c
 extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void* ptrs[] = {h->f[0], h->f[1], h->phi, h->phin, h->fb, h->err, h->partial, h->red_out, h->scratch};
     for (void* q : ptrs)
         if (q) cudaFree(q);

@@ -49,6 +49,10 @@ def config1(n=64):
     return mms.Config1(n=n)
 
 
+# non-shear relaxation rates of the porous-channel workload
+CHANNEL_RATES = dict(s_e=1.2, s_eps=1.2, s_q=1.2)
+
+
 def channel_case(nx, ny, seed=fields.DEFAULT_SEED, g=1e-6):
     phi = fields.channel_phi(nx, ny, seed)
     rho, ux, uy = fields.rest_fields(nx, ny)

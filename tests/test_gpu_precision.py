@@ -1,0 +1,101 @@
+"""Storage precision at equal manufactured-solution error.
+
+The 64 x 64 spatiotemporal manufactured solution (1000 steps, tau = 0.8) is run
+with FP64, FP32, FP16 and BF16 population storage. Each run's velocity error E_u
+(Eq. 26) against the manufactured velocity is compared with the FP64 run's, which
+is the scheme's discretisation error: FP32 and FP16 storage must stay within 1.5x
+of it. BF16 (8 significant bits) is reported; its bound is checked separately
+with the looser factor its rounding allows.
+"""
+import numpy as np
+import pytest
+
+from synth import mms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_02964_gb300 as pkg
+    pkg.capi.load()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def inputs():
+    n, T, nu = 64, 1000, 0.1
+    M = mms.Config1(n=n, T=float(T))
+    phis = [M.phi(t) for t in range(T + 1)]
+    forces = [M.force(t, nu) for t in range(T + 1)]
+    return M, n, T, phis, forces
+
+
+def _run(P, storage, inputs):
+    M, n, T, phis, forces = inputs
+    lat = P.Lattice(n, n, 0.8, s_eps=1.2, s_q=1.2, storage=storage)
+    ux0, uy0 = M.velocity(0)
+    lat.set_void_fraction(phis[0], phis[1])
+    lat.set_body_force(0.0, 0.0, forces[0])
+    lat.init_fields(np.ones((n, n)), ux0, uy0)
+    for t in range(T):
+        lat.set_void_fraction(phis[t], phis[t + 1])
+        lat.set_body_force(0.0, 0.0, forces[t])
+        lat.step(1)
+    lat.set_void_fraction(phis[T])
+    lat.set_body_force(0.0, 0.0, forces[T])
+    uxr, uyr = M.velocity(T)
+    num, den = lat.velocity_error(uxr, uyr)
+    m = {k: v.cpu().numpy() for k, v in lat.macros().items()}
+    lat.close()
+    return float(np.sqrt(num / den)), m
+
+
+@pytest.fixture(scope="module")
+def errors(P, inputs):
+    out = {}
+    for st in ("fp64", "fp32", "fp16", "bf16"):
+        out[st] = _run(P, st, inputs)
+    return out
+
+
+def test_report_errors(errors):
+    for st, (e, _) in errors.items():
+        print(f"E_u[{st}] = {e:.4e}  ({e / errors['fp64'][0]:.3f} x FP64)")
+
+
+def test_fp64_error_is_the_discretisation_error(errors):
+    e = errors["fp64"][0]
+    assert 1e-4 < e < 5e-3   # second-order scheme at n = 64 (the oracle gives 1.76e-3)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_reduced_storage_within_1p5x_of_fp64(errors, storage):
+    assert errors[storage][0] <= 1.5 * errors["fp64"][0]
+
+
+def test_bf16_error_reported(errors):
+    # BF16 keeps 8 significant bits of the deviation from rest: recorded, bounded loosely
+    assert np.isfinite(errors["bf16"][0])
+    assert errors["bf16"][0] <= 10 * errors["fp64"][0]
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_pressure_error_against_fp64(errors, inputs, storage):
+    """Density (pressure) is the conserved mode, so each step's storage rounding of
+    the 9 populations (absolute size delta) adds up as a random walk:
+    |rho - rho_64| / rho <~ 3 sqrt(T) 9 delta / phi_min, with delta = 2^-24 max|f|
+    (FP32 stores f), 2^-11 or 2^-8 max|f - f_rest| (FP16 / BF16 store deviations)."""
+    M, n, T, phis, _ = inputs
+    p64 = errors["fp64"][1]["p"]
+    p = errors[storage][1]["p"]
+    rel = np.sqrt(np.sum((p - p64) ** 2) / np.sum(p64 ** 2))
+    fmax, devmax = 0.5, 0.02      # populations of this workload: |f| < 0.5, |f - f_rest| < 0.02
+    delta = {"fp32": 2.0 ** -24 * fmax, "fp16": 2.0 ** -11 * devmax, "bf16": 2.0 ** -8 * devmax}[storage]
+    phi_min = min(float(ph.min()) for ph in phis[:: max(1, T // 20)])
+    bound = 3 * np.sqrt(T) * 9 * delta / phi_min
+    print(f"E_p[{storage}] vs FP64 = {rel:.3e} (bound {bound:.2e})")
+    assert rel < bound
