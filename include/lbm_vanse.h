@@ -132,6 +132,36 @@ lbm_status lbm_vanse_reduce(lbm_vanse_t h, double* mass, double* momx, double* m
 lbm_status lbm_vanse_velocity_error(lbm_vanse_t h, const double* ux_ref, const double* uy_ref,
                                     int on_device, double* num, double* den);
 
+/* Largest ny that lbm_vanse_reduce_noalloc accepts: its scratch holds one partial
+ * (mass, momx, momy) triple per lattice row. */
+#define LBM_VANSE_NOALLOC_MAX_ROWS 8192
+
+/* Allocation-free form of lbm_vanse_reduce, for callers that cannot allocate device
+ * memory while they run: a host loop whose memory is planned once and must not grow,
+ * an application whose allocator owns all device memory (cudaMalloc from a library
+ * would fragment or bypass it), or code that must not synchronise the device, which
+ * cudaMalloc and cudaFree may do. This method's paper has no counterpart; it is a
+ * service of this library.
+ *
+ * Computes the same FP64 sums as lbm_vanse_reduce (mass = sum_x sum_i f_i, momentum
+ * sum_x sum_i e_i f_i) and writes them to out_dev[0..2], a caller-owned DEVICE array
+ * of 3 doubles, asynchronously on the handle's stream (read it after synchronising).
+ * Nothing is allocated or freed: the per-row partial sums live in one fixed device
+ * array of LBM_VANSE_NOALLOC_MAX_ROWS x 3 doubles (192 KiB) inside the library, which
+ * every GPU that loads the library keeps until the process exits.
+ *
+ * The first call on a device looks up that array's device address with that device
+ * current; make that first call before starting any stream capture. Every call on a
+ * device shares the one array: calls whose kernels overlap on the GPU (two streams,
+ * two handles, two threads) race on it and may return mixed sums, so keep such calls
+ * ordered. Each call writes every partial it reads, so no clearing is needed and a
+ * previous call's leftovers never leak into a result.
+ *
+ * Errors: LBM_ERR_ARG for a NULL handle or output, or ny > LBM_VANSE_NOALLOC_MAX_ROWS;
+ * LBM_ERR_STATE before initialisation; LBM_ERR_CUDA if the address lookup or a launch
+ * fails. It does not check the sums for NaN (the caller reads them). */
+lbm_status lbm_vanse_reduce_noalloc(lbm_vanse_t h, double* out_dev);
+
 /* Synchronise the stream and report any deferred kernel error (LBM_ERR_TIMEOUT
  * if a bounded wait gave up, LBM_ERR_CUDA for a launch/runtime error). */
 lbm_status lbm_vanse_sync(lbm_vanse_t h);

@@ -13,6 +13,8 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_STATE,
 LBM_FP64, LBM_FP32, LBM_FP16, LBM_BF16 = 0, 1, 2, 3
 LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = 0, 1
 
+NOALLOC_MAX_ROWS = 8192  # LBM_VANSE_NOALLOC_MAX_ROWS
+
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
                 -4: "LBM_ERR_DIVERGED", -5: "LBM_ERR_STATE", -6: "LBM_ERR_TIMEOUT"}
 
@@ -21,7 +23,7 @@ EXPORTS = [
     "lbm_vanse_default_params", "lbm_vanse_create", "lbm_vanse_set_void_fraction",
     "lbm_vanse_set_body_force", "lbm_vanse_init_fields", "lbm_vanse_step", "lbm_vanse_macros",
     "lbm_vanse_get_populations", "lbm_vanse_set_populations", "lbm_vanse_reduce",
-    "lbm_vanse_velocity_error", "lbm_vanse_sync", "lbm_vanse_step_count",
+    "lbm_vanse_velocity_error", "lbm_vanse_reduce_noalloc", "lbm_vanse_sync", "lbm_vanse_step_count",
     "lbm_vanse_bytes_per_cell", "lbm_vanse_launch_shape", "lbm_vanse_last_error",
     "lbm_vanse_destroy",
 ]
@@ -72,6 +74,7 @@ def load(path: str | None = None):
         "lbm_vanse_set_populations": (i, [vp, vp, i]),
         "lbm_vanse_reduce": (i, [vp, dp, dp, dp]),
         "lbm_vanse_velocity_error": (i, [vp, vp, vp, i, dp, dp]),
+        "lbm_vanse_reduce_noalloc": (i, [vp, vp]),
         "lbm_vanse_sync": (i, [vp]),
         "lbm_vanse_step_count": (ctypes.c_longlong, [vp]),
         "lbm_vanse_bytes_per_cell": (d, [vp]),

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "lbm_vanse.h"
@@ -352,6 +353,64 @@ lbm_status ensure_scratch(lbm_vanse* h) {
 bool rate_ok(double s) { return s > 0.0 && s < 2.0; }
 
 }  // namespace
+
+// ================================================== allocation-free reduction
+// Per-row partial sums for lbm_vanse_reduce_noalloc live in this fixed array, so
+// that call needs no cudaMalloc. In host code the name is only a stand-in for the
+// device copy: its device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) double g_noalloc_rows[LBM_VANSE_NOALLOC_MAX_ROWS * 3];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_rows on h's device (looked up on first use, with that
+// device current).
+lbm_status noalloc_rows(lbm_vanse* h, double** out) {
+    if (h->device < 0 || h->device >= kMaxDevices) return fail(h, LBM_ERR_ARG, "device %d out of range", h->device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[h->device]) {
+        int prev = -1;
+        CK(h, cudaGetDevice(&prev));
+        if (prev != h->device) CK(h, cudaSetDevice(h->device));
+        void* addr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_rows);
+        if (prev != h->device) cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress(reduction rows)");
+        g_noalloc_addr[h->device] = static_cast<double*>(addr);
+    }
+    *out = g_noalloc_addr[h->device];
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status run_reduce_noalloc(lbm_vanse* h, double* rows, double* out) {
+    using R = typename Prec<S>::R;
+    const int blocks = std::min(h->prm.ny, 1024);
+    row_moments_kernel<S, R><<<blocks, kAuxThreads, 0, h->stream>>>((const S*)h->f[h->cur], (const R*)h->phi, rows,
+                                                                     make_lattice<R>(h));
+    CK(h, cudaGetLastError());
+    finish_reduce_kernel<<<1, 1024, 0, h->stream>>>(rows, h->prm.ny, out);
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_vanse_reduce_noalloc(lbm_vanse_t h, double* out_dev) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!out_dev) return fail(h, LBM_ERR_ARG, "out_dev is NULL");
+    if (h->prm.ny > LBM_VANSE_NOALLOC_MAX_ROWS)
+        return fail(h, LBM_ERR_ARG, "ny = %d exceeds the %d rows the fixed reduction scratch holds", h->prm.ny,
+                    LBM_VANSE_NOALLOC_MAX_ROWS);
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lattice not initialised");
+    double* rows = nullptr;
+    lbm_status st = noalloc_rows(h, &rows);
+    if (st != LBM_OK) return st;
+    return DISPATCH(h, run_reduce_noalloc, rows, out_dev);
+}
 
 // ============================================================================ C ABI
 

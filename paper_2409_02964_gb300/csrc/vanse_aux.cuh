@@ -253,6 +253,40 @@ __global__ void velocity_error_kernel(const double* __restrict__ ux, const doubl
     block_reduce3(num, den, 0.0, partial);
 }
 
+// Mass and momentum sums per lattice row: one partial triple per row, written to
+// partial[3*y .. 3*y+2] (rows are shared out over the blocks, grid-stride). Every
+// row 0..ny-1 gets its triple written, so the caller never needs to clear partial.
+template <typename S, typename R>
+__global__ void row_moments_kernel(const S* __restrict__ buf, const R* __restrict__ phi, double* __restrict__ partial,
+                                   const Lattice<R> L) {
+    __shared__ double sh[3][32];
+    for (int y = blockIdx.x; y < L.ny; y += gridDim.x) {
+        double m = 0, jx = 0, jy = 0;
+        for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
+            R f[9];
+            pull_cell<S, R>(buf, phi, L, x, y, f);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const double v = (double)f[i];
+                m += v; jx += ex_of(i) * v; jy += ey_of(i) * v;
+            }
+        }
+        m = warp_sum(m); jx = warp_sum(jx); jy = warp_sum(jy);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) { sh[0][wid] = m; sh[1][wid] = jx; sh[2][wid] = jy; }
+        __syncthreads();
+        if (wid == 0) {
+            const int nw = blockDim.x >> 5;
+            m = lane < nw ? sh[0][lane] : 0.0;
+            jx = lane < nw ? sh[1][lane] : 0.0;
+            jy = lane < nw ? sh[2][lane] : 0.0;
+            m = warp_sum(m); jx = warp_sum(jx); jy = warp_sum(jy);
+            if (lane == 0) { partial[3 * y + 0] = m; partial[3 * y + 1] = jx; partial[3 * y + 2] = jy; }
+        }
+        __syncthreads();
+    }
+}
+
 // Sum nblocks partial triples in a fixed order (deterministic) into out[0..2].
 __global__ void finish_reduce_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
     double a = 0, b = 0, c = 0;
