@@ -40,6 +40,26 @@ DTYPE = {"fp32": "f32", "fp16": "f32", "bf16": "f32", "fp64": "f64"}
 SBYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}
 
 
+def _kernel_traffic(cells: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu capture (a
+    smaller channel, scaled by cells), or None when the kernel sources have changed
+    since that capture."""
+    import glob
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "vanse_warp_fp32_channel_traffic.json")) as fh:
+            rec = json.load(fh)
+        h = hashlib.sha256()
+        for f in sorted(glob.glob(os.path.join(ROOT, "paper_2409_02964_gb300", "csrc", "*.cuh"))):
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return round(rec["dram_bytes_per_cell"] * cells)
+    except Exception:
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -101,11 +121,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def build_channel(n: int, storage: str, strip_rows: int = 0):
+def build_channel(n: int, storage: str, strip_rows: int = 0, kernel: int = 0):
     import paper_2409_02964_gb300 as P
     from synth import fields
     phi = fields.channel_phi(n, n)
-    lat = P.Lattice(n, n, TAU, bc_y="bounceback", storage=storage, strip_rows=strip_rows, **RATES)
+    lat = P.Lattice(n, n, TAU, bc_y="bounceback", storage=storage, strip_rows=strip_rows, kernel=kernel, **RATES)
     lat.set_void_fraction(phi)
     lat.set_body_force(G, 0.0)
     rho, ux, uy = fields.rest_fields(n, n)
@@ -219,6 +239,7 @@ def main():
     ap.add_argument("--storage", choices=["fp32", "fp16", "bf16", "fp64"], default="fp32")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--strip-rows", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=0, help="step-kernel variant (0 = the library's choice)")
     ap.add_argument("--quick", action="store_true", help="timed steps only (no e2e / variants / CPU baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -236,7 +257,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    lat, phi = build_channel(args.n, args.storage, args.strip_rows)
+    lat, phi = build_channel(args.n, args.storage, args.strip_rows, args.kernel)
     cells = args.n * args.n
     m0 = lat.reduce()[0]
     if dist:
@@ -246,12 +267,10 @@ def main():
     secs = time_steps(lat, args.steps, args.warmup)
     clocks = sampler.stop() if sampler else None
     m1 = lat.reduce()[0]
+    from paper_2409_02964_gb300.replicas import job_throughput
+    value, secs, _ = job_throughput(secs, cells * args.steps / 1e6, device=torch.device("cuda", local))
     if dist:
-        t = torch.tensor([secs], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
         dist.barrier()
-    value = world * cells * args.steps / secs / 1e6
     bpc = lat.bytes_per_cell
     step_s = secs / args.steps
     achieved = bpc * cells / step_s / 1e9
@@ -270,8 +289,11 @@ def main():
                        f"{2 * 9 * cells * SBYTES[args.storage] / 1e9:.2f} GB, L2 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single", "launch": shape},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
-                         "peak_source": f"{peak_kind} hbm_gbs", "kernel": "vanse_step_kernel"},
+                         "frac": round(achieved / peak, 4),
+                         "traffic": _kernel_traffic(cells) if (args.storage == "fp32" and shape["threads"] == 32) else None,
+                         "traffic_unit": "bytes per launch",
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel": {32: "vanse_warp_kernel"}.get(shape["threads"], "vanse_step_kernel / vanse_pair_kernel")},
             "gpu_launches": args.steps,
             "clocks": clocks,
             "mass_drift": (m1 - m0) / m0,

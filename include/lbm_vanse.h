@@ -67,6 +67,10 @@ typedef struct {
     int strip_rows;              /* rows per CTA strip of the step kernel; 0 = automatic */
     int eager;                   /* 1 = launch each step on its own; 0 = replay runs of steady
                                     steps as a captured CUDA graph (default) */
+    int kernel;                  /* step-kernel variant: 0 = automatic; 1 = one column per thread
+                                    (any storage); 2, 3, 4 = two columns per thread on packed FP32
+                                    pairs with 64 / 96 / 128-thread CTAs; 5 = one warp per CTA,
+                                    two columns per lane (2..5: not FP64) */
 } lbm_vanse_params;
 
 typedef struct lbm_vanse* lbm_vanse_t;

@@ -36,23 +36,28 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Build (if stale) and return the path of liblbm_vanse.so."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra_flags=None, out: str | None = None) -> str:
+    """Build (if stale) and return the path of liblbm_vanse.so.
+
+    extra_flags: additional nvcc flags (e.g. -D tuning knobs; also read from the
+    LBM_VANSE_NVCC_FLAGS environment variable); out: alternative output path."""
+    lib = out or LIB
+    flags = list(extra_flags or []) + os.environ.get("LBM_VANSE_NVCC_FLAGS", "").split()
+    if not force and not flags and out is None and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB + ".tmp"
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    tmp = lib + ".tmp"
     cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           f"-I{INCLUDE}", "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+           f"-I{INCLUDE}", "-o", tmp] + flags + [os.path.join(CSRC, s) for s in SOURCES]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed ({' '.join(cmd)}):\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
         print(r.stderr)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":  # pragma: no cover

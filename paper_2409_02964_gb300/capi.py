@@ -39,7 +39,7 @@ class lbm_vanse_params(ctypes.Structure):
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
         ("storage", ctypes.c_int), ("model_b", ctypes.c_int),
         ("storage_scale_log2", ctypes.c_int), ("strip_rows", ctypes.c_int),
-        ("eager", ctypes.c_int),
+        ("eager", ctypes.c_int), ("kernel", ctypes.c_int),
     ]
 
 
@@ -52,7 +52,7 @@ def load(path: str | None = None):
     if _lib is not None:
         return _lib
     if path is None:
-        path = _build.build()
+        path = os.environ.get("LBM_VANSE_LIB") or _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not found at {path}")
     L = ctypes.CDLL(path)

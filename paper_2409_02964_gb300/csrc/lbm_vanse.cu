@@ -13,16 +13,27 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "lbm_vanse.h"
 #include "vanse_aux.cuh"
+#include "vanse_pair.cuh"
 #include "vanse_step.cuh"
+#include "vanse_warp.cuh"
 
 using namespace lbmv;
 
 namespace {
 
-constexpr int kThreads = 128;       // step kernel CTA size (W = kThreads - 4 columns)
+constexpr int kThreads = 128;       // one-column step kernel: CTA size (W = kThreads - 4 columns)
+
+// Step-kernel variants (params.kernel): 1 = one column per thread; 2..4 = two
+// columns per thread on packed FP32 pairs with CTAs of 64 / 96 / 128 threads
+// (W = 2T - 4 columns), register-capped for 6 / 4 / 3 resident CTAs per SM;
+// 5 = one warp per CTA, two columns per lane, shuffle exchange (W = 60).
+constexpr int kNumKernels = 5;
+constexpr int kPairT[3] = {64, 96, 128};
+constexpr int kDefaultKernel = 5;
 constexpr int kAuxThreads = 256;
 constexpr int kReduceBlocks = 1024;
 constexpr int kGraphSteps = 32;     // steps per replayed CUDA graph (even: ping-pong returns to its buffer)
@@ -61,7 +72,7 @@ struct lbm_vanse {
     double* scratch = nullptr;    // 3 dense double fields (macros / error norms)
     long long steps = 0;
     // step-kernel launch shape
-    int W = 0, H = 0, gridx = 0, gridy = 0, wwmax = 0;
+    int W = 0, H = 0, gridx = 0, gridy = 0;
     // replayed graph of kGraphSteps steady steps, valid while its key matches
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -72,6 +83,8 @@ struct lbm_vanse {
         }
     } gkey{};
     bool use_graphs = true;
+    int kernel = 1;               // step-kernel variant (see kNumKernels)
+    bool pair = false;            // two columns per thread (packed FP32) step kernel
     std::string msg;
 };
 
@@ -132,31 +145,58 @@ int aux_blocks(long long n) {
 }
 
 template <typename S>
-size_t step_smem_bytes(const lbm_vanse* h, int nR, int* slot_stride_out) {
+size_t step_smem_bytes(const lbm_vanse* h, int nR) {
     using R = typename Prec<S>::R;
-    const int ring_off = (128 + 7 * kThreads * (int)sizeof(R) + 127) & ~127;
-    int slot = 9 * h->wwmax * (int)sizeof(S) + nR * h->wwmax * (int)sizeof(R);
-    slot = (slot + 127) & ~127;
-    if (slot_stride_out) *slot_stride_out = slot;
-    return (size_t)ring_off + (size_t)kSlots * slot;
+    switch (h->kernel) {
+        case 2: return PairLayout<S, 64>::bytes(nR);
+        case 3: return PairLayout<S, 96>::bytes(nR);
+        case 4: return PairLayout<S, 128>::bytes(nR);
+        case 5: return WarpLayout<S>::bytes(nR);
+        default: return StepLayout<S, R, kThreads>::bytes(nR);
+    }
+}
+
+int step_threads(const lbm_vanse* h) {
+    if (h->kernel == 5) return 32;
+    return h->kernel >= 2 ? kPairT[h->kernel - 2] : kThreads;
+}
+
+template <typename S>
+const void* step_kernel_ptr(const lbm_vanse* h) {
+    using R = typename Prec<S>::R;
+    if constexpr (!std::is_same<S, double>::value) {
+        switch (h->kernel) {
+            case 2: return (const void*)vanse_pair_kernel<S, 64, 6>;
+            case 3: return (const void*)vanse_pair_kernel<S, 96, 4>;
+            case 4: return (const void*)vanse_pair_kernel<S, 128, 3>;
+            case 5: return (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB>;
+            default: break;
+        }
+    }
+    return (const void*)vanse_step_kernel<S, R, kThreads>;
 }
 
 template <typename S>
 lbm_status configure(lbm_vanse* h) {
     using R = typename Prec<S>::R;
-    auto kern = vanse_step_kernel<S, R, kThreads>;
-    const size_t smax = step_smem_bytes<S>(h, 4, nullptr);
+    (void)sizeof(R);
+    const void* kern = step_kernel_ptr<S>(h);
+    const int threads = step_threads(h);
+    const size_t smax = step_smem_bytes<S>(h, 4);
     CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
-    const size_t s1 = step_smem_bytes<S>(h, 1, nullptr);
+    CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+    const size_t s1 = step_smem_bytes<S>(h, 1);
     int per_sm = 0, nsm = 0;
-    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, s1));
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, s1));
     CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     const int resident = std::max(1, per_sm * nsm);
     int H = h->prm.strip_rows;
     if (H <= 0) {
-        int nstrips = std::max(1, resident / h->gridx);
+        // about five waves of resident CTAs: short strips cost halo rows, long ones
+        // leave SMs idle in the last wave
+        const int nstrips = std::max(1, (5 * resident + h->gridx - 1) / h->gridx);
         H = (h->prm.ny + nstrips - 1) / nstrips;
-        H = std::max(H, 8);
+        H = std::max(H, 16);
     }
     h->H = std::min(H, h->prm.ny);
     h->gridy = (h->prm.ny + h->H - 1) / h->H;
@@ -183,23 +223,33 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src) {
     p.has_fb = h->has_fb;
     p.model_b = h->prm.model_b;
     const int nR = 1 + (h->unsteady ? 1 : 0) + (h->has_fb ? 2 : 0);
-    int slot_stride = 0;
-    const size_t smem = step_smem_bytes<S>(h, nR, &slot_stride);
-    p.slot_stride = slot_stride;
-    p.wwmax = h->wwmax;
+    const size_t smem = step_smem_bytes<S>(h, nR);
+    p.nR = nR;
     p.kappa = (R)h->prm.kappa;
     p.gx = (R)h->gx;
     p.gy = (R)h->gy;
-    p.s_c = (R)h->prm.s_c;
     p.s_e = (R)h->s_e;
     p.s_eps = (R)h->prm.s_eps;
     p.s_q = (R)h->prm.s_q;
     p.s_nu = (R)h->s_nu;
+    p.h_e = (R)(1.0 - 0.5 * h->s_e);
+    p.h_eps = (R)(1.0 - 0.5 * h->prm.s_eps);
+    p.h_q = (R)(1.0 - 0.5 * h->prm.s_q);
+    p.h_nu = (R)(1.0 - 0.5 * h->s_nu);
     p.scale = (R)h->scale;
     p.inv_scale = (R)h->inv_scale;
     p.rest = make_rest<R>(h);
     p.err = h->err;
     dim3 grid(h->gridx, h->gridy);
+    if constexpr (!std::is_same<S, double>::value) {
+        switch (h->kernel) {
+            case 2: vanse_pair_kernel<S, 64, 6><<<grid, 64, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
+            case 3: vanse_pair_kernel<S, 96, 4><<<grid, 96, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
+            case 4: vanse_pair_kernel<S, 128, 3><<<grid, 128, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
+            case 5: vanse_warp_kernel<S, LBMV_WARP_MINB><<<grid, 32, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
+            default: break;
+        }
+    }
     vanse_step_kernel<S, R, kThreads><<<grid, kThreads, smem, stream>>>(p);
     CK(h, cudaGetLastError());
     return LBM_OK;
@@ -470,10 +520,18 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
         h->scale = std::ldexp(1.0, k);
         h->inv_scale = std::ldexp(1.0, -k);
     }
-    h->W = kThreads - 4;
+    if (p->kernel < 0 || p->kernel > kNumKernels) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "kernel must lie in 0..%d", kNumKernels);
+    }
+    if (p->kernel >= 2 && p->storage == LBM_FP64) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "the two-column kernels run packed FP32 arithmetic; FP64 storage needs kernel 1");
+    }
+    h->kernel = p->kernel ? p->kernel : (p->storage == LBM_FP64 ? 1 : kDefaultKernel);
+    h->pair = h->kernel >= 2;
+    h->W = h->kernel == 5 ? 60 : (h->pair ? 2 * kPairT[h->kernel - 2] - 4 : kThreads - 4);
     h->gridx = (p->nx + h->W - 1) / h->W;
-    const int A = 16 / h->sbytes;
-    h->wwmax = kThreads + 2 * A;
     h->P = ((kPadCols + h->gridx * h->W + kPadCols) + 31) / 32 * 32;
     h->plane = (long long)p->ny * h->P;
 
@@ -730,7 +788,7 @@ extern "C" double lbm_vanse_bytes_per_cell(lbm_vanse_t h) {
 extern "C" lbm_status lbm_vanse_launch_shape(lbm_vanse_t h, int* threads, int* cols, int* rows, int* grid_x,
                                              int* grid_y, int* smem_bytes) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
-    if (threads) *threads = kThreads;
+    if (threads) *threads = step_threads(h);
     if (cols) *cols = h->W;
     if (rows) *rows = h->H;
     if (grid_x) *grid_x = h->gridx;
@@ -739,10 +797,10 @@ extern "C" lbm_status lbm_vanse_launch_shape(lbm_vanse_t h, int* threads, int* c
         const int nR = 1 + (h->unsteady ? 1 : 0) + (h->has_fb ? 2 : 0);
         size_t s = 0;
         switch (h->prm.storage) {
-            case LBM_FP64: s = step_smem_bytes<double>(h, nR, nullptr); break;
-            case LBM_FP32: s = step_smem_bytes<float>(h, nR, nullptr); break;
-            case LBM_FP16: s = step_smem_bytes<__half>(h, nR, nullptr); break;
-            default: s = step_smem_bytes<__nv_bfloat16>(h, nR, nullptr); break;
+            case LBM_FP64: s = step_smem_bytes<double>(h, nR); break;
+            case LBM_FP32: s = step_smem_bytes<float>(h, nR); break;
+            case LBM_FP16: s = step_smem_bytes<__half>(h, nR); break;
+            default: s = step_smem_bytes<__nv_bfloat16>(h, nR); break;
         }
         *smem_bytes = (int)s;
     }

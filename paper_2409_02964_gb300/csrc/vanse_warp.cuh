@@ -1,0 +1,412 @@
+// vanse_warp.cuh -- the fused D2Q9 MRTLB-VANSE stream + collide kernel with one
+// warp per CTA, two adjacent columns per lane on packed FP32 pairs.
+//
+// Same method and the same three row phases as vanse_step.cuh; the differences:
+//   * a CTA is one warp: lane l owns columns xa = x0 - 2 + 2l, xb = xa + 1, the
+//     warp covers 64 columns and stores W = 60 of them;
+//   * x-neighbours come from the adjacent lanes by shuffles (no shared exchange
+//     rows, no CTA barriers), so every warp runs its row pipeline independently and
+//     a stalled warp never holds the others up;
+//   * arithmetic on the packed FP32 pairs of vanse_pair.cuh (FFMA2 / FADD2 / FMUL2);
+//   * the source-row ring (cp.async.bulk + mbarriers, 8 slots) is per warp; the
+//     slot of row p - 3 is refilled with row p + 5 at the start of iteration p;
+//   * interior rows of steady, field-free strips run one branch-free block (no
+//     wall / validity / field tests), so the collision of one row can overlap the
+//     pulls and shuffles of the next two.
+// Lanes 0 and 31 carry the halo columns: lane 0 finishes nothing, lane 31 nothing;
+// lanes 1..30 store their two columns.
+#pragma once
+
+#include "vanse_common.cuh"
+#include "vanse_pair.cuh"
+#include "vanse_step.cuh"
+
+namespace lbmv {
+
+// source-row ring of the one-warp kernel: rows p-2 .. p+1 in use, the rest prefetch
+#ifndef LBMV_WARP_SLOTS
+#define LBMV_WARP_SLOTS 8
+#endif
+constexpr int kWarpSlots = LBMV_WARP_SLOTS;
+
+// resident one-warp CTAs per SM the register allocation is sized for
+#ifndef LBMV_WARP_MINB
+#define LBMV_WARP_MINB 8
+#endif
+
+template <typename S>
+struct WarpLayout {
+    static constexpr int A = 16 / (int)sizeof(S);
+    static constexpr int WW = 64 + 2 * A;           // staged row width (elements)
+    static constexpr int kPop = 128;                // after the mbarriers
+    static constexpr int kPopRow = WW * (int)sizeof(S);
+    static constexpr int kPopSlot = 9 * kPopRow;
+    static constexpr int kAux = kPop + kWarpSlots * kPopSlot;
+    static constexpr int kAuxRow = WW * 4;
+    static constexpr size_t bytes(int nR) { return (size_t)kAux + (size_t)kWarpSlots * nR * kAuxRow; }
+};
+
+__device__ __forceinline__ int wslot(int r) { return ((r % kWarpSlots) + kWarpSlots) % kWarpSlots; }
+
+template <typename S>
+struct WarpCtx {
+    using L = WarpLayout<S>;
+    const StepParams<float>& p;
+    unsigned char* smem;
+    int lane, xa, sa;
+    int y0, y1;
+    int wsp, ww;
+    int rlo, rhi;
+    int waited, issued;
+    bool aborted;
+
+    __device__ __forceinline__ uint64_t* bar(int r) const { return reinterpret_cast<uint64_t*>(smem) + wslot(r); }
+    __device__ __forceinline__ const S* pop(int r) const {
+        return reinterpret_cast<const S*>(smem + L::kPop + wslot(r) * L::kPopSlot) + sa;
+    }
+    __device__ __forceinline__ const float* aux(int r, int k) const {
+        return reinterpret_cast<const float*>(smem + L::kAux) + (wslot(r) * p.nR + k) * L::WW + sa;
+    }
+    __device__ __forceinline__ bool row_valid(int r) const { return !p.wall_y || (r >= 0 && r < p.ny); }
+    __device__ __forceinline__ uint32_t parity(int r) const { return (uint32_t)(((r - rlo) / kWarpSlots) & 1); }
+
+    // lane 0: load source row r into its slot
+    __device__ __forceinline__ void issue(int r) {
+        issued = r;
+        uint64_t* b = bar(r);
+        int gr = r;
+        if (!p.wall_y) { gr %= p.ny; if (gr < 0) gr += p.ny; }
+        const uint32_t bs = (uint32_t)(ww * (int)sizeof(S));
+        const uint32_t br = (uint32_t)(ww * 4);
+        mbar_expect_tx(b, 9u * bs + (uint32_t)p.nR * br);
+        const long long off = (long long)gr * p.P + wsp;
+        const S* src = reinterpret_cast<const S*>(p.src) + off;
+        unsigned char* ps = smem + L::kPop + wslot(r) * L::kPopSlot;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) bulk_g2s(ps + i * L::kPopRow, src + i * p.plane, bs, b);
+        float* rr = reinterpret_cast<float*>(smem + L::kAux) + wslot(r) * p.nR * L::WW;
+        int k = 0;
+        bulk_g2s(rr + (k++) * L::WW, p.phi + off, br, b);
+        if (p.unsteady) bulk_g2s(rr + (k++) * L::WW, p.phin + off, br, b);
+        if (p.has_fb) {
+            bulk_g2s(rr + (k++) * L::WW, p.fb + off, br, b);
+            bulk_g2s(rr + (k++) * L::WW, p.fb + p.plane + off, br, b);
+        }
+    }
+    __device__ __forceinline__ void wait_upto(int r) {
+        r = min(r, rhi);
+        while (waited < r) {
+            ++waited;
+            if (!mbar_wait_bounded(bar(waited), parity(waited), kWaitTries)) {
+                aborted = true;
+                atomicExch(p.err, 1);
+            }
+        }
+    }
+};
+
+// neighbour values across lanes: the left neighbour of xa is lane-1's xb, the right
+// neighbour of xb is lane+1's xa
+__device__ __forceinline__ float left_of(V2 v) { return __shfl_up_sync(0xffffffffu, v.v.y, 1); }
+__device__ __forceinline__ float right_of(V2 v) { return __shfl_down_sync(0xffffffffu, v.v.x, 1); }
+
+template <typename S, bool FAST>
+__device__ __forceinline__ void warp_phase1(const WarpCtx<S>& c, PRow& st, int r) {
+    using IO = PairIO<S>;
+    constexpr int RW = WarpLayout<S>::WW;
+    const StepParams<float>& p = c.p;
+    const V2 phi = V2{*reinterpret_cast<const float2*>(c.aux(r, 0))};
+    const float ia = p.inv_scale;
+    const V2 rax = bc(p.rest.ax), rdg = bc(p.rest.dg);
+    const V2 r0 = fma2(p.rest.rho0, phi, bc(-p.rest.k59));
+    const S* cur = c.pop(r);
+    V2 f0, f1, f2, f3, f4, f5, f6, f7, f8;
+    f0 = IO::dec(IO::al(cur), r0, ia);
+    f1 = IO::dec(IO::un(cur + 1 * RW - 1), rax, ia);
+    f3 = IO::dec(IO::un(cur + 3 * RW + 1), rax, ia);
+    if (!FAST && p.wall_y && r == 0) {
+        f2 = IO::dec(IO::al(cur + 4 * RW), rax, ia);
+        f5 = IO::dec(IO::al(cur + 7 * RW), rdg, ia);
+        f6 = IO::dec(IO::al(cur + 8 * RW), rdg, ia);
+    } else {
+        const S* lo = c.pop(r - 1);
+        f2 = IO::dec(IO::al(lo + 2 * RW), rax, ia);
+        f5 = IO::dec(IO::un(lo + 5 * RW - 1), rdg, ia);
+        f6 = IO::dec(IO::un(lo + 6 * RW + 1), rdg, ia);
+    }
+    if (!FAST && p.wall_y && r == p.ny - 1) {
+        f4 = IO::dec(IO::al(cur + 2 * RW), rax, ia);
+        f7 = IO::dec(IO::al(cur + 5 * RW), rdg, ia);
+        f8 = IO::dec(IO::al(cur + 6 * RW), rdg, ia);
+    } else {
+        const S* hi = c.pop(r + 1);
+        f4 = IO::dec(IO::al(hi + 4 * RW), rax, ia);
+        f7 = IO::dec(IO::un(hi + 7 * RW + 1), rdg, ia);
+        f8 = IO::dec(IO::un(hi + 8 * RW - 1), rdg, ia);
+    }
+    const V2 a13 = f1 + f3, a24 = f2 + f4, b57 = f5 + f7, b68 = f6 + f8;
+    const V2 sax = a13 + a24, sdg = b57 + b68;
+    const V2 d13 = f1 - f3, d24 = f2 - f4, d57 = f5 - f7;
+    const V2 dx = d57 + (f8 - f6);
+    const V2 dy = d57 + (f6 - f8);
+    st.m[0] = f0 + sax + sdg;
+    st.m[1] = fma2(-4.f, f0, fma2(2.f, sdg, -sax));
+    st.m[2] = fma2(4.f, f0, fma2(-2.f, sax, sdg));
+    st.m[3] = d13 + dx;
+    st.m[4] = fma2(-2.f, d13, dx);
+    st.m[5] = d24 + dy;
+    st.m[6] = fma2(-2.f, d24, dy);
+    st.m[7] = a13 - a24;
+    st.m[8] = b57 - b68;
+    st.rho = st.m[0] * rcp2(phi);
+}
+
+template <typename S, bool FAST>
+__device__ __forceinline__ void warp_phase2(const WarpCtx<S>& c, const PRow& An, PRow& Bs, const PRow& Cs, int p2) {
+    const StepParams<float>& p = c.p;
+    constexpr float tw = 1.0f / 12.0f;
+    V2 dlo = Cs.dr, wlo = Cs.wr, dhi = An.dr, whi = An.wr;
+    if (!FAST && p.wall_y && (p2 == 0 || p2 == p.ny - 1)) {
+        if (p2 == 0) { dlo = Bs.dr; wlo = Bs.wr; }
+        if (p2 == p.ny - 1) { dhi = Bs.dr; whi = Bs.wr; }
+    }
+    const V2 gx = tw * fma2(4.f, Bs.dr, dlo + dhi);
+    const V2 gy = tw * (whi - wlo);
+    const V2 phi = V2{*reinterpret_cast<const float2*>(c.aux(p2, 0))};
+    const V2 kp = p.model_b ? bc((p.kappa - 1.f) * (1.f / 3.f)) : (1.f / 3.f) * (bc(p.kappa) - phi);
+    V2 Fx = fma2(kp, gx, p.gx * phi);
+    V2 Fy = fma2(kp, gy, p.gy * phi);
+    if (!FAST && p.has_fb) {
+        const int k = p.unsteady ? 2 : 1;
+        Fx = Fx + V2{*reinterpret_cast<const float2*>(c.aux(p2, k))};
+        Fy = Fy + V2{*reinterpret_cast<const float2*>(c.aux(p2, k + 1))};
+    }
+    const V2 m0 = Bs.m[0];
+    const V2 inv = rcp2(m0);
+    const V2 ux = fma2(0.5f, Fx, Bs.m[3]) * inv;
+    const V2 uy = fma2(0.5f, Fy, Bs.m[5]) * inv;
+    Bs.Fx = Fx; Bs.Fy = Fy; Bs.ux = ux; Bs.uy = uy;
+    // the Eq. (10) x-differences / smoothed sums of rho u, u, phi rho u on row p2
+    const V2 Ax = Bs.rho * ux, Ay = Bs.rho * uy, Dx = m0 * ux, Dy = m0 * uy;
+    const float Axl = left_of(Ax), Axr = right_of(Ax);
+    const float Ayl = left_of(Ay), Ayr = right_of(Ay);
+    const float Bxl = left_of(ux), Bxr = right_of(ux);
+    const float Byl = left_of(uy), Byr = right_of(uy);
+    const float Dxl = left_of(Dx), Dxr = right_of(Dx);
+    const float Dyl = left_of(Dy), Dyr = right_of(Dy);
+    Bs.dAx = rpair(Ax, Axr) - lpair(Ax, Axl);
+    Bs.dBx = rpair(ux, Bxr) - lpair(ux, Bxl);
+    Bs.dBy = rpair(uy, Byr) - lpair(uy, Byl);
+    Bs.dDx = rpair(Dx, Dxr) - lpair(Dx, Dxl);
+    Bs.wAy = fma2(4.f, Ay, rpair(Ay, Ayr) + lpair(Ay, Ayl));
+    Bs.wBy = fma2(4.f, uy, rpair(uy, Byr) + lpair(uy, Byl));
+    Bs.wBx = fma2(4.f, ux, rpair(ux, Bxr) + lpair(ux, Bxl));
+    Bs.wDy = fma2(4.f, Dy, rpair(Dy, Dyr) + lpair(Dy, Dyl));
+}
+
+template <typename S, bool FAST>
+__device__ __forceinline__ void warp_phase3(const WarpCtx<S>& c, const PRow& An, const PRow& Bs, const PRow& Cs,
+                                            int p3, bool lane_ok) {
+    using IO = PairIO<S>;
+    const StepParams<float>& p = c.p;
+    constexpr float tw = 1.0f / 12.0f;
+    V2 xAx = fma2(4.f, Cs.dAx, An.dAx + Bs.dAx);
+    V2 xBx = fma2(4.f, Cs.dBx, An.dBx + Bs.dBx);
+    V2 xBy = fma2(4.f, Cs.dBy, An.dBy + Bs.dBy);
+    V2 xDx = fma2(4.f, Cs.dDx, An.dDx + Bs.dDx);
+    V2 yAy = Bs.wAy - An.wAy;
+    V2 yBy = Bs.wBy - An.wBy;
+    V2 yBx = Bs.wBx - An.wBx;
+    V2 yDy = Bs.wDy - An.wDy;
+    if (!FAST && p.wall_y && (p3 == 0 || p3 == p.ny - 1)) {
+        const bool lo = (p3 == 0), hi = (p3 == p.ny - 1);
+        const V2 dAl = lo ? -Cs.dAx : An.dAx, dAh = hi ? -Cs.dAx : Bs.dAx;
+        const V2 dBxl = lo ? -Cs.dBx : An.dBx, dBxh = hi ? -Cs.dBx : Bs.dBx;
+        const V2 dByl = lo ? -Cs.dBy : An.dBy, dByh = hi ? -Cs.dBy : Bs.dBy;
+        const V2 dDl = lo ? -Cs.dDx : An.dDx, dDh = hi ? -Cs.dDx : Bs.dDx;
+        const V2 wAl = lo ? -Cs.wAy : An.wAy, wAh = hi ? -Cs.wAy : Bs.wAy;
+        const V2 wByl = lo ? -Cs.wBy : An.wBy, wByh = hi ? -Cs.wBy : Bs.wBy;
+        const V2 wBxl = lo ? -Cs.wBx : An.wBx, wBxh = hi ? -Cs.wBx : Bs.wBx;
+        const V2 wDl = lo ? -Cs.wDy : An.wDy, wDh = hi ? -Cs.wDy : Bs.wDy;
+        xAx = fma2(4.f, Cs.dAx, dAl + dAh);
+        xBx = fma2(4.f, Cs.dBx, dBxl + dBxh);
+        xBy = fma2(4.f, Cs.dBy, dByl + dByh);
+        xDx = fma2(4.f, Cs.dDx, dDl + dDh);
+        yAy = wAh - wAl;
+        yBy = wByh - wByl;
+        yBx = wBxh - wBxl;
+        yDy = wDh - wDl;
+    }
+    const V2 phi = V2{*reinterpret_cast<const float2*>(c.aux(p3, 0))};
+    const V2 phin = (!FAST && p.unsteady) ? V2{*reinterpret_cast<const float2*>(c.aux(p3, 1))} : phi;
+    const V2 rho = Cs.rho;
+    const V2 X = p.kappa * rcp2(phi);
+    const V2 kp = p.model_b ? bc(p.kappa - 1.f) : bc(p.kappa) - phi;
+    const V2 kr = kp * rho;
+    const V2 divD = xDx + yDy, difD = xDx - yDy;
+    V2 Ca = fma2(tw, fma2(-p.kappa, xAx + yAy, fma2(2.f * kr, xBx + yBy, fma2(-2.f, X, bc(3.f)) * divD)), bc(0.f));
+    if (!FAST) Ca = fma2(-2.f, (X * rho) * (phin - phi), Ca);
+    const V2 Cb = tw * fma2(-p.kappa, xAx - yAy, fma2((2.f / 3.f) * kr, xBx - yBy, difD));
+    const V2 Cc = (1.f / 36.f) * (kr * (xBy + yBx));
+    const V2 m0 = Cs.m[0], ux = Cs.ux, uy = Cs.uy, Fx = Cs.Fx, Fy = Cs.Fy;
+    const V2 uu = fma2(ux, ux, uy * uy);
+    const V2 uF = fma2(ux, Fx, uy * Fy);
+    const V2 jxe = m0 * ux, jye = m0 * uy;
+    const V2 q = X - bc(2.f);
+    V2 a[9];
+    a[0] = m0;
+    const V2 me1 = m0 * fma2(3.f, uu, fma2(2.f, X, bc(-4.f)));
+    const V2 me2 = m0 * fma2(-3.f, uu, fma2(-3.f, X, bc(4.f)));
+    a[1] = fma2(p.h_e, fma2(6.f, uF, Ca), fma2(p.s_e, me1 - Cs.m[1], Cs.m[1]));
+    a[2] = fma2(-p.h_eps * 6.f, uF, fma2(p.s_eps, me2 - Cs.m[2], Cs.m[2]));
+    a[3] = Cs.m[3] + Fx;
+    a[4] = fma2(-p.h_q, Fx, fma2(p.s_q, fma2(q, jxe, -Cs.m[4]), Cs.m[4]));
+    a[5] = Cs.m[5] + Fy;
+    a[6] = fma2(-p.h_q, Fy, fma2(p.s_q, fma2(q, jye, -Cs.m[6]), Cs.m[6]));
+    const V2 me7 = m0 * fma2(ux, ux, -(uy * uy));
+    const V2 S7 = 2.f * fma2(ux, Fx, -(uy * Fy));
+    a[7] = fma2(p.h_nu, S7 + Cb, fma2(p.s_nu, me7 - Cs.m[7], Cs.m[7]));
+    const V2 S8 = fma2(ux, Fy, uy * Fx);
+    a[8] = fma2(p.h_nu, S8 + Cc, fma2(p.s_nu, fma2(jxe, uy, -Cs.m[8]), Cs.m[8]));
+    V2 fo[9];
+    fo[0] = (1.f / 9.f) * (a[0] - a[1] + a[2]);
+    const V2 bax = (1.f / 36.f) * fma2(4.f, a[0], -fma2(2.f, a[2], a[1]));
+    const V2 bdg = (1.f / 36.f) * fma2(4.f, a[0], fma2(2.f, a[1], a[2]));
+    const V2 xa = (1.f / 6.f) * (a[3] - a[4]);
+    const V2 ya = (1.f / 6.f) * (a[5] - a[6]);
+    const V2 pq = 0.25f * a[7];
+    const V2 xd = tw * fma2(2.f, a[3], a[4]);
+    const V2 yd = tw * fma2(2.f, a[5], a[6]);
+    const V2 pd = 0.25f * a[8];
+    const V2 t13 = bax + pq, t24 = bax - pq;
+    fo[1] = t13 + xa;
+    fo[3] = t13 - xa;
+    fo[2] = t24 + ya;
+    fo[4] = t24 - ya;
+    const V2 t57 = bdg + pd, t68 = bdg - pd;
+    const V2 spp = xd + yd, smm = xd - yd;
+    fo[5] = t57 + spp;
+    fo[7] = t57 - spp;
+    fo[6] = t68 - smm;
+    fo[8] = t68 + smm;
+
+    const V2 r0 = fma2(p.rest.rho0, phin, bc(-p.rest.k59));
+    S* row = reinterpret_cast<S*>(p.dst) + (long long)p3 * p.P + kPadCols;
+    const int xa0 = c.xa;
+    const bool va = lane_ok && xa0 < p.nx, vb = lane_ok && xa0 + 1 < p.nx;
+    if (va && vb) {
+        S* cell = row + xa0;
+        IO::st(cell, sizeof(S) == 4 ? fo[0] : p.scale * (fo[0] - r0));
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const V2 ri = bc(i <= 4 ? p.rest.ax : p.rest.dg);
+            IO::st(cell + i * p.plane, sizeof(S) == 4 ? fo[i] : p.scale * (fo[i] - ri));
+        }
+    } else if (va) {
+        S* cell = row + xa0;
+        cell[0] = IO::enc1(fo[0].v.x, r0.v.x, p.scale);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) cell[i * p.plane] = IO::enc1(fo[i].v.x, i <= 4 ? p.rest.ax : p.rest.dg, p.scale);
+    }
+    for (int k = 0; k < 2; ++k) {
+        const int x = xa0 + k;
+        if (!lane_ok || x >= p.nx || !(x < kGhost || x >= p.nx - kGhost)) continue;
+        int g = x >= p.nx - kGhost ? x - p.nx : x + p.nx;
+        while (g >= -kGhost && g < p.nx + kGhost) {
+            S* gc = row + g;
+            gc[0] = IO::enc1(k ? fo[0].v.y : fo[0].v.x, k ? r0.v.y : r0.v.x, p.scale);
+#pragma unroll
+            for (int i = 1; i < 9; ++i)
+                gc[i * p.plane] = IO::enc1(k ? fo[i].v.y : fo[i].v.x, i <= 4 ? p.rest.ax : p.rest.dg, p.scale);
+            if (g < 0) { g -= p.nx; if (g < -kGhost) { g = x + p.nx; if (g >= p.nx + kGhost) break; } }
+            else { g += p.nx; if (g >= p.nx + kGhost) break; }
+        }
+    }
+}
+
+template <typename S, int MINB>
+__global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_constant__ StepParams<float> p) {
+    using L = WarpLayout<S>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x;
+    constexpr int A = L::A;
+    const int x0 = blockIdx.x * p.W;
+    const int y0 = blockIdx.y * p.H;
+    const int y1 = min(y0 + p.H, p.ny);
+
+    WarpCtx<S> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
+    c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
+    c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
+    c.xa = x0 - 2 + 2 * lane;
+    c.sa = kPadCols + c.xa - c.wsp;
+    c.rlo = y0 - 3;
+    c.rhi = y1 + 2;
+    if (p.wall_y) { c.rlo = max(c.rlo, 0); c.rhi = min(c.rhi, p.ny - 1); }
+    c.waited = c.rlo - 1;
+    c.issued = c.rlo - 1;
+
+    if (lane == 0) {
+        for (int k = 0; k < kWarpSlots; ++k) mbar_init(reinterpret_cast<uint64_t*>(smem) + k, 1);
+        fence_mbar_init();
+        for (int r = c.rlo; r <= min(y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
+    }
+    __syncwarp();
+
+    // rows whose three phases need no wall, validity or field handling
+    const bool fast_strip = !p.unsteady && !p.has_fb;
+    const int fast_lo = p.wall_y ? max(y0, 1) : y0;                 // lowest phase-3 row
+    const int fast_hi = p.wall_y ? min(y1 + 1, p.ny - 2) : y1 + 1;  // highest phase-1 row
+
+    PRow s0, s1, s2;
+    auto iter = [&](PRow& An, PRow& Bs, PRow& Cs, const int p1) -> bool {
+        const int p2 = p1 - 1, p3 = p1 - 2;
+        // the slot of row p1-3 is no longer read: refill it with row p1-3+kWarpSlots
+        __syncwarp();
+        if (lane == 0 && p1 + kWarpSlots - 3 <= c.rhi && p1 + kWarpSlots - 3 >= c.rlo) {
+            fence_proxy_async();
+            c.issue(p1 + kWarpSlots - 3);
+        }
+        c.wait_upto(p1 + 1);
+        if (__any_sync(0xffffffffu, c.aborted)) return false;
+        const bool lane_ok = lane >= 1 && lane < 31;
+        if (fast_strip && p3 >= fast_lo && p1 <= fast_hi) {
+            // interior row of a steady, field-free strip: one branch-free block, so
+            // the collision of row p3 overlaps the pulls and shuffles of rows p1, p2
+            warp_phase1<S, true>(c, An, p1);
+            const float l = left_of(An.rho), r = right_of(An.rho);
+            An.dr = rpair(An.rho, r) - lpair(An.rho, l);
+            An.wr = fma2(4.f, An.rho, rpair(An.rho, r) + lpair(An.rho, l));
+            warp_phase2<S, true>(c, An, Bs, Cs, p2);
+            warp_phase3<S, true>(c, An, Bs, Cs, p3, lane_ok);
+            return true;
+        }
+        const bool ph1 = (p1 <= y1 + 1) && c.row_valid(p1);
+        if (ph1) {
+            warp_phase1<S, false>(c, An, p1);
+            const float l = left_of(An.rho), r = right_of(An.rho);
+            An.dr = rpair(An.rho, r) - lpair(An.rho, l);
+            An.wr = fma2(4.f, An.rho, rpair(An.rho, r) + lpair(An.rho, l));
+        }
+        const bool ph2 = (p2 >= y0 - 1) && (p2 <= y1) && c.row_valid(p2);
+        if (ph2) warp_phase2<S, false>(c, An, Bs, Cs, p2);
+        const bool ph3 = (p3 >= y0) && (p3 < y1);
+        if (ph3) warp_phase3<S, false>(c, An, Bs, Cs, p3, lane_ok);
+        return true;
+    };
+
+    const int n_it = (y1 + 1) - (y0 - 2) + 1;
+    bool ok = true;
+    for (int it = 0; it < n_it && ok; it += 3) {
+        const int p1 = y0 - 2 + it;
+        ok = iter(s0, s2, s1, p1);
+        if (ok && it + 1 < n_it) ok = iter(s1, s0, s2, p1 + 1);
+        if (ok && it + 2 < n_it) ok = iter(s2, s1, s0, p1 + 2);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        // every issued row is waited for before the CTA exits (bounded)
+        for (int r = c.waited + 1; r <= c.issued; ++r) mbar_wait_bounded(c.bar(r), c.parity(r), kWaitTries);
+    }
+}
+
+}  // namespace lbmv

@@ -64,7 +64,8 @@ class Lattice:
     def __init__(self, nx: int, ny: int, tau: float = 0.8, *, s_e: float = 0.0, s_eps: float = 1.2,
                  s_q: float = 1.4, s_c: float = 1.0, kappa: float = 0.5, rho0: float = 1.0,
                  bc_y: str = "periodic", storage: str = "fp32", model_b: bool = False,
-                 scale_log2: int | None = None, strip_rows: int = 0, eager: bool = False, stream=None):
+                 scale_log2: int | None = None, strip_rows: int = 0, eager: bool = False, kernel: int = 0,
+                 stream=None):
         L = capi.load()
         p = capi.default_params()
         p.nx, p.ny, p.tau_nu = int(nx), int(ny), float(tau)
@@ -76,6 +77,7 @@ class Lattice:
             p.storage_scale_log2 = int(scale_log2)
         p.strip_rows = int(strip_rows)
         p.eager = int(bool(eager))
+        p.kernel = int(kernel)
         self.nx, self.ny, self.storage = int(nx), int(ny), storage
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()

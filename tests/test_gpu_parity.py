@@ -44,20 +44,22 @@ def _oracle_params(O, nx, ny, tau, wall_y, kappa=0.5, s_eps=1.2, s_q=1.4, model_
 
 
 def _gpu_lattice(P, nx, ny, tau, wall_y, storage, case, model_b=False, strip_rows=0, s_eps=1.2, s_q=1.4,
-                 s_e=0.0):
+                 s_e=0.0, kernel=0):
     lat = P.Lattice(nx, ny, tau, s_e=s_e, s_eps=s_eps, s_q=s_q, bc_y="bounceback" if wall_y else "periodic",
-                    storage=storage, model_b=model_b, strip_rows=strip_rows)
+                    storage=storage, model_b=model_b, strip_rows=strip_rows, kernel=kernel)
     lat.set_void_fraction(case["phi"], case["phin"])
     lat.set_body_force(case["g"][0], case["g"][1], case["fb"])
     lat.init_fields(case["rho"], case["ux"], case["uy"])
     return lat
 
 
-def _run_both(P, O, nx, ny, case, steps, storage="fp64", tau=0.8, wall_y=False, model_b=False, strip_rows=0):
+def _run_both(P, O, nx, ny, case, steps, storage="fp64", tau=0.8, wall_y=False, model_b=False, strip_rows=0,
+              kernel=0):
     """Run the library and the oracle from the same initial fields; returns the
     device's initial and final populations, the oracle's initial and final
     populations, and the case as it stands after the steps."""
-    lat = _gpu_lattice(P, nx, ny, tau, wall_y, storage, case, model_b=model_b, strip_rows=strip_rows)
+    lat = _gpu_lattice(P, nx, ny, tau, wall_y, storage, case, model_b=model_b, strip_rows=strip_rows,
+                       kernel=kernel)
     prm = _oracle_params(O, nx, ny, tau, wall_y, model_b=int(model_b))
     fb = total_force(case)
     f = O.init(prm, case["rho"], case["ux"], case["uy"], case["phi"], fb)
@@ -103,17 +105,32 @@ def test_fp64_matches_oracle(P, O, nx, ny, wall_y, unsteady, field, g, steps):
     assert err <= 1e-12, err
 
 
+@pytest.mark.parametrize("kernel", [2, 3, 5])
+@pytest.mark.parametrize("nx,ny,wall_y,unsteady,field,g", CASES)
+def test_fp32_two_column_kernels_match_oracle(P, O, nx, ny, wall_y, unsteady, field, g, kernel):
+    """The two-column kernels on every lattice shape of the FP64 cases (ragged tails,
+    1-column and 3-column lattices, walls, moving phi, force fields)."""
+    steps = 4
+    case = random_case(nx, ny, seed=nx * 100 + ny, wall_y=wall_y, unsteady=unsteady, field=field, g=g)
+    _, _, fg, fo, case = _run_both(P, O, nx, ny, case, steps, "fp32", wall_y=wall_y, kernel=kernel)
+    tol = steps * 32 * EPS32 * np.abs(fo).max()
+    assert np.abs(fg - fo).max() <= tol
+
+
 def test_fp64_model_b_matches_oracle(P, O):
     case = random_case(70, 33, seed=7, wall_y=True, unsteady=True, field=True, g=(1e-5, 0))
     _, _, fg, fo, case = _run_both(P, O, 70, 33, case, 4, "fp64", wall_y=True, model_b=True)
     assert np.abs(fg - fo).max() / _scale(fo, case["phi"]) <= 1e-12
 
 
+@pytest.mark.parametrize("kernel", [1, 2, 4, 5])
 @pytest.mark.parametrize("storage,per_step", [("fp32", None), ("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
-def test_reduced_precision_matches_oracle(P, O, storage, per_step):
+def test_reduced_precision_matches_oracle(P, O, storage, per_step, kernel):
+    """Both step kernels (one column per thread; two columns per thread on packed
+    FP32 pairs) against the oracle."""
     nx, ny, steps = 130, 21, 5
     case = random_case(nx, ny, seed=11, wall_y=True, unsteady=True, field=True, g=(1e-5, 0.0))
-    _, _, fg, fo, case = _run_both(P, O, nx, ny, case, steps, storage, wall_y=True)
+    _, _, fg, fo, case = _run_both(P, O, nx, ny, case, steps, storage, wall_y=True, kernel=kernel)
     dev = _scale(fo, case["phi"])
     tol = steps * 32 * EPS32 * np.abs(fo).max()
     if per_step is not None:
@@ -122,15 +139,16 @@ def test_reduced_precision_matches_oracle(P, O, storage, per_step):
     assert err <= tol, (err, tol, err / dev)
 
 
-@pytest.mark.parametrize("storage,eps", [("fp64", 2.0 ** -53), ("fp32", 2.0 ** -24)])
-def test_strip_decomposition_invariance(P, storage, eps):
+@pytest.mark.parametrize("storage,eps,kernel", [("fp64", 2.0 ** -53, 1), ("fp32", 2.0 ** -24, 1),
+                                                ("fp32", 2.0 ** -24, 2), ("fp32", 2.0 ** -24, 5)])
+def test_strip_decomposition_invariance(P, storage, eps, kernel):
     """The strip height only changes which CTA (and which of the three unrolled
     copies of the row body) computes a row; results agree to rounding."""
     nx, ny = 300, 77
     case = random_case(nx, ny, seed=3, wall_y=True, unsteady=False, field=True, g=(1e-5, 0))
     outs = []
     for rows in (0, 5, 13, 77):
-        lat = _gpu_lattice(P, nx, ny, 0.7, True, storage, case, strip_rows=rows)
+        lat = _gpu_lattice(P, nx, ny, 0.7, True, storage, case, strip_rows=rows, kernel=kernel)
         lat.step(9)
         outs.append(lat.get_populations().cpu().numpy())
         lat.close()
