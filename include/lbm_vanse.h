@@ -166,6 +166,72 @@ lbm_status lbm_vanse_velocity_error(lbm_vanse_t h, const double* ux_ref, const d
  * fails. It does not check the sums for NaN (the caller reads them). */
 lbm_status lbm_vanse_reduce_noalloc(lbm_vanse_t h, double* out_dev);
 
+/* ======================================================================== batches
+ * Many independent n x n periodic lattices advanced together, each with its own
+ * relaxation time and its own spatiotemporal manufactured solution (Sec. 3.4):
+ * phi = phi0 + A sin(2 pi x/n) sin(2 pi y/n) cos(2 pi t/T), phi u = grad psi +
+ * rot Psi with lap psi = -d_t phi and Psi = (U0 n / 2 pi) sin sin, rho = rho0, and the
+ * body force of Eq. (25) without its pressure term. The void fraction and the force
+ * are evaluated inside the step kernel, so a step reads and writes only populations.
+ * One step of the whole batch is one persistent kernel that hands out work units
+ * (60 columns x H rows of one lattice, largest lattices first) from a device
+ * counter, followed by a one-thread kernel that advances the device-side clock; runs
+ * of steps are replayed as a captured CUDA graph. */
+typedef struct {
+    int n;                /* lattice size (n x n), >= 1 */
+    double tau_nu;        /* relaxation time of the shear moments (> 1/2) */
+    double amplitude;     /* A */
+    double period;        /* T in steps (> 0) */
+    double u0;            /* U0 */
+} lbm_vanse_batch_lattice;
+
+typedef struct {
+    int storage;          /* LBM_FP32, LBM_FP16 or LBM_BF16 */
+    double s_e;           /* energy rate; <= 0 derives it per lattice from nu_e = nu/3 (App. A) */
+    double s_eps, s_q;    /* rates shared by all lattices */
+    double kappa, rho0, phi0;
+    int strip_rows;       /* rows per work unit; 0 = a default (see lbm_vanse_batch_autotune) */
+    int eager;            /* 1 = launch every step on its own (no CUDA graph) */
+} lbm_vanse_batch_params;
+
+typedef struct lbm_vanse_batch* lbm_vanse_batch_t;
+
+/* Defaults: FP32, s_e derived, s_eps = s_q = 1.2, kappa = 0.5, rho0 = 1, phi0 = 0.7. */
+void lbm_vanse_batch_default_params(lbm_vanse_batch_params* p);
+
+/* Allocate count lattices (two population buffers each) on the current device.
+ * Errors: LBM_ERR_ARG (count < 1, a bad lattice or parameter), LBM_ERR_OOM. */
+lbm_status lbm_vanse_batch_create(const lbm_vanse_batch_lattice* lattices, int count,
+                                  const lbm_vanse_batch_params* p, void* cuda_stream,
+                                  lbm_vanse_batch_t* out);
+
+/* t = 0 and every lattice at f = f^eq(rho0, u(0), phi(0)) - F_i/2 (Eq. 14, 6). */
+lbm_status lbm_vanse_batch_init(lbm_vanse_batch_t b);
+
+/* Advance every lattice nsteps steps (one persistent kernel per step). */
+lbm_status lbm_vanse_batch_step(lbm_vanse_batch_t b, int nsteps);
+
+/* The same steps with one kernel launch per lattice per step (the form the
+ * persistent kernel replaces; for comparison). */
+lbm_status lbm_vanse_batch_step_each(lbm_vanse_batch_t b, int nsteps);
+
+/* Time trial_steps steps for a set of work-unit heights, keep the fastest, write it
+ * to *rows_out (may be NULL) and re-initialise the batch (t = 0). */
+lbm_status lbm_vanse_batch_autotune(lbm_vanse_batch_t b, int trial_steps, int* rows_out);
+
+/* Eq. (26) sums for lattice index at the current step against its manufactured
+ * velocity: *num = sum |u - u_ref|^2, *den = sum |u_ref|^2 (FP64, to host). */
+lbm_status lbm_vanse_batch_velocity_error(lbm_vanse_batch_t b, int index, double* num, double* den);
+
+/* Post-streaming populations of lattice index as [9][n][n] doubles. */
+lbm_status lbm_vanse_batch_get_populations(lbm_vanse_batch_t b, int index, double* f, int on_device);
+
+/* Total cells of the batch; steps taken since init. */
+long long lbm_vanse_batch_cells(lbm_vanse_batch_t b);
+long long lbm_vanse_batch_step_count(lbm_vanse_batch_t b);
+const char* lbm_vanse_batch_last_error(lbm_vanse_batch_t b);
+void lbm_vanse_batch_destroy(lbm_vanse_batch_t b);
+
 /* Synchronise the stream and report any deferred kernel error (LBM_ERR_TIMEOUT
  * if a bounded wait gave up, LBM_ERR_CUDA for a launch/runtime error). */
 lbm_status lbm_vanse_sync(lbm_vanse_t h);

@@ -2,10 +2,11 @@
 consistent MRT lattice Boltzmann method for the volume-averaged Navier-Stokes
 equations (MRTLB-VANSE, arXiv:2409.02964).
 
-``capi`` binds the C ABI of ``include/lbm_vanse.h``; ``Lattice`` is a thin handle
-over it. The computation runs only in the CUDA library (``liblbm_vanse.so``).
+``capi`` binds the C ABI of ``include/lbm_vanse.h``; ``Lattice`` (one lattice) and
+``Batch`` (many independent lattices) are thin handles over it. The computation runs only in the CUDA library (``liblbm_vanse.so``).
 """
 from . import build, capi  # noqa: F401
+from .batch import Batch, BatchLattice  # noqa: F401
 from .lattice import Lattice, LbmError  # noqa: F401
 
-__all__ = ["Lattice", "LbmError", "build", "capi"]
+__all__ = ["Batch", "BatchLattice", "Lattice", "LbmError", "build", "capi"]

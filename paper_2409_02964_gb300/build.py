@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_vanse.so")
 SOURCES = ["lbm_vanse.cu"]
-HEADERS = ["vanse_common.cuh", "vanse_step.cuh", "vanse_aux.cuh"]
+HEADERS = ["vanse_common.cuh", "vanse_step.cuh", "vanse_aux.cuh", "vanse_pair.cuh", "vanse_warp.cuh",
+           "vanse_batch.cuh", "mms_force.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

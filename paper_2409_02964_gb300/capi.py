@@ -26,6 +26,10 @@ EXPORTS = [
     "lbm_vanse_velocity_error", "lbm_vanse_reduce_noalloc", "lbm_vanse_sync", "lbm_vanse_step_count",
     "lbm_vanse_bytes_per_cell", "lbm_vanse_launch_shape", "lbm_vanse_last_error",
     "lbm_vanse_destroy",
+    "lbm_vanse_batch_default_params", "lbm_vanse_batch_create", "lbm_vanse_batch_init",
+    "lbm_vanse_batch_step", "lbm_vanse_batch_step_each", "lbm_vanse_batch_autotune",
+    "lbm_vanse_batch_velocity_error", "lbm_vanse_batch_get_populations", "lbm_vanse_batch_cells",
+    "lbm_vanse_batch_step_count", "lbm_vanse_batch_last_error", "lbm_vanse_batch_destroy",
 ]
 
 
@@ -40,6 +44,22 @@ class lbm_vanse_params(ctypes.Structure):
         ("storage", ctypes.c_int), ("model_b", ctypes.c_int),
         ("storage_scale_log2", ctypes.c_int), ("strip_rows", ctypes.c_int),
         ("eager", ctypes.c_int), ("kernel", ctypes.c_int),
+    ]
+
+
+class lbm_vanse_batch_lattice(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int), ("tau_nu", ctypes.c_double), ("amplitude", ctypes.c_double),
+        ("period", ctypes.c_double), ("u0", ctypes.c_double),
+    ]
+
+
+class lbm_vanse_batch_params(ctypes.Structure):
+    _fields_ = [
+        ("storage", ctypes.c_int),
+        ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("rho0", ctypes.c_double), ("phi0", ctypes.c_double),
+        ("strip_rows", ctypes.c_int), ("eager", ctypes.c_int),
     ]
 
 
@@ -81,6 +101,19 @@ def load(path: str | None = None):
         "lbm_vanse_launch_shape": (i, [vp, ip, ip, ip, ip, ip, ip]),
         "lbm_vanse_last_error": (ctypes.c_char_p, [vp]),
         "lbm_vanse_destroy": (None, [vp]),
+        "lbm_vanse_batch_default_params": (None, [ctypes.POINTER(lbm_vanse_batch_params)]),
+        "lbm_vanse_batch_create": (i, [ctypes.POINTER(lbm_vanse_batch_lattice), i,
+                                       ctypes.POINTER(lbm_vanse_batch_params), vp, ctypes.POINTER(vp)]),
+        "lbm_vanse_batch_init": (i, [vp]),
+        "lbm_vanse_batch_step": (i, [vp, i]),
+        "lbm_vanse_batch_step_each": (i, [vp, i]),
+        "lbm_vanse_batch_autotune": (i, [vp, i, ip]),
+        "lbm_vanse_batch_velocity_error": (i, [vp, i, dp, dp]),
+        "lbm_vanse_batch_get_populations": (i, [vp, i, vp, i]),
+        "lbm_vanse_batch_cells": (ctypes.c_longlong, [vp]),
+        "lbm_vanse_batch_step_count": (ctypes.c_longlong, [vp]),
+        "lbm_vanse_batch_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_vanse_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -93,4 +126,10 @@ def load(path: str | None = None):
 def default_params() -> lbm_vanse_params:
     p = lbm_vanse_params()
     load().lbm_vanse_default_params(ctypes.byref(p))
+    return p
+
+
+def batch_default_params() -> lbm_vanse_batch_params:
+    p = lbm_vanse_batch_params()
+    load().lbm_vanse_batch_default_params(ctypes.byref(p))
     return p

@@ -12,11 +12,14 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <string>
+#include <vector>
 #include <type_traits>
 
 #include "lbm_vanse.h"
 #include "vanse_aux.cuh"
+#include "vanse_batch.cuh"
 #include "vanse_pair.cuh"
 #include "vanse_step.cuh"
 #include "vanse_warp.cuh"
@@ -818,4 +821,414 @@ extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;
+}
+
+// ============================================================================ batches
+
+struct lbm_vanse_batch {
+    lbm_vanse_batch_params prm;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sbytes = 4;
+    float scale = 1.f, inv_scale = 1.f;
+    std::vector<lbm_vanse_batch_lattice> lat;
+    std::vector<BatchLattice> desc;      // host copy of the device descriptors
+    std::vector<size_t> offsets;         // byte offset of each lattice's two buffers
+    void* pool = nullptr;                // every population buffer
+    BatchLattice* d_desc = nullptr;
+    int* d_units = nullptr;              // lattice of each unit
+    int* d_clock = nullptr;              // [0] = t, [1] = unit counter, [2] = error flag
+    double* scratch = nullptr;           // dense rho of the largest lattice
+    double* partial = nullptr;
+    double* red_out = nullptr;
+    int nunits = 0, H = 0, grid = 0;
+    long long cells = 0, steps = 0;
+    bool initialised = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::string msg;
+};
+
+namespace {
+
+constexpr int kBatchMinBlocks = LBMV_WARP_MINB;
+constexpr int kBatchGraphSteps = 16;
+
+lbm_status bfail(lbm_vanse_batch* b, lbm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (b) b->msg = buf; else g_create_error = buf;
+    return st;
+}
+
+#define BCK(b, call)                                                                                      \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s", #call, \
+                         cudaGetErrorString(e_));                                                         \
+    } while (0)
+
+#define BDISPATCH(b, fn, ...)                                                    \
+    ([&]() -> lbm_status {                                                       \
+        switch ((b)->prm.storage) {                                              \
+            case LBM_FP16: return fn<__half>((b), ##__VA_ARGS__);                \
+            case LBM_BF16: return fn<__nv_bfloat16>((b), ##__VA_ARGS__);         \
+            default: return fn<float>((b), ##__VA_ARGS__);                       \
+        }                                                                        \
+    }())
+
+// Work units of height H for every lattice, largest lattices first.
+lbm_status batch_decompose(lbm_vanse_batch* b, int H) {
+    const int n = (int)b->lat.size();
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->lat[a].n > b->lat[c].n; });
+    std::vector<int> units;
+    for (int idx : order) {
+        BatchLattice& L = b->desc[idx];
+        L.H = std::min(H, L.ny);
+        L.strips = (L.ny + L.H - 1) / L.H;
+        L.unit0 = (int)units.size();
+        for (int u = 0; u < L.tiles_x * L.strips; ++u) units.push_back(idx);
+    }
+    b->H = H;
+    b->nunits = (int)units.size();
+    if (b->d_units) cudaFree(b->d_units);
+    b->d_units = nullptr;
+    BCK(b, cudaMalloc((void**)&b->d_units, units.size() * sizeof(int)));
+    BCK(b, cudaMemcpyAsync(b->d_units, units.data(), units.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), b->desc.size() * sizeof(BatchLattice), cudaMemcpyHostToDevice,
+                           b->stream));
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    return LBM_OK;
+}
+
+BatchParams batch_params(const lbm_vanse_batch* b) {
+    BatchParams bp;
+    bp.lat = b->d_desc;
+    bp.unit_lattice = b->d_units;
+    bp.nunits = b->nunits;
+    bp.counter = b->d_clock + 1;
+    bp.clock = b->d_clock;
+    bp.scale = b->scale;
+    bp.inv_scale = b->inv_scale;
+    bp.err = b->d_clock + 2;
+    return bp;
+}
+
+template <typename S>
+lbm_status batch_configure(lbm_vanse_batch* b) {
+    const size_t smem = WarpLayout<S>::bytes(0);
+    auto k1 = vanse_batch_kernel<S, kBatchMinBlocks>;
+    auto k2 = vanse_batch_one_kernel<S, kBatchMinBlocks>;
+    BCK(b, cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BCK(b, cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BCK(b, cudaFuncSetAttribute(k1, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+    BCK(b, cudaFuncSetAttribute(k2, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+    int per_sm = 0, nsm = 0;
+    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, 32, smem));
+    BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
+    b->grid = std::max(1, per_sm * nsm);
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status batch_enqueue_step(lbm_vanse_batch* b, cudaStream_t stream) {
+    const size_t smem = WarpLayout<S>::bytes(0);
+    vanse_batch_kernel<S, kBatchMinBlocks><<<b->grid, 32, smem, stream>>>(batch_params(b));
+    BCK(b, cudaGetLastError());
+    batch_tick_kernel<<<1, 1, 0, stream>>>(b->d_clock, b->d_clock + 1);
+    BCK(b, cudaGetLastError());
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status batch_step_graph(lbm_vanse_batch* b) {
+    if (!b->gexec) {
+        if (!b->cap_stream) BCK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+        BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        lbm_status st = LBM_OK;
+        for (int k = 0; k < kBatchGraphSteps && st == LBM_OK; ++k) st = batch_enqueue_step<S>(b, b->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (st != LBM_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { b->gexec = nullptr; return bfail(b, LBM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e)); }
+    }
+    BCK(b, cudaGraphLaunch(b->gexec, b->stream));
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status batch_run(lbm_vanse_batch* b, int nsteps) {
+    int left = nsteps;
+    while (!b->prm.eager && left >= kBatchGraphSteps) {
+        lbm_status st = batch_step_graph<S>(b);
+        if (st != LBM_OK) return st;
+        left -= kBatchGraphSteps;
+        b->steps += kBatchGraphSteps;
+    }
+    while (left-- > 0) {
+        lbm_status st = batch_enqueue_step<S>(b, b->stream);
+        if (st != LBM_OK) return st;
+        b->steps++;
+    }
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status batch_run_each(lbm_vanse_batch* b, int nsteps) {
+    const size_t smem = WarpLayout<S>::bytes(0);
+    const BatchParams bp = batch_params(b);
+    for (int s = 0; s < nsteps; ++s) {
+        for (size_t i = 0; i < b->desc.size(); ++i) {
+            const BatchLattice& L = b->desc[i];
+            vanse_batch_one_kernel<S, kBatchMinBlocks><<<L.tiles_x * L.strips, 32, smem, b->stream>>>(bp, (int)i);
+            BCK(b, cudaGetLastError());
+        }
+        batch_tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock, b->d_clock + 1);
+        BCK(b, cudaGetLastError());
+        b->steps++;
+    }
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status batch_do_init(lbm_vanse_batch* b) {
+    BCK(b, cudaMemsetAsync(b->d_clock, 0, 3 * sizeof(int), b->stream));
+    for (size_t i = 0; i < b->desc.size(); ++i) {
+        const long long n = (long long)b->desc[i].nx * b->desc[i].ny;
+        batch_init_kernel<S><<<aux_blocks(n), kAuxThreads, 0, b->stream>>>(b->d_desc, (int)i, b->scale, b->inv_scale);
+        BCK(b, cudaGetLastError());
+    }
+    b->steps = 0;
+    b->initialised = true;
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status batch_do_error(lbm_vanse_batch* b, int index, double* out3) {
+    const long long n = (long long)b->desc[index].nx * b->desc[index].ny;
+    batch_rho_kernel<S><<<aux_blocks(n), kAuxThreads, 0, b->stream>>>(b->d_desc, index, b->d_clock, b->scratch,
+                                                                       b->scale, b->inv_scale);
+    BCK(b, cudaGetLastError());
+    batch_err_kernel<S><<<kReduceBlocks, kAuxThreads, 0, b->stream>>>(b->d_desc, index, b->d_clock, b->scratch,
+                                                                      b->partial, b->scale, b->inv_scale);
+    BCK(b, cudaGetLastError());
+    finish_reduce_kernel<<<1, 1024, 0, b->stream>>>(b->partial, kReduceBlocks, b->red_out);
+    BCK(b, cudaGetLastError());
+    BCK(b, cudaMemcpyAsync(out3, b->red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status batch_do_get(lbm_vanse_batch* b, int index, double* dev_out) {
+    const long long n = (long long)b->desc[index].nx * b->desc[index].ny;
+    batch_get_kernel<S><<<aux_blocks(n), kAuxThreads, 0, b->stream>>>(b->d_desc, index, b->d_clock, dev_out, b->scale,
+                                                                       b->inv_scale);
+    BCK(b, cudaGetLastError());
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" void lbm_vanse_batch_default_params(lbm_vanse_batch_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->storage = LBM_FP32;
+    p->s_e = 0.0;
+    p->s_eps = 1.2;
+    p->s_q = 1.2;
+    p->kappa = 0.5;
+    p->rho0 = 1.0;
+    p->phi0 = 0.7;
+    p->strip_rows = 0;
+    p->eager = 0;
+}
+
+extern "C" lbm_status lbm_vanse_batch_create(const lbm_vanse_batch_lattice* lattices, int count,
+                                             const lbm_vanse_batch_params* p, void* cuda_stream,
+                                             lbm_vanse_batch_t* out) {
+    if (!out) return bfail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!lattices || count < 1) return bfail(nullptr, LBM_ERR_ARG, "need at least one lattice");
+    if (!p) return bfail(nullptr, LBM_ERR_ARG, "params is NULL");
+    if (p->storage != LBM_FP32 && p->storage != LBM_FP16 && p->storage != LBM_BF16)
+        return bfail(nullptr, LBM_ERR_ARG, "batches store FP32, FP16 or BF16 populations");
+    if (!rate_ok(p->s_eps) || !rate_ok(p->s_q) || (p->s_e > 0 && !rate_ok(p->s_e)))
+        return bfail(nullptr, LBM_ERR_ARG, "rates must lie in (0, 2)");
+    if (!(p->kappa >= 0 && p->kappa <= 1) || !(p->rho0 > 0) || !(p->phi0 > 0 && p->phi0 <= 1))
+        return bfail(nullptr, LBM_ERR_ARG, "bad kappa, rho0 or phi0");
+    if (p->strip_rows < 0) return bfail(nullptr, LBM_ERR_ARG, "strip_rows must be >= 0");
+    for (int i = 0; i < count; ++i) {
+        const lbm_vanse_batch_lattice& q = lattices[i];
+        if (q.n < 1 || q.n > 65536) return bfail(nullptr, LBM_ERR_ARG, "lattice %d: n = %d out of range", i, q.n);
+        if (!(q.tau_nu > 0.5)) return bfail(nullptr, LBM_ERR_ARG, "lattice %d: tau_nu must exceed 1/2", i);
+        if (!(q.period > 0)) return bfail(nullptr, LBM_ERR_ARG, "lattice %d: period must be positive", i);
+        if (!(std::fabs(q.amplitude) < p->phi0)) return bfail(nullptr, LBM_ERR_ARG, "lattice %d: |A| must be < phi0", i);
+    }
+    lbm_vanse_batch* b = new lbm_vanse_batch();
+    b->prm = *p;
+    b->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&b->device);
+    b->sbytes = storage_bytes(p->storage);
+    if (p->storage == LBM_FP16) { b->scale = 65536.f; b->inv_scale = 1.f / 65536.f; }
+    b->lat.assign(lattices, lattices + count);
+    b->desc.resize(count);
+    size_t total = 0;
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < count; ++i) {
+        const lbm_vanse_batch_lattice& q = lattices[i];
+        BatchLattice& L = b->desc[i];
+        std::memset(&L, 0, sizeof(L));
+        L.nx = L.ny = q.n;
+        L.tiles_x = (q.n + 59) / 60;
+        L.P = ((kPadCols + L.tiles_x * 60 + kPadCols) + 31) / 32 * 32;
+        L.plane = (long long)L.ny * L.P;
+        const double nu = (q.tau_nu - 0.5) / 3.0, s_nu = 1.0 / q.tau_nu;
+        const double s_e = p->s_e > 0 ? p->s_e : 1.0 / (nu + 0.5);  // nu_e = nu/3
+        L.s_e = (float)s_e; L.s_eps = (float)p->s_eps; L.s_q = (float)p->s_q; L.s_nu = (float)s_nu;
+        L.h_e = (float)(1 - 0.5 * s_e); L.h_eps = (float)(1 - 0.5 * p->s_eps);
+        L.h_q = (float)(1 - 0.5 * p->s_q); L.h_nu = (float)(1 - 0.5 * s_nu);
+        L.kappa = (float)p->kappa; L.rho0 = (float)p->rho0;
+        L.k = (float)(2 * pi / q.n); L.w = (float)(2 * pi / q.period);
+        L.A = (float)q.amplitude; L.U0 = (float)q.u0; L.phi0 = (float)p->phi0; L.nu = (float)nu;
+        const size_t bytes = ((size_t)9 * L.plane * b->sbytes + 255) / 256 * 256;
+        b->offsets.push_back(total);
+        total += 2 * bytes;
+        b->cells += (long long)q.n * q.n;
+    }
+    lbm_status st = LBM_OK;
+    cudaError_t e = cudaMalloc(&b->pool, total);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->pool, 0, total, b->stream);
+    if (e != cudaSuccess) { st = bfail(nullptr, LBM_ERR_OOM, "batch populations (%zu bytes): %s", total, cudaGetErrorString(e)); }
+    int nmax = 0;
+    for (auto& q : b->lat) nmax = std::max(nmax, q.n);
+    if (st == LBM_OK) {
+        for (int i = 0; i < count; ++i) {
+            const size_t bytes = ((size_t)9 * b->desc[i].plane * b->sbytes + 255) / 256 * 256;
+            b->desc[i].buf[0] = (char*)b->pool + b->offsets[i];
+            b->desc[i].buf[1] = (char*)b->pool + b->offsets[i] + bytes;
+        }
+        e = cudaMalloc((void**)&b->d_desc, count * sizeof(BatchLattice));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_clock, 4 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_clock, 0, 4 * sizeof(int), b->stream);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&b->scratch, (size_t)nmax * nmax * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&b->partial, kReduceBlocks * 3 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&b->red_out, 4 * sizeof(double));
+        if (e != cudaSuccess) st = bfail(nullptr, LBM_ERR_OOM, "batch buffers: %s", cudaGetErrorString(e));
+    }
+    if (st == LBM_OK) st = BDISPATCH(b, batch_configure);
+    if (st == LBM_OK) st = batch_decompose(b, p->strip_rows > 0 ? p->strip_rows : 48);
+    if (st != LBM_OK) {
+        if (b->msg.size()) g_create_error = b->msg;
+        lbm_vanse_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_batch_init(lbm_vanse_batch_t b) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    return BDISPATCH(b, batch_do_init);
+}
+
+extern "C" lbm_status lbm_vanse_batch_step(lbm_vanse_batch_t b, int nsteps) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps must be >= 0");
+    if (!b->initialised) return bfail(b, LBM_ERR_STATE, "call lbm_vanse_batch_init first");
+    return BDISPATCH(b, batch_run, nsteps);
+}
+
+extern "C" lbm_status lbm_vanse_batch_step_each(lbm_vanse_batch_t b, int nsteps) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "nsteps must be >= 0");
+    if (!b->initialised) return bfail(b, LBM_ERR_STATE, "call lbm_vanse_batch_init first");
+    return BDISPATCH(b, batch_run_each, nsteps);
+}
+
+extern "C" lbm_status lbm_vanse_batch_autotune(lbm_vanse_batch_t b, int trial_steps, int* rows_out) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (trial_steps < 1) return bfail(b, LBM_ERR_ARG, "trial_steps must be >= 1");
+    static const int candidates[] = {16, 24, 32, 48, 64, 96, 128};
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    int best = b->H;
+    float best_ms = 1e30f;
+    for (int H : candidates) {
+        lbm_status st = batch_decompose(b, H);
+        if (st == LBM_OK) st = lbm_vanse_batch_init(b);
+        if (st == LBM_OK) st = lbm_vanse_batch_step(b, 2);  // warm-up (and graph capture)
+        if (st != LBM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+        BCK(b, cudaEventRecord(e0, b->stream));
+        st = lbm_vanse_batch_step(b, trial_steps);
+        if (st != LBM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+        BCK(b, cudaEventRecord(e1, b->stream));
+        BCK(b, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) { best_ms = ms; best = H; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lbm_status st = batch_decompose(b, best);
+    if (st == LBM_OK) st = lbm_vanse_batch_init(b);
+    if (st == LBM_OK && rows_out) *rows_out = best;
+    return st;
+}
+
+extern "C" lbm_status lbm_vanse_batch_velocity_error(lbm_vanse_batch_t b, int index, double* num, double* den) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (index < 0 || index >= (int)b->desc.size()) return bfail(b, LBM_ERR_ARG, "index %d out of range", index);
+    if (!b->initialised) return bfail(b, LBM_ERR_STATE, "call lbm_vanse_batch_init first");
+    double r[3];
+    lbm_status st = BDISPATCH(b, batch_do_error, index, r);
+    if (st != LBM_OK) return st;
+    if (num) *num = r[0];
+    if (den) *den = r[1];
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_batch_get_populations(lbm_vanse_batch_t b, int index, double* f, int on_device) {
+    if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
+    if (index < 0 || index >= (int)b->desc.size()) return bfail(b, LBM_ERR_ARG, "index %d out of range", index);
+    if (!f) return bfail(b, LBM_ERR_ARG, "f is NULL");
+    if (!b->initialised) return bfail(b, LBM_ERR_STATE, "call lbm_vanse_batch_init first");
+    const long long n9 = 9LL * b->desc[index].nx * b->desc[index].ny;
+    double* d = f;
+    if (!on_device) BCK(b, cudaMallocAsync((void**)&d, n9 * sizeof(double), b->stream));
+    lbm_status st = BDISPATCH(b, batch_do_get, index, d);
+    if (st == LBM_OK && !on_device) {
+        cudaError_t e = cudaMemcpyAsync(f, d, n9 * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) st = bfail(b, LBM_ERR_CUDA, "copy populations: %s", cudaGetErrorString(e));
+    }
+    if (!on_device) cudaFreeAsync(d, b->stream);
+    return st;
+}
+
+extern "C" long long lbm_vanse_batch_cells(lbm_vanse_batch_t b) { return b ? b->cells : -1; }
+extern "C" long long lbm_vanse_batch_step_count(lbm_vanse_batch_t b) { return b ? b->steps : -1; }
+extern "C" const char* lbm_vanse_batch_last_error(lbm_vanse_batch_t b) {
+    return b ? b->msg.c_str() : g_create_error.c_str();
+}
+
+extern "C" void lbm_vanse_batch_destroy(lbm_vanse_batch_t b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    void* ptrs[] = {b->pool, b->d_desc, b->d_units, b->d_clock, b->scratch, b->partial, b->red_out};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete b;
 }

@@ -34,6 +34,11 @@ __device__ __forceinline__ V2 operator-(V2 a) { return V2{__fmul2_rn(make_float2
 __device__ __forceinline__ V2 fma2(V2 a, V2 b, V2 c) { return V2{__ffma2_rn(a.v, b.v, c.v)}; }
 __device__ __forceinline__ V2 fma2(float s, V2 b, V2 c) { return V2{__ffma2_rn(make_float2(s, s), b.v, c.v)}; }
 __device__ __forceinline__ V2 rcp2(V2 a) { return mk(__fdividef(1.0f, a.v.x), __fdividef(1.0f, a.v.y)); }
+__device__ __forceinline__ V2 operator+(V2 a, float s) { return V2{__fadd2_rn(a.v, make_float2(s, s))}; }
+__device__ __forceinline__ V2 operator+(float s, V2 a) { return a + s; }
+__device__ __forceinline__ V2 operator*(V2 a, float s) { return s * a; }
+__device__ __forceinline__ V2 mms_rcp(V2 a) { return rcp2(a); }
+__device__ __forceinline__ float mms_rcp(float a) { return 1.0f / a; }
 
 // storage loads of a pair at an even (aligned) element index, or a pair shifted by one
 template <typename S> struct PairIO;
@@ -81,6 +86,7 @@ struct PairLayout {
 };
 
 struct PRow {
+    float sy, cy;   // sin, cos of k y of this row (analytic sources only)
     V2 m[9];
     V2 rho;
     V2 dr, wr;

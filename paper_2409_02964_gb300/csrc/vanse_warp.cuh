@@ -51,6 +51,7 @@ __device__ __forceinline__ int wslot(int r) { return ((r % kWarpSlots) + kWarpSl
 template <typename S>
 struct WarpCtx {
     using L = WarpLayout<S>;
+    static constexpr bool kUnsteady = false;   // the fast path runs only on steady strips
     const StepParams<float>& p;
     unsigned char* smem;
     int lane, xa, sa;
@@ -59,6 +60,8 @@ struct WarpCtx {
     int rlo, rhi;
     int waited, issued;
     bool aborted;
+    bool fast_strip;
+    int fast_lo, fast_hi;
 
     __device__ __forceinline__ uint64_t* bar(int r) const { return reinterpret_cast<uint64_t*>(smem) + wslot(r); }
     __device__ __forceinline__ const S* pop(int r) const {
@@ -69,6 +72,25 @@ struct WarpCtx {
     }
     __device__ __forceinline__ bool row_valid(int r) const { return !p.wall_y || (r >= 0 && r < p.ny); }
     __device__ __forceinline__ uint32_t parity(int r) const { return (uint32_t)(((r - rlo) / kWarpSlots) & 1); }
+
+    // the per-cell sources of the step for row r (this lane's two columns): phi(t),
+    // phi(t+1) and the field part of F^B, staged with the populations
+    __device__ __forceinline__ void row_setup(int, PRow&) const {}
+    __device__ __forceinline__ V2 phi2(int r, const PRow&) const {
+        return V2{*reinterpret_cast<const float2*>(aux(r, 0))};
+    }
+    template <bool FAST>
+    __device__ __forceinline__ V2 phin2(int r, const PRow& st) const {
+        return (!FAST && p.unsteady) ? V2{*reinterpret_cast<const float2*>(aux(r, 1))} : phi2(r, st);
+    }
+    template <bool FAST>
+    __device__ __forceinline__ void add_field_force(int r, const PRow&, V2& Fx, V2& Fy) const {
+        if (!FAST && p.has_fb) {
+            const int k = p.unsteady ? 2 : 1;
+            Fx = Fx + V2{*reinterpret_cast<const float2*>(aux(r, k))};
+            Fy = Fy + V2{*reinterpret_cast<const float2*>(aux(r, k + 1))};
+        }
+    }
 
     // lane 0: load source row r into its slot
     __device__ __forceinline__ void issue(int r) {
@@ -110,12 +132,13 @@ struct WarpCtx {
 __device__ __forceinline__ float left_of(V2 v) { return __shfl_up_sync(0xffffffffu, v.v.y, 1); }
 __device__ __forceinline__ float right_of(V2 v) { return __shfl_down_sync(0xffffffffu, v.v.x, 1); }
 
-template <typename S, bool FAST>
-__device__ __forceinline__ void warp_phase1(const WarpCtx<S>& c, PRow& st, int r) {
+template <typename S, bool FAST, typename Ctx>
+__device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
     using IO = PairIO<S>;
     constexpr int RW = WarpLayout<S>::WW;
-    const StepParams<float>& p = c.p;
-    const V2 phi = V2{*reinterpret_cast<const float2*>(c.aux(r, 0))};
+    const auto& p = c.p;
+    c.row_setup(r, st);
+    const V2 phi = c.phi2(r, st);
     const float ia = p.inv_scale;
     const V2 rax = bc(p.rest.ax), rdg = bc(p.rest.dg);
     const V2 r0 = fma2(p.rest.rho0, phi, bc(-p.rest.k59));
@@ -161,9 +184,9 @@ __device__ __forceinline__ void warp_phase1(const WarpCtx<S>& c, PRow& st, int r
     st.rho = st.m[0] * rcp2(phi);
 }
 
-template <typename S, bool FAST>
-__device__ __forceinline__ void warp_phase2(const WarpCtx<S>& c, const PRow& An, PRow& Bs, const PRow& Cs, int p2) {
-    const StepParams<float>& p = c.p;
+template <typename S, bool FAST, typename Ctx>
+__device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& Bs, const PRow& Cs, int p2) {
+    const auto& p = c.p;
     constexpr float tw = 1.0f / 12.0f;
     V2 dlo = Cs.dr, wlo = Cs.wr, dhi = An.dr, whi = An.wr;
     if (!FAST && p.wall_y && (p2 == 0 || p2 == p.ny - 1)) {
@@ -172,15 +195,11 @@ __device__ __forceinline__ void warp_phase2(const WarpCtx<S>& c, const PRow& An,
     }
     const V2 gx = tw * fma2(4.f, Bs.dr, dlo + dhi);
     const V2 gy = tw * (whi - wlo);
-    const V2 phi = V2{*reinterpret_cast<const float2*>(c.aux(p2, 0))};
+    const V2 phi = c.phi2(p2, Bs);
     const V2 kp = p.model_b ? bc((p.kappa - 1.f) * (1.f / 3.f)) : (1.f / 3.f) * (bc(p.kappa) - phi);
     V2 Fx = fma2(kp, gx, p.gx * phi);
     V2 Fy = fma2(kp, gy, p.gy * phi);
-    if (!FAST && p.has_fb) {
-        const int k = p.unsteady ? 2 : 1;
-        Fx = Fx + V2{*reinterpret_cast<const float2*>(c.aux(p2, k))};
-        Fy = Fy + V2{*reinterpret_cast<const float2*>(c.aux(p2, k + 1))};
-    }
+    c.template add_field_force<FAST>(p2, Bs, Fx, Fy);
     const V2 m0 = Bs.m[0];
     const V2 inv = rcp2(m0);
     const V2 ux = fma2(0.5f, Fx, Bs.m[3]) * inv;
@@ -204,11 +223,11 @@ __device__ __forceinline__ void warp_phase2(const WarpCtx<S>& c, const PRow& An,
     Bs.wDy = fma2(4.f, Dy, rpair(Dy, Dyr) + lpair(Dy, Dyl));
 }
 
-template <typename S, bool FAST>
-__device__ __forceinline__ void warp_phase3(const WarpCtx<S>& c, const PRow& An, const PRow& Bs, const PRow& Cs,
+template <typename S, bool FAST, typename Ctx>
+__device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const PRow& Bs, const PRow& Cs,
                                             int p3, bool lane_ok) {
     using IO = PairIO<S>;
-    const StepParams<float>& p = c.p;
+    const auto& p = c.p;
     constexpr float tw = 1.0f / 12.0f;
     V2 xAx = fma2(4.f, Cs.dAx, An.dAx + Bs.dAx);
     V2 xBx = fma2(4.f, Cs.dBx, An.dBx + Bs.dBx);
@@ -237,15 +256,15 @@ __device__ __forceinline__ void warp_phase3(const WarpCtx<S>& c, const PRow& An,
         yBx = wBxh - wBxl;
         yDy = wDh - wDl;
     }
-    const V2 phi = V2{*reinterpret_cast<const float2*>(c.aux(p3, 0))};
-    const V2 phin = (!FAST && p.unsteady) ? V2{*reinterpret_cast<const float2*>(c.aux(p3, 1))} : phi;
+    const V2 phi = c.phi2(p3, Cs);
+    const V2 phin = c.template phin2<FAST>(p3, Cs);
     const V2 rho = Cs.rho;
     const V2 X = p.kappa * rcp2(phi);
     const V2 kp = p.model_b ? bc(p.kappa - 1.f) : bc(p.kappa) - phi;
     const V2 kr = kp * rho;
     const V2 divD = xDx + yDy, difD = xDx - yDy;
     V2 Ca = fma2(tw, fma2(-p.kappa, xAx + yAy, fma2(2.f * kr, xBx + yBy, fma2(-2.f, X, bc(3.f)) * divD)), bc(0.f));
-    if (!FAST) Ca = fma2(-2.f, (X * rho) * (phin - phi), Ca);
+    if (!FAST || Ctx::kUnsteady) Ca = fma2(-2.f, (X * rho) * (phin - phi), Ca);
     const V2 Cb = tw * fma2(-p.kappa, xAx - yAy, fma2((2.f / 3.f) * kr, xBx - yBy, difD));
     const V2 Cc = (1.f / 36.f) * (kr * (xBy + yBx));
     const V2 m0 = Cs.m[0], ux = Cs.ux, uy = Cs.uy, Fx = Cs.Fx, Fy = Cs.Fy;
@@ -324,39 +343,13 @@ __device__ __forceinline__ void warp_phase3(const WarpCtx<S>& c, const PRow& An,
     }
 }
 
-template <typename S, int MINB>
-__global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_constant__ StepParams<float> p) {
-    using L = WarpLayout<S>;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x;
-    constexpr int A = L::A;
-    const int x0 = blockIdx.x * p.W;
-    const int y0 = blockIdx.y * p.H;
-    const int y1 = min(y0 + p.H, p.ny);
-
-    WarpCtx<S> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
-    c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
-    c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
-    c.xa = x0 - 2 + 2 * lane;
-    c.sa = kPadCols + c.xa - c.wsp;
-    c.rlo = y0 - 3;
-    c.rhi = y1 + 2;
-    if (p.wall_y) { c.rlo = max(c.rlo, 0); c.rhi = min(c.rhi, p.ny - 1); }
-    c.waited = c.rlo - 1;
-    c.issued = c.rlo - 1;
-
-    if (lane == 0) {
-        for (int k = 0; k < kWarpSlots; ++k) mbar_init(reinterpret_cast<uint64_t*>(smem) + k, 1);
-        fence_mbar_init();
-        for (int r = c.rlo; r <= min(y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
-    }
-    __syncwarp();
-
-    // rows whose three phases need no wall, validity or field handling
-    const bool fast_strip = !p.unsteady && !p.has_fb;
-    const int fast_lo = p.wall_y ? max(y0, 1) : y0;                 // lowest phase-3 row
-    const int fast_hi = p.wall_y ? min(y1 + 1, p.ny - 2) : y1 + 1;  // highest phase-1 row
-
+// The row pipeline of one strip, shared by every one-warp kernel. Ctx supplies the
+// staged rows (issue / wait_upto / pop), the per-cell sources (phi2, phin2,
+// add_field_force, row_setup), the strip (y0, y1, source rows rlo .. rhi) and which
+// rows may take the branch-free path (fast_strip, fast_lo, fast_hi).
+template <typename S, typename Ctx>
+__device__ __forceinline__ bool warp_run_strip(Ctx& c) {
+    const int lane = c.lane, y0 = c.y0, y1 = c.y1;
     PRow s0, s1, s2;
     auto iter = [&](PRow& An, PRow& Bs, PRow& Cs, const int p1) -> bool {
         const int p2 = p1 - 1, p3 = p1 - 2;
@@ -369,9 +362,9 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
         c.wait_upto(p1 + 1);
         if (__any_sync(0xffffffffu, c.aborted)) return false;
         const bool lane_ok = lane >= 1 && lane < 31;
-        if (fast_strip && p3 >= fast_lo && p1 <= fast_hi) {
-            // interior row of a steady, field-free strip: one branch-free block, so
-            // the collision of row p3 overlaps the pulls and shuffles of rows p1, p2
+        if (c.fast_strip && p3 >= c.fast_lo && p1 <= c.fast_hi) {
+            // interior row: one branch-free block, so the collision of row p3 overlaps
+            // the pulls and shuffles of rows p1, p2
             warp_phase1<S, true>(c, An, p1);
             const float l = left_of(An.rho), r = right_of(An.rho);
             An.dr = rpair(An.rho, r) - lpair(An.rho, l);
@@ -403,6 +396,41 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
         if (ok && it + 2 < n_it) ok = iter(s2, s1, s0, p1 + 2);
     }
     __syncwarp();
+    return ok;
+}
+
+template <typename S, int MINB>
+__global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_constant__ StepParams<float> p) {
+    using L = WarpLayout<S>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x;
+    constexpr int A = L::A;
+    const int x0 = blockIdx.x * p.W;
+    const int y0 = blockIdx.y * p.H;
+    const int y1 = min(y0 + p.H, p.ny);
+
+    WarpCtx<S> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
+    c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
+    c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
+    c.xa = x0 - 2 + 2 * lane;
+    c.sa = kPadCols + c.xa - c.wsp;
+    c.rlo = y0 - 3;
+    c.rhi = y1 + 2;
+    if (p.wall_y) { c.rlo = max(c.rlo, 0); c.rhi = min(c.rhi, p.ny - 1); }
+    c.waited = c.rlo - 1;
+    c.issued = c.rlo - 1;
+    // rows whose three phases need no wall, validity or field handling
+    c.fast_strip = !p.unsteady && !p.has_fb;
+    c.fast_lo = p.wall_y ? max(y0, 1) : y0;                 // lowest phase-3 row
+    c.fast_hi = p.wall_y ? min(y1 + 1, p.ny - 2) : y1 + 1;  // highest phase-1 row
+
+    if (lane == 0) {
+        for (int k = 0; k < kWarpSlots; ++k) mbar_init(reinterpret_cast<uint64_t*>(smem) + k, 1);
+        fence_mbar_init();
+        for (int r = c.rlo; r <= min(y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
+    }
+    __syncwarp();
+    warp_run_strip<S>(c);
     if (lane == 0) {
         // every issued row is waited for before the CTA exits (bounded)
         for (int r = c.waited + 1; r <= c.issued; ++r) mbar_wait_bounded(c.bar(r), c.parity(r), kWaitTries);

@@ -1,0 +1,220 @@
+"""Batched lattices (one persistent kernel per step, lbm_vanse_batch_*) against the
+FP64 oracle: every lattice of a batch runs the spatiotemporal manufactured
+solution with its own size, relaxation time, amplitude, period and U0; the
+oracle runs each lattice alone from the same manufactured fields (synth.mms).
+
+Tolerances follow the single-lattice parity tests: FP32 compute rounds each
+population by a few tens of units of 2^-24 |f| per step (the in-kernel FP32
+evaluation of phi and of the Eq. (25) force adds errors of the same order), so
+the bound is 32 * 2^-24 * max|f| per step; FP16 / BF16 storage add 2 * 2^-11 /
+2 * 2^-8 of max|f - f_rest| per step."""
+import numpy as np
+import pytest
+
+from synth import mms
+
+from gpu_cases import rest_populations
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+# n, tau, A, T, U0: ragged tails against the 60-column units (32, 75, 130),
+# a lattice narrower than the 3-cell ghost band's reach (7), several units per lattice
+LATTICES = [
+    (32, 0.8, 0.2, 1000.0, 0.01),
+    (75, 0.55, 0.05, 300.0, 0.02),
+    (130, 1.5, 0.3, 2000.0, 0.005),
+    (7, 0.7, 0.1, 50.0, 0.01),
+    (64, 0.9, 0.15, 700.0, 0.0),
+]
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_02964_gb300 as pkg
+    pkg.capi.load()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def O(oracle_mod):
+    return oracle_mod
+
+
+def _oracle_run(O, lat, steps, phi0=0.7, s_eps=1.2, s_q=1.2):
+    n, tau, A, T, U0 = lat
+    M = mms.Config1(n=n, T=T, A=A, phi0=phi0, U0=U0)
+    nu = (tau - 0.5) / 3.0
+    prm = O.Params(nx=n, ny=n, **O.rates_from_tau(tau, s_eps=s_eps, s_q=s_q), kappa=0.5)
+    ux, uy = M.velocity(0)
+    f = O.init(prm, np.ones((n, n)), ux, uy, M.phi(0), M.force(0, nu))
+    for t in range(steps):
+        f = O.step(prm, f, M.phi(t), M.phi(t + 1), M.force(t, nu))
+    return f, M, prm
+
+
+def _check(fg, fo, phi, steps, storage):
+    dev = np.abs(fo - rest_populations(phi)).max()
+    tol = steps * 32 * EPS32 * np.abs(fo).max()
+    if storage == "fp16":
+        tol += steps * 2 * 2.0 ** -11 * dev
+    elif storage == "bf16":
+        tol += steps * 2 * 2.0 ** -8 * dev
+    err = np.abs(fg - fo).max()
+    assert err <= tol, (err, tol)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_batch_matches_oracle(P, O, storage):
+    steps = 5
+    b = P.Batch(LATTICES, storage=storage, strip_rows=16, eager=True)
+    b.init()
+    b.step(steps)
+    assert b.step_count == steps
+    for i, lat in enumerate(LATTICES):
+        fo, M, _ = _oracle_run(O, lat, steps)
+        _check(b.populations(i).cpu().numpy(), fo, M.phi(steps), steps, storage)
+    b.close()
+
+
+def test_batch_initial_populations(P, O):
+    b = P.Batch(LATTICES)
+    b.init()
+    for i, lat in enumerate(LATTICES):
+        fo, M, _ = _oracle_run(O, lat, 0)
+        _check(b.populations(i).cpu().numpy(), fo, M.phi(0), 1, "fp32")
+    b.close()
+
+
+@pytest.mark.parametrize("rows", [1, 5, 16, 200])
+def test_batch_unit_height_invariance(P, rows):
+    """The same steps with units of 1, 5, 16 and 200 rows give the same populations
+    up to rounding (the arithmetic per cell is the same; only contraction of
+    multiply-adds may differ between inlined copies)."""
+    steps = 3
+    ref = P.Batch(LATTICES, strip_rows=48, eager=True)
+    ref.init()
+    ref.step(steps)
+    b = P.Batch(LATTICES, strip_rows=rows, eager=True)
+    b.init()
+    b.step(steps)
+    for i in range(len(LATTICES)):
+        a, c = ref.populations(i).cpu().numpy(), b.populations(i).cpu().numpy()
+        assert np.abs(a - c).max() <= 64 * EPS32 * np.abs(a).max()
+    ref.close()
+    b.close()
+
+
+def test_persistent_equals_one_launch_per_lattice(P):
+    steps = 4
+    a = P.Batch(LATTICES, eager=True)
+    a.init()
+    a.step(steps)
+    b = P.Batch(LATTICES, eager=True)
+    b.init()
+    b.step_each(steps)
+    for i in range(len(LATTICES)):
+        x, y = a.populations(i).cpu().numpy(), b.populations(i).cpu().numpy()
+        assert np.abs(x - y).max() <= 64 * EPS32 * np.abs(x).max()
+    a.close()
+    b.close()
+
+
+def test_graph_replay_equals_eager(P):
+    steps = 40  # two 16-step graphs and 8 eager steps
+    a = P.Batch(LATTICES, eager=True)
+    a.init()
+    a.step(steps)
+    b = P.Batch(LATTICES, eager=False)
+    b.init()
+    b.step(steps)
+    assert b.step_count == steps
+    for i in range(len(LATTICES)):
+        assert np.array_equal(a.populations(i).cpu().numpy(), b.populations(i).cpu().numpy())
+    a.close()
+    b.close()
+
+
+def test_batch_velocity_error_matches_oracle_macros(P, O):
+    """Eq. (26) sums computed on the device equal those of the oracle's macroscopic
+    fields (Eq. 7, 13) of the same populations against the manufactured velocity."""
+    steps = 20
+    b = P.Batch(LATTICES)
+    b.init()
+    b.step(steps)
+    for i, (n, tau, A, T, U0) in enumerate(LATTICES):
+        M = mms.Config1(n=n, T=T, A=A, U0=U0)
+        nu = (tau - 0.5) / 3.0
+        prm = O.Params(nx=n, ny=n, **O.rates_from_tau(tau, s_eps=1.2, s_q=1.2), kappa=0.5)
+        f = b.populations(i).cpu().numpy()
+        m = O.macros(prm, f, M.phi(steps), M.force(steps, nu))
+        uxr, uyr = M.velocity(steps)
+        num, den = b.velocity_error(i)
+        num_o = np.sum((m["ux"] - uxr) ** 2 + (m["uy"] - uyr) ** 2)
+        den_o = np.sum(uxr ** 2 + uyr ** 2)
+        if den_o == 0:
+            continue
+        assert abs(den - den_o) <= 1e-5 * den_o
+        # u is recovered in FP32 on the device: |u| ~ 1e-2, rounding ~1e-9
+        assert abs(np.sqrt(num) - np.sqrt(num_o)) <= 1e-6 * np.sqrt(den_o) + 1e-9 * n
+    b.close()
+
+
+def test_batch_manufactured_error_matches_single_lattice_oracle(P, O):
+    """E_u (Eq. 26) of the 64 x 64 manufactured solution after 400 steps from the
+    batch (FP32) against the oracle's FP64 run: within 10 %, as the FP32 single
+    lattice is (its ratio to FP64 is about 0.99)."""
+    lat = (64, 0.8, 0.2, 1000.0, 0.01)
+    steps = 400
+    b = P.Batch([lat, (48, 0.7, 0.1, 500.0, 0.01)])
+    b.init()
+    b.step(steps)
+    e_gpu = b.relative_error(0)
+    b.close()
+    fo, M, prm = _oracle_run(O, lat, steps)
+    m = O.macros(prm, fo, M.phi(steps), M.force(steps, 0.1))
+    uxr, uyr = M.velocity(steps)
+    e_o = mms.relative_l2(m["ux"], m["uy"], uxr, uyr)
+    print(f"E_u batch {e_gpu:.4e} oracle {e_o:.4e}")
+    assert abs(e_gpu / e_o - 1) < 0.1
+
+
+def test_autotune_picks_a_candidate_and_resets(P, O):
+    b = P.Batch(LATTICES)
+    rows = b.autotune(trial_steps=4)
+    assert rows in (16, 24, 32, 48, 64, 96, 128)
+    assert b.step_count == 0
+    b.step(3)
+    fo, M, _ = _oracle_run(O, LATTICES[2], 3)
+    _check(b.populations(2).cpu().numpy(), fo, M.phi(3), 3, "fp32")
+    b.close()
+
+
+def test_batch_argument_errors(P):
+    from paper_2409_02964_gb300 import capi
+    bad = [
+        [(0, 0.8, 0.1, 100.0, 0.01)],
+        [(32, 0.5, 0.1, 100.0, 0.01)],
+        [(32, 0.8, 0.7, 100.0, 0.01)],   # |A| must be below phi0
+        [(32, 0.8, 0.1, 0.0, 0.01)],
+        [],
+    ]
+    for lats in bad:
+        with pytest.raises(P.LbmError) as e:
+            P.Batch(lats)
+        assert e.value.status == capi.LBM_ERR_ARG
+    with pytest.raises(KeyError):
+        P.Batch(LATTICES, storage="fp64")
+    b = P.Batch(LATTICES)
+    with pytest.raises(P.LbmError) as e:
+        b.step(1)
+    assert e.value.status == capi.LBM_ERR_STATE
+    b.init()
+    with pytest.raises(P.LbmError) as e:
+        b.velocity_error(len(LATTICES))
+    assert e.value.status == capi.LBM_ERR_ARG
+    b.close()
