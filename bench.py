@@ -42,16 +42,15 @@ SBYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}
 
 def _kernel_traffic(cells: int):
     """DRAM bytes per launch of the step kernel from the committed ncu capture (a
-    smaller channel, scaled by cells), or None when the kernel sources have changed
-    since that capture."""
-    import glob
+    smaller channel, scaled by cells), or None when a source the kernel is built
+    from has changed since that capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "vanse_warp_fp32_channel_traffic.json")) as fh:
             rec = json.load(fh)
         h = hashlib.sha256()
-        for f in sorted(glob.glob(os.path.join(ROOT, "paper_2409_02964_gb300", "csrc", "*.cuh"))):
-            with open(f, "rb") as fh:
+        for f in sorted(rec["sources"]):
+            with open(os.path.join(ROOT, "paper_2409_02964_gb300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
         if h.hexdigest() != rec["source_sha256"]:
             return None
@@ -167,6 +166,65 @@ def e2e_run(lat, phi: np.ndarray, steps: int):
     return dt, host_phi.numel() * 8, 3 * 8
 
 
+BATCH_WORKLOAD = ("512 independent periodic lattices, n uniform over {32,48,...,1024} (seed 2409), "
+                  "tau ~ U[0.55,1.5], phi amplitude A ~ U[0.05,0.3], spatiotemporal manufactured solution "
+                  "phi = 0.7 + A sin sin cos(2 pi t/T) with T = 1000 (n/64)^2, U0 = 0.01 (64/n), "
+                  "s_e = s_eps = s_q = 1.2, FP32, 2000 steps each")
+
+
+def batch_lattices(count: int = 512, seed: int = 2409):
+    """Seeded lattices of the batched workload: n, tau, A, T, U0 per lattice."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice(np.arange(32, 1025, 16), size=count)
+    taus = rng.uniform(0.55, 1.5, size=count)
+    amps = rng.uniform(0.05, 0.3, size=count)
+    return [(int(n), float(t), float(a), 1000.0 * (n / 64) ** 2, 0.01 * 64 / n)
+            for n, t, a in zip(sizes, taus, amps)]
+
+
+def batch_run(steps: int = 2000, count: int = 512, each_steps: int = 200):
+    """The batched workload from t = 0: all `steps` steps as one persistent kernel
+    per step in captured CUDA graphs (autotuned unit height); then, for comparison,
+    `each_steps` steps with one launch per lattice per step (each lattice cut as a
+    lone lattice would be), whose rate is steady from step to step. Device time with
+    CUDA events on the library's stream."""
+    import torch
+    import paper_2409_02964_gb300 as P
+    lats = batch_lattices(count)
+    b = P.Batch(lats, storage="fp32")
+    rows = b.autotune(trial_steps=8)
+    stream = b.stream
+    res = {}
+    errs = None
+    for mode in ("persistent", "per_lattice"):
+        b.init()
+        run = b.step if mode == "persistent" else b.step_each
+        ns = steps if mode == "persistent" else min(each_steps, steps)
+        run(16 if mode == "persistent" else 3)
+        b.init()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        run(ns)
+        ev1.record(stream)
+        ev1.synchronize()
+        secs = ev0.elapsed_time(ev1) / 1e3
+        res[mode] = {"steps": ns, "seconds": round(secs, 4),
+                     "solves_per_s": round(count * ns / steps / secs, 2),
+                     "MLUPS": round(b.cells * ns / secs / 1e6, 1),
+                     "GB_s": round(72 * b.cells * ns / secs / 1e9, 1),
+                     "gpu_launches": ns * (2 if mode == "persistent" else count + 1)}
+        if mode == "persistent":
+            errs = np.array([b.relative_error(i) for i in range(count)])
+    out = {"workload": BATCH_WORKLOAD, "lattices": count, "cells": b.cells, "steps": steps,
+           "unit_rows": rows, "bytes_per_cell": 72, **res,
+           "speedup": round(res["persistent"]["MLUPS"] / res["per_lattice"]["MLUPS"], 3),
+           "E_u": {"median": float(np.median(errs)), "max": float(np.max(errs)),
+                   "finite": int(np.isfinite(errs).sum())}}
+    b.close()
+    return out
+
+
 def oracle_rate(n_rows: int, nx: int, steps: int, threads: int):
     """FP64 oracle on a band of the channel: returns (MLUPS, seconds, cells)."""
     import oracle as O
@@ -241,11 +299,18 @@ def main():
     ap.add_argument("--strip-rows", type=int, default=0)
     ap.add_argument("--kernel", type=int, default=0, help="step-kernel variant (0 = the library's choice)")
     ap.add_argument("--quick", action="store_true", help="timed steps only (no e2e / variants / CPU baseline)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-lattice workload")
+    ap.add_argument("--batch-only", action="store_true", help="run only the batched-lattice workload")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_only:
+        print(json.dumps({"batch": batch_run(args.batch_steps, args.batch_count)}), flush=True)
+        return 0
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -318,6 +383,8 @@ def main():
                             "bytes_per_cell": lv.bytes_per_cell, "steps": ns}
             lv.close()
         out["variants"] = variants
+        if not args.no_batch:
+            out["batch"] = batch_run(args.batch_steps, args.batch_count)
         out["cpu_baseline"] = cpu_baseline(args.n)
     if rank == 0:
         print(json.dumps(out), flush=True)

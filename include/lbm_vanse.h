@@ -196,7 +196,7 @@ typedef struct {
 
 typedef struct lbm_vanse_batch* lbm_vanse_batch_t;
 
-/* Defaults: FP32, s_e derived, s_eps = s_q = 1.2, kappa = 0.5, rho0 = 1, phi0 = 0.7. */
+/* Defaults: FP32, s_e = s_eps = s_q = 1.2, kappa = 0.5, rho0 = 1, phi0 = 0.7. */
 void lbm_vanse_batch_default_params(lbm_vanse_batch_params* p);
 
 /* Allocate count lattices (two population buffers each) on the current device.
@@ -212,11 +212,13 @@ lbm_status lbm_vanse_batch_init(lbm_vanse_batch_t b);
 lbm_status lbm_vanse_batch_step(lbm_vanse_batch_t b, int nsteps);
 
 /* The same steps with one kernel launch per lattice per step (the form the
- * persistent kernel replaces; for comparison). */
+ * persistent kernel replaces; for comparison). Each lattice is cut into strips as
+ * a lone lattice would be (about five waves of resident CTAs, >= 16 rows). */
 lbm_status lbm_vanse_batch_step_each(lbm_vanse_batch_t b, int nsteps);
 
-/* Time trial_steps steps for a set of work-unit heights, keep the fastest, write it
- * to *rows_out (may be NULL) and re-initialise the batch (t = 0). */
+/* Time trial_steps steps for each work-unit height of {16, 24, 32, 48, 64, 96, 128,
+ * 192, 256}, keep the fastest, write it to *rows_out (may be NULL) and
+ * re-initialise the batch (t = 0). */
 lbm_status lbm_vanse_batch_autotune(lbm_vanse_batch_t b, int trial_steps, int* rows_out);
 
 /* Eq. (26) sums for lattice index at the current step against its manufactured

@@ -35,9 +35,11 @@ def _check(st: int, handle) -> None:
 
 
 class Batch:
-    """Lattices of one batch on the current CUDA device (see ``lbm_vanse_batch_*``)."""
+    """Lattices of one batch on the current CUDA device (see ``lbm_vanse_batch_*``).
 
-    def __init__(self, lattices, *, storage: str = "fp32", s_e: float = 0.0, s_eps: float = 1.2,
+    ``s_e <= 0`` derives the energy rate of each lattice from nu_e = nu/3."""
+
+    def __init__(self, lattices, *, storage: str = "fp32", s_e: float = 1.2, s_eps: float = 1.2,
                  s_q: float = 1.2, kappa: float = 0.5, rho0: float = 1.0, phi0: float = 0.7,
                  strip_rows: int = 0, eager: bool = False, stream=None):
         L = capi.load()

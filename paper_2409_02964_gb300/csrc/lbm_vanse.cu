@@ -842,6 +842,7 @@ struct lbm_vanse_batch {
     double* partial = nullptr;
     double* red_out = nullptr;
     int nunits = 0, H = 0, grid = 0;
+    std::vector<int> H_each;             // strip height of each lattice launched on its own
     long long cells = 0, steps = 0;
     bool initialised = false;
     cudaStream_t cap_stream = nullptr;
@@ -933,6 +934,14 @@ lbm_status batch_configure(lbm_vanse_batch* b) {
     BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, 32, smem));
     BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
     b->grid = std::max(1, per_sm * nsm);
+    // launched on its own, a lattice gets the single-lattice rule: about five waves
+    // of resident CTAs, strips of at least 16 rows
+    b->H_each.resize(b->desc.size());
+    for (size_t i = 0; i < b->desc.size(); ++i) {
+        const BatchLattice& L = b->desc[i];
+        const int nstrips = std::max(1, (5 * b->grid + L.tiles_x - 1) / L.tiles_x);
+        b->H_each[i] = std::min(L.ny, std::max(16, (L.ny + nstrips - 1) / nstrips));
+    }
     return LBM_OK;
 }
 
@@ -989,7 +998,8 @@ lbm_status batch_run_each(lbm_vanse_batch* b, int nsteps) {
     for (int s = 0; s < nsteps; ++s) {
         for (size_t i = 0; i < b->desc.size(); ++i) {
             const BatchLattice& L = b->desc[i];
-            vanse_batch_one_kernel<S, kBatchMinBlocks><<<L.tiles_x * L.strips, 32, smem, b->stream>>>(bp, (int)i);
+            const int H = b->H_each[i], strips = (L.ny + H - 1) / H;
+            vanse_batch_one_kernel<S, kBatchMinBlocks><<<L.tiles_x * strips, 32, smem, b->stream>>>(bp, (int)i, H);
             BCK(b, cudaGetLastError());
         }
         batch_tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock, b->d_clock + 1);
@@ -1043,7 +1053,7 @@ extern "C" void lbm_vanse_batch_default_params(lbm_vanse_batch_params* p) {
     if (!p) return;
     std::memset(p, 0, sizeof(*p));
     p->storage = LBM_FP32;
-    p->s_e = 0.0;
+    p->s_e = 1.2;
     p->s_eps = 1.2;
     p->s_q = 1.2;
     p->kappa = 0.5;
@@ -1158,7 +1168,7 @@ extern "C" lbm_status lbm_vanse_batch_step_each(lbm_vanse_batch_t b, int nsteps)
 extern "C" lbm_status lbm_vanse_batch_autotune(lbm_vanse_batch_t b, int trial_steps, int* rows_out) {
     if (!b) return bfail(nullptr, LBM_ERR_ARG, "batch is NULL");
     if (trial_steps < 1) return bfail(b, LBM_ERR_ARG, "trial_steps must be >= 1");
-    static const int candidates[] = {16, 24, 32, 48, 64, 96, 128};
+    static const int candidates[] = {16, 24, 32, 48, 64, 96, 128, 192, 256};
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));

@@ -402,10 +402,11 @@ __global__ void batch_err_kernel(const BatchLattice* lats, int index, const int*
     block_reduce3(num, den, 0.0, partial);
 }
 
-// One lattice's units as an ordinary grid (one unit per CTA): the launch-per-lattice
-// form the persistent kernel is compared against.
+// One lattice as an ordinary grid of tiles_x x ceil(ny / H) CTAs (one strip of H rows
+// each): the launch-per-lattice form the persistent kernel is compared against.
 template <typename S, int MINB>
-__global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_constant__ BatchParams bp, int index) {
+__global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_constant__ BatchParams bp, int index,
+                                                                  int H) {
     using L = WarpLayout<S>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x;
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     p.ny = Lt.ny;
     p.P = Lt.P;
     p.W = 60;
-    p.H = Lt.H;
+    p.H = H;
     p.wall_y = 0;
     p.unsteady = 1;
     p.has_fb = 1;
@@ -453,8 +454,8 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     sincosf(Lt.w * (float)t, &c.st, &c.ct);
     c.ct1 = cosf(Lt.w * (float)(t + 1));
     const int x0 = tx * 60;
-    c.y0 = ty * Lt.H;
-    c.y1 = min(c.y0 + Lt.H, Lt.ny);
+    c.y0 = ty * H;
+    c.y1 = min(c.y0 + H, Lt.ny);
     c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
     c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
     c.xa = x0 - 2 + 2 * lane;

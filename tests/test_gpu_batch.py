@@ -45,11 +45,20 @@ def O(oracle_mod):
     return oracle_mod
 
 
-def _oracle_run(O, lat, steps, phi0=0.7, s_eps=1.2, s_q=1.2):
+def _oracle_params(O, n, tau, s_e=1.2, s_eps=1.2, s_q=1.2):
+    """Oracle rates of a batch lattice: s_e = 1.2 (the batch default) or, for
+    s_e <= 0, derived from nu_e = nu/3."""
+    kw = O.rates_from_tau(tau, s_eps=s_eps, s_q=s_q)
+    if s_e > 0:
+        kw["s_e"] = s_e
+    return O.Params(nx=n, ny=n, **kw, kappa=0.5)
+
+
+def _oracle_run(O, lat, steps, phi0=0.7, s_e=1.2):
     n, tau, A, T, U0 = lat
     M = mms.Config1(n=n, T=T, A=A, phi0=phi0, U0=U0)
     nu = (tau - 0.5) / 3.0
-    prm = O.Params(nx=n, ny=n, **O.rates_from_tau(tau, s_eps=s_eps, s_q=s_q), kappa=0.5)
+    prm = _oracle_params(O, n, tau, s_e)
     ux, uy = M.velocity(0)
     f = O.init(prm, np.ones((n, n)), ux, uy, M.phi(0), M.force(0, nu))
     for t in range(steps):
@@ -78,6 +87,18 @@ def test_batch_matches_oracle(P, O, storage):
     for i, lat in enumerate(LATTICES):
         fo, M, _ = _oracle_run(O, lat, steps)
         _check(b.populations(i).cpu().numpy(), fo, M.phi(steps), steps, storage)
+    b.close()
+
+
+def test_batch_derived_energy_rate_matches_oracle(P, O):
+    """s_e <= 0: each lattice takes s_e from nu_e = nu/3, as the oracle's rates_from_tau."""
+    steps = 4
+    b = P.Batch(LATTICES, s_e=0.0, eager=True)
+    b.init()
+    b.step(steps)
+    for i, lat in enumerate(LATTICES):
+        fo, M, _ = _oracle_run(O, lat, steps, s_e=0.0)
+        _check(b.populations(i).cpu().numpy(), fo, M.phi(steps), steps, "fp32")
     b.close()
 
 
@@ -149,7 +170,7 @@ def test_batch_velocity_error_matches_oracle_macros(P, O):
     for i, (n, tau, A, T, U0) in enumerate(LATTICES):
         M = mms.Config1(n=n, T=T, A=A, U0=U0)
         nu = (tau - 0.5) / 3.0
-        prm = O.Params(nx=n, ny=n, **O.rates_from_tau(tau, s_eps=1.2, s_q=1.2), kappa=0.5)
+        prm = _oracle_params(O, n, tau)
         f = b.populations(i).cpu().numpy()
         m = O.macros(prm, f, M.phi(steps), M.force(steps, nu))
         uxr, uyr = M.velocity(steps)
@@ -186,7 +207,7 @@ def test_batch_manufactured_error_matches_single_lattice_oracle(P, O):
 def test_autotune_picks_a_candidate_and_resets(P, O):
     b = P.Batch(LATTICES)
     rows = b.autotune(trial_steps=4)
-    assert rows in (16, 24, 32, 48, 64, 96, 128)
+    assert rows in (16, 24, 32, 48, 64, 96, 128, 192, 256)
     assert b.step_count == 0
     b.step(3)
     fo, M, _ = _oracle_run(O, LATTICES[2], 3)
