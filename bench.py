@@ -213,7 +213,7 @@ def batch_run(steps: int = 2000, count: int = 512, each_steps: int = 200):
                      "solves_per_s": round(count * ns / steps / secs, 2),
                      "MLUPS": round(b.cells * ns / secs / 1e6, 1),
                      "GB_s": round(72 * b.cells * ns / secs / 1e9, 1),
-                     "gpu_launches": ns * (2 if mode == "persistent" else count + 1)}
+                     "gpu_launches": ns * (3 if mode == "persistent" else count + 2)}
         if mode == "persistent":
             errs = np.array([b.relative_error(i) for i in range(count)])
     out = {"workload": BATCH_WORKLOAD, "lattices": count, "cells": b.cells, "steps": steps,
@@ -359,7 +359,8 @@ def main():
                          "traffic_unit": "bytes per launch",
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "kernel": {32: "vanse_warp_kernel"}.get(shape["threads"], "vanse_step_kernel / vanse_pair_kernel")},
-            "gpu_launches": args.steps,
+            # the one-warp step kernel is followed by the ghost-column refresh
+            "gpu_launches": args.steps * (2 if shape["threads"] == 32 else 1),
             "clocks": clocks,
             "mass_drift": (m1 - m0) / m0,
         }

@@ -249,7 +249,16 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src) {
             case 2: vanse_pair_kernel<S, 64, 6><<<grid, 64, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
             case 3: vanse_pair_kernel<S, 96, 4><<<grid, 96, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
             case 4: vanse_pair_kernel<S, 128, 3><<<grid, 128, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
-            case 5: vanse_warp_kernel<S, LBMV_WARP_MINB><<<grid, 32, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
+            case 5: {
+                vanse_warp_kernel<S, LBMV_WARP_MINB><<<grid, 32, smem, stream>>>(p);
+                CK(h, cudaGetLastError());
+                // the one-warp kernel writes columns 0 .. nx-1 only
+                const long long ng = 9LL * h->prm.ny * 2 * kGhost;
+                ghost_fill_kernel<S><<<(int)std::min<long long>((ng + 255) / 256, 4096), 256, 0, stream>>>(
+                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P);
+                CK(h, cudaGetLastError());
+                return LBM_OK;
+            }
             default: break;
         }
     }
@@ -842,6 +851,7 @@ struct lbm_vanse_batch {
     double* partial = nullptr;
     double* red_out = nullptr;
     int nunits = 0, H = 0, grid = 0;
+    int ghost_blocks = 1;                // x blocks of the ghost refresh (y = lattice)
     std::vector<int> H_each;             // strip height of each lattice launched on its own
     long long cells = 0, steps = 0;
     bool initialised = false;
@@ -950,6 +960,8 @@ lbm_status batch_enqueue_step(lbm_vanse_batch* b, cudaStream_t stream) {
     const size_t smem = WarpLayout<S>::bytes(0);
     vanse_batch_kernel<S, kBatchMinBlocks><<<b->grid, 32, smem, stream>>>(batch_params(b));
     BCK(b, cudaGetLastError());
+    batch_ghost_fill_kernel<S><<<dim3(b->ghost_blocks, (unsigned)b->desc.size()), 256, 0, stream>>>(b->d_desc, b->d_clock);
+    BCK(b, cudaGetLastError());
     batch_tick_kernel<<<1, 1, 0, stream>>>(b->d_clock, b->d_clock + 1);
     BCK(b, cudaGetLastError());
     return LBM_OK;
@@ -1002,6 +1014,9 @@ lbm_status batch_run_each(lbm_vanse_batch* b, int nsteps) {
             vanse_batch_one_kernel<S, kBatchMinBlocks><<<L.tiles_x * strips, 32, smem, b->stream>>>(bp, (int)i, H);
             BCK(b, cudaGetLastError());
         }
+        batch_ghost_fill_kernel<S><<<dim3(b->ghost_blocks, (unsigned)b->desc.size()), 256, 0, b->stream>>>(b->d_desc,
+                                                                                                      b->d_clock);
+        BCK(b, cudaGetLastError());
         batch_tick_kernel<<<1, 1, 0, b->stream>>>(b->d_clock, b->d_clock + 1);
         BCK(b, cudaGetLastError());
         b->steps++;
@@ -1121,6 +1136,7 @@ extern "C" lbm_status lbm_vanse_batch_create(const lbm_vanse_batch_lattice* latt
     if (e != cudaSuccess) { st = bfail(nullptr, LBM_ERR_OOM, "batch populations (%zu bytes): %s", total, cudaGetErrorString(e)); }
     int nmax = 0;
     for (auto& q : b->lat) nmax = std::max(nmax, q.n);
+    b->ghost_blocks = (int)std::min<long long>((9LL * nmax * 2 * kGhost + 255) / 256, 32);
     if (st == LBM_OK) {
         for (int i = 0; i < count; ++i) {
             const size_t bytes = ((size_t)9 * b->desc[i].plane * b->sbytes + 255) / 256 * 256;

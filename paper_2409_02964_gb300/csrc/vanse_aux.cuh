@@ -33,6 +33,29 @@ __device__ __forceinline__ void put_with_ghosts(T* plane_base, int P, int nx, in
     for (int g = x + nx; g < nx + kGhost; g += nx) plane_base[ro + g] = v;
 }
 
+// Periodic ghost columns of the 9 population planes, refreshed from the columns
+// they image: column g in [-kGhost, 0) and [nx, nx + kGhost) takes column g mod nx
+// (a verbatim copy: an FP16 / BF16 value stays encoded against the same phi, whose
+// ghosts are images too). Runs after a step kernel that writes columns 0 .. nx-1
+// only. One thread per (plane, row, ghost column).
+template <typename S>
+__device__ __forceinline__ void fill_ghosts(S* __restrict__ buf, long long plane, int nx, int ny, int P, long long k) {
+    const int g6 = (int)(k % (2 * kGhost));
+    const long long rest = k / (2 * kGhost);
+    const int y = (int)(rest % ny), i = (int)(rest / ny);
+    const int g = g6 < kGhost ? g6 - kGhost : nx + g6 - kGhost;
+    const int sx = ((g % nx) + nx) % nx;
+    S* row = buf + i * plane + (long long)y * P + kPadCols;
+    row[g] = row[sx];
+}
+
+template <typename S>
+__global__ void ghost_fill_kernel(S* __restrict__ buf, long long plane, int nx, int ny, int P) {
+    const long long n = 9LL * ny * 2 * kGhost;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        fill_ghosts<S>(buf, plane, nx, ny, P, k);
+}
+
 // Copy a dense [ny][nx] double field into a padded R field (with ghosts).
 template <typename R>
 __global__ void pad_field_kernel(const double* __restrict__ src, R* __restrict__ dst, int nx, int ny, int P) {

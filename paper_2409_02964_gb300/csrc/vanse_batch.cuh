@@ -74,6 +74,8 @@ struct BatchCtx {
     bool fast_strip;
     int fast_lo, fast_hi;
     uint32_t phase;            // parity of the next completion of each ring slot
+    RowCopy cp;
+    bool st_pair;              // this lane stores its pair (lanes 1..30, first column inside)
     // manufactured solution at this step
     V2 sx2, cx2;               // sin, cos of k x of the lane's two columns
     float k, w, A, U0, phi0, nu, rho0;
@@ -98,18 +100,26 @@ struct BatchCtx {
         Fy = fma2(rho0, f.fy, Fy);
     }
 
-    // lane 0: load source row r (periodic) into its slot
+    // this lane's part of staging a source row: lanes 0..8 copy the population rows
+    __device__ __forceinline__ void setup_copies() {
+        const uint32_t base = smem_u32(smem);
+        cp = RowCopy{};
+        cp.bar0 = base;
+        cp.tx = 9u * (uint32_t)(ww * (int)sizeof(S));
+        if (lane < 9) {
+            cp.src = reinterpret_cast<const char*>(reinterpret_cast<const S*>(p.src) + lane * p.plane + wsp);
+            cp.pitch = (uint32_t)(p.P * (int)sizeof(S));
+            cp.dst = base + (uint32_t)(L::kPop + lane * L::kPopRow);
+            cp.stride = (uint32_t)L::kPopSlot;
+            cp.bytes = (uint32_t)(ww * (int)sizeof(S));
+        }
+    }
+    // all lanes: load source row r (periodic) into its slot
     __device__ __forceinline__ void issue(int r) {
         issued = r;
-        uint64_t* b = bar(r);
         int gr = r % p.ny;
         if (gr < 0) gr += p.ny;
-        const uint32_t bs = (uint32_t)(ww * (int)sizeof(S));
-        mbar_expect_tx(b, 9u * bs);
-        const S* src = reinterpret_cast<const S*>(p.src) + (long long)gr * p.P + wsp;
-        unsigned char* ps = smem + L::kPop + wslot(r) * L::kPopSlot;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) bulk_g2s(ps + i * L::kPopRow, src + i * p.plane, bs, b);
+        cp.issue(lane, wslot(r), gr);
     }
     __device__ __forceinline__ void wait_upto(int r) {
         r = min(r, rhi);
@@ -189,6 +199,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
         c.xa = x0 - 2 + 2 * lane;
         c.sa = kPadCols + c.xa - c.wsp;
+        c.st_pair = lane >= 1 && lane < 31 && c.xa < Lt.nx;
         float sa_, ca_, sb_, cb_;
         sincospif(2.0f * (float)c.xa / (float)Lt.nx, &sa_, &ca_);
         sincospif(2.0f * (float)(c.xa + 1) / (float)Lt.nx, &sb_, &cb_);
@@ -202,11 +213,10 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         c.fast_lo = c.y0;
         c.fast_hi = c.y1 + 1;
 
+        c.setup_copies();
         __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async();
-            for (int r = c.rlo; r <= min(c.y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
-        }
+        fence_proxy_async();
+        for (int r = c.rlo; r <= min(c.y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
         __syncwarp();
         const bool ok = warp_run_strip<S>(c);
         phase = c.phase;
@@ -220,6 +230,17 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
             break;
         }
     }
+}
+
+// After each batched step, before the tick: refresh the periodic ghost columns of the
+// buffer every lattice's step just wrote (blockIdx.y = lattice).
+template <typename S>
+__global__ void batch_ghost_fill_kernel(const BatchLattice* lats, const int* clock) {
+    const BatchLattice& L = lats[blockIdx.y];
+    S* buf = reinterpret_cast<S*>(L.buf[(*clock + 1) & 1]);
+    const long long n = 9LL * L.ny * 2 * kGhost;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        fill_ghosts<S>(buf, L.plane, L.nx, L.ny, L.P, k);
 }
 
 // After each batched step: advance the clock and re-arm the unit counter.
@@ -460,6 +481,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
     c.xa = x0 - 2 + 2 * lane;
     c.sa = kPadCols + c.xa - c.wsp;
+    c.st_pair = lane >= 1 && lane < 31 && c.xa < Lt.nx;
     float sa_, ca_, sb_, cb_;
     sincospif(2.0f * (float)c.xa / (float)Lt.nx, &sa_, &ca_);
     sincospif(2.0f * (float)(c.xa + 1) / (float)Lt.nx, &sb_, &cb_);
@@ -472,8 +494,8 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     c.fast_strip = true;
     c.fast_lo = c.y0;
     c.fast_hi = c.y1 + 1;
-    if (lane == 0)
-        for (int r = c.rlo; r <= min(c.y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
+    c.setup_copies();
+    for (int r = c.rlo; r <= min(c.y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
     __syncwarp();
     const bool ok = warp_run_strip<S>(c);
     if (!ok && lane == 0)

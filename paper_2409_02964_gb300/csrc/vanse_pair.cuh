@@ -33,7 +33,14 @@ __device__ __forceinline__ V2 operator*(float s, V2 b) { return V2{__fmul2_rn(ma
 __device__ __forceinline__ V2 operator-(V2 a) { return V2{__fmul2_rn(make_float2(-1.f, -1.f), a.v)}; }
 __device__ __forceinline__ V2 fma2(V2 a, V2 b, V2 c) { return V2{__ffma2_rn(a.v, b.v, c.v)}; }
 __device__ __forceinline__ V2 fma2(float s, V2 b, V2 c) { return V2{__ffma2_rn(make_float2(s, s), b.v, c.v)}; }
-__device__ __forceinline__ V2 rcp2(V2 a) { return mk(__fdividef(1.0f, a.v.x), __fdividef(1.0f, a.v.y)); }
+// 1/a by the approximate reciprocal instruction (rcp.approx, relative error below
+// 2^-23; the operands here are densities and void fractions of order one)
+__device__ __forceinline__ float rcp_approx(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ V2 rcp2(V2 a) { return mk(rcp_approx(a.v.x), rcp_approx(a.v.y)); }
 __device__ __forceinline__ V2 operator+(V2 a, float s) { return V2{__fadd2_rn(a.v, make_float2(s, s))}; }
 __device__ __forceinline__ V2 operator+(float s, V2 a) { return a + s; }
 __device__ __forceinline__ V2 operator*(V2 a, float s) { return s * a; }

@@ -46,7 +46,33 @@ struct WarpLayout {
     static constexpr size_t bytes(int nR) { return (size_t)kAux + (size_t)kWarpSlots * nR * kAuxRow; }
 };
 
-__device__ __forceinline__ int wslot(int r) { return ((r % kWarpSlots) + kWarpSlots) % kWarpSlots; }
+// ring slot of source row r (r >= -3); a mask when the ring size is a power of two
+__device__ __forceinline__ int wslot(int r) {
+    if constexpr ((kWarpSlots & (kWarpSlots - 1)) == 0) return r & (kWarpSlots - 1);
+    else return ((r % kWarpSlots) + kWarpSlots) % kWarpSlots;
+}
+
+// One source row of a strip is staged by up to 13 one-dimensional bulk copies (the 9
+// population rows, then phi, phi(t+1), F^B_x, F^B_y where the step reads them). Lane
+// i issues copy i, so a row costs the warp a handful of instructions; lane 0 first
+// arms the slot's mbarrier with the row's total byte count.
+struct RowCopy {
+    const char* src = nullptr;   // this lane's source at row 0
+    uint32_t pitch = 0;          // bytes per source row
+    uint32_t dst = 0;            // shared address of this lane's destination in slot 0
+    uint32_t stride = 0;         // bytes between ring slots
+    uint32_t bytes = 0;          // bytes of this lane's copy (0: none)
+    uint32_t tx = 0;             // bytes of the whole row (every lane)
+    uint32_t bar0 = 0;           // shared address of the slot-0 mbarrier
+
+    // all lanes: stage global row gr into ring slot s
+    __device__ __forceinline__ void issue(int lane, int s, int gr) const {
+        const uint32_t b = bar0 + 8u * (uint32_t)s;
+        if (lane == 0) mbar_expect_tx_at(b, tx);
+        __syncwarp();
+        if (bytes) bulk_g2s_at(dst + (uint32_t)s * stride, src + (long long)gr * (long long)pitch, bytes, b);
+    }
+};
 
 template <typename S>
 struct WarpCtx {
@@ -62,6 +88,8 @@ struct WarpCtx {
     bool aborted;
     bool fast_strip;
     int fast_lo, fast_hi;
+    RowCopy cp;
+    bool st_pair;              // this lane stores its pair (lanes 1..30, first column inside)
 
     __device__ __forceinline__ uint64_t* bar(int r) const { return reinterpret_cast<uint64_t*>(smem) + wslot(r); }
     __device__ __forceinline__ const S* pop(int r) const {
@@ -92,28 +120,36 @@ struct WarpCtx {
         }
     }
 
-    // lane 0: load source row r into its slot
+    // this lane's part of staging a source row (see RowCopy)
+    __device__ __forceinline__ void setup_copies() {
+        const uint32_t base = smem_u32(smem);
+        cp.bar0 = base;
+        cp.tx = 9u * (uint32_t)(ww * (int)sizeof(S)) + (uint32_t)p.nR * (uint32_t)(ww * 4);
+        if (lane < 9) {
+            cp.src = reinterpret_cast<const char*>(reinterpret_cast<const S*>(p.src) + lane * p.plane + wsp);
+            cp.pitch = (uint32_t)(p.P * (int)sizeof(S));
+            cp.dst = base + (uint32_t)(L::kPop + lane * L::kPopRow);
+            cp.stride = (uint32_t)L::kPopSlot;
+            cp.bytes = (uint32_t)(ww * (int)sizeof(S));
+        } else if (lane < 9 + p.nR) {
+            // aux rows in the order phi, phi(t+1) (unsteady), F^B_x, F^B_y (force field)
+            const int k = lane - 9;
+            const float* a = p.phi;
+            if (k == 1 && p.unsteady) a = p.phin;
+            else if (k >= 1) a = p.fb + (k - (p.unsteady ? 2 : 1)) * p.plane;
+            cp.src = reinterpret_cast<const char*>(a + wsp);
+            cp.pitch = (uint32_t)(p.P * 4);
+            cp.dst = base + (uint32_t)(L::kAux + k * L::kAuxRow);
+            cp.stride = (uint32_t)(p.nR * L::kAuxRow);
+            cp.bytes = (uint32_t)(ww * 4);
+        }
+    }
+    // all lanes: load source row r into its slot
     __device__ __forceinline__ void issue(int r) {
         issued = r;
-        uint64_t* b = bar(r);
         int gr = r;
         if (!p.wall_y) { gr %= p.ny; if (gr < 0) gr += p.ny; }
-        const uint32_t bs = (uint32_t)(ww * (int)sizeof(S));
-        const uint32_t br = (uint32_t)(ww * 4);
-        mbar_expect_tx(b, 9u * bs + (uint32_t)p.nR * br);
-        const long long off = (long long)gr * p.P + wsp;
-        const S* src = reinterpret_cast<const S*>(p.src) + off;
-        unsigned char* ps = smem + L::kPop + wslot(r) * L::kPopSlot;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) bulk_g2s(ps + i * L::kPopRow, src + i * p.plane, bs, b);
-        float* rr = reinterpret_cast<float*>(smem + L::kAux) + wslot(r) * p.nR * L::WW;
-        int k = 0;
-        bulk_g2s(rr + (k++) * L::WW, p.phi + off, br, b);
-        if (p.unsteady) bulk_g2s(rr + (k++) * L::WW, p.phin + off, br, b);
-        if (p.has_fb) {
-            bulk_g2s(rr + (k++) * L::WW, p.fb + off, br, b);
-            bulk_g2s(rr + (k++) * L::WW, p.fb + p.plane + off, br, b);
-        }
+        cp.issue(lane, wslot(r), gr);
     }
     __device__ __forceinline__ void wait_upto(int r) {
         r = min(r, rhi);
@@ -310,35 +346,17 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     fo[8] = t68 + smm;
 
     const V2 r0 = fma2(p.rest.rho0, phin, bc(-p.rest.k59));
-    S* row = reinterpret_cast<S*>(p.dst) + (long long)p3 * p.P + kPadCols;
-    const int xa0 = c.xa;
-    const bool va = lane_ok && xa0 < p.nx, vb = lane_ok && xa0 + 1 < p.nx;
-    if (va && vb) {
-        S* cell = row + xa0;
+    // one 2-wide store per population for every lane whose first column is inside
+    // the lattice; the second column may then be the first ghost column, which the
+    // ghost refresh after the step overwrites (the one-warp kernels leave all ghost
+    // columns to ghost_fill_kernel, so the row loop holds no edge code)
+    if (lane_ok) {
+        S* cell = reinterpret_cast<S*>(p.dst) + (long long)p3 * p.P + kPadCols + c.xa;
         IO::st(cell, sizeof(S) == 4 ? fo[0] : p.scale * (fo[0] - r0));
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const V2 ri = bc(i <= 4 ? p.rest.ax : p.rest.dg);
             IO::st(cell + i * p.plane, sizeof(S) == 4 ? fo[i] : p.scale * (fo[i] - ri));
-        }
-    } else if (va) {
-        S* cell = row + xa0;
-        cell[0] = IO::enc1(fo[0].v.x, r0.v.x, p.scale);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) cell[i * p.plane] = IO::enc1(fo[i].v.x, i <= 4 ? p.rest.ax : p.rest.dg, p.scale);
-    }
-    for (int k = 0; k < 2; ++k) {
-        const int x = xa0 + k;
-        if (!lane_ok || x >= p.nx || !(x < kGhost || x >= p.nx - kGhost)) continue;
-        int g = x >= p.nx - kGhost ? x - p.nx : x + p.nx;
-        while (g >= -kGhost && g < p.nx + kGhost) {
-            S* gc = row + g;
-            gc[0] = IO::enc1(k ? fo[0].v.y : fo[0].v.x, k ? r0.v.y : r0.v.x, p.scale);
-#pragma unroll
-            for (int i = 1; i < 9; ++i)
-                gc[i * p.plane] = IO::enc1(k ? fo[i].v.y : fo[i].v.x, i <= 4 ? p.rest.ax : p.rest.dg, p.scale);
-            if (g < 0) { g -= p.nx; if (g < -kGhost) { g = x + p.nx; if (g >= p.nx + kGhost) break; } }
-            else { g += p.nx; if (g >= p.nx + kGhost) break; }
         }
     }
 }
@@ -351,17 +369,16 @@ template <typename S, typename Ctx>
 __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
     const int lane = c.lane, y0 = c.y0, y1 = c.y1;
     PRow s0, s1, s2;
-    auto iter = [&](PRow& An, PRow& Bs, PRow& Cs, const int p1) -> bool {
+    auto iter = [&](PRow& An, PRow& Bs, PRow& Cs, const int p1) {
         const int p2 = p1 - 1, p3 = p1 - 2;
         // the slot of row p1-3 is no longer read: refill it with row p1-3+kWarpSlots
         __syncwarp();
-        if (lane == 0 && p1 + kWarpSlots - 3 <= c.rhi && p1 + kWarpSlots - 3 >= c.rlo) {
+        if (p1 + kWarpSlots - 3 <= c.rhi && p1 + kWarpSlots - 3 >= c.rlo) {
             fence_proxy_async();
             c.issue(p1 + kWarpSlots - 3);
         }
         c.wait_upto(p1 + 1);
-        if (__any_sync(0xffffffffu, c.aborted)) return false;
-        const bool lane_ok = lane >= 1 && lane < 31;
+        const bool lane_ok = c.st_pair;
         if (c.fast_strip && p3 >= c.fast_lo && p1 <= c.fast_hi) {
             // interior row: one branch-free block, so the collision of row p3 overlaps
             // the pulls and shuffles of rows p1, p2
@@ -371,7 +388,7 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
             An.wr = fma2(4.f, An.rho, rpair(An.rho, r) + lpair(An.rho, l));
             warp_phase2<S, true>(c, An, Bs, Cs, p2);
             warp_phase3<S, true>(c, An, Bs, Cs, p3, lane_ok);
-            return true;
+            return;
         }
         const bool ph1 = (p1 <= y1 + 1) && c.row_valid(p1);
         if (ph1) {
@@ -384,16 +401,18 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
         if (ph2) warp_phase2<S, false>(c, An, Bs, Cs, p2);
         const bool ph3 = (p3 >= y0) && (p3 < y1);
         if (ph3) warp_phase3<S, false>(c, An, Bs, Cs, p3, lane_ok);
-        return true;
     };
 
     const int n_it = (y1 + 1) - (y0 - 2) + 1;
     bool ok = true;
     for (int it = 0; it < n_it && ok; it += 3) {
         const int p1 = y0 - 2 + it;
-        ok = iter(s0, s2, s1, p1);
-        if (ok && it + 1 < n_it) ok = iter(s1, s0, s2, p1 + 1);
-        if (ok && it + 2 < n_it) ok = iter(s2, s1, s0, p1 + 2);
+        iter(s0, s2, s1, p1);
+        if (it + 1 < n_it) iter(s1, s0, s2, p1 + 1);
+        if (it + 2 < n_it) iter(s2, s1, s0, p1 + 2);
+        // a timed-out wait (bounded, flagged by wait_upto) ends the strip after
+        // this group of three rows
+        ok = !__any_sync(0xffffffffu, c.aborted);
     }
     __syncwarp();
     return ok;
@@ -414,6 +433,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
     c.xa = x0 - 2 + 2 * lane;
     c.sa = kPadCols + c.xa - c.wsp;
+    c.st_pair = lane >= 1 && lane < 31 && c.xa < p.nx;
     c.rlo = y0 - 3;
     c.rhi = y1 + 2;
     if (p.wall_y) { c.rlo = max(c.rlo, 0); c.rhi = min(c.rhi, p.ny - 1); }
@@ -424,11 +444,13 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     c.fast_lo = p.wall_y ? max(y0, 1) : y0;                 // lowest phase-3 row
     c.fast_hi = p.wall_y ? min(y1 + 1, p.ny - 2) : y1 + 1;  // highest phase-1 row
 
+    c.setup_copies();
     if (lane == 0) {
         for (int k = 0; k < kWarpSlots; ++k) mbar_init(reinterpret_cast<uint64_t*>(smem) + k, 1);
         fence_mbar_init();
-        for (int r = c.rlo; r <= min(y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
     }
+    __syncwarp();
+    for (int r = c.rlo; r <= min(y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
     __syncwarp();
     warp_run_strip<S>(c);
     if (lane == 0) {
