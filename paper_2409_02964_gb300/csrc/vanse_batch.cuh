@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         fence_proxy_async();
         for (int r = c.rlo; r <= min(c.y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
         __syncwarp();
-        const bool ok = warp_run_strip<S>(c);
+        const bool ok = warp_run_strip<S, true>(c);
         phase = c.phase;
         if (!ok) {
             if (lane == 0)
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     c.setup_copies();
     for (int r = c.rlo; r <= min(c.y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
     __syncwarp();
-    const bool ok = warp_run_strip<S>(c);
+    const bool ok = warp_run_strip<S, true>(c);
     if (!ok && lane == 0)
         for (int r = c.waited + 1; r <= c.issued; ++r) {
             const int s = wslot(r);

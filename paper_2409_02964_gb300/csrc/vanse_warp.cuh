@@ -365,10 +365,16 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
 // staged rows (issue / wait_upto / pop), the per-cell sources (phi2, phin2,
 // add_field_force, row_setup), the strip (y0, y1, source rows rlo .. rhi) and which
 // rows may take the branch-free path (fast_strip, fast_lo, fast_hi).
-template <typename S, typename Ctx>
+//
+// ONLY_FAST: every row takes the branch-free path, including the first four rows of
+// the strip, whose phase-2/3 work on rows below y0 reads row states no phase 1 has
+// filled; those results feed only phase 3 of rows below y0, which store nothing.
+// Valid for strips whose staged rows y0-3 .. y1+2 hold no wall row and whose sources
+// need no per-cell field handling (the caller checks).
+template <typename S, bool ONLY_FAST, typename Ctx>
 __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
     const int lane = c.lane, y0 = c.y0, y1 = c.y1;
-    PRow s0, s1, s2;
+    PRow s0{}, s1{}, s2{};
     auto iter = [&](PRow& An, PRow& Bs, PRow& Cs, const int p1) {
         const int p2 = p1 - 1, p3 = p1 - 2;
         // the slot of row p1-3 is no longer read: refill it with row p1-3+kWarpSlots
@@ -379,6 +385,15 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
         }
         c.wait_upto(p1 + 1);
         const bool lane_ok = c.st_pair;
+        if constexpr (ONLY_FAST) {
+            warp_phase1<S, true>(c, An, p1);
+            const float l = left_of(An.rho), r = right_of(An.rho);
+            An.dr = rpair(An.rho, r) - lpair(An.rho, l);
+            An.wr = fma2(4.f, An.rho, rpair(An.rho, r) + lpair(An.rho, l));
+            warp_phase2<S, true>(c, An, Bs, Cs, p2);
+            warp_phase3<S, true>(c, An, Bs, Cs, p3, lane_ok && p3 >= y0);
+            return;
+        }
         if (c.fast_strip && p3 >= c.fast_lo && p1 <= c.fast_hi) {
             // interior row: one branch-free block, so the collision of row p3 overlaps
             // the pulls and shuffles of rows p1, p2
@@ -452,7 +467,9 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     __syncwarp();
     for (int r = c.rlo; r <= min(y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
     __syncwarp();
-    warp_run_strip<S>(c);
+    // strips that stage no wall row run the loop that holds only the branch-free path
+    if (c.fast_strip && (!p.wall_y || (y0 >= 3 && y1 <= p.ny - 3))) warp_run_strip<S, true>(c);
+    else warp_run_strip<S, false>(c);
     if (lane == 0) {
         // every issued row is waited for before the CTA exits (bounded)
         for (int r = c.waited + 1; r <= c.issued; ++r) mbar_wait_bounded(c.bar(r), c.parity(r), kWaitTries);
