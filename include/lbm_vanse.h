@@ -234,6 +234,47 @@ long long lbm_vanse_batch_step_count(lbm_vanse_batch_t b);
 const char* lbm_vanse_batch_last_error(lbm_vanse_batch_t b);
 void lbm_vanse_batch_destroy(lbm_vanse_batch_t b);
 
+/* ------------------------------------------------------------------------------
+ * Gradient with respect to the void fraction (discrete adjoint, FP64).
+ *
+ * Problem: steady phi(x) on the lattice of p (x periodic, y as p->bc_y; bc_x must
+ * be periodic); body force F^B = phi (gx, gy) (the Eq. 6 forcing of Sec. 3.1);
+ * initial populations f(0) = f^eq(rho = 1, u = 0, phi) - F_i/2 (Eq. 14, 6); then
+ * nsteps steps of Eq. (16) with streaming. After step n the objective samples
+ *   O(n) = sum over y of (phi rho u_x)(x_out, y) = sum_y (j_x + F_x / 2)(x_out, y)
+ * (Eq. 7), and J = sum of O(n) over n = nsteps - avg_steps + 1 .. nsteps divided by
+ * avg_steps * ny: the mean outlet x-momentum over the last avg_steps steps.
+ * dJ/dphi(x) is the exact derivative of this discrete J (every path by which phi
+ * enters: Eq. 7 rho, Eq. 13 F^p, X = kappa / phi in Eq. 18 and Eq. 20, F^B and
+ * f(0)), computed by a hand-written adjoint of the step run backwards in time. The
+ * forward pass stores a checkpoint every checkpoint_every steps; the backward pass
+ * recomputes one segment at a time, holding its states. Everything runs in FP64 on
+ * the stream given, whatever p->storage says. The paper has no adjoint; this is the
+ * differentiable-design use of its method. */
+typedef struct {
+    int nsteps;            /* >= 1 */
+    int avg_steps;         /* 1 .. nsteps */
+    int checkpoint_every;  /* >= 1 */
+    int x_out;             /* outlet column, 0 .. nx - 1 */
+    double gx, gy;         /* F^B = phi (gx, gy) */
+} lbm_vanse_adjoint_params;
+
+typedef struct {
+    double forward_ms;     /* device time of the forward pass (with checkpoints) */
+    double backward_ms;    /* device time of the backward pass (with recomputation) */
+    long long device_bytes;  /* device memory the call held at its peak */
+} lbm_vanse_adjoint_stats;
+
+/* phi: [ny][nx] doubles, on the device (on_device = 1) or host; read only. J
+ * receives the objective (host pointer). dJdphi: [ny][nx] doubles, device or host
+ * like phi, or NULL for the objective alone (no backward pass). stats may be NULL.
+ * The call allocates its own device memory on cuda_stream and frees it before it
+ * returns; it synchronises the stream. Errors: LBM_ERR_ARG (a bad parameter or
+ * NULL), LBM_ERR_OOM, LBM_ERR_CUDA; the message is in lbm_vanse_last_error(NULL). */
+lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, const lbm_vanse_adjoint_params* a,
+                                          const double* phi, int on_device, void* cuda_stream, double* J,
+                                          double* dJdphi, lbm_vanse_adjoint_stats* stats);
+
 /* Synchronise the stream and report any deferred kernel error (LBM_ERR_TIMEOUT
  * if a bounded wait gave up, LBM_ERR_CUDA for a launch/runtime error). */
 lbm_status lbm_vanse_sync(lbm_vanse_t h);

@@ -6,7 +6,9 @@ equations (MRTLB-VANSE, arXiv:2409.02964).
 ``Batch`` (many independent lattices) are thin handles over it. The computation runs only in the CUDA library (``liblbm_vanse.so``).
 """
 from . import build, capi  # noqa: F401
+from .adjoint import Channel, OutletMomentum, outlet_momentum  # noqa: F401
 from .batch import Batch, BatchLattice  # noqa: F401
 from .lattice import Lattice, LbmError  # noqa: F401
 
-__all__ = ["Batch", "BatchLattice", "Lattice", "LbmError", "build", "capi"]
+__all__ = ["Batch", "BatchLattice", "Channel", "Lattice", "LbmError", "OutletMomentum", "build", "capi",
+           "outlet_momentum"]

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_vanse.so")
 SOURCES = ["lbm_vanse.cu"]
 HEADERS = ["vanse_common.cuh", "vanse_step.cuh", "vanse_aux.cuh", "vanse_pair.cuh", "vanse_warp.cuh",
-           "vanse_batch.cuh", "mms_force.cuh"]
+           "vanse_batch.cuh", "mms_force.cuh", "vanse_adjoint.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -30,6 +30,7 @@ EXPORTS = [
     "lbm_vanse_batch_step", "lbm_vanse_batch_step_each", "lbm_vanse_batch_autotune",
     "lbm_vanse_batch_velocity_error", "lbm_vanse_batch_get_populations", "lbm_vanse_batch_cells",
     "lbm_vanse_batch_step_count", "lbm_vanse_batch_last_error", "lbm_vanse_batch_destroy",
+    "lbm_vanse_outlet_momentum_grad",
 ]
 
 
@@ -61,6 +62,18 @@ class lbm_vanse_batch_params(ctypes.Structure):
         ("kappa", ctypes.c_double), ("rho0", ctypes.c_double), ("phi0", ctypes.c_double),
         ("strip_rows", ctypes.c_int), ("eager", ctypes.c_int),
     ]
+
+
+class lbm_vanse_adjoint_params(ctypes.Structure):
+    _fields_ = [
+        ("nsteps", ctypes.c_int), ("avg_steps", ctypes.c_int), ("checkpoint_every", ctypes.c_int),
+        ("x_out", ctypes.c_int), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+    ]
+
+
+class lbm_vanse_adjoint_stats(ctypes.Structure):
+    _fields_ = [("forward_ms", ctypes.c_double), ("backward_ms", ctypes.c_double),
+                ("device_bytes", ctypes.c_longlong)]
 
 
 _lib = None
@@ -114,6 +127,8 @@ def load(path: str | None = None):
         "lbm_vanse_batch_step_count": (ctypes.c_longlong, [vp]),
         "lbm_vanse_batch_last_error": (ctypes.c_char_p, [vp]),
         "lbm_vanse_batch_destroy": (None, [vp]),
+        "lbm_vanse_outlet_momentum_grad": (i, [pp, ctypes.POINTER(lbm_vanse_adjoint_params), vp, i, vp, dp, vp,
+                                               ctypes.POINTER(lbm_vanse_adjoint_stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "lbm_vanse.h"
+#include "vanse_adjoint.cuh"
 #include "vanse_aux.cuh"
 #include "vanse_batch.cuh"
 #include "vanse_pair.cuh"
@@ -1257,4 +1258,171 @@ extern "C" void lbm_vanse_batch_destroy(lbm_vanse_batch_t b) {
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete b;
+}
+
+// ============================================================================ adjoint
+
+namespace {
+
+struct AdjBuffers {
+    std::vector<void*> held;
+    long long bytes = 0;
+    cudaStream_t st = nullptr;
+    cudaError_t err = cudaSuccess;
+    double* get(long long n) {
+        void* q = nullptr;
+        if (err == cudaSuccess) err = cudaMallocAsync(&q, (size_t)n * sizeof(double), st);
+        if (err != cudaSuccess) return nullptr;
+        held.push_back(q);
+        bytes += n * (long long)sizeof(double);
+        return (double*)q;
+    }
+    ~AdjBuffers() {
+        for (void* q : held) cudaFreeAsync(q, st);
+        cudaStreamSynchronize(st);
+    }
+};
+
+struct AdjEvents {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~AdjEvents() {
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+}  // namespace
+
+extern "C" lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, const lbm_vanse_adjoint_params* a,
+                                                     const double* phi, int on_device, void* cuda_stream, double* J,
+                                                     double* dJdphi, lbm_vanse_adjoint_stats* stats) {
+    if (!p || !a || !phi || !J) return fail(nullptr, LBM_ERR_ARG, "p, a, phi and J must not be NULL");
+    if (p->nx < 1 || p->ny < 1 || p->nx > 65536 || p->ny > 65536) return fail(nullptr, LBM_ERR_ARG, "bad lattice size");
+    if (!(p->tau_nu > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau_nu must exceed 1/2");
+    if (!rate_ok(p->s_eps) || !rate_ok(p->s_q) || (p->s_e > 0 && !rate_ok(p->s_e)))
+        return fail(nullptr, LBM_ERR_ARG, "rates must lie in (0, 2)");
+    if (p->bc_x != LBM_BC_PERIODIC) return fail(nullptr, LBM_ERR_ARG, "bc_x must be periodic");
+    if (a->nsteps < 1 || a->avg_steps < 1 || a->avg_steps > a->nsteps || a->checkpoint_every < 1)
+        return fail(nullptr, LBM_ERR_ARG, "need nsteps >= 1, 1 <= avg_steps <= nsteps, checkpoint_every >= 1");
+    if (a->x_out < 0 || a->x_out >= p->nx) return fail(nullptr, LBM_ERR_ARG, "x_out out of range");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const long long N = (long long)p->nx * p->ny, N9 = 9 * N;
+    const double nu = (p->tau_nu - 0.5) / 3.0;
+    adj::Params P;
+    P.nx = p->nx;
+    P.ny = p->ny;
+    P.N = N;
+    P.wall_y = p->bc_y == LBM_BC_BOUNCEBACK;
+    P.model_b = p->model_b;
+    P.kappa = p->kappa;
+    P.gx = a->gx;
+    P.gy = a->gy;
+    P.s_e = p->s_e > 0 ? p->s_e : 1.0 / (nu + 0.5);   // nu_e = nu / 3
+    P.s_eps = p->s_eps;
+    P.s_q = p->s_q;
+    P.s_nu = 1.0 / p->tau_nu;
+    P.x_out = a->x_out;
+    const int T = a->nsteps, M = a->avg_steps, K = a->checkpoint_every;
+    const int nck = (T - 1) / K + 1;
+    const bool want_grad = dJdphi != nullptr;
+
+    AdjBuffers B;
+    B.st = st;
+    double* d_phi = B.get(N);
+    double* fa = B.get(N9);
+    double* fb = B.get(N9);
+    double* ck = B.get((long long)nck * N9);
+    adj::Fields F;
+    F.s = B.get(N); F.rho = B.get(N); F.ux = B.get(N); F.uy = B.get(N); F.Fx = B.get(N); F.Fy = B.get(N);
+    F.drx = B.get(N); F.dry = B.get(N); F.fld = B.get(6 * N);
+    double* acc = B.get(1);
+    double *seg = nullptr, *lam = nullptr, *lam2 = nullptr, *gphi = nullptr;
+    adj::Adj A;
+    if (want_grad) {
+        seg = B.get((long long)std::min(K, T) * N9);
+        lam = B.get(N9);
+        lam2 = B.get(N9);
+        gphi = B.get(N);
+        A.lm = B.get(N9);
+        A.lux = B.get(N); A.luy = B.get(N); A.lFx = B.get(N); A.lFy = B.get(N); A.lrho = B.get(N);
+        A.lg = B.get(8 * N);
+        A.ldrx = B.get(N); A.ldry = B.get(N);
+    }
+    if (B.err != cudaSuccess)
+        return fail(nullptr, B.err == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "adjoint buffers (%lld bytes): %s",
+                    B.bytes, cudaGetErrorString(B.err));
+#define ACK(call)                                                                                              \
+    do {                                                                                                       \
+        cudaError_t e_ = (call);                                                                               \
+        if (e_ != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+    ACK(cudaMemcpyAsync(d_phi, phi, N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    ACK(cudaMemsetAsync(acc, 0, sizeof(double), st));
+    const int nb = aux_blocks(N), nt = kAuxThreads;
+    AdjEvents ev;
+    for (cudaEvent_t& x : ev.e) ACK(cudaEventCreate(&x));
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1], e2 = ev.e[2];
+    ACK(cudaEventRecord(e0, st));
+    auto fwd_fields = [&](const double* f) {
+        adj::adj_fwd_rho<<<nb, nt, 0, st>>>(P, f, d_phi, F);
+        adj::adj_fwd_u<<<nb, nt, 0, st>>>(P, f, d_phi, F);
+    };
+    auto fwd_step = [&](const double* f, double* fn) {
+        fwd_fields(f);
+        adj::adj_fwd_collide<<<nb, nt, 0, st>>>(P, f, d_phi, F, fn);
+    };
+    // forward: f(0), checkpoints every K steps, objective over the last M steps
+    adj::adj_init_kernel<<<nb, nt, 0, st>>>(P, d_phi, fa);
+    double *cur = fa, *nxt = fb;
+    for (int n = 0; n < T; ++n) {
+        if (n % K == 0) ACK(cudaMemcpyAsync(ck + (long long)(n / K) * N9, cur, N9 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        fwd_step(cur, nxt);
+        std::swap(cur, nxt);
+        if (n + 1 > T - M) {
+            fwd_fields(cur);
+            adj::adj_objective<<<1, 256, 0, st>>>(P, cur, F, acc);
+        }
+    }
+    ACK(cudaGetLastError());
+    ACK(cudaEventRecord(e1, st));
+    double Jsum = 0.0;
+    ACK(cudaMemcpyAsync(&Jsum, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    const double wgt = 1.0 / ((double)M * p->ny);
+    if (want_grad) {
+        ACK(cudaMemsetAsync(gphi, 0, N * sizeof(double), st));
+        // n = T: only the objective (lambda(T+1) = 0); cur holds f(T)
+        fwd_fields(cur);
+        adj::adj_bwd_collide<<<nb, nt, 0, st>>>(P, cur, d_phi, F, nullptr, A, gphi);
+        adj::adj_bwd_u<<<nb, nt, 0, st>>>(P, cur, d_phi, F, A, wgt, gphi);
+        adj::adj_bwd_rho<<<nb, nt, 0, st>>>(P, d_phi, F, A, lam, gphi);
+        for (int k = nck - 1; k >= 0; --k) {
+            const int n0 = k * K, n1 = std::min(n0 + K, T);
+            ACK(cudaMemcpyAsync(seg, ck + (long long)k * N9, N9 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            for (int j = 1; j < n1 - n0; ++j) fwd_step(seg + (long long)(j - 1) * N9, seg + (long long)j * N9);
+            for (int n = n1 - 1; n >= n0; --n) {
+                const double* fn = seg + (long long)(n - n0) * N9;
+                fwd_fields(fn);
+                adj::adj_bwd_collide<<<nb, nt, 0, st>>>(P, fn, d_phi, F, lam, A, gphi);
+                adj::adj_bwd_u<<<nb, nt, 0, st>>>(P, fn, d_phi, F, A, n > T - M ? wgt : 0.0, gphi);
+                adj::adj_bwd_rho<<<nb, nt, 0, st>>>(P, d_phi, F, A, lam2, gphi);
+                std::swap(lam, lam2);
+            }
+        }
+        adj::adj_bwd_init<<<nb, nt, 0, st>>>(P, lam, gphi);
+        ACK(cudaGetLastError());
+        ACK(cudaMemcpyAsync(dJdphi, gphi, N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    ACK(cudaEventRecord(e2, st));
+    ACK(cudaStreamSynchronize(st));
+    *J = Jsum * wgt;
+    if (stats) {
+        float f_ms = 0.f, b_ms = 0.f;
+        cudaEventElapsedTime(&f_ms, e0, e1);
+        cudaEventElapsedTime(&b_ms, e1, e2);
+        stats->forward_ms = f_ms;
+        stats->backward_ms = want_grad ? b_ms : 0.0;
+        stats->device_bytes = B.bytes;
+    }
+#undef ACK
+    return LBM_OK;
 }
