@@ -225,6 +225,30 @@ def batch_run(steps: int = 2000, count: int = 512, each_steps: int = 200):
     return out
 
 
+ADJOINT_WORKLOAD = ("1024x1024 porous channel (the 4096^2 channel recipe regenerated at 1024^2), walls, "
+                    "tau=0.6, s_e=s_eps=s_q=1.2, kappa=0.5, g_x=1e-6; J = mean outlet phi rho u_x over the last "
+                    "100 of 4000 steps from rest; dJ/dphi for every cell; FP64; checkpoint every 200 steps")
+
+
+def adjoint_run(n: int = 1024, nsteps: int = 4000, avg: int = 100, ckpt: int = 200):
+    """The differentiation workload: J and dJ/dphi through the C ABI; forward and
+    backward device time from CUDA events inside the call."""
+    import paper_2409_02964_gb300 as P
+    from synth import fields
+    ch = P.Channel(nx=n, ny=n, nsteps=nsteps, avg_steps=avg, checkpoint_every=ckpt)
+    phi = fields.channel_phi(n, n)
+    P.outlet_momentum(phi[:64, :64], P.Channel(nx=64, ny=64, nsteps=4, avg_steps=2, checkpoint_every=2))  # warm-up
+    J, g, st = P.outlet_momentum(phi, ch)
+    fwd_s, bwd_s = st["forward_ms"] / 1e3, st["backward_ms"] / 1e3
+    lups = n * n * nsteps
+    ga = g.abs()
+    return {"workload": ADJOINT_WORKLOAD, "J": J, "max_abs_grad": float(ga.max()),
+            "forward_s": round(fwd_s, 3), "backward_s": round(bwd_s, 3),
+            "forward_MLUPS": round(lups / fwd_s / 1e6, 1),
+            "forward_backward_MLUPS": round(lups / (fwd_s + bwd_s) / 1e6, 1),
+            "device_bytes": st["device_bytes"], "dtype": "f64"}
+
+
 def oracle_rate(n_rows: int, nx: int, steps: int, threads: int):
     """FP64 oracle on a band of the channel: returns (MLUPS, seconds, cells)."""
     import oracle as O
@@ -301,6 +325,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="timed steps only (no e2e / variants / CPU baseline)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-lattice workload")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-lattice workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiation workload")
+    ap.add_argument("--adjoint-only", action="store_true", help="run only the differentiation workload")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=2000)
     args = ap.parse_args()
@@ -308,6 +334,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint_only:
+        print(json.dumps({"adjoint": adjoint_run()}), flush=True)
+        return 0
     if args.batch_only:
         print(json.dumps({"batch": batch_run(args.batch_steps, args.batch_count)}), flush=True)
         return 0
@@ -386,6 +415,8 @@ def main():
         out["variants"] = variants
         if not args.no_batch:
             out["batch"] = batch_run(args.batch_steps, args.batch_count)
+        if not args.no_adjoint:
+            out["adjoint"] = adjoint_run()
         out["cpu_baseline"] = cpu_baseline(args.n)
     if rank == 0:
         print(json.dumps(out), flush=True)
