@@ -40,6 +40,9 @@ class _Params(ctypes.Structure):
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
         ("model_b", ctypes.c_int),
         ("nthreads", ctypes.c_int),
+        ("eq_order", ctypes.c_int),
+        ("drag_d0", ctypes.c_double), ("drag_d1", ctypes.c_double),
+        ("us_x", ctypes.c_double), ("us_y", ctypes.c_double),
     ]
 
 
@@ -58,11 +61,16 @@ class Params:
     bc_y: int = 0
     model_b: int = 0
     nthreads: int = 1
+    eq_order: int = 3      # 2: App. B equilibrium and penalty
+    drag_d0: float = 0.0   # F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi))
+    drag_d1: float = 0.0
+    us_x: float = 0.0
+    us_y: float = 0.0
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, self.s_c, self.s_e, self.s_eps, self.s_q,
                        self.s_nu, self.kappa, self.bc_x, self.bc_y, self.model_b,
-                       self.nthreads)
+                       self.nthreads, self.eq_order, self.drag_d0, self.drag_d1, self.us_x, self.us_y)
 
 
 def build(force: bool = False, openmp: bool = True) -> str:
@@ -105,6 +113,9 @@ def lib():
         L.vo_meq.argtypes = [d, d, d, d, d, dp]
         L.vo_force_moments.argtypes = [d, d, d, d, dp]
         L.vo_penalty.argtypes = [d, d, d, dp, dp, dp, d, ctypes.c_int, dp]
+        L.vo_feq_order.argtypes = [ctypes.c_int, d, d, d, d, d, dp]
+        L.vo_meq_order.argtypes = [ctypes.c_int, d, d, d, d, d, dp]
+        L.vo_penalty_order.argtypes = [ctypes.c_int, d, d, d, dp, dp, dp, d, ctypes.c_int, dp]
         L.vo_gradient.argtypes = [pp, dp, ctypes.c_int, dp, dp]
         L.vo_macros.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp, dp]
         L.vo_step.argtypes = [pp, dp, dp, dp, dp, dp]
@@ -154,9 +165,10 @@ def moments(f):
     return m
 
 
-def feq(kappa, phi, rho, ux, uy):
+def feq(kappa, phi, rho, ux, uy, order=3):
+    """Eq. (14) (order 3) or Eq. (B1) (order 2)."""
     out = np.zeros(Q)
-    lib().vo_feq(kappa, phi, rho, ux, uy, _p(out))
+    lib().vo_feq_order(int(order), kappa, phi, rho, ux, uy, _p(out))
     return out
 
 
@@ -166,9 +178,10 @@ def guo_force(ux, uy, Fx, Fy):
     return out
 
 
-def meq(kappa, phi, rho, ux, uy):
+def meq(kappa, phi, rho, ux, uy, order=3):
+    """Eq. (18) (order 3) or Eq. (B2) (order 2)."""
     out = np.zeros(Q)
-    lib().vo_meq(kappa, phi, rho, ux, uy, _p(out))
+    lib().vo_meq_order(int(order), kappa, phi, rho, ux, uy, _p(out))
     return out
 
 
@@ -178,11 +191,12 @@ def force_moments(ux, uy, Fx, Fy):
     return out
 
 
-def penalty(kappa, phi, rho, dA, dB, dD, dtphi, model_b=0):
-    """Eq. (20). dX = (d_x X_x, d_y X_y, d_x X_y, d_y X_x) for X = rho u, u, phi rho u."""
+def penalty(kappa, phi, rho, dA, dB, dD, dtphi, model_b=0, order=3):
+    """Eq. (20) (order 3) or Eq. (B3) (order 2). dX = (d_x X_x, d_y X_y, d_x X_y, d_y X_x)
+    for X = rho u, u, phi rho u."""
     out = np.zeros(Q)
-    lib().vo_penalty(kappa, phi, rho, _p(_f64(dA)), _p(_f64(dB)), _p(_f64(dD)), dtphi,
-                     int(model_b), _p(out))
+    lib().vo_penalty_order(int(order), kappa, phi, rho, _p(_f64(dA)), _p(_f64(dB)), _p(_f64(dD)), dtphi,
+                           int(model_b), _p(out))
     return out
 
 

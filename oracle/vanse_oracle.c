@@ -22,6 +22,11 @@
  *   vo_macros           Eq. (7), (13)       density, pressure-correction force, velocity
  *   vo_step             Eq. (16) + streaming (Sec. 2.3) + half-way bounce-back (Sec. 3.1)
  *   vo_init             f = f^eq - F_i/2    (the paper is silent; reading c7)
+ *   eq_order = 2        App. B: Eq. (B1) equilibrium, (B2) moments, (B3) penalty
+ *   drag_d0, drag_d1,   a body force linear in u, F^B += -beta (u - u_s) with
+ *   us_x, us_y          beta = phi^2 (d0 + d1 (1 - phi)): the Darcy term of Sec. 3.1
+ *                       (d0 = nu / k0) and the drag law of Eq. (23) (d1 = 1); u is
+ *                       solved implicitly from Eq. (7) (reading c8)
  *
  * Readings where the paper is silent or garbled (all listed in the design notes):
  *   - the relaxation "tau"s of the paper are rates (the diagonal of Gamma);
@@ -62,6 +67,8 @@ typedef struct {
     int bc_x, bc_y;    /* 0 = periodic, 1 = half-way bounce-back walls at both ends */
     int model_b;       /* 1: kappa - phi -> kappa - 1 in Eq. (13) and Eq. (20) */
     int nthreads;      /* OpenMP threads for the cell loops; <= 0 keeps the default */
+    int eq_order;      /* 3: Eq. (14), (18), (20) (default); 2: App. B, Eq. (B1)-(B3) */
+    double drag_d0, drag_d1, us_x, us_y;   /* linear drag, see the header */
 } vo_params;
 
 /* ---------------------------------------------------------------- Eq. (5) */
@@ -138,7 +145,7 @@ void vo_moments(const double* f, double* m)
 }
 
 /* ---------------------------------------------------------------- Eq. (14) */
-void vo_feq(double kappa, double phi, double rho, double ux, double uy, double* feq)
+void vo_feq_order(int order, double kappa, double phi, double rho, double ux, double uy, double* feq)
 {
     int e[Q][2];
     double w[Q];
@@ -152,10 +159,16 @@ void vo_feq(double kappa, double phi, double rho, double ux, double uy, double* 
     for (int i = 1; i < Q; ++i) {
         double eu = e[i][0] * ux + e[i][1] * uy;
         double ee = (double)(e[i][0] * e[i][0] + e[i][1] * e[i][1]);
-        double first = eu / cs2 * (1.0 + 0.5 * (X - 1.0) * (ee / cs2 - 4.0));
+        /* Eq. (14) adjusts the first-order term by X; Eq. (B1) keeps the plain one */
+        double first = order == 2 ? eu / cs2 : eu / cs2 * (1.0 + 0.5 * (X - 1.0) * (ee / cs2 - 4.0));
         double second = eu * eu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2);
         feq[i] = w[i] * (kappa * rho + phi * rho * (first + second));
     }
+}
+
+void vo_feq(double kappa, double phi, double rho, double ux, double uy, double* feq)
+{
+    vo_feq_order(3, kappa, phi, rho, ux, uy, feq);
 }
 
 /* ----------------------------------------------------------------- Eq. (6) */
@@ -174,7 +187,7 @@ void vo_guo_force(double ux, double uy, double Fx, double Fy, double* Fi)
 }
 
 /* ---------------------------------------------------------------- Eq. (18) */
-void vo_meq(double kappa, double phi, double rho, double ux, double uy, double* meq)
+void vo_meq_order(int order, double kappa, double phi, double rho, double ux, double uy, double* meq)
 {
     const double X = kappa / phi;
     const double pr = phi * rho;
@@ -183,11 +196,18 @@ void vo_meq(double kappa, double phi, double rho, double ux, double uy, double* 
     meq[1] = pr * (-4.0 + 3.0 * uu + 2.0 * X);
     meq[2] = pr * (4.0 - 3.0 * uu - 3.0 * X);
     meq[3] = pr * ux;
-    meq[4] = pr * (X - 2.0) * ux;
+    /* Eq. (18): (X - 2) on the energy fluxes; Eq. (B2): -1 */
+    const double qf = order == 2 ? -1.0 : (X - 2.0);
+    meq[4] = pr * qf * ux;
     meq[5] = pr * uy;
-    meq[6] = pr * (X - 2.0) * uy;
+    meq[6] = pr * qf * uy;
     meq[7] = pr * (ux * ux - uy * uy);
     meq[8] = pr * ux * uy;
+}
+
+void vo_meq(double kappa, double phi, double rho, double ux, double uy, double* meq)
+{
+    vo_meq_order(3, kappa, phi, rho, ux, uy, meq);
 }
 
 /* ---------------------------------------------------------------- Eq. (19) */
@@ -212,8 +232,8 @@ void vo_force_moments(double ux, double uy, double Fx, double Fy, double* S)
  * Model B (Sec. 2.3): every "kappa - phi" factor becomes "kappa - 1".
  * C is returned as the 9-vector (0, C_a, 0, 0, 0, 0, 0, C_b, C_c).
  */
-void vo_penalty(double kappa, double phi, double rho, const double* dA, const double* dB,
-                const double* dD, double dtphi, int model_b, double* C)
+void vo_penalty_order(int order, double kappa, double phi, double rho, const double* dA, const double* dB,
+                      const double* dD, double dtphi, int model_b, double* C)
 {
     const double X = kappa / phi;
     const double kp = model_b ? (kappa - 1.0) : (kappa - phi);
@@ -221,14 +241,28 @@ void vo_penalty(double kappa, double phi, double rho, const double* dA, const do
     const double divB = dB[0] + dB[1], difB = dB[0] - dB[1];
     const double crsB = dB[2] + dB[3];
     const double divD = dD[0] + dD[1], difD = dD[0] - dD[1];
-    const double Ca = -kappa * divA + 2.0 * kp * rho * divB + (3.0 - 2.0 * X) * divD
-                      - 2.0 * X * rho * dtphi;
-    const double Cb = -kappa * difA + (2.0 / 3.0) * kp * rho * difB + difD;
-    const double Cc = (1.0 / 3.0) * kp * rho * crsB;
+    double Ca, Cb, Cc;
+    if (order == 2) {
+        /* Eq. (B3) */
+        const double crsA = dA[2] + dA[3], crsD = dD[2] + dD[3];
+        Ca = -2.0 * kappa * divA + 2.0 * kp * rho * divB + (4.0 - 2.0 * X) * divD - 2.0 * X * rho * dtphi;
+        Cb = -(2.0 / 3.0) * kappa * difA + (2.0 / 3.0) * kp * rho * difB + (2.0 / 3.0) * difD;
+        Cc = -(kappa / 3.0) * crsA + (1.0 / 3.0) * kp * rho * crsB + (1.0 / 3.0) * crsD;
+    } else {
+        Ca = -kappa * divA + 2.0 * kp * rho * divB + (3.0 - 2.0 * X) * divD - 2.0 * X * rho * dtphi;
+        Cb = -kappa * difA + (2.0 / 3.0) * kp * rho * difB + difD;
+        Cc = (1.0 / 3.0) * kp * rho * crsB;
+    }
     for (int k = 0; k < Q; ++k) C[k] = 0.0;
     C[1] = Ca;
     C[7] = Cb;
     C[8] = Cc;
+}
+
+void vo_penalty(double kappa, double phi, double rho, const double* dA, const double* dB,
+                const double* dD, double dtphi, int model_b, double* C)
+{
+    vo_penalty_order(3, kappa, phi, rho, dA, dB, dD, dtphi, model_b, C);
 }
 
 /* --------------------------------------------------------- neighbour rule */
@@ -327,8 +361,15 @@ void vo_macros(const vo_params* p, const double* f, const double* phi, const dou
         const double kp = p->model_b ? (p->kappa - 1.0) : (p->kappa - phi[c]);
         double fx = kp * cs2 * gx[c] + (fb ? fb[c] : 0.0);
         double fy = kp * cs2 * gy[c] + (fb ? fb[N + c] : 0.0);
-        if (ux) ux[c] = (jx + 0.5 * fx) / s;
-        if (uy) uy[c] = (jy + 0.5 * fy) / s;
+        /* a drag -beta (u - u_s) in F makes Eq. (7) implicit in u; being linear it is
+         * solved exactly: u (sum f + beta / 2) = j + (F_rest + beta u_s) / 2 */
+        const double beta = phi[c] * phi[c] * (p->drag_d0 + p->drag_d1 * (1.0 - phi[c]));
+        const double vx = (jx + 0.5 * (fx + beta * p->us_x)) / (s + 0.5 * beta);
+        const double vy = (jy + 0.5 * (fy + beta * p->us_y)) / (s + 0.5 * beta);
+        fx -= beta * (vx - p->us_x);
+        fy -= beta * (vy - p->us_y);
+        if (ux) ux[c] = vx;
+        if (uy) uy[c] = vy;
         if (Fx) Fx[c] = fx;
         if (Fy) Fy[c] = fy;
     }
@@ -425,14 +466,14 @@ int vo_step(const vo_params* p, const double* f, double* f_new, const double* ph
         double fc[Q], m[Q], meq[Q], S[Q], C[Q], mp[Q], fp[Q];
         for (int i = 0; i < Q; ++i) fc[i] = f[i * N + c];
         vo_moments(fc, m);
-        vo_meq(kappa, phi_t[c], rho[c], ux[c], uy[c], meq);
+        vo_meq_order(p->eq_order, kappa, phi_t[c], rho[c], ux[c], uy[c], meq);
         vo_force_moments(ux[c], uy[c], Fx[c], Fy[c], S);
         /* derivative sets (d_x X_x, d_y X_y, d_x X_y, d_y X_x) */
         const double dA[4] = {grd[0 * N + c], grd[3 * N + c], grd[2 * N + c], grd[1 * N + c]};
         const double dB[4] = {grd[4 * N + c], grd[7 * N + c], grd[6 * N + c], grd[5 * N + c]};
         const double dD[4] = {grd[8 * N + c], grd[11 * N + c], grd[10 * N + c], grd[9 * N + c]};
         const double dtphi = phi_next ? (phi_next[c] - phi_t[c]) : 0.0;
-        vo_penalty(kappa, phi_t[c], rho[c], dA, dB, dD, dtphi, p->model_b, C);
+        vo_penalty_order(p->eq_order, kappa, phi_t[c], rho[c], dA, dB, dD, dtphi, p->model_b, C);
         for (int k = 0; k < Q; ++k)
             mp[k] = m[k] - G[k] * (m[k] - meq[k]) + (1.0 - 0.5 * G[k]) * (S[k] + C[k]);
         matvec((const double(*)[Q])Minv, mp, fp);
@@ -463,9 +504,10 @@ void vo_init(const vo_params* p, const double* rho, const double* ux, const doub
     for (size_t c = 0; c < N; ++c) {
         double feq[Q], Fi[Q];
         const double kp = p->model_b ? (p->kappa - 1.0) : (p->kappa - phi[c]);
-        const double fx = kp * cs2 * gx[c] + (fb ? fb[c] : 0.0);
-        const double fy = kp * cs2 * gy[c] + (fb ? fb[N + c] : 0.0);
-        vo_feq(p->kappa, phi[c], rho[c], ux[c], uy[c], feq);
+        const double beta = phi[c] * phi[c] * (p->drag_d0 + p->drag_d1 * (1.0 - phi[c]));
+        const double fx = kp * cs2 * gx[c] + (fb ? fb[c] : 0.0) - beta * (ux[c] - p->us_x);
+        const double fy = kp * cs2 * gy[c] + (fb ? fb[N + c] : 0.0) - beta * (uy[c] - p->us_y);
+        vo_feq_order(p->eq_order, p->kappa, phi[c], rho[c], ux[c], uy[c], feq);
         vo_guo_force(ux[c], uy[c], fx, fy, Fi);
         for (int i = 0; i < Q; ++i) f[i * N + c] = feq[i] - 0.5 * Fi[i];
     }

@@ -1,0 +1,171 @@
+"""Pins of the oracle's physics variants:
+
+App. B (eq_order = 2): the 2nd-order equilibrium (B1) against its printed moments
+(B2); the exact reduction to a textbook BGK with Guo forcing at phi = kappa (where
+(B3) vanishes and (B1) is the textbook equilibrium of density kappa rho); the bulk
+viscosity nu_e = nu/3 through sound damping at uniform phi != kappa (sensitive to
+the div(phi rho u) coefficient of C_a); second-order convergence on the
+spatiotemporal manufactured solution (sensitive to C_b and C_c).
+
+Linear drag F^B = phi G - beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi)), with u
+solved implicitly (reading c8): the Darcy-Brinkman channel of Eq. (21)-(22 I)
+against its analytic profile, converging at second order; the nonuniform particle
+flow of Eq. (23) (steady, u_s = 0) against u = G / (a phi); the momentum balance
+sum j(t+1) - sum j(t) = sum F(t) with the drag inside F.
+"""
+import numpy as np
+import pytest
+
+from synth import mms
+
+from test_oracle_step import _textbook_bgk_guo_step
+
+E = np.array([(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)])
+
+
+def test_appb_equilibrium_has_the_printed_moments(oracle_mod):
+    M = oracle_mod.M()
+    rng = np.random.default_rng(21)
+    for _ in range(50):
+        kappa, phi = rng.uniform(0.3, 1.0), rng.uniform(0.2, 1.0)
+        rho, ux, uy = rng.uniform(0.8, 1.2), rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1)
+        f = oracle_mod.feq(kappa, phi, rho, ux, uy, order=2)
+        m = oracle_mod.meq(kappa, phi, rho, ux, uy, order=2)
+        pr, X, uu = phi * rho, kappa / phi, ux * ux + uy * uy
+        printed = pr * np.array([1, -4 + 3 * uu + 2 * X, 4 - 3 * uu - 3 * X, ux, -ux, uy, -uy, ux * ux - uy * uy,
+                                 ux * uy])
+        assert np.abs(M @ f - m).max() < 1e-14
+        assert np.abs(m - printed).max() < 1e-14
+
+
+@pytest.mark.parametrize("wall_y", [0, 1])
+def test_appb_reduces_to_textbook_bgk_when_phi_equals_kappa(oracle_mod, wall_y):
+    ny, nx = 9, 11
+    kappa = 0.5
+    s = 1 / 0.7
+    p = oracle_mod.Params(nx=nx, ny=ny, s_nu=s, s_e=s, s_eps=s, s_q=s, s_c=s, kappa=kappa, bc_y=wall_y,
+                          eq_order=2)
+    rng = np.random.default_rng(12)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    phi = np.full((ny, nx), kappa)
+    rho = 1 + 0.01 * np.sin(2 * np.pi * x / nx) * np.cos(2 * np.pi * y / ny)
+    ux = 0.03 * np.cos(2 * np.pi * y / ny)
+    uy = 0.02 * np.sin(2 * np.pi * x / nx)
+    fb = rng.normal(size=(2, ny, nx)) * 1e-4
+    f = oracle_mod.init(p, rho, ux, uy, phi, fb)
+    g = f.copy()
+    for _ in range(25):
+        f = oracle_mod.step(p, f, phi, None, fb)
+        g = _textbook_bgk_guo_step(g, s, fb, wall_y)
+    assert np.abs(f - g).max() < 1e-14
+
+
+@pytest.mark.parametrize("phi0", [0.8, 0.35])
+def test_appb_sound_wave_damping_pins_bulk_viscosity(oracle_mod, phi0):
+    n, tau = 64, 0.8
+    nu = (tau - 0.5) / 3
+    p = oracle_mod.Params(nx=n, ny=1, **oracle_mod.rates_from_tau(tau), kappa=0.5, eq_order=2)
+    x = np.arange(n, dtype=float)[None, :]
+    k = 2 * np.pi / n
+    phi = np.full((1, n), phi0)
+    f = oracle_mod.init(p, 1 + 1e-4 * np.cos(k * x), np.zeros((1, n)), np.zeros((1, n)), phi)
+    amps, steps = [], [0, 400, 800, 1200]
+    for t in range(steps[-1] + 1):
+        if t in steps:
+            m = oracle_mod.macros(p, f, phi)
+            a_rho = 2 / n * np.sum((m["rho"] - 1) * np.cos(k * x))
+            a_u = 2 / n * np.sum(m["ux"] * np.sin(k * x))
+            amps.append(np.sqrt(a_rho ** 2 + 3 * a_u ** 2))
+        f = oracle_mod.step(p, f, phi)
+    rate = -np.polyfit(steps, np.log(amps), 1)[0]
+    assert abs(rate / ((2.0 / 3.0) * nu * k * k) - 1) < 0.05
+
+
+def _mms_error(oracle_mod, n, order):
+    M = mms.Config1.refined(n)
+    tau = 0.8
+    nu = (tau - 0.5) / 3
+    p = oracle_mod.Params(nx=n, ny=n, **oracle_mod.rates_from_tau(tau, s_eps=1.2, s_q=1.2), kappa=0.5,
+                          eq_order=order)
+    ux, uy = M.velocity(0)
+    f = oracle_mod.init(p, np.ones((n, n)), ux, uy, M.phi(0), M.force(0, nu))
+    nsteps = int(round(M.T))
+    phi_next = M.phi(0)
+    for t in range(nsteps):
+        phi_t, phi_next = phi_next, M.phi(t + 1)
+        f = oracle_mod.step(p, f, phi_t, phi_next, M.force(t, nu))
+    mac = oracle_mod.macros(p, f, M.phi(nsteps), M.force(nsteps, nu))
+    return mms.relative_l2(mac["ux"], mac["uy"], *M.velocity(nsteps))
+
+
+def test_appb_manufactured_solution_second_order_convergence(oracle_mod):
+    errs = [_mms_error(oracle_mod, n, 2) for n in (16, 32, 64)]
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(slopes > 1.85) and np.all(slopes < 2.15), (errs, slopes)
+    assert errs[-1] < 5e-3
+
+
+def _darcy_brinkman(oracle_mod, ny, phi0=0.5, tau=0.8, G=1e-6, da=1e-2, steps=8000):
+    nx = 3
+    nu = (tau - 0.5) / 3
+    k0 = da * ny * ny
+    p = oracle_mod.Params(nx=nx, ny=ny, **oracle_mod.rates_from_tau(tau, s_eps=1.2, s_q=1.2), kappa=0.5, bc_y=1,
+                          drag_d0=nu / k0)
+    phi = np.full((ny, nx), phi0)
+    fb = np.stack([phi * G, 0 * phi])
+    f = oracle_mod.init(p, np.ones((ny, nx)), 0 * phi, 0 * phi, phi, fb)
+    for _ in range(steps):
+        f = oracle_mod.step(p, f, phi, None, fb)
+    u = oracle_mod.macros(p, f, phi, fb)["ux"][:, 0]
+    y = np.arange(ny) + 0.5          # walls half-way: at y = 0 and y = H = ny
+    r = np.sqrt(phi0 / k0)
+    ua = G * k0 / (phi0 * nu) * (1 - np.cosh(r * (y - ny / 2)) / np.cosh(r * ny / 2))
+    return np.sqrt(np.sum((u - ua) ** 2) / np.sum(ua ** 2))
+
+
+def test_drag_darcy_brinkman_channel_matches_eq22(oracle_mod):
+    e16, e32 = _darcy_brinkman(oracle_mod, 16), _darcy_brinkman(oracle_mod, 32)
+    assert e32 < 2e-3
+    assert 3.3 < e16 / e32 < 4.7, (e16, e32)
+
+
+def _particle_flow(oracle_mod, L, a=0.3, G=1e-6, tau=0.8, steps=20000):
+    nx, ny = L, 3
+    p = oracle_mod.Params(nx=nx, ny=ny, **oracle_mod.rates_from_tau(tau, s_eps=1.2, s_q=1.2), kappa=0.5, drag_d1=1.0)
+    phi = np.tile(1 + a * (np.sin(2 * np.pi * np.arange(nx) / L) - 1), (ny, 1))
+    fb = np.stack([phi * G, 0 * phi])
+    f = oracle_mod.init(p, np.ones((ny, nx)), 0 * phi, 0 * phi, phi, fb)
+    for _ in range(steps):
+        f = oracle_mod.step(p, f, phi, None, fb)
+    u = oracle_mod.macros(p, f, phi, fb)["ux"][0]
+    ua = G / (a * phi[0])
+    return np.sqrt(np.sum((u - ua) ** 2) / np.sum(ua ** 2))
+
+
+def test_drag_nonuniform_particle_flow_matches_eq23(oracle_mod):
+    e50, e100 = _particle_flow(oracle_mod, 50), _particle_flow(oracle_mod, 100)
+    assert e100 < 5e-4
+    assert 3.3 < e50 / e100 < 4.7, (e50, e100)
+
+
+def test_drag_momentum_balance(oracle_mod):
+    nx, ny = 12, 9
+    rng = np.random.default_rng(31)
+    p = oracle_mod.Params(nx=nx, ny=ny, **oracle_mod.rates_from_tau(0.7), kappa=0.5, drag_d0=0.02, drag_d1=0.5,
+                          us_x=3e-3, us_y=-1e-3)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    phi = 0.6 + 0.2 * np.sin(2 * np.pi * x / nx) * np.cos(2 * np.pi * y / ny)
+    fb = rng.normal(size=(2, ny, nx)) * 1e-4
+    f = oracle_mod.init(p, 1 + 0.01 * np.cos(2 * np.pi * y / ny), 0.02 * np.cos(2 * np.pi * y / ny),
+                        0.01 * np.sin(2 * np.pi * x / nx), phi, fb)
+    for _ in range(5):
+        m = oracle_mod.macros(p, f, phi, fb)
+        j0 = np.array([np.sum(E[:, 0][:, None, None] * f), np.sum(E[:, 1][:, None, None] * f)])
+        f = oracle_mod.step(p, f, phi, None, fb)
+        j1 = np.array([np.sum(E[:, 0][:, None, None] * f), np.sum(E[:, 1][:, None, None] * f)])
+        dF = np.array([m["Fx"].sum(), m["Fy"].sum()])
+        assert np.abs(j1 - j0 - dF).max() < 1e-14
+    # the drag is inside F: u solves u sum f = j + F/2 with F evaluated at that u
+    m = oracle_mod.macros(p, f, phi, fb)
+    jx = np.einsum("i,iyx->yx", E[:, 0].astype(float), f)
+    assert np.abs(m["ux"] * f.sum(0) - (jx + 0.5 * m["Fx"])).max() < 1e-15
