@@ -120,11 +120,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def build_channel(n: int, storage: str, strip_rows: int = 0, kernel: int = 0):
+def build_channel(n: int, storage: str, strip_rows: int = 0, kernel: int = 0, eq_order: int = 3, drag=None):
     import paper_2409_02964_gb300 as P
     from synth import fields
     phi = fields.channel_phi(n, n)
-    lat = P.Lattice(n, n, TAU, bc_y="bounceback", storage=storage, strip_rows=strip_rows, kernel=kernel, **RATES)
+    lat = P.Lattice(n, n, TAU, bc_y="bounceback", storage=storage, strip_rows=strip_rows, kernel=kernel,
+                    eq_order=eq_order, **RATES)
+    if drag:
+        lat.set_drag(*drag)
     lat.set_void_fraction(phi)
     lat.set_body_force(G, 0.0)
     rho, ux, uy = fields.rest_fields(n, n)
@@ -170,6 +173,23 @@ BATCH_WORKLOAD = ("512 independent periodic lattices, n uniform over {32,48,...,
                   "tau ~ U[0.55,1.5], phi amplitude A ~ U[0.05,0.3], spatiotemporal manufactured solution "
                   "phi = 0.7 + A sin sin cos(2 pi t/T) with T = 1000 (n/64)^2, U0 = 0.01 (64/n), "
                   "s_e = s_eps = s_q = 1.2, FP32, 2000 steps each")
+
+
+def mms_errors(steps: int = 1000):
+    """E_u (Eq. 26) of the 64 x 64 spatiotemporal manufactured solution (A = 0.2,
+    T = 1000, U0 = 0.01, tau = 0.8, s_e from nu_e = nu/3, s_eps = s_q = 1.2) after
+    `steps` steps, per population storage, with phi and the Eq. (25) force evaluated
+    in the kernel (a one-lattice batch): the accuracy side of the FP16-vs-FP32
+    comparison."""
+    import paper_2409_02964_gb300 as P
+    out = {}
+    for st in ("fp32", "fp16", "bf16"):
+        b = P.Batch([(64, 0.8, 0.2, 1000.0, 0.01)], storage=st, s_e=0.0)
+        b.init()
+        b.step(steps)
+        out[st] = b.relative_error(0)
+        b.close()
+    return out
 
 
 def batch_lattices(count: int = 512, seed: int = 2409):
@@ -412,6 +432,19 @@ def main():
                             "GB_s": round(lv.bytes_per_cell * cells * ns / s / 1e9, 1),
                             "bytes_per_cell": lv.bytes_per_cell, "steps": ns}
             lv.close()
+        # physics variants on the same channel: a Darcy drag (Sec. 3.1, Da = k0 / H^2 = 1e-2;
+        # the one-warp kernel's general row path) and the App. B equilibrium (kernel 1)
+        nu = (TAU - 0.5) / 3
+        for name, kw in (("fp32_darcy_drag", dict(drag=(nu / (1e-2 * args.n * args.n), 0.0, 0.0, 0.0))),
+                         ("fp32_appB_eq2", dict(eq_order=2))):
+            lv, _ = build_channel(args.n, "fp32", **kw)
+            s = time_steps(lv, 1000, 5)
+            variants[name] = {"MLUPS": round(cells * 1000 / s / 1e6, 1), "steps": 1000,
+                              "kernel": lv.launch_shape()["threads"]}
+            lv.close()
+        errs = mms_errors()
+        for st, e in errs.items():
+            variants.setdefault(st, {})["mms64_E_u"] = e
         out["variants"] = variants
         if not args.no_batch:
             out["batch"] = batch_run(args.batch_steps, args.batch_count)

@@ -71,6 +71,8 @@ typedef struct {
                                     (any storage); 2, 3, 4 = two columns per thread on packed FP32
                                     pairs with 64 / 96 / 128-thread CTAs; 5 = one warp per CTA,
                                     two columns per lane (2..5: not FP64) */
+    int eq_order;                /* 3 (or 0): the 3rd-order equilibrium of Eq. (14) with Eq. (18), (20);
+                                    2: App. B, Eq. (B1)-(B3) (kernel 1 only) */
 } lbm_vanse_params;
 
 typedef struct lbm_vanse* lbm_vanse_t;
@@ -99,6 +101,15 @@ lbm_status lbm_vanse_set_void_fraction(lbm_vanse_t h, const double* phi_t, const
  * next call. */
 lbm_status lbm_vanse_set_body_force(lbm_vanse_t h, double gx, double gy, const double* field,
                                     int on_device);
+
+/* Linear drag added to the body force (Sec. 3.1, Eq. 21 and 23):
+ *   F^B += -beta (u - u_s),  beta(x) = phi(x)^2 (d0 + d1 (1 - phi(x))),
+ * so d0 = nu / k0 gives the Darcy resistance phi nu u / k0 of Sec. 3.1 (with F^B =
+ * phi G from set_body_force) and d1 = 1 the fluid-solid drag of Eq. (23). Because the
+ * drag is linear in u, Eq. (7) is solved exactly for u each step. d0, d1 >= 0;
+ * d0 = d1 = 0 removes it. Runs on step kernels 1 and 5 (LBM_ERR_ARG on 2-4); it
+ * takes the row loop's general path. Also used by init_fields and macros. */
+lbm_status lbm_vanse_set_drag(lbm_vanse_t h, double d0, double d1, double us_x, double us_y);
 
 /* Initial populations f = f^eq(rho, u, phi) - F_i(u, F)/2 (Eq. 14, Eq. 6 with
  * F = F^p + F^B, F^p from grad rho by Eq. 10 and 13), so that Eq. (7) returns u.

@@ -68,6 +68,8 @@ struct lbm_vanse {
     void* fb = nullptr;           // body-force field (2 planes), R, padded
     bool unsteady = false, has_fb = false, phi_set = false, initialised = false;
     double gx = 0, gy = 0;
+    bool has_drag = false;        // F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi))
+    double drag_d0 = 0, drag_d1 = 0, us_x = 0, us_y = 0;
     double s_nu = 0, s_e = 0;
     double scale = 1, inv_scale = 1;
     int* err = nullptr;           // device flag set by bounded waits
@@ -81,9 +83,11 @@ struct lbm_vanse {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     struct GraphKey {
-        const void* phi; const void* fb; int has_fb; double gx, gy; int cur;
+        const void* phi; const void* fb; int has_fb; double gx, gy; int cur; double drag[4]; int has_drag;
         bool operator==(const GraphKey& o) const {
-            return phi == o.phi && fb == o.fb && has_fb == o.has_fb && gx == o.gx && gy == o.gy && cur == o.cur;
+            return phi == o.phi && fb == o.fb && has_fb == o.has_fb && gx == o.gx && gy == o.gy && cur == o.cur &&
+                   has_drag == o.has_drag && drag[0] == o.drag[0] && drag[1] == o.drag[1] && drag[2] == o.drag[2] &&
+                   drag[3] == o.drag[3];
         }
     } gkey{};
     bool use_graphs = true;
@@ -140,6 +144,12 @@ Lattice<R> make_lattice(const lbm_vanse* h) {
     L.scale = (R)h->scale;
     L.inv_scale = (R)h->inv_scale;
     L.rest = make_rest<R>(h);
+    L.eq2 = h->prm.eq_order == 2;
+    L.has_drag = h->has_drag;
+    L.drag_d0 = (R)h->drag_d0;
+    L.drag_d1 = (R)h->drag_d1;
+    L.us_x = (R)h->us_x;
+    L.us_y = (R)h->us_y;
     return L;
 }
 
@@ -244,6 +254,12 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src) {
     p.inv_scale = (R)h->inv_scale;
     p.rest = make_rest<R>(h);
     p.err = h->err;
+    p.eq2 = h->prm.eq_order == 2;
+    p.has_drag = h->has_drag;
+    p.drag_d0 = (R)h->drag_d0;
+    p.drag_d1 = (R)h->drag_d1;
+    p.us_x = (R)h->us_x;
+    p.us_y = (R)h->us_y;
     dim3 grid(h->gridx, h->gridy);
     if constexpr (!std::is_same<S, double>::value) {
         switch (h->kernel) {
@@ -299,13 +315,15 @@ lbm_status build_graph(lbm_vanse* h) {
     e = cudaGraphInstantiate(&h->gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
-    h->gkey = {h->phi, h->fb, (int)h->has_fb, h->gx, h->gy, h->cur};
+    h->gkey = {h->phi, h->fb, (int)h->has_fb, h->gx, h->gy, h->cur, {h->drag_d0, h->drag_d1, h->us_x, h->us_y},
+               (int)h->has_drag};
     return LBM_OK;
 }
 
 template <typename S>
 lbm_status replay_graph(lbm_vanse* h) {
-    lbm_vanse::GraphKey key{h->phi, h->fb, (int)h->has_fb, h->gx, h->gy, h->cur};
+    lbm_vanse::GraphKey key{h->phi, h->fb, (int)h->has_fb, h->gx, h->gy, h->cur,
+                            {h->drag_d0, h->drag_d1, h->us_x, h->us_y}, (int)h->has_drag};
     if (!h->gexec || !(key == h->gkey)) {
         lbm_status st = build_graph<S>(h);
         if (st != LBM_OK) return st;
@@ -494,6 +512,7 @@ extern "C" void lbm_vanse_default_params(lbm_vanse_params* p) {
     p->storage_scale_log2 = -1000;  // sentinel: per-precision default
     p->strip_rows = 0;
     p->eager = 0;
+    p->eq_order = 3;
 }
 
 extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_vanse_t* out) {
@@ -541,7 +560,16 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
         delete h;
         return fail(nullptr, LBM_ERR_ARG, "the two-column kernels run packed FP32 arithmetic; FP64 storage needs kernel 1");
     }
-    h->kernel = p->kernel ? p->kernel : (p->storage == LBM_FP64 ? 1 : kDefaultKernel);
+    if (p->eq_order != 0 && p->eq_order != 2 && p->eq_order != 3) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "eq_order must be 2 (App. B) or 3 (Eq. 14; 0 = 3)");
+    }
+    if (p->eq_order == 2 && p->kernel >= 2) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "the App. B equilibrium runs on kernel 1 only");
+    }
+    if (h->prm.eq_order == 0) h->prm.eq_order = 3;
+    h->kernel = p->kernel ? p->kernel : ((p->storage == LBM_FP64 || p->eq_order == 2) ? 1 : kDefaultKernel);
     h->pair = h->kernel >= 2;
     h->W = h->kernel == 5 ? 60 : (h->pair ? 2 * kPairT[h->kernel - 2] - 4 : kThreads - 4);
     h->gridx = (p->nx + h->W - 1) / h->W;
@@ -619,6 +647,21 @@ extern "C" lbm_status lbm_vanse_set_body_force(lbm_vanse_t h, double gx, double 
     if (owned) cudaFreeAsync(d, h->stream);
     if (st != LBM_OK) return st;
     h->has_fb = true;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_set_drag(lbm_vanse_t h, double d0, double d1, double us_x, double us_y) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!std::isfinite(d0) || !std::isfinite(d1) || !std::isfinite(us_x) || !std::isfinite(us_y) || d0 < 0 || d1 < 0)
+        return fail(h, LBM_ERR_ARG, "drag coefficients must be finite and >= 0, u_s finite");
+    const bool on = d0 > 0 || d1 > 0;
+    if (on && h->kernel >= 2 && h->kernel <= 4)
+        return fail(h, LBM_ERR_ARG, "the drag runs on kernels 1 and 5 (this lattice uses kernel %d)", h->kernel);
+    h->has_drag = on;
+    h->drag_d0 = d0;
+    h->drag_d1 = d1;
+    h->us_x = us_x;
+    h->us_y = us_y;
     return LBM_OK;
 }
 
@@ -1302,6 +1345,7 @@ extern "C" lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, 
     if (!rate_ok(p->s_eps) || !rate_ok(p->s_q) || (p->s_e > 0 && !rate_ok(p->s_e)))
         return fail(nullptr, LBM_ERR_ARG, "rates must lie in (0, 2)");
     if (p->bc_x != LBM_BC_PERIODIC) return fail(nullptr, LBM_ERR_ARG, "bc_x must be periodic");
+    if (p->eq_order == 2) return fail(nullptr, LBM_ERR_ARG, "the adjoint covers the Eq. (14) equilibrium only");
     if (a->nsteps < 1 || a->avg_steps < 1 || a->avg_steps > a->nsteps || a->checkpoint_every < 1)
         return fail(nullptr, LBM_ERR_ARG, "need nsteps >= 1, 1 <= avg_steps <= nsteps, checkpoint_every >= 1");
     if (a->x_out < 0 || a->x_out >= p->nx) return fail(nullptr, LBM_ERR_ARG, "x_out out of range");

@@ -20,7 +20,16 @@ struct Lattice {
     R kappa, gx, gy;
     R scale, inv_scale;
     Rest<R> rest;
+    int eq2 = 0;                       // App. B equilibrium (B1) instead of Eq. (14)
+    int has_drag = 0;                  // F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi))
+    R drag_d0 = 0, drag_d1 = 0, us_x = 0, us_y = 0;
 };
+
+// the linear drag coefficient beta(phi) of a lattice (0 without drag)
+template <typename R>
+__device__ __forceinline__ R drag_beta(const Lattice<R>& L, R ph) {
+    return L.has_drag ? ph * ph * (L.drag_d0 + L.drag_d1 * ((R)1 - ph)) : (R)0;
+}
 
 __device__ __forceinline__ long long cell_off(int P, int x, int y) { return (long long)y * P + kPadCols + x; }
 
@@ -138,6 +147,9 @@ __global__ void init_kernel(S* __restrict__ buf, const R* __restrict__ phi, cons
         const R kp = (L.model_b ? (L.kappa - (R)1) : (L.kappa - ph)) / (R)3;
         R Fx = kp * gx + ph * L.gx, Fy = kp * gy + ph * L.gy;
         if (fb) { Fx += fb[co]; Fy += fb[L.plane + co]; }
+        const R beta = drag_beta(L, ph);
+        Fx -= beta * (ux - L.us_x);
+        Fy -= beta * (uy - L.us_y);
         const R X = L.kappa / ph;
         const R pr = ph * rho;
         const R uu = ux * ux + uy * uy;
@@ -150,7 +162,8 @@ __global__ void init_kernel(S* __restrict__ buf, const R* __restrict__ phi, cons
                 feq = pr - (R)(5.0 / 9.0) * L.kappa * rho - (R)(2.0 / 3.0) * pr * uu;
             } else {
                 const R w = (i <= 4) ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0);
-                const R g = (i <= 4) ? ((R)3 - X) * (R)0.5 : X;   // 1 + (X-1)(3|e|^2 - 4)/2
+                // Eq. (14): 1 + (X-1)(3|e|^2 - 4)/2 on the first-order term; (B1): 1
+                const R g = L.eq2 ? (R)1 : ((i <= 4) ? ((R)3 - X) * (R)0.5 : X);
                 feq = w * (L.kappa * rho + pr * ((R)3 * eu * g + (R)4.5 * eu * eu - (R)1.5 * uu));
             }
             const R w = (i == 0) ? (R)(4.0 / 9.0) : ((i <= 4) ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0));
@@ -221,8 +234,10 @@ __global__ void vel_kernel(const S* __restrict__ buf, const R* __restrict__ phi,
         const R kp = (L.model_b ? (L.kappa - (R)1) : (L.kappa - ph)) / (R)3;
         R Fx = kp * gx + ph * L.gx, Fy = kp * gy + ph * L.gy;
         if (fb) { Fx += fb[co]; Fy += fb[L.plane + co]; }
-        if (ux) ux[k] = (double)((jx + (R)0.5 * Fx) / s);
-        if (uy) uy[k] = (double)((jy + (R)0.5 * Fy) / s);
+        // Eq. (7) with the drag -beta (u - u_s) inside F, solved for u
+        const R beta = drag_beta(L, ph);
+        if (ux) ux[k] = (double)((jx + (R)0.5 * (Fx + beta * L.us_x)) / (s + (R)0.5 * beta));
+        if (uy) uy[k] = (double)((jy + (R)0.5 * (Fy + beta * L.us_y)) / (s + (R)0.5 * beta));
         if (pr) pr[k] = rho[k] / 3.0;
     }
 }

@@ -188,6 +188,9 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         p.rest.k59 = Lt.kappa * Lt.rho0 * (5.f / 9.f);
         p.rest.rho0 = Lt.rho0;
         p.err = bp.err;
+        p.eq2 = 0;
+        p.has_drag = 0;
+        p.drag_d0 = p.drag_d1 = p.us_x = p.us_y = 0.f;
         c.k = Lt.k; c.w = Lt.w; c.A = Lt.A; c.U0 = Lt.U0; c.phi0 = Lt.phi0; c.nu = Lt.nu; c.rho0 = Lt.rho0;
         sincosf(Lt.w * (float)t, &c.st, &c.ct);
         c.ct1 = cosf(Lt.w * (float)(t + 1));
@@ -471,6 +474,9 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     p.rest.k59 = Lt.kappa * Lt.rho0 * (5.f / 9.f);
     p.rest.rho0 = Lt.rho0;
     p.err = bp.err;
+    p.eq2 = 0;
+    p.has_drag = 0;
+    p.drag_d0 = p.drag_d1 = p.us_x = p.us_y = 0.f;
     c.k = Lt.k; c.w = Lt.w; c.A = Lt.A; c.U0 = Lt.U0; c.phi0 = Lt.phi0; c.nu = Lt.nu; c.rho0 = Lt.rho0;
     sincosf(Lt.w * (float)t, &c.st, &c.ct);
     c.ct1 = cosf(Lt.w * (float)(t + 1));

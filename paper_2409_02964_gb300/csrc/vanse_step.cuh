@@ -73,6 +73,9 @@ struct StepParams {
     R scale, inv_scale;   // deviation-storage scale (FP16/BF16)
     Rest<R> rest;
     int* err;             // set to 1 when a bounded wait gives up
+    int eq2;              // App. B: (B2) energy-flux equilibria and the (B3) penalty (kernel 1 only)
+    int has_drag;         // F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi)); u solved implicitly
+    R drag_d0, drag_d1, us_x, us_y;
 };
 
 // Per-row register state (see the header comment for who writes what when).
@@ -84,6 +87,7 @@ struct RowState {
     R Fx, Fy, ux, uy;              // force and velocity (phase 2)
     R dAx, dBx, dBy, dDx;          // x-differences of rho u_x, u_x, u_y, phi rho u_x
     R wAy, wBy, wBx, wDy;          // smoothed sums of rho u_y, u_y, u_x, phi rho u_y
+    R dAy, wAx, dDy, wDx;          // App. B only: the cross derivatives of rho u and phi rho u
 };
 
 __device__ __forceinline__ float rcp_r(float x) { return __fdividef(1.0f, x); }
@@ -228,9 +232,20 @@ __device__ __forceinline__ void phase2(const StepCtx<S, R, T>& c, const RowState
         Fy += *c.aux(p2, k + 1);
     }
     const R m0 = Bs.m[0];
-    const R inv = rcp_r(m0);
-    const R ux = (Bs.m[3] + (R)0.5 * Fx) * inv;
-    const R uy = (Bs.m[5] + (R)0.5 * Fy) * inv;
+    R ux, uy;
+    if (p.has_drag) {
+        // Eq. (7) with F^B += -beta (u - u_s): linear in u, solved exactly
+        const R beta = phi * phi * (p.drag_d0 + p.drag_d1 * ((R)1 - phi));
+        const R inv = (R)1 / (m0 + (R)0.5 * beta);
+        ux = (Bs.m[3] + (R)0.5 * (Fx + beta * p.us_x)) * inv;
+        uy = (Bs.m[5] + (R)0.5 * (Fy + beta * p.us_y)) * inv;
+        Fx -= beta * (ux - p.us_x);
+        Fy -= beta * (uy - p.us_y);
+    } else {
+        const R inv = rcp_r(m0);
+        ux = (Bs.m[3] + (R)0.5 * Fx) * inv;
+        uy = (Bs.m[5] + (R)0.5 * Fy) * inv;
+    }
     Bs.Fx = Fx; Bs.Fy = Fy; Bs.ux = ux; Bs.uy = uy;
     const int t = c.t;
     fbuf[0 * T + t] = Bs.rho * ux;
@@ -283,18 +298,37 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
     const R X = p.kappa * rcp_r(phi);
     const R kp = p.model_b ? (p.kappa - (R)1) : (p.kappa - phi);
     const R kr = kp * rho;
-    // Eq. (20)
-    const R Ca = (-p.kappa * (xAx + yAy) + (R)2 * kr * (xBx + yBy) + ((R)3 - (R)2 * X) * (xDx + yDy)) * twelfth
-                 - (R)2 * X * rho * (phin - phi);
-    const R Cb = (-p.kappa * (xAx - yAy) + ((R)2 / (R)3) * kr * (xBx - yBy) + (xDx - yDy)) * twelfth;
-    const R Cc = kr * (xBy + yBx) * ((R)1 / (R)36);
+    R Ca, Cb, Cc;
+    if (!p.eq2) {
+        // Eq. (20)
+        Ca = (-p.kappa * (xAx + yAy) + (R)2 * kr * (xBx + yBy) + ((R)3 - (R)2 * X) * (xDx + yDy)) * twelfth
+             - (R)2 * X * rho * (phin - phi);
+        Cb = (-p.kappa * (xAx - yAy) + ((R)2 / (R)3) * kr * (xBx - yBy) + (xDx - yDy)) * twelfth;
+        Cc = kr * (xBy + yBx) * ((R)1 / (R)36);
+    } else {
+        // Eq. (B3): 12 x the cross derivatives d_x(rho u_y), d_y(rho u_x), d_x(phi rho u_y), d_y(phi rho u_x)
+        R xAy = An.dAy + (R)4 * Cs.dAy + Bs.dAy, yAx = Bs.wAx - An.wAx;
+        R xDy = An.dDy + (R)4 * Cs.dDy + Bs.dDy, yDx = Bs.wDx - An.wDx;
+        if (p.wall_y && (p3 == 0 || p3 == p.ny - 1)) {
+            const bool lo = (p3 == 0), hi = (p3 == p.ny - 1);
+            xAy = (lo ? -Cs.dAy : An.dAy) + (R)4 * Cs.dAy + (hi ? -Cs.dAy : Bs.dAy);
+            xDy = (lo ? -Cs.dDy : An.dDy) + (R)4 * Cs.dDy + (hi ? -Cs.dDy : Bs.dDy);
+            yAx = (hi ? -Cs.wAx : Bs.wAx) - (lo ? -Cs.wAx : An.wAx);
+            yDx = (hi ? -Cs.wDx : Bs.wDx) - (lo ? -Cs.wDx : An.wDx);
+        }
+        const R t3 = (R)2 / (R)3;
+        Ca = ((R)-2 * p.kappa * (xAx + yAy) + (R)2 * kr * (xBx + yBy) + ((R)4 - (R)2 * X) * (xDx + yDy)) * twelfth
+             - (R)2 * X * rho * (phin - phi);
+        Cb = (-t3 * p.kappa * (xAx - yAy) + t3 * kr * (xBx - yBy) + t3 * (xDx - yDy)) * twelfth;
+        Cc = (-p.kappa * (xAy + yAx) + kr * (xBy + yBx) + (xDy + yDx)) * ((R)1 / (R)36);
+    }
 
     // Eq. (18), (19), (16); the conserved moments map to m_0 and j + F for any s_c
     const R m0 = Cs.m[0], ux = Cs.ux, uy = Cs.uy, Fx = Cs.Fx, Fy = Cs.Fy;
     const R uu = ux * ux + uy * uy;
     const R uF = ux * Fx + uy * Fy;
     const R jxe = m0 * ux, jye = m0 * uy;
-    const R q = X - (R)2;
+    const R q = p.eq2 ? (R)-1 : X - (R)2;   // Eq. (18) / (B2) energy-flux equilibria
     R a[9];
     a[0] = m0;
     a[1] = Cs.m[1] + p.s_e * (m0 * ((R)-4 + (R)3 * uu + (R)2 * X) - Cs.m[1]) + p.h_e * ((R)6 * uF + Ca);
@@ -430,6 +464,12 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
             Bs.wBy = (R)4 * Bs.uy + (Byr + Byl);
             Bs.wBx = (R)4 * Bs.ux + (Bxr + Bxl);
             Bs.wDy = (R)4 * (Bs.m[0] * Bs.uy) + (Dyr + Dyl);
+            if (p.eq2) {
+                Bs.dAy = Ayr - Ayl;
+                Bs.wAx = (R)4 * (Bs.rho * Bs.ux) + (Axr + Axl);
+                Bs.dDy = Dyr - Dyl;
+                Bs.wDx = (R)4 * (Bs.m[0] * Bs.ux) + (Dxr + Dxl);
+            }
         }
         const bool ph3 = (p3 >= y0) && (p3 < y1);
         if (ph3 && ph3_thread && c.xc < p.nx) phase3<S, R, T>(c, An, Bs, Cs, p3);

@@ -237,9 +237,20 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
     V2 Fy = fma2(kp, gy, p.gy * phi);
     c.template add_field_force<FAST>(p2, Bs, Fx, Fy);
     const V2 m0 = Bs.m[0];
-    const V2 inv = rcp2(m0);
-    const V2 ux = fma2(0.5f, Fx, Bs.m[3]) * inv;
-    const V2 uy = fma2(0.5f, Fy, Bs.m[5]) * inv;
+    V2 ux, uy;
+    if (!FAST && p.has_drag) {
+        // Eq. (7) with F^B += -beta (u - u_s): linear in u, solved exactly (never on the fast path)
+        const V2 beta = (phi * phi) * fma2(-p.drag_d1, phi, bc(p.drag_d0 + p.drag_d1));
+        const V2 inv = rcp2(fma2(0.5f, beta, m0));
+        ux = fma2(0.5f, fma2(p.us_x, beta, Fx), Bs.m[3]) * inv;
+        uy = fma2(0.5f, fma2(p.us_y, beta, Fy), Bs.m[5]) * inv;
+        Fx = Fx - beta * (ux + (-p.us_x));
+        Fy = Fy - beta * (uy + (-p.us_y));
+    } else {
+        const V2 inv = rcp2(m0);
+        ux = fma2(0.5f, Fx, Bs.m[3]) * inv;
+        uy = fma2(0.5f, Fy, Bs.m[5]) * inv;
+    }
     Bs.Fx = Fx; Bs.Fy = Fy; Bs.ux = ux; Bs.uy = uy;
     // the Eq. (10) x-differences / smoothed sums of rho u, u, phi rho u on row p2
     const V2 Ax = Bs.rho * ux, Ay = Bs.rho * uy, Dx = m0 * ux, Dy = m0 * uy;
@@ -455,7 +466,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     c.waited = c.rlo - 1;
     c.issued = c.rlo - 1;
     // rows whose three phases need no wall, validity or field handling
-    c.fast_strip = !p.unsteady && !p.has_fb;
+    c.fast_strip = !p.unsteady && !p.has_fb && !p.has_drag;
     c.fast_lo = p.wall_y ? max(y0, 1) : y0;                 // lowest phase-3 row
     c.fast_hi = p.wall_y ? min(y1 + 1, p.ny - 2) : y1 + 1;  // highest phase-1 row
 

@@ -65,7 +65,7 @@ class Lattice:
                  s_q: float = 1.4, s_c: float = 1.0, kappa: float = 0.5, rho0: float = 1.0,
                  bc_y: str = "periodic", storage: str = "fp32", model_b: bool = False,
                  scale_log2: int | None = None, strip_rows: int = 0, eager: bool = False, kernel: int = 0,
-                 stream=None):
+                 eq_order: int = 3, stream=None):
         L = capi.load()
         p = capi.default_params()
         p.nx, p.ny, p.tau_nu = int(nx), int(ny), float(tau)
@@ -78,6 +78,7 @@ class Lattice:
         p.strip_rows = int(strip_rows)
         p.eager = int(bool(eager))
         p.kernel = int(kernel)
+        p.eq_order = int(eq_order)
         self.nx, self.ny, self.storage = int(nx), int(ny), storage
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -125,6 +126,10 @@ class Lattice:
     def set_body_force(self, gx: float = 0.0, gy: float = 0.0, field=None) -> None:
         a = _Arg(field, 2 * self.n, self.device)
         _check(self._L.lbm_vanse_set_body_force(self._h, float(gx), float(gy), a.ptr, a.on_device), self._h)
+
+    def set_drag(self, d0: float = 0.0, d1: float = 0.0, us_x: float = 0.0, us_y: float = 0.0) -> None:
+        """F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi)) (lbm_vanse_set_drag)."""
+        _check(self._L.lbm_vanse_set_drag(self._h, float(d0), float(d1), float(us_x), float(us_y)), self._h)
 
     def init_fields(self, rho, ux, uy) -> None:
         args = [_Arg(v, self.n, self.device) for v in (rho, ux, uy)]
