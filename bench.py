@@ -192,6 +192,34 @@ def mms_errors(steps: int = 1000):
     return out
 
 
+def channel_precision(n: int = 512, steps: int = 10000):
+    """The channel recipe regenerated at n x n, `steps` steps from rest per storage;
+    relative L2 error of u, and RMS error of p = rho/3, against the FP64 path (which
+    matches the FP64 oracle to 1e-12)."""
+    import paper_2409_02964_gb300 as P
+    from synth import fields
+    phi = fields.channel_phi(n, n)
+    rho, ux, uy = fields.rest_fields(n, n)
+    res = {}
+    for st in ("fp64", "fp32", "fp16", "bf16"):
+        lat = P.Lattice(n, n, TAU, bc_y="bounceback", storage=st, **RATES)
+        lat.set_void_fraction(phi)
+        lat.set_body_force(G, 0.0)
+        lat.init_fields(rho, ux, uy)
+        lat.step(steps)
+        res[st] = {k: v.cpu().numpy() for k, v in lat.macros().items()}
+        lat.close()
+    r = res["fp64"]
+    den = np.sum(r["ux"] ** 2 + r["uy"] ** 2)
+    out = {"workload": f"channel recipe at {n}x{n}, {steps} steps from rest, vs the FP64 path",
+           "u_max_fp64": float(np.abs(r["ux"]).max())}
+    for st in ("fp32", "fp16", "bf16"):
+        m = res[st]
+        out[st] = {"E_u": float(np.sqrt(np.sum((m["ux"] - r["ux"]) ** 2 + (m["uy"] - r["uy"]) ** 2) / den)),
+                   "p_rms_err": float(np.sqrt(np.mean((m["p"] - r["p"]) ** 2)))}
+    return out
+
+
 def batch_lattices(count: int = 512, seed: int = 2409):
     """Seeded lattices of the batched workload: n, tau, A, T, U0 per lattice."""
     rng = np.random.default_rng(seed)
@@ -442,6 +470,7 @@ def main():
             variants[name] = {"MLUPS": round(cells * 1000 / s / 1e6, 1), "steps": 1000,
                               "kernel": lv.launch_shape()["threads"]}
             lv.close()
+        out["precision_channel_512"] = channel_precision()
         errs = mms_errors()
         for st, e in errs.items():
             variants.setdefault(st, {})["mms64_E_u"] = e

@@ -169,3 +169,77 @@ def test_drag_momentum_balance(oracle_mod):
     m = oracle_mod.macros(p, f, phi, fb)
     jx = np.einsum("i,iyx->yx", E[:, 0].astype(float), f)
     assert np.abs(m["ux"] * f.sum(0) - (jx + 0.5 * m["Fx"])).max() < 1e-15
+
+
+def _db(oracle_mod, ny, phi0, da, kappa, tau=0.8, G=1e-6, steps=15000):
+    nx = 3
+    nu = (tau - 0.5) / 3
+    k0 = da * ny * ny
+    p = oracle_mod.Params(nx=nx, ny=ny, **oracle_mod.rates_from_tau(tau, s_eps=1.2, s_q=1.2), kappa=kappa, bc_y=1,
+                          drag_d0=nu / k0)
+    phi = np.full((ny, nx), phi0)
+    fb = np.stack([phi * G, 0 * phi])
+    f = oracle_mod.init(p, np.ones((ny, nx)), 0 * phi, 0 * phi, phi, fb)
+    for _ in range(steps):
+        f = oracle_mod.step(p, f, phi, None, fb)
+    u = oracle_mod.macros(p, f, phi, fb)["ux"][:, 0]
+    y = np.arange(ny) + 0.5
+    r = np.sqrt(phi0 / k0)
+    ua = G * k0 / (phi0 * nu) * (1 - np.cosh(r * (y - ny / 2)) / np.cosh(r * ny / 2))
+    return np.sqrt(np.sum((u - ua) ** 2) / np.sum(ua ** 2))
+
+
+@pytest.mark.parametrize("phi0,da,kappa,bound", [(0.3, 1e-3, 0.5, 1e-3), (0.1, 1e-4, 0.25, 4e-3)])
+def test_x1_porous_poiseuille_across_darcy_numbers(oracle_mod, phi0, da, kappa, bound):
+    """Eq. (22 I) at smaller Da and phi (the thin Brinkman layer, sqrt(k0 / phi) = 0.06 H
+    and 0.03 H, needs ny >= 64 to be resolved): the error falls towards second order
+    under refinement. phi = 0.1 runs kappa = 0.25 (reading c23: X = kappa / phi <= 2.5)."""
+    e64, e128 = _db(oracle_mod, 64, phi0, da, kappa), _db(oracle_mod, 128, phi0, da, kappa)
+    assert e128 < bound
+    assert e64 / e128 > 2.9, (e64, e128)
+
+
+def test_x3_transient_particle_flow(oracle_mod):
+    """Eq. (23) with a moving void fraction (a = 0.45, u_s = 1e-3; phi down to 0.1, so
+    kappa = 0.25): the velocity follows u_s + G / (a phi) with the same small
+    deviation at every sampled time (periodic in the frame of the void fraction)."""
+    L, ny, a, us, G, tau = 100, 3, 0.45, 1e-3, 1e-6, 0.8
+    p = oracle_mod.Params(nx=L, ny=ny, **oracle_mod.rates_from_tau(tau, s_eps=1.2, s_q=1.2), kappa=0.25,
+                          drag_d1=1.0, us_x=us)
+    x = np.arange(L)
+
+    def phi_of(t):
+        return np.tile(1 + a * (np.sin(2 * np.pi * (x - us * t) / L) - 1), (ny, 1))
+
+    def fb(ph):
+        return np.stack([ph * G, 0 * ph])
+
+    ph0 = phi_of(0)
+    f = oracle_mod.init(p, np.ones((ny, L)), us + G / (a * ph0), 0 * ph0, ph0, fb(ph0))
+    errs = []
+    for t in range(6000):
+        f = oracle_mod.step(p, f, phi_of(t), phi_of(t + 1), fb(phi_of(t)))
+        if (t + 1) % 2000 == 0:
+            ph = phi_of(t + 1)
+            u = oracle_mod.macros(p, f, ph, fb(ph))["ux"][0]
+            ua = us + G / (a * ph[0])
+            errs.append(np.sqrt(np.sum((u - ua) ** 2) / np.sum((ua - us) ** 2)))
+    assert max(errs) < 0.04, errs
+    assert max(errs) - min(errs) < 1e-3 * max(errs)
+
+
+@pytest.mark.parametrize("kappa,stable", [(0.25, True), (0.31, False)])
+def test_provisional_eos_stability_limit(oracle_mod, kappa, stable):
+    """Reading c23: the provisional equation of state gives an effective sound speed
+    sqrt(X / 3), X = kappa / phi, which must stay below the lattice speed: a decaying
+    shear wave at uniform phi = 0.1 stays bounded at X = 2.5 and blows up at X = 3.1."""
+    nx, ny = 4, 32
+    p = oracle_mod.Params(nx=nx, ny=ny, **oracle_mod.rates_from_tau(0.8, s_eps=1.2, s_q=1.2), kappa=kappa)
+    phi = np.full((ny, nx), 0.1)
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    f = oracle_mod.init(p, np.ones((ny, nx)), 1e-3 * np.sin(2 * np.pi * y / ny), 0 * phi, phi)
+    with np.errstate(all="ignore"):
+        for _ in range(3000):
+            f = oracle_mod.step(p, f, phi)
+    finite = bool(np.isfinite(f).all() and np.abs(f).max() < 10)
+    assert finite == stable
