@@ -1,33 +1,40 @@
 #!/usr/bin/env python3
 """Generate mms_force.cuh: the body force of Eq. (25) for the spatiotemporal
-manufactured solution, in closed form, for the batched kernel's in-kernel source.
+manufactured solution, evaluated inside the batched kernel.
 
 Fields (lattice units, n x n periodic lattice, k = 2 pi / n, w = 2 pi / T):
     phi = phi0 + A sin(kx) sin(ky) cos(wt)
-    phi u = grad psi + rot Psi,  psi = -(A w sin(wt) / (2 k^2)) sin(kx) sin(ky),
-                                 Psi = (U0 / k) sin(kx) sin(ky)
-so that d_t phi + div(phi u) = 0 with rho = rho0; the force is Eq. (25) with the
-pressure term dropped (constant density). The derivatives are taken symbolically,
-then sin/cos of kx, ky, wt are replaced by the arguments sx, cx, sy, cy, ct, st and
-common subexpressions are shared. The emitted function is a template over the
-arithmetic type, so the same code serves scalars and packed pairs.
+    q = phi u = grad psi + rot Psi,  psi = -(A w sin(wt) / (2 k^2)) sin(kx) sin(ky),
+                                     Psi = (U0 / k) sin(kx) sin(ky)
+so that d_t phi + div q = 0 with rho = rho0; the force is Eq. (25) with the pressure
+term dropped (constant density):
+    F / rho0 = d_t q + div(q u) - nu div(phi tau),  tau = grad u + grad u^T - (2/3) div u I.
+
+The emitted code evaluates this in a structured way rather than as one expanded
+rational expression: phi and q with their first and second derivatives are short
+products of sin/cos of kx, ky (the arguments sx, cx, sy, cy) with step constants;
+u = q / phi and its derivatives follow from the quotient rule with one reciprocal;
+the force is then assembled from those. At generation time the structured result
+is checked against the direct symbolic derivation (sympy) at random points.
 
 Run from this directory:  python gen_mms_force.py  (needs sympy; the generated
 header is committed, so building the library does not).
 """
 import os
+import random
 
 import sympy as sp
 
 
-def main() -> None:
+def direct_force():
+    """Eq. (25) by symbolic differentiation of the fields (the reference form)."""
     x, y, t = sp.symbols("x y t", real=True)
     k, w, A, U0, phi0, nu = sp.symbols("k w A U0 phi0 nu", positive=True)
-    sx, sy, cx, cy = sp.sin(k * x), sp.sin(k * y), sp.cos(k * x), sp.cos(k * y)
-    phi = phi0 + A * sx * sy * sp.cos(w * t)
-    a = -(A * w / (2 * k)) * sp.sin(w * t)
-    qx = a * cx * sy + U0 * sx * cy
-    qy = a * sx * cy - U0 * cx * sy
+    s_x, s_y, c_x, c_y = sp.sin(k * x), sp.sin(k * y), sp.cos(k * x), sp.cos(k * y)
+    phi = phi0 + A * s_x * s_y * sp.cos(w * t)
+    b = -(A * w / (2 * k)) * sp.sin(w * t)
+    qx = b * c_x * s_y + U0 * s_x * c_y
+    qy = b * s_x * c_y - U0 * c_x * s_y
     ux, uy = qx / phi, qy / phi
     div = sp.diff(ux, x) + sp.diff(uy, y)
     txx = 2 * sp.diff(ux, x) - sp.Rational(2, 3) * div
@@ -35,37 +42,129 @@ def main() -> None:
     txy = sp.diff(ux, y) + sp.diff(uy, x)
     Fx = sp.diff(qx, t) + sp.diff(qx * ux, x) + sp.diff(qx * uy, y) - nu * (sp.diff(phi * txx, x) + sp.diff(phi * txy, y))
     Fy = sp.diff(qy, t) + sp.diff(qy * ux, x) + sp.diff(qy * uy, y) - nu * (sp.diff(phi * txy, x) + sp.diff(phi * tyy, y))
-    Sx, Sy, Cx, Cy, Ct, St = sp.symbols("sx sy cx cy ct st")
-    rep = {sp.sin(k * x): Sx, sp.sin(k * y): Sy, sp.cos(k * x): Cx, sp.cos(k * y): Cy,
-           sp.cos(w * t): Ct, sp.sin(w * t): St}
-    Fx = sp.together(Fx.subs(rep))
-    Fy = sp.together(Fy.subs(rep))
-    reps, (ex, ey) = sp.cse([Fx, Fy], symbols=sp.numbered_symbols("e"), optimizations="basic")
+    return (x, y, t, k, w, A, U0, phi0, nu), Fx, Fy
 
-    scalars = {"k", "w", "A", "U0", "phi0", "nu", "ct", "st"}
-    fields = {"sx", "sy", "cx", "cy"}
 
-    def emit(expr) -> str:
-        return _emit(sp.expand_power_base(expr), scalars, fields)
+# The structured evaluation: (name, kind, expression text). kind "s" = float scalar
+# (uniform per lattice and step), "v" = per-cell value of type T. Expressions use the
+# inputs sx, cx, sy, cy (T), ct, st, k, w, A, U0, phi0, nu (float) and earlier names.
+STEPS = [
+    # step constants
+    ("a", "s", "A * ct"),                        # phi = phi0 + a sx sy
+    ("b", "s", "-(A * w * st) / (2 * k)"),       # q_x = b cx sy + U0 sx cy, q_y = b sx cy - U0 cx sy
+    ("bt", "s", "-(A * w * w * ct) / (2 * k)"),  # d_t b
+    ("ak", "s", "a * k"),
+    ("akk", "s", "a * k * k"),
+    ("bk", "s", "b * k"),
+    ("uk", "s", "U0 * k"),
+    ("kk", "s", "k * k"),
+    # products of the trig arguments
+    ("ss", "v", "sx * sy"),
+    ("cc", "v", "cx * cy"),
+    ("cs", "v", "cx * sy"),
+    ("sc", "v", "sx * cy"),
+    # phi and its derivatives
+    ("ph", "v", "phi0 + a * ss"),
+    ("phx", "v", "ak * cs"),
+    ("phy", "v", "ak * sc"),
+    ("phxx", "v", "-akk * ss"),                 # = phi_yy
+    ("phxy", "v", "akk * cc"),
+    # q and its derivatives
+    ("qx", "v", "b * cs + U0 * sc"),
+    ("qy", "v", "b * sc - U0 * cs"),
+    ("qxt", "v", "bt * cs"),
+    ("qyt", "v", "bt * sc"),
+    ("qxx", "v", "uk * cc - bk * ss"),          # d_x q_x
+    ("qxy", "v", "bk * cc - uk * ss"),          # d_y q_x
+    ("qyx", "v", "bk * cc + uk * ss"),          # d_x q_y
+    ("qyy", "v", "-bk * ss - uk * cc"),         # d_y q_y
+    ("qmx", "v", "-kk * (b * sc + U0 * cs)"),   # d_x d_y q_x
+    ("qmy", "v", "kk * (U0 * sc - b * cs)"),    # d_x d_y q_y  (d_xx q = d_yy q = -k^2 q)
+    # u = q / phi and its derivatives (quotient rule)
+    ("ip", "v", "1 / ph"),
+    ("ux", "v", "qx * ip"),
+    ("uy", "v", "qy * ip"),
+    ("uxx", "v", "(qxx - ux * phx) * ip"),
+    ("uxy", "v", "(qxy - ux * phy) * ip"),
+    ("uyx", "v", "(qyx - uy * phx) * ip"),
+    ("uyy", "v", "(qyy - uy * phy) * ip"),
+    ("uxXX", "v", "(-kk * qx - 2 * uxx * phx - ux * phxx) * ip"),
+    ("uxYY", "v", "(-kk * qx - 2 * uxy * phy - ux * phxx) * ip"),
+    ("uxXY", "v", "(qmx - uxx * phy - uxy * phx - ux * phxy) * ip"),
+    ("uyXX", "v", "(-kk * qy - 2 * uyx * phx - uy * phxx) * ip"),
+    ("uyYY", "v", "(-kk * qy - 2 * uyy * phy - uy * phxx) * ip"),
+    ("uyXY", "v", "(qmy - uyx * phy - uyy * phx - uy * phxy) * ip"),
+    # viscous stress and its divergence terms
+    ("dv", "v", "uxx + uyy"),
+    ("txx", "v", "2 * uxx - (2.0 / 3.0) * dv"),
+    ("tyy", "v", "2 * uyy - (2.0 / 3.0) * dv"),
+    ("txy", "v", "uxy + uyx"),
+    ("dxtxx", "v", "(4.0 / 3.0) * uxXX - (2.0 / 3.0) * uyXY"),
+    ("dytyy", "v", "(4.0 / 3.0) * uyYY - (2.0 / 3.0) * uxXY"),
+    ("dytxy", "v", "uxYY + uyXY"),
+    ("dxtxy", "v", "uxXY + uyXX"),
+    ("vx", "v", "phx * txx + ph * dxtxx + phy * txy + ph * dytxy"),
+    ("vy", "v", "phx * txy + ph * dxtxy + phy * tyy + ph * dytyy"),
+    # Eq. (25) without the pressure term, per unit rho0
+    ("fx", "out", "qxt + qxx * ux + qx * uxx + qxy * uy + qx * uyy - nu * vx"),
+    ("fy", "out", "qyt + qyx * ux + qy * uxx + qyy * uy + qy * uyy - nu * vy"),
+]
 
+INPUTS_V = ("sx", "cx", "sy", "cy")
+INPUTS_S = ("ct", "st", "k", "w", "A", "U0", "phi0", "nu")
+
+
+def check_against_direct(trials: int = 12) -> float:
+    """Largest relative difference between the structured and the direct force."""
+    syms, Fx, Fy = direct_force()
+    x, y, t, k, w, A, U0, phi0, nu = syms
+    rng = random.Random(2409)
+    worst = 0.0
+    for _ in range(trials):
+        vals = {k: 2 * 3.141592653589793 / rng.choice([16, 32, 48, 64]), w: 2 * 3.141592653589793 / rng.uniform(200, 3000),
+                A: rng.uniform(0.05, 0.3), U0: rng.uniform(0.0, 0.02), phi0: 0.7, nu: rng.uniform(0.02, 0.3),
+                x: rng.uniform(0, 64), y: rng.uniform(0, 64), t: rng.uniform(0, 5000)}
+        ref = [sp.N(F.subs(vals), 30) for F in (Fx, Fy)]
+        env = {"sx": sp.sin(vals[k] * vals[x]), "cx": sp.cos(vals[k] * vals[x]), "sy": sp.sin(vals[k] * vals[y]),
+               "cy": sp.cos(vals[k] * vals[y]), "ct": sp.cos(vals[w] * vals[t]), "st": sp.sin(vals[w] * vals[t]),
+               "k": vals[k], "w": vals[w], "A": vals[A], "U0": vals[U0], "phi0": vals[phi0], "nu": vals[nu]}
+        for name, _, expr in STEPS:
+            env[name] = sp.N(sp.sympify(expr, locals=dict(env)), 30)
+        scale = max(abs(r) for r in ref) or 1
+        for got, want in zip((env["fx"], env["fy"]), ref):
+            worst = max(worst, float(abs(got - want) / scale))
+    return worst
+
+
+def emit(expr: str, kind: str) -> str:
+    """C++ text: numbers as float literals, 1 / T as mms_rcp(T)."""
+    import re
+    text = expr.replace("1 / ph", "mms_rcp(ph)")
+    text = re.sub(r"(?<![\w.])(\d+\.\d+|\d+)(?![\w.])", lambda m: f"{float(m.group(1))!r}f", text)
+    return text
+
+
+def main() -> None:
+    err = check_against_direct()
+    assert err < 1e-12, f"structured force differs from the direct derivation by {err}"
     lines = []
-    for sym, e in reps:
-        if _is_scalar(e, scalars):
-            scalars.add(str(sym))
-            lines.append(f"    const float {sym} = {emit(e)};")
+    for name, kind, expr in STEPS:
+        if kind == "s":
+            lines.append(f"    const float {name} = {emit(expr, kind)};")
+        elif kind == "v":
+            lines.append(f"    const T {name} = {emit(expr, kind)};")
         else:
-            lines.append(f"    const T {sym} = {emit(e)};")
-    lines.append(f"    fx = {emit(ex)};")
-    lines.append(f"    fy = {emit(ey)};")
+            lines.append(f"    {name} = {emit(expr, kind)};")
     body = "\n".join(lines)
     text = f'''// mms_force.cuh -- GENERATED by gen_mms_force.py; do not edit by hand.
 //
 // Body force of Eq. (25) (constant density, pressure term dropped) for the
 // spatiotemporal manufactured solution phi = phi0 + A sin(kx) sin(ky) cos(wt),
-// phi u = grad psi + rot Psi (see the generator for the definitions). Arguments:
-// sx, cx = sin, cos of k x; sy, cy = sin, cos of k y; ct, st = cos, sin of w t.
-// T is the arithmetic type (float or a packed pair); it must provide + and *
-// between T values and with a float on either side, and mms_rcp(T).
+// phi u = grad psi + rot Psi (see the generator for the definitions), per unit rho0.
+// Arguments: sx, cx = sin, cos of k x; sy, cy = sin, cos of k y; ct, st = cos, sin
+// of w t. Evaluated from phi, q = phi u and their derivatives, u by the quotient rule.
+// T is the arithmetic type (float or a packed pair); it must provide + - * between
+// T values and with a float on either side, unary -, and mms_rcp(T).
 #pragma once
 
 namespace lbmv {{
@@ -81,46 +180,7 @@ __device__ __forceinline__ void mms_force(T sx, T cx, T sy, T cy, float ct, floa
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mms_force.cuh")
     with open(out, "w") as fh:
         fh.write(text)
-    print(out, len(reps), "subexpressions")
-
-
-def _emit(e, scalars, fields) -> str:
-    """C++ text of a sympy expression over T (field symbols / subexpressions) and
-    float scalars; divisions become multiplications by mms_rcp."""
-    if e.is_Symbol:
-        return str(e)
-    if e.is_Number:
-        return f"{float(e)!r}f"
-    if e.is_Add:
-        terms = [_emit(a, scalars, fields) for a in e.args]
-        return "(" + " + ".join(terms) + ")"
-    if e.is_Mul:
-        num, den = [], []
-        for a in e.args:
-            if a.is_Pow and a.exp.is_Number and a.exp < 0:
-                den.append(sp.Pow(a.base, -a.exp))
-            else:
-                num.append(a)
-        # scalar factors first so that float * T products come out
-        num.sort(key=lambda a: 0 if _is_scalar(a, scalars) else 1)
-        parts = [_emit(a, scalars, fields) for a in num] or ["1.0f"]
-        s = " * ".join(parts)
-        if den:
-            d = " * ".join(_emit(a, scalars, fields) for a in den)
-            s = f"({s}) * mms_rcp({d})"
-        return "(" + s + ")"
-    if e.is_Pow:
-        b, p = e.base, e.exp
-        if p.is_Integer and p > 0:
-            return "(" + " * ".join([_emit(b, scalars, fields)] * int(p)) + ")"
-        if p.is_Integer and p < 0:
-            return f"mms_rcp({_emit(sp.Pow(b, -p), scalars, fields)})"
-        raise ValueError(f"unsupported power {e}")
-    raise ValueError(f"unsupported expression {e} ({type(e)})")
-
-
-def _is_scalar(e, scalars) -> bool:
-    return all(str(s) in scalars for s in e.free_symbols) if e.free_symbols else True
+    print(out, f"{len(STEPS)} steps, structured vs direct: {err:.1e}")
 
 
 if __name__ == "__main__":
