@@ -290,7 +290,14 @@ def adjoint_run(n: int = 1024, nsteps: int = 4000, avg: int = 100, ckpt: int = 2
     fwd_s, bwd_s = st["forward_ms"] / 1e3, st["backward_ms"] / 1e3
     lups = n * n * nsteps
     ga = g.abs()
+    # FP64 flops per cell of one forward step (598) and of one backward step with its
+    # segment recompute (1614), from the ncu instruction counts of the adjoint kernels
+    flops = 598.0 + 1614.0
+    achieved = flops * lups / (fwd_s + bwd_s) / 1e12
     return {"workload": ADJOINT_WORKLOAD, "J": J, "max_abs_grad": float(ga.max()),
+            "roofline": {"bound": "alu", "unit": "FP64 TFLOP/s", "achieved": round(achieved, 3), "peak": 1.25,
+                         "frac": round(achieved / 1.25, 3), "flops_per_cell_step": flops,
+                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)"},
             "forward_s": round(fwd_s, 3), "backward_s": round(bwd_s, 3),
             "forward_MLUPS": round(lups / fwd_s / 1e6, 1),
             "forward_backward_MLUPS": round(lups / (fwd_s + bwd_s) / 1e6, 1),
@@ -376,6 +383,8 @@ def main():
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-lattice workload")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiation workload")
     ap.add_argument("--adjoint-only", action="store_true", help="run only the differentiation workload")
+    ap.add_argument("--adjoint-n", type=int, default=1024)
+    ap.add_argument("--adjoint-steps", type=int, default=4000)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=2000)
     args = ap.parse_args()
@@ -384,7 +393,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.adjoint_only:
-        print(json.dumps({"adjoint": adjoint_run()}), flush=True)
+        print(json.dumps({"adjoint": adjoint_run(args.adjoint_n, args.adjoint_steps, min(100, args.adjoint_steps),
+                                                  min(200, args.adjoint_steps))}), flush=True)
         return 0
     if args.batch_only:
         print(json.dumps({"batch": batch_run(args.batch_steps, args.batch_count)}), flush=True)

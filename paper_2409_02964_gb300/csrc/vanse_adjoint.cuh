@@ -35,25 +35,34 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "vanse_common.cuh"
+
 namespace lbmv {
 
 namespace adj {
 
-__constant__ int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__constant__ int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-__constant__ int kOpp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-__constant__ double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-// Eq. (17) / (A1): m = M f, and 36 M^-1
-__constant__ double kM[9][9] = {
-    {1, 1, 1, 1, 1, 1, 1, 1, 1},        {-4, -1, -1, -1, -1, 2, 2, 2, 2}, {4, -2, -2, -2, -2, 1, 1, 1, 1},
-    {0, 1, 0, -1, 0, 1, -1, -1, 1},     {0, -2, 0, 2, 0, 1, -1, -1, 1},   {0, 0, 1, 0, -1, 1, 1, -1, -1},
-    {0, 0, -2, 0, 2, 1, 1, -1, -1},     {0, 1, -1, 1, -1, 0, 0, 0, 0},    {0, 0, 0, 0, 0, 1, -1, 1, -1},
-};
-__constant__ double kMinv36[9][9] = {
-    {4, -4, 4, 0, 0, 0, 0, 0, 0},   {4, -1, -2, 6, -6, 0, 0, 9, 0},  {4, -1, -2, 0, 0, 6, -6, -9, 0},
-    {4, -1, -2, -6, 6, 0, 0, 9, 0}, {4, -1, -2, 0, 0, -6, 6, -9, 0}, {4, 2, 1, 6, 3, 6, 3, 0, 9},
-    {4, 2, 1, -6, -3, 6, 3, 0, -9}, {4, 2, 1, -6, -3, -6, -3, 0, 9}, {4, 2, 1, 6, 3, -6, -3, 0, -9},
-};
+// D2Q9 (Eq. 5) and the moment basis of Eq. (17) / (A1) as compile-time functions, so
+// that unrolled loops fold the zero and unit entries. The rows of M are orthogonal,
+// M M^T = diag(9, 36, 36, 6, 12, 6, 12, 4, 4), hence M^-1 = M^T diag(1 / |row|^2).
+__host__ __device__ constexpr double w_of(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+__host__ __device__ constexpr double m_of(int k, int i) {
+    // rows: 1, e = -4 + 3|c|^2, eps = 4 - 21|c|^2/2 + 9|c|^4/2, c_x, q_x = (-5 + 3|c|^2) c_x,
+    // c_y, q_y, c_x^2 - c_y^2, c_x c_y
+    return k == 0 ? 1.0
+         : k == 1 ? -4.0 + 3.0 * (ex_of(i) * ex_of(i) + ey_of(i) * ey_of(i))
+         : k == 2 ? 4.0 - 10.5 * (ex_of(i) * ex_of(i) + ey_of(i) * ey_of(i)) +
+                        4.5 * (ex_of(i) * ex_of(i) + ey_of(i) * ey_of(i)) * (ex_of(i) * ex_of(i) + ey_of(i) * ey_of(i))
+         : k == 3 ? (double)ex_of(i)
+         : k == 4 ? (-5.0 + 3.0 * (ex_of(i) * ex_of(i) + ey_of(i) * ey_of(i))) * ex_of(i)
+         : k == 5 ? (double)ey_of(i)
+         : k == 6 ? (-5.0 + 3.0 * (ex_of(i) * ex_of(i) + ey_of(i) * ey_of(i))) * ey_of(i)
+         : k == 7 ? (double)(ex_of(i) * ex_of(i) - ey_of(i) * ey_of(i))
+                  : (double)(ex_of(i) * ey_of(i));
+}
+__host__ __device__ constexpr double mnorm_of(int k) {
+    return k == 0 ? 9.0 : (k <= 2 ? 36.0 : (k == 4 || k == 6 ? 12.0 : (k == 3 || k == 5 ? 6.0 : 4.0)));
+}
+__host__ __device__ constexpr double minv_of(int i, int k) { return m_of(k, i) / mnorm_of(k); }
 
 struct Params {
     int nx, ny;
@@ -104,12 +113,13 @@ __device__ __forceinline__ void grad_at(const Params& p, const double* v, int x,
                                         double& gy) {
     gx = 0.0;
     gy = 0.0;
+#pragma unroll
     for (int i = 1; i < 9; ++i) {
         double sg;
-        const long long c = stencil_cell(p, x, y, kEx[i], kEy[i], sg);
+        const long long c = stencil_cell(p, x, y, ex_of(i), ey_of(i), sg);
         const double val = odd ? sg * v[c] : v[c];
-        gx += 3.0 * kW[i] * kEx[i] * val;
-        gy += 3.0 * kW[i] * kEy[i] * val;
+        gx += 3.0 * w_of(i) * ex_of(i) * val;
+        gy += 3.0 * w_of(i) * ey_of(i) * val;
     }
 }
 
@@ -119,9 +129,10 @@ __device__ __forceinline__ void grad_at(const Params& p, const double* v, int x,
 __device__ __forceinline__ double grad_T_at(const Params& p, const double* lx, const double* ly, int x, int y,
                                             bool odd) {
     double acc = 0.0;
+#pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const int ex = kEx[i], ey = kEy[i];
-        const double wgt = 3.0 * kW[i];
+        const int ex = ex_of(i), ey = ey_of(i);
+        const double wgt = 3.0 * w_of(i);
         int xs = x - ex;
         xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
         // direct: the stencil point (xs, ys) + e_i is (x, y)
@@ -149,9 +160,10 @@ __device__ __forceinline__ double grad_T_at(const Params& p, const double* lx, c
 // f(0) = f^eq(1, 0, phi) - F_i(0, phi g)/2
 __global__ void adj_init_kernel(Params p, const double* __restrict__ phi, double* __restrict__ f) {
     ADJ_LOOP(c, p.N) {
+    #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const double feq = i == 0 ? phi[c] - (5.0 / 9.0) * p.kappa : kW[i] * p.kappa;
-            const double Fi = 3.0 * kW[i] * (kEx[i] * p.gx + kEy[i] * p.gy) * phi[c];
+            const double feq = i == 0 ? phi[c] - (5.0 / 9.0) * p.kappa : w_of(i) * p.kappa;
+            const double Fi = 3.0 * w_of(i) * (ex_of(i) * p.gx + ey_of(i) * p.gy) * phi[c];
             f[i * p.N + c] = feq - 0.5 * Fi;
         }
     }
@@ -160,6 +172,7 @@ __global__ void adj_init_kernel(Params p, const double* __restrict__ phi, double
 __global__ void adj_fwd_rho(Params p, const double* __restrict__ f, const double* __restrict__ phi, Fields F) {
     ADJ_LOOP(c, p.N) {
         double s = 0.0;
+    #pragma unroll
         for (int i = 0; i < 9; ++i) s += f[i * p.N + c];
         F.s[c] = s;
         F.rho[c] = s / phi[c];
@@ -170,9 +183,10 @@ __global__ void adj_fwd_u(Params p, const double* __restrict__ f, const double* 
     ADJ_LOOP(c, p.N) {
         const int x = (int)(c % p.nx), y = (int)(c / p.nx);
         double jx = 0.0, jy = 0.0;
+    #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            jx += kEx[i] * f[i * p.N + c];
-            jy += kEy[i] * f[i * p.N + c];
+            jx += ex_of(i) * f[i * p.N + c];
+            jy += ey_of(i) * f[i * p.N + c];
         }
         double gx, gy;
         grad_at(p, F.rho, x, y, false, gx, gy);
@@ -215,10 +229,13 @@ struct Local {
 __device__ __forceinline__ void load_local(const Params& p, const double* f, const double* phi, const Fields& F,
                                            long long c, int x, int y, Local& L) {
     double fc[9];
+#pragma unroll
     for (int i = 0; i < 9; ++i) fc[i] = f[i * p.N + c];
+#pragma unroll
     for (int k = 0; k < 9; ++k) {
         double a = 0.0;
-        for (int i = 0; i < 9; ++i) a += kM[k][i] * fc[i];
+    #pragma unroll
+        for (int i = 0; i < 9; ++i) a += m_of(k, i) * fc[i];
         L.m[k] = a;
     }
     L.s = F.s[c];
@@ -265,16 +282,17 @@ __global__ void adj_fwd_collide(Params p, const double* __restrict__ f, const do
         load_local(p, f, phi, F, c, x, y, L);
         double mp[9];
         collide(p, L, mp);
+    #pragma unroll
         for (int i = 0; i < 9; ++i) {
             double v = 0.0;
-            for (int k = 0; k < 9; ++k) v += kMinv36[i][k] * mp[k];
-            v *= (1.0 / 36.0);
-            int xd = x + kEx[i];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v += minv_of(i, k) * mp[k];
+            int xd = x + ex_of(i);
             xd = xd < 0 ? xd + p.nx : (xd >= p.nx ? xd - p.nx : xd);
-            int yd = y + kEy[i];
+            int yd = y + ey_of(i);
             if (yd < 0 || yd >= p.ny) {
                 if (p.wall_y) {
-                    fn[kOpp[i] * p.N + c] = v;
+                    fn[opp_of(i) * p.N + c] = v;
                     continue;
                 }
                 yd = yd < 0 ? yd + p.ny : yd - p.ny;
@@ -291,7 +309,8 @@ __global__ void adj_objective(Params p, const double* __restrict__ f, Fields F, 
     for (int y = threadIdx.x; y < p.ny; y += blockDim.x) {
         const long long c = (long long)y * p.nx + p.x_out;
         double jx = 0.0;
-        for (int i = 1; i < 9; ++i) jx += kEx[i] * f[i * p.N + c];
+    #pragma unroll
+        for (int i = 1; i < 9; ++i) jx += ex_of(i) * f[i * p.N + c];
         v += jx + 0.5 * F.Fx[c];
     }
     part[threadIdx.x] = v;
@@ -310,20 +329,23 @@ __global__ void adj_bwd_collide(Params p, const double* __restrict__ f, const do
     ADJ_LOOP(c, p.N) {
         const int x = (int)(c % p.nx), y = (int)(c / p.nx);
         double lmp[9], lm[9];
+    #pragma unroll
         for (int k = 0; k < 9; ++k) lm[k] = 0.0;
         double lux = 0, luy = 0, lFx = 0, lFy = 0, lrho = 0, lphi = 0;
         double lg[8];
+    #pragma unroll
         for (int k = 0; k < 8; ++k) lg[k] = 0.0;
         if (lam_next) {
             // transpose of streaming
             double lp[9];
+#pragma unroll
             for (int i = 0; i < 9; ++i) {
-                int xd = x + kEx[i];
+                int xd = x + ex_of(i);
                 xd = xd < 0 ? xd + p.nx : (xd >= p.nx ? xd - p.nx : xd);
-                int yd = y + kEy[i];
+                int yd = y + ey_of(i);
                 if (yd < 0 || yd >= p.ny) {
                     if (p.wall_y) {
-                        lp[i] = lam_next[kOpp[i] * p.N + c];
+                        lp[i] = lam_next[opp_of(i) * p.N + c];
                         continue;
                     }
                     yd = yd < 0 ? yd + p.ny : yd - p.ny;
@@ -331,10 +353,12 @@ __global__ void adj_bwd_collide(Params p, const double* __restrict__ f, const do
                 lp[i] = lam_next[i * p.N + (long long)yd * p.nx + xd];
             }
             // f+ = M^-1 m+  ->  lambda m+ = M^-T lambda f+
+#pragma unroll
             for (int k = 0; k < 9; ++k) {
                 double a = 0.0;
-                for (int i = 0; i < 9; ++i) a += kMinv36[i][k] * lp[i];
-                lmp[k] = a * (1.0 / 36.0);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) a += minv_of(i, k) * lp[i];
+                lmp[k] = a;
             }
             Local L;
             load_local(p, f, phi, F, c, x, y, L);
@@ -393,7 +417,9 @@ __global__ void adj_bwd_collide(Params p, const double* __restrict__ f, const do
             lg[7] = ldivD - ldifD;
             lm[0] += ls;
         }
+    #pragma unroll
         for (int k = 0; k < 9; ++k) A.lm[k * p.N + c] = lm[k];
+    #pragma unroll
         for (int k = 0; k < 8; ++k) A.lg[k * p.N + c] = lg[k];
         A.lux[c] = lux;
         A.luy[c] = luy;
@@ -452,12 +478,15 @@ __global__ void adj_bwd_rho(Params p, const double* __restrict__ phi, Fields F, 
         const double lrho = A.lrho[c] + grad_T_at(p, A.ldrx, A.ldry, x, y, false);
         const double ph = phi[c];
         double lm[9];
+    #pragma unroll
         for (int k = 0; k < 9; ++k) lm[k] = A.lm[k * p.N + c];
         lm[0] += lrho / ph;
         gphi[c] += -lrho * F.s[c] / (ph * ph);
+    #pragma unroll
         for (int i = 0; i < 9; ++i) {
             double a = 0.0;
-            for (int k = 0; k < 9; ++k) a += kM[k][i] * lm[k];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) a += m_of(k, i) * lm[k];
             lam[i * p.N + c] = a;
         }
     }
@@ -467,7 +496,8 @@ __global__ void adj_bwd_rho(Params p, const double* __restrict__ phi, Fields F, 
 __global__ void adj_bwd_init(Params p, const double* __restrict__ lam, double* __restrict__ gphi) {
     ADJ_LOOP(c, p.N) {
         double a = lam[c];
-        for (int i = 1; i < 9; ++i) a -= 1.5 * kW[i] * (kEx[i] * p.gx + kEy[i] * p.gy) * lam[i * p.N + c];
+    #pragma unroll
+        for (int i = 1; i < 9; ++i) a -= 1.5 * w_of(i) * (ex_of(i) * p.gx + ey_of(i) * p.gy) * lam[i * p.N + c];
         gphi[c] += a;
     }
 }
