@@ -220,14 +220,9 @@ def channel_precision(n: int = 512, steps: int = 10000):
     return out
 
 
-def batch_lattices(count: int = 512, seed: int = 2409):
-    """Seeded lattices of the batched workload: n, tau, A, T, U0 per lattice."""
-    rng = np.random.default_rng(seed)
-    sizes = rng.choice(np.arange(32, 1025, 16), size=count)
-    taus = rng.uniform(0.55, 1.5, size=count)
-    amps = rng.uniform(0.05, 0.3, size=count)
-    return [(int(n), float(t), float(a), 1000.0 * (n / 64) ** 2, 0.01 * 64 / n)
-            for n, t, a in zip(sizes, taus, amps)]
+def batch_lattices(count: int = 512):
+    from synth import fields
+    return fields.batch_lattices(count)
 
 
 def batch_run(steps: int = 2000, count: int = 512, each_steps: int = 200):

@@ -55,3 +55,16 @@ def channel_phi(nx: int, ny: int, seed: int = DEFAULT_SEED, lo: float = 0.35, hi
 def rest_fields(nx: int, ny: int, rho0: float = 1.0):
     """rho = rho0, u = 0 everywhere (a channel starting from rest)."""
     return (np.full((ny, nx), rho0), np.zeros((ny, nx)), np.zeros((ny, nx)))
+
+
+def batch_lattices(count: int = 512, seed: int = DEFAULT_SEED):
+    """The batched workload's lattices: n uniform over {32, 48, ..., 1024}, tau ~
+    U[0.55, 1.5], amplitude A ~ U[0.05, 0.3] of the spatiotemporal manufactured
+    solution, with the diffusive scaling T = 1000 (n/64)^2, U0 = 0.01 (64/n).
+    Returns (n, tau, A, T, U0) per lattice."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice(np.arange(32, 1025, 16), size=count)
+    taus = rng.uniform(0.55, 1.5, size=count)
+    amps = rng.uniform(0.05, 0.3, size=count)
+    return [(int(n), float(t), float(a), 1000.0 * (n / 64) ** 2, 0.01 * 64 / n)
+            for n, t, a in zip(sizes, taus, amps)]

@@ -137,3 +137,25 @@ def test_adjoint_argument_errors(P):
             P.outlet_momentum(phi, P.Channel(**base))
     with pytest.raises(ValueError):
         P.outlet_momentum(phi[:, :9], P.Channel(nx=10, ny=8, nsteps=10, avg_steps=3))
+
+
+def test_full_size_workload_central_differences(P):
+    """The differentiation workload at full size (1024 x 1024 channel recipe, 4000
+    steps, J over the last 100, a checkpoint every 200): dJ/dphi against central
+    differences of the device's own J (h = 1e-4) at three cells: the largest
+    |dJ/dphi|, a cell of the outlet column and a seeded interior cell."""
+    n = 1024
+    ch = P.Channel(nx=n, ny=n, nsteps=4000, avg_steps=100, checkpoint_every=200)
+    phi = fields.channel_phi(n, n)
+    J, g, _ = P.outlet_momentum(phi, ch)
+    g = g.cpu().numpy()
+    rng = np.random.default_rng(2409)
+    cells = [tuple(int(v) for v in np.unravel_index(np.argmax(np.abs(g)), g.shape)), (n // 2, n - 1),
+             (int(rng.integers(n)), int(rng.integers(n)))]
+    h = 1e-4
+    for y, x in cells:
+        pp, pm = phi.copy(), phi.copy()
+        pp[y, x] += h
+        pm[y, x] -= h
+        fd = (P.outlet_momentum(pp, ch, grad=False)[0] - P.outlet_momentum(pm, ch, grad=False)[0]) / (2 * h)
+        assert abs(fd - g[y, x]) <= 1e-4 * np.abs(g).max(), (y, x, fd, g[y, x])

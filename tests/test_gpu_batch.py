@@ -239,3 +239,30 @@ def test_batch_argument_errors(P):
         b.velocity_error(len(LATTICES))
     assert e.value.status == capi.LBM_ERR_ARG
     b.close()
+
+
+def test_full_batch_sampled_lattices_match_oracle(P, O):
+    """The batched workload at full size (512 seeded lattices, 192.9 M cells) in the
+    launch configuration the benchmark times (persistent kernel, autotuned work-unit
+    height): 3 steps, then the smallest, a median and the largest lattice each
+    against the oracle run on that lattice alone."""
+    from synth import fields
+    lats = fields.batch_lattices(512)
+    b = P.Batch(lats)
+    b.autotune(trial_steps=2)
+    steps = 3
+    b.step(steps)
+    order = sorted(range(len(lats)), key=lambda i: lats[i][0])
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        n, tau, A, T, U0 = lats[i]
+        M = mms.Config1(n=n, T=T, A=A, U0=U0)
+        nu = (tau - 0.5) / 3.0
+        kw = O.rates_from_tau(tau, s_eps=1.2, s_q=1.2)
+        kw["s_e"] = 1.2
+        prm = O.Params(nx=n, ny=n, **kw, kappa=0.5, nthreads=0)
+        ux, uy = M.velocity(0)
+        f = O.init(prm, np.ones((n, n)), ux, uy, M.phi(0), M.force(0, nu))
+        for t in range(steps):
+            f = O.step(prm, f, M.phi(t), M.phi(t + 1), M.force(t, nu))
+        _check(b.populations(i).cpu().numpy(), f, M.phi(steps), steps, "fp32")
+    b.close()
