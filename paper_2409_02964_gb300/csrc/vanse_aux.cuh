@@ -259,20 +259,29 @@ __device__ __forceinline__ void block_reduce3(double a, double b, double c, doub
     }
 }
 
-// Mass sum f and momentum sum e f per cell, FP64 partial sums per block.
+// Mass sum f and momentum sum e f of one cell's nine populations, in the compute
+// type R. Used by both reductions below so that their per-cell terms are identical.
+template <typename R>
+__device__ __forceinline__ void cell_moments(const R f[9], R& m, R& jx, R& jy) {
+    m = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    jx = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
+    jy = (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
+}
+
+// Mass and momentum sums, FP64 partial sums per block. Rows are dealt to blocks and
+// columns to threads (32-bit indices, coalesced pulls); each cell's three sums are
+// formed in R and only the accumulation across cells runs in FP64, which keeps the
+// FP64 pipe (a small fraction of the FP32 rate on this part) off the critical path.
 template <typename S, typename R>
 __global__ void moments_reduce_kernel(const S* __restrict__ buf, const R* __restrict__ phi, double* __restrict__ partial,
                                       const Lattice<R> L) {
-    const long long n = (long long)L.nx * L.ny;
     double m = 0, jx = 0, jy = 0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(k / L.nx), x = (int)(k % L.nx);
-        R f[9];
-        pull_cell<S, R>(buf, phi, L, x, y, f);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const double v = (double)f[i];
-            m += v; jx += ex_of(i) * v; jy += ey_of(i) * v;
+    for (int y = blockIdx.x; y < L.ny; y += gridDim.x) {
+        for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
+            R f[9], cm, cx, cy;
+            pull_cell<S, R>(buf, phi, L, x, y, f);
+            cell_moments(f, cm, cx, cy);
+            m += (double)cm; jx += (double)cx; jy += (double)cy;
         }
     }
     block_reduce3(m, jx, jy, partial);
@@ -301,13 +310,10 @@ __global__ void row_moments_kernel(const S* __restrict__ buf, const R* __restric
     for (int y = blockIdx.x; y < L.ny; y += gridDim.x) {
         double m = 0, jx = 0, jy = 0;
         for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
-            R f[9];
+            R f[9], cm, cx, cy;
             pull_cell<S, R>(buf, phi, L, x, y, f);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const double v = (double)f[i];
-                m += v; jx += ex_of(i) * v; jy += ey_of(i) * v;
-            }
+            cell_moments(f, cm, cx, cy);
+            m += (double)cm; jx += (double)cx; jy += (double)cy;
         }
         m = warp_sum(m); jx = warp_sum(jx); jy = warp_sum(jy);
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
