@@ -138,6 +138,19 @@ static void matvec(const double A[Q][Q], const double* x, double* y)
     }
 }
 
+/* f = M^-1 m with the printed inverse (A1) applied as its integer matrix followed by
+ * one division by the common factor 36. Multiplying by rounded entries such as 4/36
+ * instead would scale the mass sum_i f_i = m_0 by 9 * fl(1/9) != 1 on every step,
+ * a steady drift of the quantity the step conserves exactly (S_0 = C_0 = 0). */
+static void apply_minv(const double* m, double* f)
+{
+    for (int i = 0; i < Q; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < Q; ++j) s += MINV36_TAB[i][j] * m[j];
+        f[i] = s / 36.0;
+    }
+}
+
 /* m = M f, Eq. (17) */
 void vo_moments(const double* f, double* m)
 {
@@ -429,9 +442,6 @@ int vo_step(const vo_params* p, const double* f, double* f_new, const double* ph
     const size_t N = (size_t)p->nx * p->ny;
     const double kappa = p->kappa;
     const double G[Q] = {p->s_c, p->s_e, p->s_eps, p->s_c, p->s_q, p->s_c, p->s_q, p->s_nu, p->s_nu};
-    double Minv[Q][Q];
-    vo_Minv(Minv);
-
     double* rho = (double*)malloc(N * sizeof(double));
     double* ux = (double*)malloc(N * sizeof(double));
     double* uy = (double*)malloc(N * sizeof(double));
@@ -476,7 +486,7 @@ int vo_step(const vo_params* p, const double* f, double* f_new, const double* ph
         vo_penalty_order(p->eq_order, kappa, phi_t[c], rho[c], dA, dB, dD, dtphi, p->model_b, C);
         for (int k = 0; k < Q; ++k)
             mp[k] = m[k] - G[k] * (m[k] - meq[k]) + (1.0 - 0.5 * G[k]) * (S[k] + C[k]);
-        matvec((const double(*)[Q])Minv, mp, fp);
+        apply_minv(mp, fp);
         for (int i = 0; i < Q; ++i) fplus[i * N + c] = fp[i];
     }
 
