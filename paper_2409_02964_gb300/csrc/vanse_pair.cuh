@@ -341,16 +341,19 @@ __device__ __forceinline__ void pair_phase3(const PairCtx<S, T>& c, const PRow& 
     a[7] = fma2(p.h_nu, S7 + Cb, fma2(p.s_nu, me7 - Cs.m[7], Cs.m[7]));
     const V2 S8 = fma2(ux, Fy, uy * Fx);
     a[8] = fma2(p.h_nu, S8 + Cc, fma2(p.s_nu, fma2(jxe, uy, -Cs.m[8]), Cs.m[8]));
-    // f+ = M^-1 m+ (A1)
+    // f+ = M^-1 m+ (A1); f_0 and the diagonal-link x/y parts as what m_0 and j leave
+    // after the other populations, so the rounded fractions of M^-1 do not scale the
+    // cell's mass and momentum by a fixed factor every step
     V2 fo[9];
-    fo[0] = (1.f / 9.f) * (a[0] - a[1] + a[2]);
     const V2 bax = (1.f / 36.f) * fma2(4.f, a[0], -fma2(2.f, a[2], a[1]));
-    const V2 bdg = (1.f / 36.f) * fma2(4.f, a[0], fma2(2.f, a[1], a[2]));
+    const V2 sbd = (1.f / 36.f) * fma2(8.f, a[0], a[1] - a[2]);
+    const V2 bdg = sbd - bax;
+    fo[0] = fma2(-4.f, sbd, a[0]);
     const V2 xa = (1.f / 6.f) * (a[3] - a[4]);
     const V2 ya = (1.f / 6.f) * (a[5] - a[6]);
     const V2 pq = 0.25f * a[7];
-    const V2 xd = tw * fma2(2.f, a[3], a[4]);
-    const V2 yd = tw * fma2(2.f, a[5], a[6]);
+    const V2 xd = 0.25f * fma2(-2.f, xa, a[3]);
+    const V2 yd = 0.25f * fma2(-2.f, ya, a[5]);
     const V2 pd = 0.25f * a[8];
     const V2 t13 = bax + pq, t24 = bax - pq;
     fo[1] = t13 + xa;

@@ -340,16 +340,21 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
     a[7] = Cs.m[7] + p.s_nu * (m0 * (ux * ux - uy * uy) - Cs.m[7]) + p.h_nu * ((R)2 * (ux * Fx - uy * Fy) + Cb);
     a[8] = Cs.m[8] + p.s_nu * (jxe * uy - Cs.m[8]) + p.h_nu * ((ux * Fy + uy * Fx) + Cc);
 
-    // f+ = M^-1 m+ (A1), the 1/36 folded into the coefficients
+    // f+ = M^-1 m+ (A1), the 1/36 folded into the coefficients. f_0 and the
+    // diagonal-link x/y parts are formed as what m_0 and j leave after the other
+    // populations (equal to (A1)'s rows; s = bax + bdg first, bdg = s - bax, exact
+    // near rest), so the rounded 1/9, 1/36, 1/6 and 1/12 do not scale the cell's mass
+    // and momentum by a fixed factor every step.
     R fo[9];
-    fo[0] = (a[0] - a[1] + a[2]) * ((R)1 / (R)9);
     const R bax = ((R)4 * a[0] - a[1] - (R)2 * a[2]) * ((R)1 / (R)36);
-    const R bdg = ((R)4 * a[0] + (R)2 * a[1] + a[2]) * ((R)1 / (R)36);
+    const R sbd = ((R)8 * a[0] + (a[1] - a[2])) * ((R)1 / (R)36);
+    const R bdg = sbd - bax;
+    fo[0] = a[0] - (R)4 * sbd;
     const R xa = (a[3] - a[4]) * ((R)1 / (R)6);
     const R ya = (a[5] - a[6]) * ((R)1 / (R)6);
     const R pq = a[7] * (R)0.25;
-    const R xd = ((R)2 * a[3] + a[4]) * twelfth;
-    const R yd = ((R)2 * a[5] + a[6]) * twelfth;
+    const R xd = (a[3] - (R)2 * xa) * (R)0.25;
+    const R yd = (a[5] - (R)2 * ya) * (R)0.25;
     const R pd = a[8] * (R)0.25;
     const R t13 = bax + pq, t24 = bax - pq;
     fo[1] = t13 + xa;
