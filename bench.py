@@ -150,11 +150,12 @@ def time_steps(lat, steps: int, warmup: int):
     return ev0.elapsed_time(ev1) / 1e3
 
 
-def e2e_run(lat, phi: np.ndarray, steps: int):
+def e2e_run(lat, phi: np.ndarray, steps: int, dtype=np.float32):
     """The per-step user sequence through the public API with host buffers: upload
-    phi(x, t) from pinned host memory, advance one step, read the FP64 mass back."""
+    phi(x, t) from pinned host memory (float32, the precision the FP32/FP16/BF16
+    storages compute with phi in), advance one step, read the FP64 mass back."""
     import torch
-    host_phi = torch.from_numpy(np.ascontiguousarray(phi, dtype=np.float64)).pin_memory()
+    host_phi = torch.from_numpy(np.ascontiguousarray(phi, dtype=dtype)).pin_memory()
     lat.set_void_fraction(host_phi)
     lat.step(1)
     lat.reduce()
@@ -166,7 +167,7 @@ def e2e_run(lat, phi: np.ndarray, steps: int):
         lat.reduce()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return dt, host_phi.numel() * 8, 3 * 8
+    return dt, host_phi.numel() * host_phi.element_size(), 3 * 8
 
 
 BATCH_WORKLOAD = ("512 independent periodic lattices, n uniform over {32,48,...,1024} (seed 2409), "
@@ -449,10 +450,12 @@ def main():
         }
     if not args.quick and rank == 0:
         e2e_steps = 30
-        dt, h2d, d2h = e2e_run(lat, phi, e2e_steps)
+        e2e_dtype = np.float64 if args.storage == "fp64" else np.float32
+        dt, h2d, d2h = e2e_run(lat, phi, e2e_steps, e2e_dtype)
         out["e2e"] = {"value": round(world * cells * e2e_steps / dt / 1e6, 1), "unit": "MLUPS",
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                      "sequence": "set_void_fraction(host phi) + step(1) + reduce() per step"}
+                      "sequence": f"set_void_fraction(pinned host phi, {np.dtype(e2e_dtype).name}) + step(1) + "
+                                  "reduce() per step"}
     lat.close()
     if not args.quick and rank == 0:
         variants = {}

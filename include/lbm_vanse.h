@@ -95,6 +95,13 @@ lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_va
 lbm_status lbm_vanse_set_void_fraction(lbm_vanse_t h, const double* phi_t, const double* phi_next,
                                        int on_device);
 
+/* The same with float arrays [ny][nx] (same meaning, ownership and errors). The
+ * FP32/FP16/BF16 storages compute with phi in FP32, so this form moves half the bytes
+ * of the double one and gives identical results for values that are floats already;
+ * FP64 storage widens the floats exactly. */
+lbm_status lbm_vanse_set_void_fraction_f32(lbm_vanse_t h, const float* phi_t, const float* phi_next,
+                                           int on_device);
+
 /* Body force F^B(x, t) = phi(x, t) * (gx, gy) + field(x) (Eq. 6; the phi G form of
  * Sec. 3.1 plus an optional per-cell part, [2][ny][nx], x component first, e.g.
  * the manufactured force of Eq. 25). field may be NULL. Stays in effect until the

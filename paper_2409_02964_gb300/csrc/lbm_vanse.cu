@@ -403,24 +403,52 @@ lbm_status run_reduce(lbm_vanse* h) {
 
 // Copy a caller array to device memory if it lives on the host; returns the
 // device pointer to use (caller's own pointer when on_device).
-lbm_status stage_in(lbm_vanse* h, const double* src, long long count, int on_device, double** dev, bool* owned) {
+template <typename T>
+lbm_status stage_in(lbm_vanse* h, const T* src, long long count, int on_device, T** dev, bool* owned) {
     *owned = false;
-    if (on_device) { *dev = const_cast<double*>(src); return LBM_OK; }
-    CK(h, cudaMallocAsync((void**)dev, (size_t)count * sizeof(double), h->stream));
+    if (on_device) { *dev = const_cast<T*>(src); return LBM_OK; }
+    CK(h, cudaMallocAsync((void**)dev, (size_t)count * sizeof(T), h->stream));
     *owned = true;
-    CK(h, cudaMemcpyAsync(*dev, src, (size_t)count * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(*dev, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice, h->stream));
     return LBM_OK;
 }
 
-lbm_status pad_into(lbm_vanse* h, const double* dev_src, void* dst) {
-    const long long n = (long long)h->prm.nx * h->prm.ny;
+template <typename T>
+lbm_status pad_into(lbm_vanse* h, const T* dev_src, void* dst) {
+    const int blocks = std::min(h->prm.ny, 65535);
     if (h->rbytes == 8)
-        pad_field_kernel<double><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>(dev_src, (double*)dst, h->prm.nx,
-                                                                               h->prm.ny, h->P);
+        pad_field_kernel<T, double><<<blocks, kAuxThreads, 0, h->stream>>>(dev_src, (double*)dst, h->prm.nx,
+                                                                           h->prm.ny, h->P);
     else
-        pad_field_kernel<float><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>(dev_src, (float*)dst, h->prm.nx,
-                                                                              h->prm.ny, h->P);
+        pad_field_kernel<T, float><<<blocks, kAuxThreads, 0, h->stream>>>(dev_src, (float*)dst, h->prm.nx,
+                                                                          h->prm.ny, h->P);
     CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+// lbm_vanse_set_void_fraction for double or float caller arrays.
+template <typename T>
+lbm_status set_void_fraction_impl(lbm_vanse* h, const T* phi_t, const T* phi_next, int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!phi_t) return fail(h, LBM_ERR_ARG, "phi_t is NULL");
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    T* d = nullptr;
+    bool owned = false;
+    lbm_status st = stage_in<T>(h, phi_t, n, on_device, &d, &owned);
+    if (st != LBM_OK) return st;
+    st = pad_into<T>(h, d, h->phi);
+    if (owned) cudaFreeAsync(d, h->stream);
+    if (st != LBM_OK) return st;
+    h->unsteady = false;
+    if (phi_next) {
+        st = stage_in<T>(h, phi_next, n, on_device, &d, &owned);
+        if (st != LBM_OK) return st;
+        st = pad_into<T>(h, d, h->phin);
+        if (owned) cudaFreeAsync(d, h->stream);
+        if (st != LBM_OK) return st;
+        h->unsteady = true;
+    }
+    h->phi_set = true;
     return LBM_OK;
 }
 
@@ -601,27 +629,12 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
 
 extern "C" lbm_status lbm_vanse_set_void_fraction(lbm_vanse_t h, const double* phi_t, const double* phi_next,
                                                   int on_device) {
-    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
-    if (!phi_t) return fail(h, LBM_ERR_ARG, "phi_t is NULL");
-    const long long n = (long long)h->prm.nx * h->prm.ny;
-    double* d = nullptr;
-    bool owned = false;
-    lbm_status st = stage_in(h, phi_t, n, on_device, &d, &owned);
-    if (st != LBM_OK) return st;
-    st = pad_into(h, d, h->phi);
-    if (owned) cudaFreeAsync(d, h->stream);
-    if (st != LBM_OK) return st;
-    h->unsteady = false;
-    if (phi_next) {
-        st = stage_in(h, phi_next, n, on_device, &d, &owned);
-        if (st != LBM_OK) return st;
-        st = pad_into(h, d, h->phin);
-        if (owned) cudaFreeAsync(d, h->stream);
-        if (st != LBM_OK) return st;
-        h->unsteady = true;
-    }
-    h->phi_set = true;
-    return LBM_OK;
+    return set_void_fraction_impl<double>(h, phi_t, phi_next, on_device);
+}
+
+extern "C" lbm_status lbm_vanse_set_void_fraction_f32(lbm_vanse_t h, const float* phi_t, const float* phi_next,
+                                                      int on_device) {
+    return set_void_fraction_impl<float>(h, phi_t, phi_next, on_device);
 }
 
 extern "C" lbm_status lbm_vanse_set_body_force(lbm_vanse_t h, double gx, double gy, const double* field,

@@ -65,13 +65,13 @@ __global__ void ghost_fill_kernel(S* __restrict__ buf, long long plane, int nx, 
         fill_ghosts<S>(buf, plane, nx, ny, P, k);
 }
 
-// Copy a dense [ny][nx] double field into a padded R field (with ghosts).
-template <typename R>
-__global__ void pad_field_kernel(const double* __restrict__ src, R* __restrict__ dst, int nx, int ny, int P) {
-    const long long n = (long long)nx * ny;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(k / nx), x = (int)(k % nx);
-        put_with_ghosts<R>(dst, P, nx, x, y, (R)src[k]);
+// Copy a dense [ny][nx] field (double or float) into a padded R field (with
+// ghosts). Rows are dealt to blocks and columns to threads (32-bit indices).
+template <typename Tin, typename R>
+__global__ void pad_field_kernel(const Tin* __restrict__ src, R* __restrict__ dst, int nx, int ny, int P) {
+    for (int y = blockIdx.x; y < ny; y += gridDim.x) {
+        const Tin* row = src + (long long)y * nx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) put_with_ghosts<R>(dst, P, nx, x, y, (R)row[x]);
     }
 }
 
@@ -268,22 +268,46 @@ __device__ __forceinline__ void cell_moments(const R f[9], R& m, R& jx, R& jy) {
     jy = (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
 }
 
-// Mass and momentum sums, FP64 partial sums per block. Rows are dealt to blocks and
-// columns to threads (32-bit indices, coalesced pulls); each cell's three sums are
-// formed in R and only the accumulation across cells runs in FP64, which keeps the
-// FP64 pipe (a small fraction of the FP32 rate on this part) off the critical path.
+// Compensated (Kahan) accumulation in R: s + c carries the sum to about one ulp of s
+// however many terms are added.
+template <typename R>
+__device__ __forceinline__ void kahan_add(R& s, R& c, R v) {
+    const R y = v - c;
+    const R t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// This thread's share of row y (columns threadIdx.x, + blockDim.x, ...): the three
+// sums of cell_moments, accumulated in R with compensation and added to m, jx, jy
+// in FP64. The FP64 pipe runs at a small fraction of the FP32 rate on this part, so
+// it sees three additions per thread and row instead of three per cell. Both
+// reductions below call this with the same block size, so their per-thread terms
+// are identical.
+template <typename S, typename R>
+__device__ __forceinline__ void row_thread_moments(const S* __restrict__ buf, const R* __restrict__ phi,
+                                                   const Lattice<R>& L, int y, double& m, double& jx, double& jy) {
+    R sm = 0, sx = 0, sy = 0, cm = 0, cx = 0, cy = 0;
+    for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
+        R f[9], vm, vx, vy;
+        pull_cell<S, R>(buf, phi, L, x, y, f);
+        cell_moments(f, vm, vx, vy);
+        kahan_add(sm, cm, vm);
+        kahan_add(sx, cx, vx);
+        kahan_add(sy, cy, vy);
+    }
+    m += (double)sm - (double)cm;
+    jx += (double)sx - (double)cx;
+    jy += (double)sy - (double)cy;
+}
+
+// Mass and momentum sums, FP64 partial sums per block; rows are dealt to blocks and
+// columns to threads (32-bit indices, coalesced pulls).
 template <typename S, typename R>
 __global__ void moments_reduce_kernel(const S* __restrict__ buf, const R* __restrict__ phi, double* __restrict__ partial,
                                       const Lattice<R> L) {
     double m = 0, jx = 0, jy = 0;
-    for (int y = blockIdx.x; y < L.ny; y += gridDim.x) {
-        for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
-            R f[9], cm, cx, cy;
-            pull_cell<S, R>(buf, phi, L, x, y, f);
-            cell_moments(f, cm, cx, cy);
-            m += (double)cm; jx += (double)cx; jy += (double)cy;
-        }
-    }
+    for (int y = blockIdx.x; y < L.ny; y += gridDim.x) row_thread_moments<S, R>(buf, phi, L, y, m, jx, jy);
     block_reduce3(m, jx, jy, partial);
 }
 
@@ -309,12 +333,7 @@ __global__ void row_moments_kernel(const S* __restrict__ buf, const R* __restric
     __shared__ double sh[3][32];
     for (int y = blockIdx.x; y < L.ny; y += gridDim.x) {
         double m = 0, jx = 0, jy = 0;
-        for (int x = threadIdx.x; x < L.nx; x += blockDim.x) {
-            R f[9], cm, cx, cy;
-            pull_cell<S, R>(buf, phi, L, x, y, f);
-            cell_moments(f, cm, cx, cy);
-            m += (double)cm; jx += (double)cx; jy += (double)cy;
-        }
+        row_thread_moments<S, R>(buf, phi, L, y, m, jx, jy);
         m = warp_sum(m); jx = warp_sum(jx); jy = warp_sum(jy);
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         if (lane == 0) { sh[0][wid] = m; sh[1][wid] = jx; sh[2][wid] = jy; }

@@ -31,25 +31,31 @@ def _check(st: int, handle) -> None:
 
 
 class _Arg:
-    """Holds a caller array as (pointer, on_device) for one call."""
+    """Holds a caller array as (pointer, on_device) for one call, converted to
+    ``dtype`` (float64, or float32 for the entry points that take floats)."""
 
-    def __init__(self, a, count: int, device: torch.device):
+    def __init__(self, a, count: int, device: torch.device, dtype=np.float64):
         if a is None:
             self.ptr, self.on_device, self._keep = None, 1, None
             return
         if isinstance(a, torch.Tensor) and a.is_cuda:
             if a.device != device:
                 raise ValueError(f"tensor on {a.device}, lattice on {device}")
-            t = a.detach().to(torch.float64).contiguous()
+            t = a.detach().to({np.float64: torch.float64, np.float32: torch.float32}[dtype]).contiguous()
             if t.numel() != count:
                 raise ValueError(f"expected {count} elements, got {t.numel()}")
             self.ptr, self.on_device, self._keep = t.data_ptr(), 1, t
         else:
             arr = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else np.asarray(a)
-            arr = np.ascontiguousarray(arr, dtype=np.float64)
+            arr = np.ascontiguousarray(arr, dtype=dtype)
             if arr.size != count:
                 raise ValueError(f"expected {count} elements, got {arr.size}")
             self.ptr, self.on_device, self._keep = arr.ctypes.data, 0, arr
+
+
+def _is_f32(a) -> bool:
+    return (isinstance(a, torch.Tensor) and a.dtype == torch.float32) or (
+        isinstance(a, np.ndarray) and a.dtype == np.float32)
 
 
 class Lattice:
@@ -117,11 +123,15 @@ class Lattice:
 
     # -- inputs
     def set_void_fraction(self, phi_t, phi_next=None) -> None:
-        a, b = _Arg(phi_t, self.n, self.device), _Arg(phi_next, self.n, self.device)
-        on = a.on_device if phi_next is None else a.on_device
+        """float32 arrays (numpy or torch) go through lbm_vanse_set_void_fraction_f32,
+        everything else as float64 through lbm_vanse_set_void_fraction."""
+        f32 = _is_f32(phi_t) and (phi_next is None or _is_f32(phi_next))
+        dt = np.float32 if f32 else np.float64
+        a, b = _Arg(phi_t, self.n, self.device, dt), _Arg(phi_next, self.n, self.device, dt)
         if phi_next is not None and a.on_device != b.on_device:
             raise ValueError("phi_t and phi_next must both be on the device or both on the host")
-        _check(self._L.lbm_vanse_set_void_fraction(self._h, a.ptr, b.ptr, on), self._h)
+        fn = self._L.lbm_vanse_set_void_fraction_f32 if f32 else self._L.lbm_vanse_set_void_fraction
+        _check(fn(self._h, a.ptr, b.ptr, a.on_device), self._h)
 
     def set_body_force(self, gx: float = 0.0, gy: float = 0.0, field=None) -> None:
         a = _Arg(field, 2 * self.n, self.device)

@@ -288,6 +288,35 @@ def test_fp32_long_run_conserves_mass_and_momentum(P, kernel):
     assert abs(jy1 - jy0) < 2e-4 * abs(jy0), (jy0, jy1)
 
 
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16"])
+def test_float_void_fraction_upload_equals_double(P, storage):
+    """lbm_vanse_set_void_fraction_f32 (host, pinned host and device float arrays)
+    gives bit-identical steps to the double entry point fed the same values."""
+    import torch
+    nx, ny = 77, 30
+    case = random_case(nx, ny, seed=5, wall_y=True, unsteady=True, field=True, g=(1e-5, 0.0))
+    phi32, phin32 = case["phi"].astype(np.float32), case["phin"].astype(np.float32)
+    case = dict(case, phi=phi32.astype(np.float64), phin=phin32.astype(np.float64))
+    out = []
+    for form in ("f64", "host", "pinned", "device"):
+        if form == "f64":
+            lat = _gpu_lattice(P, nx, ny, 0.8, True, storage, case)
+        else:
+            lat = P.Lattice(nx, ny, 0.8, s_eps=1.2, s_q=1.4, bc_y="bounceback", storage=storage)
+            a, b = phi32, phin32
+            if form != "host":
+                a, b = torch.from_numpy(a), torch.from_numpy(b)
+                a, b = (a.pin_memory(), b.pin_memory()) if form == "pinned" else (a.cuda(), b.cuda())
+            lat.set_void_fraction(a, b)
+            lat.set_body_force(case["g"][0], case["g"][1], case["fb"])
+            lat.init_fields(case["rho"], case["ux"], case["uy"])
+        lat.step(5)
+        out.append(lat.get_populations().cpu().numpy())
+        lat.close()
+    for f in out[1:]:
+        assert np.array_equal(f, out[0])
+
+
 def test_populations_roundtrip(P):
     nx, ny = 40, 17
     case = random_case(nx, ny, seed=9)
