@@ -91,7 +91,10 @@ lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_va
 /* Void fraction phi(x, t) of the next step and phi(x, t+1) (Eq. 7, 13, 14, 20;
  * d_t phi = phi(t+1) - phi(t), Sec. 2.3). phi_next = NULL means steady. After a
  * step, phi(t) takes the value of phi(t+1) and the field is steady until the next
- * call. Values must lie in (0, 1]. Must be called before lbm_vanse_init_fields. */
+ * call. Values must lie in (0, 1]. Must be called before lbm_vanse_init_fields.
+ * Host arrays in pinned (page-locked) memory are copied on a stream of the
+ * library's own, so the copy overlaps the steps still queued on the lattice's
+ * stream; the call returns once the arrays have been read, as for any host array. */
 lbm_status lbm_vanse_set_void_fraction(lbm_vanse_t h, const double* phi_t, const double* phi_next,
                                        int on_device);
 
@@ -147,6 +150,15 @@ lbm_status lbm_vanse_set_populations(lbm_vanse_t h, const double* f, int on_devi
  * momentum sum_x sum_i e_i f_i (= sum of j = phi rho u - F/2, Eq. 17). Results to
  * host memory (synchronises). Returns LBM_ERR_DIVERGED if any is NaN/Inf. */
 lbm_status lbm_vanse_reduce(lbm_vanse_t h, double* mass, double* momx, double* momy);
+
+/* The same three sums without waiting for them: the reduction and a copy of the
+ * result to out[0..2] (mass, momentum x, momentum y; FP64) are queued on the
+ * lattice's stream and the call returns at once. out is device memory when
+ * on_device, else host memory (pinned, for the copy to be asynchronous); it must
+ * stay valid until the stream has passed the copy, and holds the sums only then
+ * (after lbm_vanse_sync, or an event recorded on the stream after this call). No
+ * divergence check: the caller tests the values for finiteness. */
+lbm_status lbm_vanse_reduce_async(lbm_vanse_t h, double* out, int on_device);
 
 /* Velocity error of Eq. (26), accumulated in FP64:
  * *num = sum |u - u_ref|^2, *den = sum |u_ref|^2 (E_u = sqrt(num/den)).

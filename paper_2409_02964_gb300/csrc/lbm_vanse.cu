@@ -91,6 +91,12 @@ struct lbm_vanse {
         }
     } gkey{};
     bool use_graphs = true;
+    // uploads from pinned host memory: copied on their own stream into device staging
+    // buffers (phi(t), phi(t+1)), so the copy overlaps the work already queued on
+    // `stream`; staging_free marks the last read of the staging buffers on `stream`
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_done = nullptr, staging_free = nullptr;
+    void* staging[2] = {nullptr, nullptr};
     int kernel = 1;               // step-kernel variant (see kNumKernels)
     bool pair = false;            // two columns per thread (packed FP32) step kernel
     std::string msg;
@@ -401,8 +407,16 @@ lbm_status run_reduce(lbm_vanse* h) {
         }                                                                        \
     }())
 
+bool host_pinned(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeHost;
+}
+
 // Copy a caller array to device memory if it lives on the host; returns the
-// device pointer to use (caller's own pointer when on_device).
+// device pointer to use (caller's own pointer when on_device). A copy from pinned
+// memory is asynchronous, so the call waits for it: the caller may reuse its array
+// as soon as the entry point returns.
 template <typename T>
 lbm_status stage_in(lbm_vanse* h, const T* src, long long count, int on_device, T** dev, bool* owned) {
     *owned = false;
@@ -410,6 +424,7 @@ lbm_status stage_in(lbm_vanse* h, const T* src, long long count, int on_device, 
     CK(h, cudaMallocAsync((void**)dev, (size_t)count * sizeof(T), h->stream));
     *owned = true;
     CK(h, cudaMemcpyAsync(*dev, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    if (host_pinned(src)) CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
 
@@ -426,12 +441,48 @@ lbm_status pad_into(lbm_vanse* h, const T* dev_src, void* dst) {
     return LBM_OK;
 }
 
+// Upload of phi(t) [and phi(t+1)] from pinned host arrays: the copies run on the
+// copy stream into the staging buffers, overlapping whatever `stream` is still
+// executing (e.g. the previous step); the call returns once the caller's arrays
+// have been read, and the padding kernels follow on `stream`.
+template <typename T>
+lbm_status upload_void_fraction_pinned(lbm_vanse* h, const T* phi_t, const T* phi_next) {
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    const size_t bytes = (size_t)n * sizeof(T);
+    if (!h->copy_stream) {
+        CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        CK(h, cudaEventCreateWithFlags(&h->copy_done, cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->staging_free, cudaEventDisableTiming));
+        CK(h, cudaEventRecord(h->staging_free, h->stream));
+    }
+    for (int k = 0; k < (phi_next ? 2 : 1); ++k)
+        if (!h->staging[k]) CK(h, cudaMalloc(&h->staging[k], (size_t)n * sizeof(double)));
+    CK(h, cudaStreamWaitEvent(h->copy_stream, h->staging_free, 0));
+    CK(h, cudaMemcpyAsync(h->staging[0], phi_t, bytes, cudaMemcpyHostToDevice, h->copy_stream));
+    if (phi_next) CK(h, cudaMemcpyAsync(h->staging[1], phi_next, bytes, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(h, cudaEventRecord(h->copy_done, h->copy_stream));
+    CK(h, cudaEventSynchronize(h->copy_done));
+    CK(h, cudaStreamWaitEvent(h->stream, h->copy_done, 0));
+    lbm_status st = pad_into<T>(h, (const T*)h->staging[0], h->phi);
+    if (st == LBM_OK && phi_next) st = pad_into<T>(h, (const T*)h->staging[1], h->phin);
+    if (st != LBM_OK) return st;
+    CK(h, cudaEventRecord(h->staging_free, h->stream));
+    return LBM_OK;
+}
+
 // lbm_vanse_set_void_fraction for double or float caller arrays.
 template <typename T>
 lbm_status set_void_fraction_impl(lbm_vanse* h, const T* phi_t, const T* phi_next, int on_device) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (!phi_t) return fail(h, LBM_ERR_ARG, "phi_t is NULL");
     const long long n = (long long)h->prm.nx * h->prm.ny;
+    if (!on_device && host_pinned(phi_t) && (!phi_next || host_pinned(phi_next))) {
+        lbm_status st = upload_void_fraction_pinned<T>(h, phi_t, phi_next);
+        if (st != LBM_OK) return st;
+        h->unsteady = phi_next != nullptr;
+        h->phi_set = true;
+        return LBM_OK;
+    }
     T* d = nullptr;
     bool owned = false;
     lbm_status st = stage_in<T>(h, phi_t, n, on_device, &d, &owned);
@@ -804,6 +855,17 @@ extern "C" lbm_status lbm_vanse_reduce(lbm_vanse_t h, double* mass, double* momx
     return LBM_OK;
 }
 
+extern "C" lbm_status lbm_vanse_reduce_async(lbm_vanse_t h, double* out, int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lattice not initialised");
+    lbm_status st = DISPATCH(h, run_reduce);
+    if (st != LBM_OK) return st;
+    CK(h, cudaMemcpyAsync(out, h->red_out, 3 * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_vanse_velocity_error(lbm_vanse_t h, const double* ux_ref, const double* uy_ref,
                                                int on_device, double* num, double* den) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
@@ -883,7 +945,14 @@ extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
     cudaStreamSynchronize(h->stream);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    void* ptrs[] = {h->f[0], h->f[1], h->phi, h->phin, h->fb, h->err, h->partial, h->red_out, h->scratch};
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+        cudaEventDestroy(h->copy_done);
+        cudaEventDestroy(h->staging_free);
+    }
+    void* ptrs[] = {h->f[0], h->f[1], h->phi, h->phin, h->fb, h->err, h->partial, h->red_out, h->scratch,
+                    h->staging[0], h->staging[1]};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;

@@ -189,6 +189,19 @@ class Lattice:
         _check(self._L.lbm_vanse_reduce(self._h, ctypes.byref(m), ctypes.byref(jx), ctypes.byref(jy)), self._h)
         return m.value, jx.value, jy.value
 
+    def reduce_async(self, out: torch.Tensor) -> None:
+        """Queue the mass and momentum sums into ``out`` (3 float64, on this device or
+        in pinned host memory) without waiting; they are there once the stream has
+        passed this point (e.g. a ``torch.cuda.Event`` recorded after the call)."""
+        if out.dtype != torch.float64 or out.numel() < 3 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of at least 3 elements")
+        if out.is_cuda:
+            if out.device != self.device:
+                raise ValueError(f"tensor on {out.device}, lattice on {self.device}")
+        elif not out.is_pinned():
+            raise ValueError("a host out tensor must be in pinned memory")
+        _check(self._L.lbm_vanse_reduce_async(self._h, out.data_ptr(), int(out.is_cuda)), self._h)
+
     def velocity_error(self, ux_ref, uy_ref):
         a, b = _Arg(ux_ref, self.n, self.device), _Arg(uy_ref, self.n, self.device)
         num, den = ctypes.c_double(), ctypes.c_double()

@@ -298,16 +298,22 @@ def test_float_void_fraction_upload_equals_double(P, storage):
     phi32, phin32 = case["phi"].astype(np.float32), case["phin"].astype(np.float32)
     case = dict(case, phi=phi32.astype(np.float64), phin=phin32.astype(np.float64))
     out = []
-    for form in ("f64", "host", "pinned", "device"):
+    for form in ("f64", "host", "pinned", "device", "pinned64"):
         if form == "f64":
             lat = _gpu_lattice(P, nx, ny, 0.8, True, storage, case)
         else:
             lat = P.Lattice(nx, ny, 0.8, s_eps=1.2, s_q=1.4, bc_y="bounceback", storage=storage)
             a, b = phi32, phin32
+            if form == "pinned64":
+                a, b = a.astype(np.float64), b.astype(np.float64)
             if form != "host":
                 a, b = torch.from_numpy(a), torch.from_numpy(b)
-                a, b = (a.pin_memory(), b.pin_memory()) if form == "pinned" else (a.cuda(), b.cuda())
+                a, b = (a.cuda(), b.cuda()) if form == "device" else (a.pin_memory(), b.pin_memory())
             lat.set_void_fraction(a, b)
+            if form.startswith("pinned"):
+                # the call returns once the pinned arrays are read: reusing them at once is safe
+                a.fill_(0.25)
+                b.fill_(0.25)
             lat.set_body_force(case["g"][0], case["g"][1], case["fb"])
             lat.init_fields(case["rho"], case["ux"], case["uy"])
         lat.step(5)
@@ -315,6 +321,38 @@ def test_float_void_fraction_upload_equals_double(P, storage):
         lat.close()
     for f in out[1:]:
         assert np.array_equal(f, out[0])
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_reduce_async_and_overlapped_uploads(P, storage):
+    """lbm_vanse_reduce_async into device and pinned host memory gives reduce()'s
+    sums; pinned void-fraction uploads queued between steps (copied on the library's
+    own stream while the previous step runs) give the same populations as uploads
+    from device memory."""
+    import torch
+    nx, ny, steps = 200, 64, 12
+    case = channel_case(nx, ny, g=1e-5)
+    rng = np.random.default_rng(8)
+    phis = [np.clip(case["phi"] + 0.01 * rng.normal(size=case["phi"].shape), 0.3, 1.0) for _ in range(steps)]
+    res = []
+    for form in ("device", "pinned"):
+        lat = _gpu_lattice(P, nx, ny, 0.6, True, storage, case, **CHANNEL_RATES)
+        host = torch.zeros((steps, 3), dtype=torch.float64).pin_memory()
+        dev = torch.zeros((steps, 3), dtype=torch.float64, device="cuda")
+        for t in range(steps):
+            ph = torch.from_numpy(phis[t])
+            lat.set_void_fraction(ph.cuda() if form == "device" else ph.pin_memory())
+            lat.step(1)
+            lat.reduce_async(host[t])
+            lat.reduce_async(dev[t])
+        lat.sync()
+        want = np.array(lat.reduce())
+        assert np.array_equal(host[-1].numpy(), want)
+        assert np.array_equal(dev[-1].cpu().numpy(), want)
+        res.append((host.numpy().copy(), lat.get_populations().cpu().numpy()))
+        lat.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
 
 
 def test_populations_roundtrip(P):
