@@ -153,25 +153,23 @@ def time_steps(lat, steps: int, warmup: int):
 def e2e_run(lat, phi: np.ndarray, steps: int, dtype=np.float32):
     """The per-step user sequence through the public API with host buffers: upload
     phi(x, t) from pinned host memory (float32, the precision the FP32/FP16/BF16
-    storages compute with phi in), advance one step, and read that step's FP64 mass
-    and momentum back into pinned host memory (lbm_vanse_reduce_async). The host
-    reads each step's sums one step later, so the upload of step t+1 (copied on the
-    library's own stream) overlaps step t on the device."""
+    storages compute with phi in), advance one step whose kernel also sums the FP64
+    mass and momentum it writes, and copy those sums into pinned host memory
+    (lbm_vanse_step_sums). The host reads each step's sums one step later, so the
+    upload of step t+1 (copied on the library's own stream) overlaps step t."""
     import torch
     host_phi = torch.from_numpy(np.ascontiguousarray(phi, dtype=dtype)).pin_memory()
     out = torch.zeros((2, 3), dtype=torch.float64).pin_memory()
     ev = [torch.cuda.Event(), torch.cuda.Event()]
     lat.set_void_fraction(host_phi)
-    lat.step(1)
-    lat.reduce_async(out[0])
+    lat.step_sums(out[0])
     torch.cuda.synchronize()
     mass = []
     t0 = time.perf_counter()
     for t in range(steps):
         k = t & 1
         lat.set_void_fraction(host_phi)
-        lat.step(1)
-        lat.reduce_async(out[k])
+        lat.step_sums(out[k])
         ev[k].record(lat.stream)
         if t:
             ev[k ^ 1].synchronize()
@@ -468,9 +466,9 @@ def main():
         dt, h2d, d2h = e2e_run(lat, phi, e2e_steps, e2e_dtype)
         out["e2e"] = {"value": round(world * cells * e2e_steps / dt / 1e6, 1), "unit": "MLUPS",
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                      "sequence": f"set_void_fraction(pinned host phi, {np.dtype(e2e_dtype).name}) + step(1) + "
-                                  "reduce_async(pinned host out) per step; each step's FP64 mass read on the "
-                                  "host one step later"}
+                      "sequence": f"set_void_fraction(pinned host phi, {np.dtype(e2e_dtype).name}) + "
+                                  "step_sums(pinned host out) per step (one step that also sums its FP64 mass "
+                                  "and momentum); each step's sums read on the host one step later"}
     lat.close()
     if not args.quick and rank == 0:
         variants = {}

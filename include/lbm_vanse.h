@@ -160,6 +160,15 @@ lbm_status lbm_vanse_reduce(lbm_vanse_t h, double* mass, double* momx, double* m
  * divergence check: the caller tests the values for finiteness. */
 lbm_status lbm_vanse_reduce_async(lbm_vanse_t h, double* out, int on_device);
 
+/* One step (as lbm_vanse_step(h, 1)) whose kernel also sums, over the lattice, the
+ * post-collision moments it writes: out[0] = sum m_0+ (the mass, which Eq. 16
+ * conserves), out[1..2] = sum j+ = sum (j + F) (Eq. 16 with S_3 = F_x, S_5 = F_y):
+ * the momentum of the new populations before they stream. FP64 sums of per-thread
+ * compensated partials; no separate pass over the populations. Queued like
+ * lbm_vanse_reduce_async (same rules for out and on_device; no waiting, no
+ * divergence check). Step kernels 1 and 5 (the defaults); LBM_ERR_ARG for 2-4. */
+lbm_status lbm_vanse_step_sums(lbm_vanse_t h, double* out, int on_device);
+
 /* Velocity error of Eq. (26), accumulated in FP64:
  * *num = sum |u - u_ref|^2, *den = sum |u_ref|^2 (E_u = sqrt(num/den)).
  * ux_ref, uy_ref: [ny][nx]. Results to host memory. */

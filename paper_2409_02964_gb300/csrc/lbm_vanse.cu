@@ -91,6 +91,7 @@ struct lbm_vanse {
         }
     } gkey{};
     bool use_graphs = true;
+    bool sums_configured = false; // shared-memory attributes set on the step-sum kernel variant
     // uploads from pinned host memory: copied on their own stream into device staging
     // buffers (phi(t), phi(t+1)), so the copy overlaps the work already queued on
     // `stream`; staging_free marks the last read of the staging buffers on `stream`
@@ -223,8 +224,20 @@ lbm_status configure(lbm_vanse* h) {
     return LBM_OK;
 }
 
+// The step-sum variant of the handle's step kernel (kernels 1 and 5; nullptr for
+// the others).
 template <typename S>
-lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src) {
+const void* step_sums_kernel_ptr(const lbm_vanse* h) {
+    using R = typename Prec<S>::R;
+    if constexpr (!std::is_same<S, double>::value) {
+        if (h->kernel == 5) return (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB, true>;
+        if (h->kernel != 1) return nullptr;
+    }
+    return (const void*)vanse_step_kernel<S, R, kThreads, true>;
+}
+
+template <typename S>
+lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums = nullptr) {
     using R = typename Prec<S>::R;
     StepParams<R> p;
     p.src = h->f[src];
@@ -266,7 +279,33 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src) {
     p.drag_d1 = (R)h->drag_d1;
     p.us_x = (R)h->us_x;
     p.us_y = (R)h->us_y;
+    p.sums = sums;
     dim3 grid(h->gridx, h->gridy);
+    if (sums) {
+        if (!h->sums_configured) {
+            const void* kern = step_sums_kernel_ptr<S>(h);
+            if (!kern) return fail(h, LBM_ERR_ARG, "step sums need step kernel 1 or 5 (kernel %d)", h->kernel);
+            CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)step_smem_bytes<S>(h, 4)));
+            CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared));
+            h->sums_configured = true;
+        }
+        if constexpr (!std::is_same<S, double>::value) {
+            if (h->kernel == 5) {
+                vanse_warp_kernel<S, LBMV_WARP_MINB, true><<<grid, 32, smem, stream>>>(p);
+                CK(h, cudaGetLastError());
+                const long long ng = 9LL * h->prm.ny * 2 * kGhost;
+                ghost_fill_kernel<S><<<(int)std::min<long long>((ng + 255) / 256, 4096), 256, 0, stream>>>(
+                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P);
+                CK(h, cudaGetLastError());
+                return LBM_OK;
+            }
+        }
+        vanse_step_kernel<S, R, kThreads, true><<<grid, kThreads, smem, stream>>>(p);
+        CK(h, cudaGetLastError());
+        return LBM_OK;
+    }
     if constexpr (!std::is_same<S, double>::value) {
         switch (h->kernel) {
             case 2: vanse_pair_kernel<S, 64, 6><<<grid, 64, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
@@ -291,8 +330,8 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src) {
 }
 
 template <typename S>
-lbm_status launch_step(lbm_vanse* h) {
-    lbm_status st = enqueue_step<S>(h, h->stream, h->cur);
+lbm_status launch_step(lbm_vanse* h, double* sums = nullptr) {
+    lbm_status st = enqueue_step<S>(h, h->stream, h->cur, sums);
     if (st != LBM_OK) return st;
     h->cur = 1 - h->cur;
     if (h->unsteady) {
@@ -852,6 +891,20 @@ extern "C" lbm_status lbm_vanse_reduce(lbm_vanse_t h, double* mass, double* momx
     if (momy) *momy = r[2];
     if (!std::isfinite(r[0]) || !std::isfinite(r[1]) || !std::isfinite(r[2]))
         return fail(h, LBM_ERR_DIVERGED, "non-finite populations (mass %g)", r[0]);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_step_sums(lbm_vanse_t h, double* out, int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!out) return fail(h, LBM_ERR_ARG, "out is NULL");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "init_fields or set_populations must come first");
+    if (h->kernel != 1 && h->kernel != 5)
+        return fail(h, LBM_ERR_ARG, "step sums need step kernel 1 or 5 (kernel %d)", h->kernel);
+    CK(h, cudaMemsetAsync(h->red_out, 0, 3 * sizeof(double), h->stream));
+    lbm_status st = DISPATCH(h, launch_step, h->red_out);
+    if (st != LBM_OK) return st;
+    CK(h, cudaMemcpyAsync(out, h->red_out, 3 * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
     return LBM_OK;
 }
 

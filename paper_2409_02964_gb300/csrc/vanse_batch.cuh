@@ -63,6 +63,7 @@ template <typename S>
 struct BatchCtx {
     using L = WarpLayout<S>;
     static constexpr bool kUnsteady = true;
+    static constexpr bool kSums = false;
     StepParams<float> p;       // this lattice's scalars (pointers and sizes included)
     unsigned char* smem;
     int lane, xa, sa;

@@ -76,6 +76,22 @@ struct StepParams {
     int eq2;              // App. B: (B2) energy-flux equilibria and the (B3) penalty (kernel 1 only)
     int has_drag;         // F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi)); u solved implicitly
     R drag_d0, drag_d1, us_x, us_y;
+    double* sums;         // step-sum variants: FP64 sums of m_0+, j_x+, j_y+ over the cells written (added)
+};
+
+// Compensated (Kahan) sums of the post-collision m_0, j_x, j_y of the cells one
+// thread writes, for the step-sum kernel variants: the running sums stay within
+// about one ulp of their value over the whole strip.
+template <typename R>
+struct MomentSums {
+    R s[3] = {0, 0, 0}, c[3] = {0, 0, 0};
+    __device__ __forceinline__ void add(int k, R v) {
+        const R y = v - c[k];
+        const R t = s[k] + y;
+        c[k] = (t - s[k]) - y;
+        s[k] = t;
+    }
+    __device__ __forceinline__ double value(int k) const { return (double)s[k] - (double)c[k]; }
 };
 
 // Per-row register state (see the header comment for who writes what when).
@@ -257,9 +273,9 @@ __device__ __forceinline__ void phase2(const StepCtx<S, R, T>& c, const RowState
 }
 
 // Phase 3 for row p3 (state Cs), rows p3-1 / p3+1 in An / Bs: C, collision, store.
-template <typename S, typename R, int T>
+template <typename S, typename R, int T, bool SUMS = false>
 __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState<R>& An, const RowState<R>& Bs,
-                                       const RowState<R>& Cs, int p3) {
+                                       const RowState<R>& Cs, int p3, MomentSums<R>* sums = nullptr) {
     const StepParams<R>& p = c.p;
     const R twelfth = (R)1 / (R)12;
     // 12 x the Eq. (10) derivatives
@@ -340,6 +356,8 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
     a[7] = Cs.m[7] + p.s_nu * (m0 * (ux * ux - uy * uy) - Cs.m[7]) + p.h_nu * ((R)2 * (ux * Fx - uy * Fy) + Cb);
     a[8] = Cs.m[8] + p.s_nu * (jxe * uy - Cs.m[8]) + p.h_nu * ((ux * Fy + uy * Fx) + Cc);
 
+    if constexpr (SUMS) { sums->add(0, a[0]); sums->add(1, a[3]); sums->add(2, a[5]); }
+
     // f+ = M^-1 m+ (A1), the 1/36 folded into the coefficients. f_0 and the
     // diagonal-link x/y parts are formed as what m_0 and j leave after the other
     // populations (equal to (A1)'s rows; s = bax + bdg first, bdg = s - bax, exact
@@ -392,7 +410,7 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
     }
 }
 
-template <typename S, typename R, int T>
+template <typename S, typename R, int T, bool SUMS = false>
 __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ StepParams<R> p) {
     using L = StepLayout<S, R, T>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -429,6 +447,7 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
     const bool ph2_thread = (t >= 1 && t < T - 1);
 
     RowState<R> s0, s1, s2;
+    MomentSums<R> sums;
 
     // one iteration: new row p1 -> An, row p1-1 -> Bs, row p1-2 -> Cs
     auto iter = [&](RowState<R>& An, RowState<R>& Bs, RowState<R>& Cs, const int p1) -> bool {
@@ -477,7 +496,7 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
             }
         }
         const bool ph3 = (p3 >= y0) && (p3 < y1);
-        if (ph3 && ph3_thread && c.xc < p.nx) phase3<S, R, T>(c, An, Bs, Cs, p3);
+        if (ph3 && ph3_thread && c.xc < p.nx) phase3<S, R, T, SUMS>(c, An, Bs, Cs, p3, &sums);
         return true;
     };
 
@@ -494,6 +513,15 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
         for (int r = c.waited + 1; r <= c.issued; ++r) {
             const uint32_t parity = (uint32_t)(((r - c.rlo) >> 3) & 1);
             mbar_wait_bounded(c.bar(r), parity, kWaitTries);
+        }
+    }
+    if constexpr (SUMS) {
+        // one FP64 atomic per CTA and sum (warps reduce by shuffles, then lane 0 adds)
+        for (int k = 0; k < 3; ++k) {
+            double v = sums.value(k);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((t & 31) == 0) atomicAdd(p.sums + k, v);
         }
     }
 }

@@ -74,10 +74,26 @@ struct RowCopy {
     }
 };
 
-template <typename S>
+// Compensated sums of the post-collision m_0, j_x, j_y of the column pairs a lane
+// writes (step-sum variants of the one-warp kernel).
+struct PairSums {
+    V2 s[3] = {bc(0.f), bc(0.f), bc(0.f)}, c[3] = {bc(0.f), bc(0.f), bc(0.f)};
+    __device__ __forceinline__ void add(int k, V2 v) {
+        const V2 y = v - c[k];
+        const V2 t = s[k] + y;
+        c[k] = (t - s[k]) - y;
+        s[k] = t;
+    }
+    __device__ __forceinline__ double value(int k) const {
+        return ((double)s[k].v.x - (double)c[k].v.x) + ((double)s[k].v.y - (double)c[k].v.y);
+    }
+};
+
+template <typename S, bool SUMS = false>
 struct WarpCtx {
     using L = WarpLayout<S>;
     static constexpr bool kUnsteady = false;   // the fast path runs only on steady strips
+    static constexpr bool kSums = SUMS;        // accumulate the written cells' m_0+, j+ (PairSums)
     const StepParams<float>& p;
     unsigned char* smem;
     int lane, xa, sa;
@@ -90,6 +106,7 @@ struct WarpCtx {
     int fast_lo, fast_hi;
     RowCopy cp;
     bool st_pair;              // this lane stores its pair (lanes 1..30, first column inside)
+    mutable PairSums sums;     // used when kSums
 
     __device__ __forceinline__ uint64_t* bar(int r) const { return reinterpret_cast<uint64_t*>(smem) + wslot(r); }
     __device__ __forceinline__ const S* pop(int r) const {
@@ -370,6 +387,14 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     // ghost refresh after the step overwrites (the one-warp kernels leave all ghost
     // columns to ghost_fill_kernel, so the row loop holds no edge code)
     if (lane_ok) {
+        if constexpr (Ctx::kSums) {
+            // the second column of the pair may lie past nx (its store lands in the
+            // first ghost column, overwritten by the ghost refresh): count it only when inside
+            const V2 in = V2{make_float2(1.f, c.xa + 1 < p.nx ? 1.f : 0.f)};
+            c.sums.add(0, a[0] * in);
+            c.sums.add(1, a[3] * in);
+            c.sums.add(2, a[5] * in);
+        }
         S* cell = reinterpret_cast<S*>(p.dst) + (long long)p3 * p.P + kPadCols + c.xa;
         IO::st(cell, sizeof(S) == 4 ? fo[0] : p.scale * (fo[0] - r0));
 #pragma unroll
@@ -452,7 +477,7 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
     return ok;
 }
 
-template <typename S, int MINB>
+template <typename S, int MINB, bool SUMS = false>
 __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_constant__ StepParams<float> p) {
     using L = WarpLayout<S>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -462,7 +487,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     const int y0 = blockIdx.y * p.H;
     const int y1 = min(y0 + p.H, p.ny);
 
-    WarpCtx<S> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
+    WarpCtx<S, SUMS> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
     c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
     c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
     c.xa = x0 - 2 + 2 * lane;
@@ -492,6 +517,14 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     if (lane == 0) {
         // every issued row is waited for before the CTA exits (bounded)
         for (int r = c.waited + 1; r <= c.issued; ++r) mbar_wait_bounded(c.bar(r), c.parity(r), kWaitTries);
+    }
+    if constexpr (SUMS) {
+        for (int k = 0; k < 3; ++k) {
+            double v = c.sums.value(k);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) atomicAdd(p.sums + k, v);
+        }
     }
 }
 

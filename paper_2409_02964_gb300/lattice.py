@@ -53,6 +53,18 @@ class _Arg:
             self.ptr, self.on_device, self._keep = arr.ctypes.data, 0, arr
 
 
+def _check_out(out: torch.Tensor, device: torch.device) -> None:
+    """An asynchronous result buffer: 3 contiguous float64 on the lattice's device or
+    in pinned host memory."""
+    if out.dtype != torch.float64 or out.numel() < 3 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 tensor of at least 3 elements")
+    if out.is_cuda:
+        if out.device != device:
+            raise ValueError(f"tensor on {out.device}, lattice on {device}")
+    elif not out.is_pinned():
+        raise ValueError("a host out tensor must be in pinned memory")
+
+
 def _is_f32(a) -> bool:
     return (isinstance(a, torch.Tensor) and a.dtype == torch.float32) or (
         isinstance(a, np.ndarray) and a.dtype == np.float32)
@@ -189,17 +201,18 @@ class Lattice:
         _check(self._L.lbm_vanse_reduce(self._h, ctypes.byref(m), ctypes.byref(jx), ctypes.byref(jy)), self._h)
         return m.value, jx.value, jy.value
 
+    def step_sums(self, out: torch.Tensor) -> None:
+        """One step that also queues the sums of the post-collision m_0 and j over the
+        lattice into ``out`` (3 float64, on this device or pinned host memory), without
+        waiting (lbm_vanse_step_sums)."""
+        _check_out(out, self.device)
+        _check(self._L.lbm_vanse_step_sums(self._h, out.data_ptr(), int(out.is_cuda)), self._h)
+
     def reduce_async(self, out: torch.Tensor) -> None:
         """Queue the mass and momentum sums into ``out`` (3 float64, on this device or
         in pinned host memory) without waiting; they are there once the stream has
         passed this point (e.g. a ``torch.cuda.Event`` recorded after the call)."""
-        if out.dtype != torch.float64 or out.numel() < 3 or not out.is_contiguous():
-            raise ValueError("out must be a contiguous float64 tensor of at least 3 elements")
-        if out.is_cuda:
-            if out.device != self.device:
-                raise ValueError(f"tensor on {out.device}, lattice on {self.device}")
-        elif not out.is_pinned():
-            raise ValueError("a host out tensor must be in pinned memory")
+        _check_out(out, self.device)
         _check(self._L.lbm_vanse_reduce_async(self._h, out.data_ptr(), int(out.is_cuda)), self._h)
 
     def velocity_error(self, ux_ref, uy_ref):

@@ -355,6 +355,45 @@ def test_reduce_async_and_overlapped_uploads(P, storage):
     assert np.array_equal(res[0][1], res[1][1])
 
 
+@pytest.mark.parametrize("storage,kernel", [("fp64", 1), ("fp32", 1), ("fp32", 5), ("fp16", 5), ("bf16", 5)])
+@pytest.mark.parametrize("wall_y", [False, True])
+def test_step_sums_match_oracle_moments(P, O, storage, kernel, wall_y):
+    """lbm_vanse_step_sums: the sums over the lattice of the post-collision m_0 and
+    j + F (Eq. 16) of the step it runs, against the oracle's sum f and sum (e f + F)
+    of the populations the step starts from (odd nx: the last column pair of the
+    one-warp kernel has one column outside the lattice; a moving phi and a force
+    field on the first step)."""
+    import torch
+    nx, ny = 77, 30
+    case = random_case(nx, ny, seed=21 + wall_y, wall_y=wall_y, unsteady=True, field=True, g=(1e-5, -2e-6))
+    lat = _gpu_lattice(P, nx, ny, 0.8, wall_y, storage, case, kernel=kernel)
+    f = lat.get_populations().cpu().numpy()
+    mo = O.macros(_oracle_params(O, nx, ny, 0.8, wall_y), f, case["phi"], total_force(case))
+    E = np.array([(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)], dtype=float)
+    want = np.array([f.sum(), np.einsum("i,iyx->", E[:, 0], f) + mo["Fx"].sum(),
+                     np.einsum("i,iyx->", E[:, 1], f) + mo["Fy"].sum()])
+    out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+    host = torch.full((3,), float("nan"), dtype=torch.float64).pin_memory()
+    lat.step_sums(out)
+    lat.sync()
+    got = out.cpu().numpy()
+    tol = (1e-13 if storage == "fp64" else 1e-7) * want[0]
+    assert np.all(np.abs(got - want) <= tol), (got, want, tol)
+    # a second step: host output, and the sums follow the state reduce() sees
+    m_before, _, _ = lat.reduce()
+    lat.step_sums(host)
+    lat.sync()
+    assert abs(host[0].item() - m_before) <= tol
+    assert lat.step_count == 2
+    lat.close()
+    lat = P.Lattice(16, 8, 0.8, kernel=2, storage="fp32")
+    lat.set_void_fraction(np.full((8, 16), 0.7))
+    lat.init_fields(np.ones((8, 16)), np.zeros((8, 16)), np.zeros((8, 16)))
+    with pytest.raises(P.LbmError):
+        lat.step_sums(out)
+    lat.close()
+
+
 def test_populations_roundtrip(P):
     nx, ny = 40, 17
     case = random_case(nx, ny, seed=9)
