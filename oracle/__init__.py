@@ -43,6 +43,7 @@ class _Params(ctypes.Structure):
         ("eq_order", ctypes.c_int),
         ("drag_d0", ctypes.c_double), ("drag_d1", ctypes.c_double),
         ("us_x", ctypes.c_double), ("us_y", ctypes.c_double),
+        ("nee_top", ctypes.c_int), ("uw_x", ctypes.c_double), ("uw_y", ctypes.c_double),
     ]
 
 
@@ -66,11 +67,15 @@ class Params:
     drag_d1: float = 0.0
     us_x: float = 0.0
     us_y: float = 0.0
+    nee_top: int = 0       # with bc_y = 1: row ny-1 is a moving wall (non-equilibrium extrapolation)
+    uw_x: float = 0.0      # its velocity
+    uw_y: float = 0.0
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, self.s_c, self.s_e, self.s_eps, self.s_q,
                        self.s_nu, self.kappa, self.bc_x, self.bc_y, self.model_b,
-                       self.nthreads, self.eq_order, self.drag_d0, self.drag_d1, self.us_x, self.us_y)
+                       self.nthreads, self.eq_order, self.drag_d0, self.drag_d1, self.us_x, self.us_y,
+                       self.nee_top, self.uw_x, self.uw_y)
 
 
 def build(force: bool = False, openmp: bool = True) -> str:

@@ -23,6 +23,9 @@
  *   vo_step             Eq. (16) + streaming (Sec. 2.3) + half-way bounce-back (Sec. 3.1)
  *   vo_init             f = f^eq - F_i/2    (the paper is silent; reading c7)
  *   eq_order = 2        App. B: Eq. (B1) equilibrium, (B2) moments, (B3) penalty
+ *   nee_top, uw_x, uw_y the moving wall of the Couette case (Sec. 3.1, Eq. 22 II) by
+ *                       non-equilibrium extrapolation (the scheme the paper cites);
+ *                       the readings it needs are listed at nee_fill below
  *   drag_d0, drag_d1,   a body force linear in u, F^B += -beta (u - u_s) with
  *   us_x, us_y          beta = phi^2 (d0 + d1 (1 - phi)): the Darcy term of Sec. 3.1
  *                       (d0 = nu / k0) and the drag law of Eq. (23) (d1 = 1); u is
@@ -69,6 +72,9 @@ typedef struct {
     int nthreads;      /* OpenMP threads for the cell loops; <= 0 keeps the default */
     int eq_order;      /* 3: Eq. (14), (18), (20) (default); 2: App. B, Eq. (B1)-(B3) */
     double drag_d0, drag_d1, us_x, us_y;   /* linear drag, see the header */
+    int nee_top;       /* 1 (with bc_y = 1): the top row ny-1 is a velocity wall by
+                        * non-equilibrium extrapolation (Sec. 3.1), wall velocity uw */
+    double uw_x, uw_y;
 } vo_params;
 
 /* ---------------------------------------------------------------- Eq. (5) */
@@ -329,10 +335,19 @@ void vo_gradient(const vo_params* p, const double* psi, int odd, double* gx, dou
         for (int x = 0; x < nx; ++x) {
             double sx = 0.0, sy = 0.0;
             for (int i = 0; i < Q; ++i) {
-                int sgn;
-                int c = neighbour(p, x + e[i][0], y + e[i][1], &sgn);
-                double v = psi[c];
-                if (odd && sgn < 0) v = -v;
+                double v;
+                if (p->nee_top && y + e[i][1] == ny) {
+                    /* past the NEE wall row: linear extrapolation from rows ny-1, ny-2 */
+                    int s1, s2;
+                    const int c1 = neighbour(p, x + e[i][0], ny - 1, &s1);
+                    const int c2 = neighbour(p, x + e[i][0], ny - 2, &s2);
+                    v = 2.0 * psi[c1] - psi[c2];
+                } else {
+                    int sgn;
+                    int c = neighbour(p, x + e[i][0], y + e[i][1], &sgn);
+                    v = psi[c];
+                    if (odd && sgn < 0) v = -v;
+                }
                 sx += w[i] * v * e[i][0];
                 sy += w[i] * v * e[i][1];
             }
@@ -340,6 +355,39 @@ void vo_gradient(const vo_params* p, const double* psi, int odd, double* gx, dou
             gy[y * nx + x] = sy / cs2;
         }
     }
+}
+
+/*
+ * Eq. (7) at one cell c of the post-streaming populations f (N cells per plane),
+ * given the Eq. (10) gradient of rho there and the prescribed part of F^B:
+ * F = F^p + F^B with F^p = (kappa - phi) cs^2 grad rho (model B: kappa - 1);
+ * a drag -beta (u - u_s) in F makes Eq. (7) implicit in u, and being linear it
+ * is solved exactly: u (sum f + beta / 2) = j + (F_rest + beta u_s) / 2.
+ */
+static void cell_velocity(const vo_params* p, const double* f, size_t N, size_t c, double phi, double grx,
+                          double gry, double fbx, double fby, double* ux, double* uy, double* Fx, double* Fy)
+{
+    static const int ex[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    static const int ey[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const double cs2 = 1.0 / 3.0;
+    double s = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        s += f[i * N + c];
+        jx += ex[i] * f[i * N + c];
+        jy += ey[i] * f[i * N + c];
+    }
+    const double kp = p->model_b ? (p->kappa - 1.0) : (p->kappa - phi);
+    double fx = kp * cs2 * grx + fbx;
+    double fy = kp * cs2 * gry + fby;
+    const double beta = phi * phi * (p->drag_d0 + p->drag_d1 * (1.0 - phi));
+    const double vx = (jx + 0.5 * (fx + beta * p->us_x)) / (s + 0.5 * beta);
+    const double vy = (jy + 0.5 * (fy + beta * p->us_y)) / (s + 0.5 * beta);
+    fx -= beta * (vx - p->us_x);
+    fy -= beta * (vy - p->us_y);
+    *ux = vx;
+    *uy = vy;
+    *Fx = fx;
+    *Fy = fy;
 }
 
 /*
@@ -351,11 +399,7 @@ void vo_gradient(const vo_params* p, const double* psi, int odd, double* gx, dou
 void vo_macros(const vo_params* p, const double* f, const double* phi, const double* fb,
                double* rho, double* ux, double* uy, double* Fx, double* Fy)
 {
-    int e[Q][2];
-    double w[Q];
-    vo_lattice(e, w);
     const size_t N = (size_t)p->nx * p->ny;
-    const double cs2 = 1.0 / 3.0;
     double* gx = (double*)malloc(N * sizeof(double));
     double* gy = (double*)malloc(N * sizeof(double));
     for (size_t c = 0; c < N; ++c) {
@@ -365,27 +409,61 @@ void vo_macros(const vo_params* p, const double* f, const double* phi, const dou
     }
     vo_gradient(p, rho, 0, gx, gy);
     for (size_t c = 0; c < N; ++c) {
-        double s = 0.0, jx = 0.0, jy = 0.0;
-        for (int i = 0; i < Q; ++i) {
-            s += f[i * N + c];
-            jx += e[i][0] * f[i * N + c];
-            jy += e[i][1] * f[i * N + c];
-        }
-        const double kp = p->model_b ? (p->kappa - 1.0) : (p->kappa - phi[c]);
-        double fx = kp * cs2 * gx[c] + (fb ? fb[c] : 0.0);
-        double fy = kp * cs2 * gy[c] + (fb ? fb[N + c] : 0.0);
-        /* a drag -beta (u - u_s) in F makes Eq. (7) implicit in u; being linear it is
-         * solved exactly: u (sum f + beta / 2) = j + (F_rest + beta u_s) / 2 */
-        const double beta = phi[c] * phi[c] * (p->drag_d0 + p->drag_d1 * (1.0 - phi[c]));
-        const double vx = (jx + 0.5 * (fx + beta * p->us_x)) / (s + 0.5 * beta);
-        const double vy = (jy + 0.5 * (fy + beta * p->us_y)) / (s + 0.5 * beta);
-        fx -= beta * (vx - p->us_x);
-        fy -= beta * (vy - p->us_y);
+        double vx, vy, fx, fy;
+        cell_velocity(p, f, N, c, phi[c], gx[c], gy[c], fb ? fb[c] : 0.0, fb ? fb[N + c] : 0.0, &vx, &vy, &fx, &fy);
         if (ux) ux[c] = vx;
         if (uy) uy[c] = vy;
         if (Fx) Fx[c] = fx;
         if (Fy) Fy[c] = fy;
     }
+    free(gx);
+    free(gy);
+}
+
+/*
+ * Moving wall by non-equilibrium extrapolation (Sec. 3.1; the scheme of the paper's
+ * reference [47], Guo, Zheng and Shi). Readings where the paper is silent:
+ *   - the wall nodes are the top row y = ny-1 (the wall passes through them); the
+ *     fluid node next to each is (x, ny-2); the bottom stays a half-way bounce-back
+ *     wall, so the channel height is H = ny - 1/2;
+ *   - before the collision of each step, every population of a wall node is
+ *     replaced by f_i = f_i^eq(rho_b, u_w, phi_b) + f_i(x_f) - f_i^eq(rho_f, u_f, phi_f)
+ *     with rho_b = rho_f (extrapolated density) and f^eq of Eq. (14) (Eq. B1 when
+ *     eq_order = 2);
+ *   - u_f is Eq. (7) at the fluid node, with F^p from the Eq. (10) gradient of rho
+ *     that already uses rho_b in the wall row, and the drag solved implicitly;
+ *   - the Eq. (10) stencil of a wall node reads a ghost row above the wall that
+ *     extrapolates linearly from rows ny-1 and ny-2 (every field; vo_gradient);
+ *   - the wall node then collides like a fluid node; what it streams upward is
+ *     replaced again at the next step.
+ * f_out = f with the wall row replaced (f itself unchanged).
+ */
+static void nee_fill(const vo_params* p, const double* f, const double* phi, const double* fb, double* f_out)
+{
+    const int nx = p->nx, ny = p->ny;
+    const size_t N = (size_t)nx * ny;
+    double* rho = (double*)malloc(N * sizeof(double));
+    double* gx = (double*)malloc(N * sizeof(double));
+    double* gy = (double*)malloc(N * sizeof(double));
+    memcpy(f_out, f, Q * N * sizeof(double));
+    for (size_t c = 0; c < N; ++c) {
+        double s = 0.0;
+        for (int i = 0; i < Q; ++i) s += f[i * N + c];
+        rho[c] = s / phi[c];
+    }
+    for (int x = 0; x < nx; ++x) rho[(size_t)(ny - 1) * nx + x] = rho[(size_t)(ny - 2) * nx + x];
+    vo_gradient(p, rho, 0, gx, gy);
+    for (int x = 0; x < nx; ++x) {
+        const size_t cf = (size_t)(ny - 2) * nx + x, cb = (size_t)(ny - 1) * nx + x;
+        double vx, vy, fx, fy;
+        cell_velocity(p, f, N, cf, phi[cf], gx[cf], gy[cf], fb ? fb[cf] : 0.0, fb ? fb[N + cf] : 0.0,
+                      &vx, &vy, &fx, &fy);
+        double eb[Q], ef[Q];
+        vo_feq_order(p->eq_order, p->kappa, phi[cb], rho[cf], p->uw_x, p->uw_y, eb);
+        vo_feq_order(p->eq_order, p->kappa, phi[cf], rho[cf], vx, vy, ef);
+        for (int i = 0; i < Q; ++i) f_out[i * N + cb] = eb[i] + (f[i * N + cf] - ef[i]);
+    }
+    free(rho);
     free(gx);
     free(gy);
 }
@@ -451,6 +529,13 @@ int vo_step(const vo_params* p, const double* f, double* f_new, const double* ph
     double* fld = (double*)malloc(6 * N * sizeof(double));
     double* grd = (double*)malloc(12 * N * sizeof(double));
     double* fplus = (double*)malloc(Q * N * sizeof(double));
+    double* fnee = NULL;
+    if (p->nee_top && p->bc_y == 1 && p->ny >= 3) {
+        /* the moving wall's populations, before anything reads them */
+        fnee = (double*)malloc(Q * N * sizeof(double));
+        nee_fill(p, f, phi_t, fb, fnee);
+        f = fnee;
+    }
 
     /* steps 1-3: rho, F, u (Eq. 7, 10, 13) */
     vo_macros(p, f, phi_t, fb, rho, ux, uy, Fx, Fy);
@@ -495,6 +580,7 @@ int vo_step(const vo_params* p, const double* f, double* f_new, const double* ph
 
     free(rho); free(ux); free(uy); free(Fx); free(Fy);
     free(fld); free(grd); free(fplus);
+    free(fnee);
     return 0;
 }
 

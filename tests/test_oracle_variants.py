@@ -243,3 +243,47 @@ def test_provisional_eos_stability_limit(oracle_mod, kappa, stable):
             f = oracle_mod.step(p, f, phi)
     finite = bool(np.isfinite(f).all() and np.abs(f).max() < 10)
     assert finite == stable
+
+
+def _couette(oracle_mod, ny, da, kappa, phi0=0.5, tau=0.8, uh=1e-3):
+    """Eq. (22 II): half-way bounce-back at the bottom (y = 0), the moving wall by
+    non-equilibrium extrapolation on row ny-1 (y = H = ny - 1/2), G = 0; relative L2
+    error of u on the fluid rows against the analytic profile."""
+    nx = 3
+    nu = (tau - 0.5) / 3
+    H = ny - 0.5
+    drag = {}
+    if da:
+        k0 = da * H * H
+        drag = dict(drag_d0=nu / k0)
+    p = oracle_mod.Params(nx=nx, ny=ny, **oracle_mod.rates_from_tau(tau, s_eps=1.2, s_q=1.2), kappa=kappa, bc_y=1,
+                          nee_top=1, uw_x=uh, **drag)
+    phi = np.full((ny, nx), phi0)
+    f = oracle_mod.init(p, np.ones((ny, nx)), 0 * phi, 0 * phi, phi)
+    steps = int(30 * min(H * H / nu, k0 / (phi0 * nu)) + 2000) if da else int(6 * H * H / nu)
+    for _ in range(steps):
+        f = oracle_mod.step(p, f, phi)
+    u = oracle_mod.macros(p, f, phi)["ux"][:-1, 0]
+    y = np.arange(ny - 1) + 0.5
+    if da:
+        r = np.sqrt(phi0 / k0)
+        ua = uh * np.sinh(r * y) / np.sinh(r * H)
+    else:
+        ua = uh * y / H
+    return np.sqrt(np.sum((u - ua) ** 2) / np.sum(ua ** 2))
+
+
+def test_x2_plain_couette_is_linear(oracle_mod):
+    """Without the Darcy term the moving-wall channel converges to the linear Couette
+    profile u_H y / H exactly (to the convergence of the run)."""
+    assert _couette(oracle_mod, 16, None, 0.5) < 1e-9
+
+
+@pytest.mark.parametrize("kappa", [0.5, 0.3])
+def test_x2_porous_couette_matches_eq22(oracle_mod, kappa):
+    """Eq. (22 II) with phi = 0.5, Da = 1e-2, u_H = 1e-3: second-order convergence of
+    the profile to u_H sinh(r y) / sinh(r H), r = sqrt(phi / k0) (kappa = 0.3: phi !=
+    kappa, so F^p and C are active next to the wall)."""
+    e16, e32 = _couette(oracle_mod, 16, 1e-2, kappa), _couette(oracle_mod, 32, 1e-2, kappa)
+    assert e32 < 8e-3
+    assert 3.0 < e16 / e32 < 4.7, (e16, e32)
