@@ -121,6 +121,19 @@ lbm_status lbm_vanse_set_body_force(lbm_vanse_t h, double gx, double gy, const d
  * takes the row loop's general path. Also used by init_fields and macros. */
 lbm_status lbm_vanse_set_drag(lbm_vanse_t h, double d0, double d1, double us_x, double us_y);
 
+/* Moving wall (Sec. 3.1, the Couette case of Eq. 22 II): with enable = 1 the top row
+ * y = ny-1 becomes a row of wall nodes moving at (uw_x, uw_y), imposed by
+ * non-equilibrium extrapolation, the scheme the paper uses: before each collision
+ * the wall node's populations become f^eq(rho_f, u_w, phi_b) + f(x_f) - f^eq(rho_f,
+ * u_f, phi_f), x_f = (x, ny-2) the fluid node below, rho_f and u_f its Eq. (7) values
+ * (F^p there uses rho_b = rho_f), f^eq of Eq. (14) (B1 with eq_order 2). The wall
+ * row's Eq. (10) stencil reads a ghost row extrapolated linearly from rows ny-1 and
+ * ny-2. The bottom stays a half-way bounce-back wall, so the channel height is
+ * ny - 1/2. Needs bc_y = LBM_BC_BOUNCEBACK, ny >= 3 and step kernel 1 (LBM_ERR_ARG
+ * otherwise); enable = 0 restores the half-way wall. lbm_vanse_macros reports the
+ * wall row from its populations before the replacement. */
+lbm_status lbm_vanse_set_moving_wall(lbm_vanse_t h, int enable, double uw_x, double uw_y);
+
 /* Initial populations f = f^eq(rho, u, phi) - F_i(u, F)/2 (Eq. 14, Eq. 6 with
  * F = F^p + F^B, F^p from grad rho by Eq. 10 and 13), so that Eq. (7) returns u.
  * rho, ux, uy: [ny][nx]. Uses the void fraction and body force set before. */

@@ -70,6 +70,8 @@ struct lbm_vanse {
     double gx = 0, gy = 0;
     bool has_drag = false;        // F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi))
     double drag_d0 = 0, drag_d1 = 0, us_x = 0, us_y = 0;
+    bool nee_top = false;         // row ny-1: moving wall by non-equilibrium extrapolation
+    double uw_x = 0, uw_y = 0;
     double s_nu = 0, s_e = 0;
     double scale = 1, inv_scale = 1;
     int* err = nullptr;           // device flag set by bounded waits
@@ -84,10 +86,11 @@ struct lbm_vanse {
     cudaGraphExec_t gexec = nullptr;
     struct GraphKey {
         const void* phi; const void* fb; int has_fb; double gx, gy; int cur; double drag[4]; int has_drag;
+        int nee; double uw[2];
         bool operator==(const GraphKey& o) const {
             return phi == o.phi && fb == o.fb && has_fb == o.has_fb && gx == o.gx && gy == o.gy && cur == o.cur &&
                    has_drag == o.has_drag && drag[0] == o.drag[0] && drag[1] == o.drag[1] && drag[2] == o.drag[2] &&
-                   drag[3] == o.drag[3];
+                   drag[3] == o.drag[3] && nee == o.nee && uw[0] == o.uw[0] && uw[1] == o.uw[1];
         }
     } gkey{};
     bool use_graphs = true;
@@ -280,6 +283,9 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
     p.us_x = (R)h->us_x;
     p.us_y = (R)h->us_y;
     p.sums = sums;
+    p.nee_top = h->nee_top;
+    p.uw_x = (R)h->uw_x;
+    p.uw_y = (R)h->uw_y;
     dim3 grid(h->gridx, h->gridy);
     if (sums) {
         if (!h->sums_configured) {
@@ -361,14 +367,15 @@ lbm_status build_graph(lbm_vanse* h) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
     h->gkey = {h->phi, h->fb, (int)h->has_fb, h->gx, h->gy, h->cur, {h->drag_d0, h->drag_d1, h->us_x, h->us_y},
-               (int)h->has_drag};
+               (int)h->has_drag, (int)h->nee_top, {h->uw_x, h->uw_y}};
     return LBM_OK;
 }
 
 template <typename S>
 lbm_status replay_graph(lbm_vanse* h) {
     lbm_vanse::GraphKey key{h->phi, h->fb, (int)h->has_fb, h->gx, h->gy, h->cur,
-                            {h->drag_d0, h->drag_d1, h->us_x, h->us_y}, (int)h->has_drag};
+                            {h->drag_d0, h->drag_d1, h->us_x, h->us_y}, (int)h->has_drag,
+                            (int)h->nee_top, {h->uw_x, h->uw_y}};
     if (!h->gexec || !(key == h->gkey)) {
         lbm_status st = build_graph<S>(h);
         if (st != LBM_OK) return st;
@@ -765,6 +772,20 @@ extern "C" lbm_status lbm_vanse_set_drag(lbm_vanse_t h, double d0, double d1, do
     h->drag_d1 = d1;
     h->us_x = us_x;
     h->us_y = us_y;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_set_moving_wall(lbm_vanse_t h, int enable, double uw_x, double uw_y) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!enable) { h->nee_top = false; h->uw_x = h->uw_y = 0; return LBM_OK; }
+    if (!std::isfinite(uw_x) || !std::isfinite(uw_y)) return fail(h, LBM_ERR_ARG, "wall velocity must be finite");
+    if (h->prm.bc_y != LBM_BC_BOUNCEBACK) return fail(h, LBM_ERR_ARG, "the moving wall needs bc_y = bounce-back");
+    if (h->prm.ny < 3) return fail(h, LBM_ERR_ARG, "the moving wall needs ny >= 3");
+    if (h->kernel != 1)
+        return fail(h, LBM_ERR_ARG, "the moving wall runs on step kernel 1 (this lattice uses kernel %d)", h->kernel);
+    h->nee_top = true;
+    h->uw_x = uw_x;
+    h->uw_y = uw_y;
     return LBM_OK;
 }
 

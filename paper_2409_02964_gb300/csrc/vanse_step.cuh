@@ -77,6 +77,8 @@ struct StepParams {
     int has_drag;         // F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi)); u solved implicitly
     R drag_d0, drag_d1, us_x, us_y;
     double* sums;         // step-sum variants: FP64 sums of m_0+, j_x+, j_y+ over the cells written (added)
+    int nee_top;          // row ny-1 is a moving wall by non-equilibrium extrapolation (kernel 1 only)
+    R uw_x, uw_y;         // its velocity
 };
 
 // Compensated (Kahan) sums of the post-collision m_0, j_x, j_y of the cells one
@@ -234,7 +236,10 @@ __device__ __forceinline__ void phase2(const StepCtx<S, R, T>& c, const RowState
     R dlo = Cs.dr, wlo = Cs.wr, dhi = An.dr, whi = An.wr;
     if (p.wall_y && (p2 == 0 || p2 == p.ny - 1)) {  // rho's wall ghost: the mirror row itself
         if (p2 == 0) { dlo = Bs.dr; wlo = Bs.wr; }
-        if (p2 == p.ny - 1) { dhi = Bs.dr; whi = Bs.wr; }
+        if (p2 == p.ny - 1) {
+            if (p.nee_top) { dhi = (R)2 * Bs.dr - Cs.dr; whi = (R)2 * Bs.wr - Cs.wr; }   // linear extrapolation
+            else { dhi = Bs.dr; whi = Bs.wr; }
+        }
     }
     const R gx = (dlo + (R)4 * Bs.dr + dhi) * twelfth;
     const R gy = (whi - wlo) * twelfth;
@@ -287,17 +292,20 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
     R yBy = Bs.wBy - An.wBy;
     R yBx = Bs.wBx - An.wBx;
     R yDy = Bs.wDy - An.wDy;
+    // the row above a wall row: past a half-way wall the negated mirror row (no-slip),
+    // past the moving (NEE) wall row the linear extrapolation 2 (row ny-1) - (row ny-2)
+    const bool nee_hi = p.nee_top && p3 == p.ny - 1;
+    auto ghi = [&](R cs, R an, R bs) { return nee_hi ? (R)2 * cs - an : (p3 == p.ny - 1 ? -cs : bs); };
     if (p.wall_y && (p3 == 0 || p3 == p.ny - 1)) {
-        // the ghost row past a wall is the negated mirror row (no-slip)
-        const bool lo = (p3 == 0), hi = (p3 == p.ny - 1);
-        const R dAl = lo ? -Cs.dAx : An.dAx, dAh = hi ? -Cs.dAx : Bs.dAx;
-        const R dBxl = lo ? -Cs.dBx : An.dBx, dBxh = hi ? -Cs.dBx : Bs.dBx;
-        const R dByl = lo ? -Cs.dBy : An.dBy, dByh = hi ? -Cs.dBy : Bs.dBy;
-        const R dDl = lo ? -Cs.dDx : An.dDx, dDh = hi ? -Cs.dDx : Bs.dDx;
-        const R wAl = lo ? -Cs.wAy : An.wAy, wAh = hi ? -Cs.wAy : Bs.wAy;
-        const R wByl = lo ? -Cs.wBy : An.wBy, wByh = hi ? -Cs.wBy : Bs.wBy;
-        const R wBxl = lo ? -Cs.wBx : An.wBx, wBxh = hi ? -Cs.wBx : Bs.wBx;
-        const R wDl = lo ? -Cs.wDy : An.wDy, wDh = hi ? -Cs.wDy : Bs.wDy;
+        const bool lo = (p3 == 0);
+        const R dAl = lo ? -Cs.dAx : An.dAx, dAh = ghi(Cs.dAx, An.dAx, Bs.dAx);
+        const R dBxl = lo ? -Cs.dBx : An.dBx, dBxh = ghi(Cs.dBx, An.dBx, Bs.dBx);
+        const R dByl = lo ? -Cs.dBy : An.dBy, dByh = ghi(Cs.dBy, An.dBy, Bs.dBy);
+        const R dDl = lo ? -Cs.dDx : An.dDx, dDh = ghi(Cs.dDx, An.dDx, Bs.dDx);
+        const R wAl = lo ? -Cs.wAy : An.wAy, wAh = ghi(Cs.wAy, An.wAy, Bs.wAy);
+        const R wByl = lo ? -Cs.wBy : An.wBy, wByh = ghi(Cs.wBy, An.wBy, Bs.wBy);
+        const R wBxl = lo ? -Cs.wBx : An.wBx, wBxh = ghi(Cs.wBx, An.wBx, Bs.wBx);
+        const R wDl = lo ? -Cs.wDy : An.wDy, wDh = ghi(Cs.wDy, An.wDy, Bs.wDy);
         xAx = dAl + (R)4 * Cs.dAx + dAh;
         xBx = dBxl + (R)4 * Cs.dBx + dBxh;
         xBy = dByl + (R)4 * Cs.dBy + dByh;
@@ -326,11 +334,11 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
         R xAy = An.dAy + (R)4 * Cs.dAy + Bs.dAy, yAx = Bs.wAx - An.wAx;
         R xDy = An.dDy + (R)4 * Cs.dDy + Bs.dDy, yDx = Bs.wDx - An.wDx;
         if (p.wall_y && (p3 == 0 || p3 == p.ny - 1)) {
-            const bool lo = (p3 == 0), hi = (p3 == p.ny - 1);
-            xAy = (lo ? -Cs.dAy : An.dAy) + (R)4 * Cs.dAy + (hi ? -Cs.dAy : Bs.dAy);
-            xDy = (lo ? -Cs.dDy : An.dDy) + (R)4 * Cs.dDy + (hi ? -Cs.dDy : Bs.dDy);
-            yAx = (hi ? -Cs.wAx : Bs.wAx) - (lo ? -Cs.wAx : An.wAx);
-            yDx = (hi ? -Cs.wDx : Bs.wDx) - (lo ? -Cs.wDx : An.wDx);
+            const bool lo = (p3 == 0);
+            xAy = (lo ? -Cs.dAy : An.dAy) + (R)4 * Cs.dAy + ghi(Cs.dAy, An.dAy, Bs.dAy);
+            xDy = (lo ? -Cs.dDy : An.dDy) + (R)4 * Cs.dDy + ghi(Cs.dDy, An.dDy, Bs.dDy);
+            yAx = ghi(Cs.wAx, An.wAx, Bs.wAx) - (lo ? -Cs.wAx : An.wAx);
+            yDx = ghi(Cs.wDx, An.wDx, Bs.wDx) - (lo ? -Cs.wDx : An.wDx);
         }
         const R t3 = (R)2 / (R)3;
         Ca = ((R)-2 * p.kappa * (xAx + yAy) + (R)2 * kr * (xBx + yBy) + ((R)4 - (R)2 * X) * (xDx + yDy)) * twelfth
@@ -410,6 +418,36 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
     }
 }
 
+// The equilibrium moments M f^eq of Eq. (18) (App. B: Eq. B2, eq2) at (phi, rho, u).
+template <typename R>
+__device__ __forceinline__ void eq_moments(const StepParams<R>& p, R phi, R rho, R ux, R uy, R m[9]) {
+    const R m0 = phi * rho, X = p.kappa / phi, uu = ux * ux + uy * uy;
+    const R q = p.eq2 ? (R)-1 : X - (R)2;
+    m[0] = m0;
+    m[1] = m0 * ((R)-4 + (R)3 * uu + (R)2 * X);
+    m[2] = m0 * ((R)4 - (R)3 * uu - (R)3 * X);
+    m[3] = m0 * ux;
+    m[4] = q * (m0 * ux);
+    m[5] = m0 * uy;
+    m[6] = q * (m0 * uy);
+    m[7] = m0 * (ux * ux - uy * uy);
+    m[8] = (m0 * ux) * uy;
+}
+
+// Moving wall by non-equilibrium extrapolation (Sec. 3.1) on row ny-1 (Wa), next to
+// fluid row ny-2 (Fl, its Eq. 7 velocity done): the wall node's moments become
+// M f^eq(rho_f, u_w, phi_b) + m_f - M f^eq(rho_f, u_f, phi_f), with rho_b = rho_f
+// (already in Wa.rho). In moment space, since M is linear.
+template <typename R>
+__device__ __forceinline__ void nee_wall_moments(const StepParams<R>& p, RowState<R>& Wa, const RowState<R>& Fl,
+                                                 R phi_b, R phi_f) {
+    R eb[9], ef[9];
+    eq_moments(p, phi_b, Fl.rho, p.uw_x, p.uw_y, eb);
+    eq_moments(p, phi_f, Fl.rho, Fl.ux, Fl.uy, ef);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Wa.m[k] = eb[k] + (Fl.m[k] - ef[k]);
+}
+
 template <typename S, typename R, int T, bool SUMS = false>
 __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ StepParams<R> p) {
     using L = StepLayout<S, R, T>;
@@ -456,6 +494,8 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
         const bool ph1 = (p1 <= y1 + 1) && c.row_valid(p1);
         if (ph1) {
             phase1<S, R, T>(c, An, p1);
+            // moving wall row: rho_b = rho of the fluid row below (its moments follow below)
+            if (p.nee_top && p1 == p.ny - 1) An.rho = Bs.rho;
             rbuf[t] = An.rho;
         }
         __syncthreads();  // A: rho row p1 visible; slot p1-3 free
@@ -470,7 +510,10 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
             An.dr = r - l;
             An.wr = (R)4 * An.rho + (r + l);
         }
-        if (ph2 && ph2_thread) phase2<S, R, T>(c, An, Bs, Cs, p2, fbuf);
+        if (ph2 && ph2_thread) {
+            phase2<S, R, T>(c, An, Bs, Cs, p2, fbuf);
+            if (p.nee_top && p1 == p.ny - 1 && ph1) nee_wall_moments(p, An, Bs, *c.aux(p1, 0), *c.aux(p2, 0));
+        }
         __syncthreads();  // B: field row p2 visible
         if (ph2 && ph3_thread) {
             const R* F0 = fbuf + t;

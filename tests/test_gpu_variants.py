@@ -142,3 +142,102 @@ def test_variant_argument_errors(P):
     with pytest.raises(P.LbmError):
         P.Lattice(16, 8, 0.8, eq_order=4)
     assert P.Lattice(16, 8, 0.8, eq_order=2).launch_shape()["threads"] == 128
+
+
+def _run_wall(P, O, nx, ny, case, steps, storage, uw, drag=None, eq_order=3, model_b=False, tau=0.8):
+    lat = P.Lattice(nx, ny, tau, s_eps=1.2, s_q=1.4, bc_y="bounceback", storage=storage, kernel=1,
+                    eq_order=eq_order, model_b=model_b)
+    lat.set_moving_wall(*uw)
+    if drag:
+        lat.set_drag(drag["d0"], drag["d1"], drag["us_x"], drag["us_y"])
+    lat.set_void_fraction(case["phi"], case["phin"])
+    lat.set_body_force(case["g"][0], case["g"][1], case["fb"])
+    lat.init_fields(case["rho"], case["ux"], case["uy"])
+    kw = dict(drag_d0=drag["d0"], drag_d1=drag["d1"], us_x=drag["us_x"], us_y=drag["us_y"]) if drag else {}
+    prm = O.Params(nx=nx, ny=ny, **O.rates_from_tau(tau, s_eps=1.2, s_q=1.4), kappa=0.5, bc_y=1,
+                   eq_order=eq_order, model_b=int(model_b), nee_top=1, uw_x=uw[0], uw_y=uw[1], **kw)
+    fb = total_force(case)
+    f = O.init(prm, case["rho"], case["ux"], case["uy"], case["phi"], fb)
+    for k in range(steps):
+        phin = case["phin"] if k == 0 else None
+        if k == 1 and case["phin"] is not None:
+            case = dict(case, phi=case["phin"], phin=None)
+            fb = total_force(case)
+        f = O.step(prm, f, case["phi"], phin, fb)
+    lat.step(steps)
+    lat.sync()
+    fg = lat.get_populations().cpu().numpy()
+    lat.close()
+    return fg, f, case
+
+
+WALL_CASES = [
+    (37, 21, True, True, (2e-5, -1e-5), (2e-3, 0.0)),
+    (130, 40, False, False, (1e-5, 0.0), (1e-3, 4e-4)),
+    (9, 5, True, False, (0.0, 3e-5), (-1e-3, 0.0)),
+    (3, 3, False, True, (0.0, 0.0), (5e-4, 0.0)),
+]
+
+
+@pytest.mark.parametrize("nx,ny,unsteady,field,g,uw", WALL_CASES)
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_moving_wall_matches_oracle(P, oracle_mod, nx, ny, unsteady, field, g, uw, storage):
+    """The non-equilibrium-extrapolation wall on row ny-1 (kernel 1) against the
+    oracle, 6 steps, with moving phi, force fields and a tangential and a normal
+    wall velocity; every population, the wall row's included."""
+    steps = 6
+    case = random_case(nx, ny, seed=5 * nx + ny, wall_y=True, unsteady=unsteady, field=field, g=g)
+    fg, fo, case = _run_wall(P, oracle_mod, nx, ny, case, steps, storage, uw)
+    if storage == "fp64":
+        assert np.abs(fg - fo).max() / np.abs(fo - rest_populations(case["phi"])).max() <= 1e-12
+    else:
+        assert np.abs(fg - fo).max() <= steps * 32 * EPS32 * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("variant", ["drag", "appb", "model_b"])
+def test_moving_wall_with_variants_matches_oracle(P, oracle_mod, variant):
+    nx, ny = 50, 23
+    case = random_case(nx, ny, seed=77, wall_y=True, unsteady=True, field=True, g=(1e-5, 0.0))
+    kw = {"drag": dict(drag=DRAG), "appb": dict(eq_order=2), "model_b": dict(model_b=True)}[variant]
+    fg, fo, case = _run_wall(P, oracle_mod, nx, ny, case, 6, "fp64", (1.5e-3, 0.0), **kw)
+    assert np.abs(fg - fo).max() / np.abs(fo - rest_populations(case["phi"])).max() <= 1e-12
+
+
+@pytest.mark.parametrize("da,bound", [(None, 1e-9), (1e-2, 8e-3)])
+def test_couette_on_device(P, da, bound):
+    """Eq. (22 II) on the device (FP64, ny = 32, phi = 0.5, u_H = 1e-3): the linear
+    Couette profile without the Darcy term, and u_H sinh(r y) / sinh(r H) with
+    Da = 1e-2 within the oracle's own error at this resolution (7.5e-3)."""
+    ny, nx, tau, phi0, uh = 32, 4, 0.8, 0.5, 1e-3
+    nu = (tau - 0.5) / 3
+    H = ny - 0.5
+    lat = P.Lattice(nx, ny, tau, s_eps=1.2, s_q=1.2, bc_y="bounceback", storage="fp64", kernel=1)
+    lat.set_moving_wall(uh, 0.0)
+    if da:
+        k0 = da * H * H
+        lat.set_drag(nu / k0, 0.0)
+        steps = int(30 * min(H * H / nu, k0 / (phi0 * nu)) + 2000)
+    else:
+        steps = int(6 * H * H / nu)
+    phi = np.full((ny, nx), phi0)
+    lat.set_void_fraction(phi)
+    lat.init_fields(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    lat.step(steps)
+    u = lat.macros()["ux"].cpu().numpy()[:-1, 0]
+    lat.close()
+    y = np.arange(ny - 1) + 0.5
+    ua = uh * (np.sinh(np.sqrt(phi0 / k0) * y) / np.sinh(np.sqrt(phi0 / k0) * H) if da else y / H)
+    assert np.sqrt(np.sum((u - ua) ** 2) / np.sum(ua ** 2)) < bound
+
+
+def test_moving_wall_argument_errors(P):
+    with pytest.raises(P.LbmError):
+        P.Lattice(16, 8, 0.8, bc_y="bounceback", kernel=5).set_moving_wall(1e-3)
+    with pytest.raises(P.LbmError):
+        P.Lattice(16, 8, 0.8, bc_y="periodic", kernel=1).set_moving_wall(1e-3)
+    with pytest.raises(P.LbmError):
+        P.Lattice(16, 2, 0.8, bc_y="bounceback", kernel=1).set_moving_wall(1e-3)
+    lat = P.Lattice(16, 8, 0.8, bc_y="bounceback", kernel=1)
+    lat.set_moving_wall(1e-3)
+    lat.set_moving_wall(enable=False)
+    lat.close()
