@@ -23,6 +23,9 @@
  *   vo_step             Eq. (16) + streaming (Sec. 2.3) + half-way bounce-back (Sec. 3.1)
  *   vo_init             f = f^eq - F_i/2    (the paper is silent; reading c7)
  *   eq_order = 2        App. B: Eq. (B1) equilibrium, (B2) moments, (B3) penalty
+ *   phi = 0             a solid (impermeable) cell: half-way bounce-back links and a
+ *                       mirrored Eq. (10) ghost (solid_ghost; the phi_0 = 0 block of
+ *                       Sec. 3.3)
  *   nee_top, uw_x, uw_y the moving wall of the Couette case (Sec. 3.1, Eq. 22 II) by
  *                       non-equilibrium extrapolation (the scheme the paper cites);
  *                       the readings it needs are listed at nee_fill below
@@ -321,7 +324,46 @@ static int neighbour(const vo_params* p, int x, int y, int* sign)
  * odd = 1 for a vector-field component (negated in a wall ghost cell),
  * odd = 0 for a scalar (copied).
  */
+/*
+ * Solid cells (phi = 0, the impermeable block of Sec. 3.3 with phi_0 = 0) are not
+ * part of the fluid. Their links are half-way bounce-back links (stream below); in
+ * the Eq. (10) stencil of a fluid cell x a solid neighbour x + e_i reads a ghost
+ * value mirrored about the solid surface, the rule of the straight walls above
+ * applied link by link (the paper is silent):
+ *   - an axis neighbour mirrors onto x itself;
+ *   - a diagonal neighbour mirrors onto x + (e_ix, 0) and onto x + (0, e_iy); the
+ *     fluid ones of these two are averaged (a straight wall leaves exactly the one
+ *     the wall rule uses); if both are solid it mirrors onto x;
+ *   - a vector-field component takes the negated mirror value (no-slip).
+ */
+static double solid_ghost(const vo_params* p, const double* psi, const double* phi, int odd, int x, int y,
+                          int ex, int ey)
+{
+    const double sg = odd ? -1.0 : 1.0;
+    if (ex == 0 || ey == 0) return sg * psi[(size_t)y * p->nx + x];
+    double acc = 0.0;
+    int n = 0;
+    int sa, sb;
+    const int a = neighbour(p, x + ex, y, &sa);
+    const int b = neighbour(p, x, y + ey, &sb);
+    if (phi[a] != 0.0) { acc += (odd && sa < 0) ? -psi[a] : psi[a]; ++n; }
+    if (phi[b] != 0.0) { acc += (odd && sb < 0) ? -psi[b] : psi[b]; ++n; }
+    if (n == 0) return sg * psi[(size_t)y * p->nx + x];
+    return sg * (acc / n);
+}
+
+/* Eq. (10) with solid cells (phi[c] = 0) treated by solid_ghost; phi may be NULL (no
+ * solid cells). The gradient at a solid cell is set to zero (never used). */
+static void gradient_masked(const vo_params* p, const double* psi, int odd, const double* phi, double* gx,
+                            double* gy);
+
 void vo_gradient(const vo_params* p, const double* psi, int odd, double* gx, double* gy)
+{
+    gradient_masked(p, psi, odd, NULL, gx, gy);
+}
+
+static void gradient_masked(const vo_params* p, const double* psi, int odd, const double* phi, double* gx,
+                            double* gy)
 {
     int e[Q][2];
     double w[Q];
@@ -334,9 +376,18 @@ void vo_gradient(const vo_params* p, const double* psi, int odd, double* gx, dou
     for (int y = 0; y < ny; ++y) {
         for (int x = 0; x < nx; ++x) {
             double sx = 0.0, sy = 0.0;
+            if (phi && phi[(size_t)y * nx + x] == 0.0) {
+                gx[y * nx + x] = 0.0;
+                gy[y * nx + x] = 0.0;
+                continue;
+            }
             for (int i = 0; i < Q; ++i) {
                 double v;
-                if (p->nee_top && y + e[i][1] == ny) {
+                int sn;
+                const int cn = neighbour(p, x + e[i][0], y + e[i][1], &sn);
+                if (phi && phi[cn] == 0.0 && !(p->nee_top && y + e[i][1] == ny)) {
+                    v = solid_ghost(p, psi, phi, odd, x, y, e[i][0], e[i][1]);
+                } else if (p->nee_top && y + e[i][1] == ny) {
                     /* past the NEE wall row: linear extrapolation from rows ny-1, ny-2 */
                     int s1, s2;
                     const int c1 = neighbour(p, x + e[i][0], ny - 1, &s1);
@@ -405,11 +456,18 @@ void vo_macros(const vo_params* p, const double* f, const double* phi, const dou
     for (size_t c = 0; c < N; ++c) {
         double s = 0.0;
         for (int i = 0; i < Q; ++i) s += f[i * N + c];
-        rho[c] = s / phi[c];
+        rho[c] = phi[c] != 0.0 ? s / phi[c] : 0.0;   /* solid cells report zeros */
     }
-    vo_gradient(p, rho, 0, gx, gy);
+    gradient_masked(p, rho, 0, phi, gx, gy);
     for (size_t c = 0; c < N; ++c) {
         double vx, vy, fx, fy;
+        if (phi[c] == 0.0) {
+            if (ux) ux[c] = 0.0;
+            if (uy) uy[c] = 0.0;
+            if (Fx) Fx[c] = 0.0;
+            if (Fy) Fy[c] = 0.0;
+            continue;
+        }
         cell_velocity(p, f, N, c, phi[c], gx[c], gy[c], fb ? fb[c] : 0.0, fb ? fb[N + c] : 0.0, &vx, &vy, &fx, &fy);
         if (ux) ux[c] = vx;
         if (uy) uy[c] = vy;
@@ -449,10 +507,10 @@ static void nee_fill(const vo_params* p, const double* f, const double* phi, con
     for (size_t c = 0; c < N; ++c) {
         double s = 0.0;
         for (int i = 0; i < Q; ++i) s += f[i * N + c];
-        rho[c] = s / phi[c];
+        rho[c] = phi[c] != 0.0 ? s / phi[c] : 0.0;
     }
     for (int x = 0; x < nx; ++x) rho[(size_t)(ny - 1) * nx + x] = rho[(size_t)(ny - 2) * nx + x];
-    vo_gradient(p, rho, 0, gx, gy);
+    gradient_masked(p, rho, 0, phi, gx, gy);
     for (int x = 0; x < nx; ++x) {
         const size_t cf = (size_t)(ny - 2) * nx + x, cb = (size_t)(ny - 1) * nx + x;
         double vx, vy, fx, fy;
@@ -479,15 +537,19 @@ static int opposite(int i)
  * leaves the fluid through a half-way bounce-back wall returns to the same cell
  * in the opposite direction (Sec. 3.1).
  */
-static void stream(const vo_params* p, const double* fplus, double* fout)
+static void stream(const vo_params* p, const double* fplus, double* fout, const double* phi)
 {
     int e[Q][2];
     double w[Q];
     vo_lattice(e, w);
     const int nx = p->nx, ny = p->ny;
     const size_t N = (size_t)nx * ny;
+    /* a solid cell (phi = 0) neither sends nor receives: its populations stay zero,
+     * and a fluid link into it bounces back half-way like a wall link */
+    memset(fout, 0, Q * N * sizeof(double));
     for (int y = 0; y < ny; ++y) {
         for (int x = 0; x < nx; ++x) {
+            if (phi[(size_t)y * nx + x] == 0.0) continue;
             for (int i = 0; i < Q; ++i) {
                 int xd = x + e[i][0], yd = y + e[i][1];
                 int wall = 0;
@@ -497,6 +559,7 @@ static void stream(const vo_params* p, const double* fplus, double* fout)
                 if (yd < 0 || yd >= ny) {
                     if (p->bc_y == 0) yd = (yd + ny) % ny; else wall = 1;
                 }
+                if (!wall && phi[(size_t)yd * nx + xd] == 0.0) wall = 1;
                 double v = fplus[i * N + (size_t)y * nx + x];
                 if (wall)
                     fout[opposite(i) * N + (size_t)y * nx + x] = v;
@@ -550,7 +613,7 @@ int vo_step(const vo_params* p, const double* f, double* f_new, const double* ph
         fld[5 * N + c] = phi_t[c] * rho[c] * uy[c];
     }
     for (int k = 0; k < 6; ++k)
-        vo_gradient(p, fld + k * N, 1, grd + (2 * k) * N, grd + (2 * k + 1) * N);
+        gradient_masked(p, fld + k * N, 1, phi_t, grd + (2 * k) * N, grd + (2 * k + 1) * N);
 
     /* steps 5-6: moments, relaxation (Eq. 16), back-transform (A1) */
 #ifdef _OPENMP
@@ -559,6 +622,10 @@ int vo_step(const vo_params* p, const double* f, double* f_new, const double* ph
     for (long long cc = 0; cc < (long long)N; ++cc) {
         const size_t c = (size_t)cc;
         double fc[Q], m[Q], meq[Q], S[Q], C[Q], mp[Q], fp[Q];
+        if (phi_t[c] == 0.0) {   /* solid cell: nothing to collide */
+            for (int i = 0; i < Q; ++i) fplus[i * N + c] = 0.0;
+            continue;
+        }
         for (int i = 0; i < Q; ++i) fc[i] = f[i * N + c];
         vo_moments(fc, m);
         vo_meq_order(p->eq_order, kappa, phi_t[c], rho[c], ux[c], uy[c], meq);
@@ -576,7 +643,7 @@ int vo_step(const vo_params* p, const double* f, double* f_new, const double* ph
     }
 
     /* step 7: streaming and bounce-back */
-    stream(p, fplus, f_new);
+    stream(p, fplus, f_new, phi_t);
 
     free(rho); free(ux); free(uy); free(Fx); free(Fy);
     free(fld); free(grd); free(fplus);
@@ -596,9 +663,13 @@ void vo_init(const vo_params* p, const double* rho, const double* ux, const doub
     const double cs2 = 1.0 / 3.0;
     double* gx = (double*)malloc(N * sizeof(double));
     double* gy = (double*)malloc(N * sizeof(double));
-    vo_gradient(p, rho, 0, gx, gy);
+    gradient_masked(p, rho, 0, phi, gx, gy);
     for (size_t c = 0; c < N; ++c) {
         double feq[Q], Fi[Q];
+        if (phi[c] == 0.0) {   /* solid cell */
+            for (int i = 0; i < Q; ++i) f[i * N + c] = 0.0;
+            continue;
+        }
         const double kp = p->model_b ? (p->kappa - 1.0) : (p->kappa - phi[c]);
         const double beta = phi[c] * phi[c] * (p->drag_d0 + p->drag_d1 * (1.0 - phi[c]));
         const double fx = kp * cs2 * gx[c] + (fb ? fb[c] : 0.0) - beta * (ux[c] - p->us_x);
