@@ -134,6 +134,18 @@ lbm_status lbm_vanse_set_drag(lbm_vanse_t h, double d0, double d1, double us_x, 
  * wall row from its populations before the replacement. */
 lbm_status lbm_vanse_set_moving_wall(lbm_vanse_t h, int enable, double uw_x, double uw_y);
 
+/* Solid cells (the impermeable block of Sec. 3.3, Eq. 24 with phi_0 = 0): with
+ * enable = 1, a cell whose void fraction is exactly 0 is solid. It holds no
+ * populations (reported as zeros; macros report rho = u = p = 0 there), every link
+ * from a fluid cell into it is a half-way bounce-back link, and in the Eq. (10)
+ * stencil of a fluid cell it reads a ghost value mirrored about the solid surface: an
+ * axis neighbour the cell itself, a diagonal neighbour the mean of the fluid ones of
+ * its two axis images (the cell itself if both are solid), vector components negated.
+ * Solid cells must stay solid (phi(t+1) = 0 where phi(t) = 0). Step kernel 1 only
+ * (LBM_ERR_ARG otherwise); call before lbm_vanse_init_fields. Without it a zero in
+ * phi is an error, reported by the next lbm_vanse_sync. */
+lbm_status lbm_vanse_set_solid_cells(lbm_vanse_t h, int enable);
+
 /* Initial populations f = f^eq(rho, u, phi) - F_i(u, F)/2 (Eq. 14, Eq. 6 with
  * F = F^p + F^B, F^p from grad rho by Eq. 10 and 13), so that Eq. (7) returns u.
  * rho, ux, uy: [ny][nx]. Uses the void fraction and body force set before. */

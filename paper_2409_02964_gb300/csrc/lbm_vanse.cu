@@ -72,6 +72,8 @@ struct lbm_vanse {
     double drag_d0 = 0, drag_d1 = 0, us_x = 0, us_y = 0;
     bool nee_top = false;         // row ny-1: moving wall by non-equilibrium extrapolation
     double uw_x = 0, uw_y = 0;
+    bool has_solid = false;       // phi = 0 marks solid cells (kernel 1)
+    int* zero_phi = nullptr;      // device flag: the last phi upload held a zero
     double s_nu = 0, s_e = 0;
     double scale = 1, inv_scale = 1;
     int* err = nullptr;           // device flag set by bounded waits
@@ -95,6 +97,7 @@ struct lbm_vanse {
     } gkey{};
     bool use_graphs = true;
     bool sums_configured = false; // shared-memory attributes set on the step-sum kernel variant
+    bool solid_configured = false;  // ... and on the solid-cell variants
     // uploads from pinned host memory: copied on their own stream into device staging
     // buffers (phi(t), phi(t+1)), so the copy overlaps the work already queued on
     // `stream`; staging_free marks the last read of the staging buffers on `stream`
@@ -160,6 +163,7 @@ Lattice<R> make_lattice(const lbm_vanse* h) {
     L.drag_d1 = (R)h->drag_d1;
     L.us_x = (R)h->us_x;
     L.us_y = (R)h->us_y;
+    L.has_solid = h->has_solid;
     return L;
 }
 
@@ -176,8 +180,18 @@ size_t step_smem_bytes(const lbm_vanse* h, int nR) {
         case 3: return PairLayout<S, 96>::bytes(nR);
         case 4: return PairLayout<S, 128>::bytes(nR);
         case 5: return WarpLayout<S>::bytes(nR);
-        default: return StepLayout<S, R, kThreads>::bytes(nR);
+        default:
+            return StepLayout<S, R, kThreads>::bytes(nR) +
+                   (h->has_solid ? StepLayout<S, R, kThreads>::solid_bytes() : 0);
     }
+}
+
+// the largest dynamic shared memory a launch of the handle's step kernel may ask for
+template <typename S>
+size_t step_smem_max(const lbm_vanse* h) {
+    using R = typename Prec<S>::R;
+    const size_t b = step_smem_bytes<S>(h, 4);
+    return (h->kernel >= 2 && h->kernel <= 5) ? b : b + (h->has_solid ? 0 : StepLayout<S, R, kThreads>::solid_bytes());
 }
 
 int step_threads(const lbm_vanse* h) {
@@ -206,7 +220,7 @@ lbm_status configure(lbm_vanse* h) {
     (void)sizeof(R);
     const void* kern = step_kernel_ptr<S>(h);
     const int threads = step_threads(h);
-    const size_t smax = step_smem_bytes<S>(h, 4);
+    const size_t smax = step_smem_max<S>(h);
     CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
     const size_t s1 = step_smem_bytes<S>(h, 1);
@@ -236,7 +250,33 @@ const void* step_sums_kernel_ptr(const lbm_vanse* h) {
         if (h->kernel == 5) return (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB, true>;
         if (h->kernel != 1) return nullptr;
     }
-    return (const void*)vanse_step_kernel<S, R, kThreads, true>;
+    return h->has_solid ? (const void*)vanse_step_kernel<S, R, kThreads, true, true>
+                        : (const void*)vanse_step_kernel<S, R, kThreads, true>;
+}
+
+// Kernel 1 with solid cells: a variant of its own (the neighbour-by-neighbour stencil
+// and the 3-row rings stay out of the other kernels); shared-memory attributes set on
+// first use.
+template <typename S>
+lbm_status launch_solid_step(lbm_vanse* h, const StepParams<typename Prec<S>::R>& p, dim3 grid, size_t smem,
+                             cudaStream_t stream, bool sums) {
+    using R = typename Prec<S>::R;
+    const void* kern = sums ? (const void*)vanse_step_kernel<S, R, kThreads, true, true>
+                            : (const void*)vanse_step_kernel<S, R, kThreads, false, true>;
+    if (!h->solid_configured) {
+        for (const void* k : {(const void*)vanse_step_kernel<S, R, kThreads, true, true>,
+                              (const void*)vanse_step_kernel<S, R, kThreads, false, true>}) {
+            CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem_max<S>(h)));
+            CK(h, cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared));
+        }
+        h->solid_configured = true;
+    }
+    (void)kern;
+    if (sums) vanse_step_kernel<S, R, kThreads, true, true><<<grid, kThreads, smem, stream>>>(p);
+    else vanse_step_kernel<S, R, kThreads, false, true><<<grid, kThreads, smem, stream>>>(p);
+    CK(h, cudaGetLastError());
+    return LBM_OK;
 }
 
 template <typename S>
@@ -286,13 +326,15 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
     p.nee_top = h->nee_top;
     p.uw_x = (R)h->uw_x;
     p.uw_y = (R)h->uw_y;
+    p.has_solid = h->has_solid;
     dim3 grid(h->gridx, h->gridy);
+    if (h->has_solid) return launch_solid_step<S>(h, p, grid, smem, stream, sums != nullptr);
     if (sums) {
         if (!h->sums_configured) {
             const void* kern = step_sums_kernel_ptr<S>(h);
             if (!kern) return fail(h, LBM_ERR_ARG, "step sums need step kernel 1 or 5 (kernel %d)", h->kernel);
             CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)step_smem_bytes<S>(h, 4)));
+                                       (int)step_smem_max<S>(h)));
             CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        cudaSharedmemCarveoutMaxShared));
             h->sums_configured = true;
@@ -475,14 +517,14 @@ lbm_status stage_in(lbm_vanse* h, const T* src, long long count, int on_device, 
 }
 
 template <typename T>
-lbm_status pad_into(lbm_vanse* h, const T* dev_src, void* dst) {
+lbm_status pad_into(lbm_vanse* h, const T* dev_src, void* dst, int* zero_seen = nullptr) {
     const int blocks = std::min(h->prm.ny, 65535);
     if (h->rbytes == 8)
         pad_field_kernel<T, double><<<blocks, kAuxThreads, 0, h->stream>>>(dev_src, (double*)dst, h->prm.nx,
-                                                                           h->prm.ny, h->P);
+                                                                           h->prm.ny, h->P, zero_seen);
     else
         pad_field_kernel<T, float><<<blocks, kAuxThreads, 0, h->stream>>>(dev_src, (float*)dst, h->prm.nx,
-                                                                          h->prm.ny, h->P);
+                                                                          h->prm.ny, h->P, zero_seen);
     CK(h, cudaGetLastError());
     return LBM_OK;
 }
@@ -509,8 +551,9 @@ lbm_status upload_void_fraction_pinned(lbm_vanse* h, const T* phi_t, const T* ph
     CK(h, cudaEventRecord(h->copy_done, h->copy_stream));
     CK(h, cudaEventSynchronize(h->copy_done));
     CK(h, cudaStreamWaitEvent(h->stream, h->copy_done, 0));
-    lbm_status st = pad_into<T>(h, (const T*)h->staging[0], h->phi);
-    if (st == LBM_OK && phi_next) st = pad_into<T>(h, (const T*)h->staging[1], h->phin);
+    CK(h, cudaMemsetAsync(h->zero_phi, 0, sizeof(int), h->stream));
+    lbm_status st = pad_into<T>(h, (const T*)h->staging[0], h->phi, h->zero_phi);
+    if (st == LBM_OK && phi_next) st = pad_into<T>(h, (const T*)h->staging[1], h->phin, h->zero_phi);
     if (st != LBM_OK) return st;
     CK(h, cudaEventRecord(h->staging_free, h->stream));
     return LBM_OK;
@@ -531,16 +574,17 @@ lbm_status set_void_fraction_impl(lbm_vanse* h, const T* phi_t, const T* phi_nex
     }
     T* d = nullptr;
     bool owned = false;
+    CK(h, cudaMemsetAsync(h->zero_phi, 0, sizeof(int), h->stream));
     lbm_status st = stage_in<T>(h, phi_t, n, on_device, &d, &owned);
     if (st != LBM_OK) return st;
-    st = pad_into<T>(h, d, h->phi);
+    st = pad_into<T>(h, d, h->phi, h->zero_phi);
     if (owned) cudaFreeAsync(d, h->stream);
     if (st != LBM_OK) return st;
     h->unsteady = false;
     if (phi_next) {
         st = stage_in<T>(h, phi_next, n, on_device, &d, &owned);
         if (st != LBM_OK) return st;
-        st = pad_into<T>(h, d, h->phin);
+        st = pad_into<T>(h, d, h->phin, h->zero_phi);
         if (owned) cudaFreeAsync(d, h->stream);
         if (st != LBM_OK) return st;
         h->unsteady = true;
@@ -712,7 +756,8 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
     const size_t popb = (size_t)9 * h->plane * h->sbytes;
     const size_t fldb = (size_t)h->plane * h->rbytes;
     bool ok = alloc(&h->f[0], popb) && alloc(&h->f[1], popb) && alloc(&h->phi, fldb) && alloc(&h->phin, fldb) &&
-              alloc((void**)&h->err, sizeof(int)) && alloc((void**)&h->partial, kReduceBlocks * 3 * sizeof(double)) &&
+              alloc((void**)&h->err, sizeof(int)) && alloc((void**)&h->zero_phi, sizeof(int)) &&
+              alloc((void**)&h->partial, kReduceBlocks * 3 * sizeof(double)) &&
               alloc((void**)&h->red_out, 4 * sizeof(double));
     if (ok) st = DISPATCH(h, configure);
     if (!ok || st != LBM_OK) {
@@ -772,6 +817,15 @@ extern "C" lbm_status lbm_vanse_set_drag(lbm_vanse_t h, double d0, double d1, do
     h->drag_d1 = d1;
     h->us_x = us_x;
     h->us_y = us_y;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_set_solid_cells(lbm_vanse_t h, int enable) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (enable && h->kernel != 1)
+        return fail(h, LBM_ERR_ARG, "solid cells run on step kernel 1 (this lattice uses kernel %d)", h->kernel);
+    h->has_solid = enable != 0;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // the step's shared memory changes
     return LBM_OK;
 }
 
@@ -977,6 +1031,10 @@ extern "C" lbm_status lbm_vanse_sync(lbm_vanse_t h) {
     int flag = 0;
     CK(h, cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) return fail(h, LBM_ERR_TIMEOUT, "a step kernel gave up waiting for its staged rows");
+    if (!h->has_solid) {
+        CK(h, cudaMemcpy(&flag, h->zero_phi, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) return fail(h, LBM_ERR_ARG, "phi holds zeros: solid cells need lbm_vanse_set_solid_cells (kernel 1)");
+    }
     return LBM_OK;
 }
 
@@ -1026,7 +1084,7 @@ extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
         cudaEventDestroy(h->staging_free);
     }
     void* ptrs[] = {h->f[0], h->f[1], h->phi, h->phin, h->fb, h->err, h->partial, h->red_out, h->scratch,
-                    h->staging[0], h->staging[1]};
+                    h->staging[0], h->staging[1], h->zero_phi};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;

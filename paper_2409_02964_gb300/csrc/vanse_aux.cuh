@@ -23,6 +23,7 @@ struct Lattice {
     int eq2 = 0;                       // App. B equilibrium (B1) instead of Eq. (14)
     int has_drag = 0;                  // F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi))
     R drag_d0 = 0, drag_d1 = 0, us_x = 0, us_y = 0;
+    int has_solid = 0;                 // cells with phi = 0 are solid (half-way bounce-back links)
 };
 
 // the linear drag coefficient beta(phi) of a lattice (0 without drag)
@@ -67,19 +68,34 @@ __global__ void ghost_fill_kernel(S* __restrict__ buf, long long plane, int nx, 
 
 // Copy a dense [ny][nx] field (double or float) into a padded R field (with
 // ghosts). Rows are dealt to blocks and columns to threads (32-bit indices).
+// zero_seen (optional): set to 1 when a value is exactly zero (a solid cell in phi).
 template <typename Tin, typename R>
-__global__ void pad_field_kernel(const Tin* __restrict__ src, R* __restrict__ dst, int nx, int ny, int P) {
+__global__ void pad_field_kernel(const Tin* __restrict__ src, R* __restrict__ dst, int nx, int ny, int P,
+                                 int* __restrict__ zero_seen = nullptr) {
+    bool zero = false;
     for (int y = blockIdx.x; y < ny; y += gridDim.x) {
         const Tin* row = src + (long long)y * nx;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) put_with_ghosts<R>(dst, P, nx, x, y, (R)row[x]);
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const R v = (R)row[x];
+            zero = zero || v == (R)0;
+            put_with_ghosts<R>(dst, P, nx, x, y, v);
+        }
     }
+    if (zero_seen && zero) *zero_seen = 1;
 }
 
 // Pull the post-streaming populations of cell (x, y) from the stored planes.
+// With solid cells: a solid cell has no populations (zeros), and a population whose
+// source cell is solid comes back from the half-way link (opposite slot, same cell).
 template <typename S, typename R>
 __device__ __forceinline__ void pull_cell(const S* __restrict__ buf, const R* __restrict__ phi, const Lattice<R>& L,
                                           int x, int y, R f[9]) {
     const R ph = phi[cell_off(L.P, x, y)];
+    if (L.has_solid && ph == (R)0) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = (R)0;
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         int sx = x - ex_of(i), sy = y - ey_of(i);
@@ -88,6 +104,7 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ buf, const R* __
             if (L.wall_y) { sx = x; sy = y; pi = opp_of(i); }
             else sy = (sy + L.ny) % L.ny;
         }
+        if (L.has_solid && pi == i && phi[cell_off(L.P, sx, sy)] == (R)0) { sx = x; sy = y; pi = opp_of(i); }
         const S v = buf[pi * L.plane + cell_off(L.P, sx, sy)];
         const R rest = (i == 0) ? L.rest.r0(ph) : L.rest.ri(i);
         f[i] = dec(v, rest, L.inv_scale);
@@ -97,33 +114,55 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ buf, const R* __
 // Store post-streaming value f_i(x, y) where the next pull will find it.
 template <typename S, typename R>
 __device__ __forceinline__ void scatter_cell(S* __restrict__ buf, const Lattice<R>& L, int x, int y, int i, R fi,
-                                             R phi_cell) {
+                                             R phi_cell, const R* __restrict__ phi = nullptr) {
     int tx = x - ex_of(i), ty = y - ey_of(i);
     int pi = i;
     if (ty < 0 || ty >= L.ny) {
         if (L.wall_y) { tx = x; ty = y; pi = opp_of(i); }
         else ty = (ty + L.ny) % L.ny;
     }
+    if (L.has_solid && pi == i && phi[cell_off(L.P, tx, ty)] == (R)0) { tx = x; ty = y; pi = opp_of(i); }
     tx = (tx + L.nx) % L.nx;
     const R rest = (i == 0) ? L.rest.r0(phi_cell) : L.rest.ri(i);
     put_with_ghosts<S>(buf + pi * L.plane, L.P, L.nx, tx, ty, enc<S, R>(fi, rest, L.scale));
 }
 
-// Eq. (10) on a dense [ny][nx] double field; rho-like (even) ghost rule at walls.
+// the row a stencil row y + dy maps to: periodic wrap, or the mirror row at a wall
+template <typename R>
+__device__ __forceinline__ int map_row(const Lattice<R>& L, int yy) {
+    if (yy < 0 || yy >= L.ny) {
+        if (L.wall_y) return yy < 0 ? -1 - yy : 2 * L.ny - 1 - yy;
+        return (yy + L.ny) % L.ny;
+    }
+    return yy;
+}
+
+// Eq. (10) on a dense [ny][nx] double field; rho-like (even) ghost rule at walls. With
+// solid cells (phi = 0) a solid neighbour reads the mirrored value: an axis neighbour
+// the cell itself, a diagonal one the mean of the fluid ones of its two axis images
+// (the cell itself if both are solid).
 template <typename R>
 __device__ __forceinline__ void grad_dense_even(const double* __restrict__ a, const Lattice<R>& L, int x, int y, R& gx,
-                                                R& gy) {
+                                                R& gy, const R* __restrict__ phi = nullptr) {
     R sx = 0, sy = 0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         int nx_ = (x + ex_of(i) + L.nx) % L.nx;
-        int ny_ = y + ey_of(i);
-        if (ny_ < 0 || ny_ >= L.ny) {
-            if (L.wall_y) ny_ = ny_ < 0 ? -1 - ny_ : 2 * L.ny - 1 - ny_;
-            else ny_ = (ny_ + L.ny) % L.ny;
-        }
+        int ny_ = map_row(L, y + ey_of(i));
         const R w = (i <= 4) ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0);
-        const R v = (R)a[(long long)ny_ * L.nx + nx_];
+        R v = (R)a[(long long)ny_ * L.nx + nx_];
+        if (L.has_solid && phi[cell_off(L.P, nx_, ny_)] == (R)0) {
+            const R own = (R)a[(long long)y * L.nx + x];
+            v = own;
+            if (ex_of(i) != 0 && ey_of(i) != 0) {
+                const int ax = nx_, by = map_row(L, y + ey_of(i));
+                const bool fa = phi[cell_off(L.P, ax, y)] != (R)0, fb_ = phi[cell_off(L.P, x, by)] != (R)0;
+                const R va = (R)a[(long long)y * L.nx + ax], vb = (R)a[(long long)by * L.nx + x];
+                if (fa && fb_) v = (va + vb) / (R)2;
+                else if (fa) v = va;
+                else if (fb_) v = vb;
+            }
+        }
         sx += w * v * (R)ex_of(i);
         sy += w * v * (R)ey_of(i);
     }
@@ -141,9 +180,10 @@ __global__ void init_kernel(S* __restrict__ buf, const R* __restrict__ phi, cons
         const int y = (int)(k / L.nx), x = (int)(k % L.nx);
         const long long co = cell_off(L.P, x, y);
         const R ph = phi[co];
+        if (L.has_solid && ph == (R)0) continue;   // a solid cell holds no populations
         const R rho = (R)rho_in[k], ux = (R)ux_in[k], uy = (R)uy_in[k];
         R gx, gy;
-        grad_dense_even<R>(rho_in, L, x, y, gx, gy);
+        grad_dense_even<R>(rho_in, L, x, y, gx, gy, phi);
         const R kp = (L.model_b ? (L.kappa - (R)1) : (L.kappa - ph)) / (R)3;
         R Fx = kp * gx + ph * L.gx, Fy = kp * gy + ph * L.gy;
         if (fb) { Fx += fb[co]; Fy += fb[L.plane + co]; }
@@ -168,7 +208,7 @@ __global__ void init_kernel(S* __restrict__ buf, const R* __restrict__ phi, cons
             }
             const R w = (i == 0) ? (R)(4.0 / 9.0) : ((i <= 4) ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0));
             const R Fi = w * (((R)3 * (exi - ux) + (R)9 * eu * exi) * Fx + ((R)3 * (eyi - uy) + (R)9 * eu * eyi) * Fy);
-            scatter_cell<S, R>(buf, L, x, y, i, feq - (R)0.5 * Fi, ph);
+            scatter_cell<S, R>(buf, L, x, y, i, feq - (R)0.5 * Fi, ph, phi);
         }
     }
 }
@@ -193,8 +233,9 @@ __global__ void set_pop_kernel(S* __restrict__ buf, const R* __restrict__ phi, c
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(k / L.nx), x = (int)(k % L.nx);
         const R ph = phi[cell_off(L.P, x, y)];
+        if (L.has_solid && ph == (R)0) continue;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) scatter_cell<S, R>(buf, L, x, y, i, (R)in[i * n + k], ph);
+        for (int i = 0; i < 9; ++i) scatter_cell<S, R>(buf, L, x, y, i, (R)in[i * n + k], ph, phi);
     }
 }
 
@@ -210,7 +251,8 @@ __global__ void rho_kernel(const S* __restrict__ buf, const R* __restrict__ phi,
         R s = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) s += f[i];
-        rho[k] = (double)(s / phi[cell_off(L.P, x, y)]);
+        const R ph = phi[cell_off(L.P, x, y)];
+        rho[k] = (L.has_solid && ph == (R)0) ? 0.0 : (double)(s / ph);
     }
 }
 
@@ -228,9 +270,15 @@ __global__ void vel_kernel(const S* __restrict__ buf, const R* __restrict__ phi,
         R s = 0, jx = 0, jy = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) { s += f[i]; jx += (R)ex_of(i) * f[i]; jy += (R)ey_of(i) * f[i]; }
-        R gx, gy;
-        grad_dense_even<R>(rho, L, x, y, gx, gy);
         const R ph = phi[co];
+        if (L.has_solid && ph == (R)0) {   // a solid cell reports zeros
+            if (ux) ux[k] = 0.0;
+            if (uy) uy[k] = 0.0;
+            if (pr) pr[k] = 0.0;
+            continue;
+        }
+        R gx, gy;
+        grad_dense_even<R>(rho, L, x, y, gx, gy, phi);
         const R kp = (L.model_b ? (L.kappa - (R)1) : (L.kappa - ph)) / (R)3;
         R Fx = kp * gx + ph * L.gx, Fy = kp * gy + ph * L.gy;
         if (fb) { Fx += fb[co]; Fy += fb[L.plane + co]; }

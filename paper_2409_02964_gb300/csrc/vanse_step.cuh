@@ -52,7 +52,11 @@ struct StepLayout {
     static constexpr int kPopSlot = 9 * kPopRow;
     static constexpr int kAux = kPop + kSlots * kPopSlot;     // aux ring: kSlots x nR rows of WW R
     static constexpr int kAuxRow = WW * (int)sizeof(R);
-    static constexpr size_t bytes(int nR) { return (size_t)kAux + (size_t)kSlots * nR * kAuxRow; }
+    __host__ __device__ static constexpr size_t bytes(int nR) { return (size_t)kAux + (size_t)kSlots * nR * kAuxRow; }
+    // with solid cells: rho, the six Eq. (20) fields and phi of the last three rows
+    // (8 x 3 x T R; phase 3 cannot read phi of row p3-1 from the staging ring, whose slot
+    // is refilled in the same row iteration)
+    __host__ __device__ static constexpr size_t solid_bytes() { return (size_t)24 * T * sizeof(R); }
 };
 
 template <typename R>
@@ -79,6 +83,7 @@ struct StepParams {
     double* sums;         // step-sum variants: FP64 sums of m_0+, j_x+, j_y+ over the cells written (added)
     int nee_top;          // row ny-1 is a moving wall by non-equilibrium extrapolation (kernel 1 only)
     R uw_x, uw_y;         // its velocity
+    int has_solid;        // cells with phi = 0 are solid (the SOLID variants of kernel 1; see solid_grad12)
 };
 
 // Compensated (Kahan) sums of the post-collision m_0, j_x, j_y of the cells one
@@ -175,7 +180,7 @@ struct StepCtx {
 };
 
 // Phase 1: pull + moments + rho for row r into st.
-template <typename S, typename R, int T>
+template <typename S, typename R, int T, bool SOLID = false>
 __device__ __forceinline__ void phase1(const StepCtx<S, R, T>& c, RowState<R>& st, int r) {
     using L = StepLayout<S, R, T>;
     constexpr int RW = L::WW;  // elements between population rows of a slot
@@ -208,6 +213,32 @@ __device__ __forceinline__ void phase1(const StepCtx<S, R, T>& c, RowState<R>& s
         f7 = dec(hi[7 * RW + 1], rs.dg, ia);
         f8 = dec(hi[8 * RW - 1], rs.dg, ia);
     }
+    if constexpr (SOLID) {
+        // a solid cell (phi = 0) has no populations; a link from a solid cell is a
+        // half-way bounce-back link: the population comes from the opposite slot of
+        // this cell
+        if (phi == (R)0) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) st.m[k] = (R)0;
+            st.rho = (R)0;
+            return;
+        }
+        const R* ph0 = c.aux(r, 0);
+        if (ph0[-1] == (R)0) f1 = dec(cur[3 * RW], rs.ax, ia);
+        if (ph0[1] == (R)0) f3 = dec(cur[1 * RW], rs.ax, ia);
+        if (!(p.wall_y && r == 0)) {
+            const R* phl = c.aux(r - 1, 0);
+            if (phl[0] == (R)0) f2 = dec(cur[4 * RW], rs.ax, ia);
+            if (phl[-1] == (R)0) f5 = dec(cur[7 * RW], rs.dg, ia);
+            if (phl[1] == (R)0) f6 = dec(cur[8 * RW], rs.dg, ia);
+        }
+        if (!(p.wall_y && r == p.ny - 1)) {
+            const R* phh = c.aux(r + 1, 0);
+            if (phh[0] == (R)0) f4 = dec(cur[2 * RW], rs.ax, ia);
+            if (phh[1] == (R)0) f7 = dec(cur[5 * RW], rs.dg, ia);
+            if (phh[-1] == (R)0) f8 = dec(cur[6 * RW], rs.dg, ia);
+        }
+    }
     // m = M f with the row structure of (A1)
     const R a13 = f1 + f3, a24 = f2 + f4, b57 = f5 + f7, b68 = f6 + f8;
     const R sax = a13 + a24, sdg = b57 + b68;
@@ -227,12 +258,88 @@ __device__ __forceinline__ void phase1(const StepCtx<S, R, T>& c, RowState<R>& s
     st.rho = st.m[0] * rcp_r(phi);
 }
 
+// 3-row ring index of a (possibly negative) row number
+__device__ __forceinline__ int ring3(int r) { return ((r % 3) + 3) % 3; }
+
+// 12 x the Eq. (10) gradient of a field at the fluid cell (thread column, row y) when
+// solid cells (phi = 0) may be among its neighbours. val(row, dx) reads the field of
+// a staged row, phi_at(row, dx) its void fraction. Neighbours map as everywhere (a row
+// past a half-way wall is the mirror row, a vector component changing sign; the row
+// past the moving wall extrapolates linearly); a solid neighbour then reads the ghost
+// value mirrored about the solid surface: an axis neighbour the cell itself, a
+// diagonal one the mean of the fluid ones of its two axis images (the cell itself if
+// both are solid), negated for a vector component (odd). Returns false (and leaves
+// g unset) when no neighbour is solid.
+template <typename R, typename Val, typename Phi>
+__device__ __forceinline__ bool solid_grad12(const StepParams<R>& p, int y, bool odd, Val val, Phi phi_at, R& gx12,
+                                             R& gy12) {
+    auto rowsel = [&](int dy, int& sg) {
+        const int yy = y + dy;
+        sg = 1;
+        if (p.wall_y && (yy < 0 || yy >= p.ny)) { sg = -1; return y; }
+        return yy;
+    };
+    bool any = false;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            int sg;
+            const int rr = rowsel(dy, sg);
+            const bool nee_row = p.nee_top && y + dy == p.ny;
+            any = any || (!nee_row && phi_at(rr, dx) == (R)0);
+        }
+    if (!any) return false;
+    const R osg = odd ? (R)-1 : (R)1;
+    R sx = 0, sy = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            int sg;
+            const int rr = rowsel(dy, sg);
+            const bool nee_row = p.nee_top && y + dy == p.ny;
+            R v;
+            if (!nee_row && phi_at(rr, dx) == (R)0) {
+                v = val(y, 0);
+                if (dx != 0 && dy != 0) {
+                    int sb;
+                    const int rb = rowsel(dy, sb);
+                    const bool fa = phi_at(y, dx) != (R)0, fb = phi_at(rb, 0) != (R)0;
+                    const R va = val(y, dx), vb = (odd && sb < 0) ? -val(rb, 0) : val(rb, 0);
+                    if (fa && fb) v = (va + vb) / (R)2;
+                    else if (fa) v = va;
+                    else if (fb) v = vb;
+                }
+                v = osg * v;
+            } else if (nee_row) {
+                v = (R)2 * val(y, dx) - val(y - 1, dx);
+            } else {
+                v = (odd && sg < 0) ? -val(rr, dx) : val(rr, dx);
+            }
+            const R cw = (dx != 0 && dy != 0) ? (R)1 : (R)4;   // 36 w_i
+            sx += cw * v * (R)dx;
+            sy += cw * v * (R)dy;
+        }
+    gx12 = sx;
+    gy12 = sy;
+    return true;
+}
+
 // Phase 2 for row p2 (state Bs), rows p2-1 / p2+1 in Cs / An.
-template <typename S, typename R, int T>
+template <typename S, typename R, int T, bool SOLID = false>
 __device__ __forceinline__ void phase2(const StepCtx<S, R, T>& c, const RowState<R>& An, RowState<R>& Bs,
-                                       const RowState<R>& Cs, int p2, R* fbuf) {
+                                       const RowState<R>& Cs, int p2, R* fbuf, const R* rho3 = nullptr) {
     const StepParams<R>& p = c.p;
     const R twelfth = (R)1 / (R)12;
+    if (SOLID && *c.aux(p2, 0) == (R)0) {   // solid cell: no velocity, no force, zero fields
+        Bs.Fx = Bs.Fy = Bs.ux = Bs.uy = (R)0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fbuf[k * T + c.t] = (R)0;
+        return;
+    }
     R dlo = Cs.dr, wlo = Cs.wr, dhi = An.dr, whi = An.wr;
     if (p.wall_y && (p2 == 0 || p2 == p.ny - 1)) {  // rho's wall ghost: the mirror row itself
         if (p2 == 0) { dlo = Bs.dr; wlo = Bs.wr; }
@@ -241,8 +348,15 @@ __device__ __forceinline__ void phase2(const StepCtx<S, R, T>& c, const RowState
             else { dhi = Bs.dr; whi = Bs.wr; }
         }
     }
-    const R gx = (dlo + (R)4 * Bs.dr + dhi) * twelfth;
-    const R gy = (whi - wlo) * twelfth;
+    R gx = (dlo + (R)4 * Bs.dr + dhi) * twelfth;
+    R gy = (whi - wlo) * twelfth;
+    if constexpr (SOLID) {
+        R gx12, gy12;
+        const int t = c.t;
+        auto val = [&](int row, int dx) { return rho3[ring3(row) * T + t + dx]; };
+        auto phi_at = [&](int row, int dx) { return c.aux(row, 0)[dx]; };
+        if (solid_grad12(p, p2, false, val, phi_at, gx12, gy12)) { gx = gx12 * twelfth; gy = gy12 * twelfth; }
+    }
     const R phi = *c.aux(p2, 0);
     const R kp = (p.model_b ? (p.kappa - (R)1) : (p.kappa - phi)) * ((R)1 / (R)3);
     R Fx = kp * gx + phi * p.gx;
@@ -278,11 +392,13 @@ __device__ __forceinline__ void phase2(const StepCtx<S, R, T>& c, const RowState
 }
 
 // Phase 3 for row p3 (state Cs), rows p3-1 / p3+1 in An / Bs: C, collision, store.
-template <typename S, typename R, int T, bool SUMS = false>
+template <typename S, typename R, int T, bool SUMS = false, bool SOLID = false>
 __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState<R>& An, const RowState<R>& Bs,
-                                       const RowState<R>& Cs, int p3, MomentSums<R>* sums = nullptr) {
+                                       const RowState<R>& Cs, int p3, MomentSums<R>* sums = nullptr,
+                                       const R* fld3 = nullptr) {
     const StepParams<R>& p = c.p;
     const R twelfth = (R)1 / (R)12;
+    if (SOLID && *c.aux(p3, 0) == (R)0) return;   // a solid cell neither collides nor stores
     // 12 x the Eq. (10) derivatives
     R xAx = An.dAx + (R)4 * Cs.dAx + Bs.dAx;
     R xBx = An.dBx + (R)4 * Cs.dBx + Bs.dBx;
@@ -316,6 +432,29 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
         yDy = wDh - wDl;
     }
 
+    // App. B cross derivatives, replaced below next to solid cells
+    R xAy_s = 0, yAx_s = 0, xDy_s = 0, yDx_s = 0;
+    bool solid_nb = false;
+    if constexpr (SOLID) {
+        const int t = c.t;
+        // phi of rows p3-1 .. p3+1 from the ring phase 2 fills (the staging slot of row
+        // p3-1 is being refilled by now)
+        auto phi_at = [&](int row, int dx) { return fld3[18 * T + ring3(row) * T + t + dx]; };
+        R g[6][2];
+        for (int k = 0; k < 6 && (k == 0 || solid_nb); ++k) {
+            auto val = [&](int row, int dx) { return fld3[(ring3(row) * 6 + k) * T + t + dx]; };
+            const bool any = solid_grad12(p, p3, true, val, phi_at, g[k][0], g[k][1]);
+            if (k == 0) solid_nb = any;
+        }
+        if (solid_nb) {
+            // fields 0..5: rho u_x, rho u_y, u_x, u_y, phi rho u_x, phi rho u_y
+            xAx = g[0][0]; yAy = g[1][1];
+            xBx = g[2][0]; yBy = g[3][1]; xBy = g[3][0]; yBx = g[2][1];
+            xDx = g[4][0]; yDy = g[5][1];
+            xAy_s = g[1][0]; yAx_s = g[0][1]; xDy_s = g[5][0]; yDx_s = g[4][1];
+        }
+    }
+
     const R phi = *c.aux(p3, 0);
     const R phin = p.unsteady ? *c.aux(p3, 1) : phi;
     const R rho = Cs.rho;
@@ -340,6 +479,7 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
             yAx = ghi(Cs.wAx, An.wAx, Bs.wAx) - (lo ? -Cs.wAx : An.wAx);
             yDx = ghi(Cs.wDx, An.wDx, Bs.wDx) - (lo ? -Cs.wDx : An.wDx);
         }
+        if (solid_nb) { xAy = xAy_s; yAx = yAx_s; xDy = xDy_s; yDx = yDx_s; }
         const R t3 = (R)2 / (R)3;
         Ca = ((R)-2 * p.kappa * (xAx + yAy) + (R)2 * kr * (xBx + yBy) + ((R)4 - (R)2 * X) * (xDx + yDy)) * twelfth
              - (R)2 * X * rho * (phin - phi);
@@ -448,7 +588,7 @@ __device__ __forceinline__ void nee_wall_moments(const StepParams<R>& p, RowStat
     for (int k = 0; k < 9; ++k) Wa.m[k] = eb[k] + (Fl.m[k] - ef[k]);
 }
 
-template <typename S, typename R, int T, bool SUMS = false>
+template <typename S, typename R, int T, bool SUMS = false, bool SOLID = false>
 __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ StepParams<R> p) {
     using L = StepLayout<S, R, T>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -486,6 +626,10 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
 
     RowState<R> s0, s1, s2;
     MomentSums<R> sums;
+    // with solid cells: rho and the six fields of the last three rows, for the
+    // neighbour-by-neighbour stencil next to solid cells
+    R* rho3 = SOLID ? reinterpret_cast<R*>(smem + L::bytes(p.nR)) : nullptr;
+    R* fld3 = SOLID ? rho3 + 3 * T : nullptr;        // [3][6][T]; phi of the same rows follows at fld3 + 18 T
 
     // one iteration: new row p1 -> An, row p1-1 -> Bs, row p1-2 -> Cs
     auto iter = [&](RowState<R>& An, RowState<R>& Bs, RowState<R>& Cs, const int p1) -> bool {
@@ -493,10 +637,11 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
         c.wait_upto(p1 + 1);
         const bool ph1 = (p1 <= y1 + 1) && c.row_valid(p1);
         if (ph1) {
-            phase1<S, R, T>(c, An, p1);
+            phase1<S, R, T, SOLID>(c, An, p1);
             // moving wall row: rho_b = rho of the fluid row below (its moments follow below)
             if (p.nee_top && p1 == p.ny - 1) An.rho = Bs.rho;
             rbuf[t] = An.rho;
+            if constexpr (SOLID) rho3[ring3(p1) * T + t] = An.rho;
         }
         __syncthreads();  // A: rho row p1 visible; slot p1-3 free
         if (s_abort) return false;
@@ -511,7 +656,12 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
             An.wr = (R)4 * An.rho + (r + l);
         }
         if (ph2 && ph2_thread) {
-            phase2<S, R, T>(c, An, Bs, Cs, p2, fbuf);
+            phase2<S, R, T, SOLID>(c, An, Bs, Cs, p2, fbuf, rho3);
+            if constexpr (SOLID) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) fld3[(ring3(p2) * 6 + k) * T + t] = fbuf[k * T + t];
+                fld3[18 * T + ring3(p2) * T + t] = *c.aux(p2, 0);
+            }
             if (p.nee_top && p1 == p.ny - 1 && ph1) nee_wall_moments(p, An, Bs, *c.aux(p1, 0), *c.aux(p2, 0));
         }
         __syncthreads();  // B: field row p2 visible
@@ -539,7 +689,7 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
             }
         }
         const bool ph3 = (p3 >= y0) && (p3 < y1);
-        if (ph3 && ph3_thread && c.xc < p.nx) phase3<S, R, T, SUMS>(c, An, Bs, Cs, p3, &sums);
+        if (ph3 && ph3_thread && c.xc < p.nx) phase3<S, R, T, SUMS, SOLID>(c, An, Bs, Cs, p3, &sums, fld3);
         return true;
     };
 

@@ -153,6 +153,11 @@ class Lattice:
         """F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi)) (lbm_vanse_set_drag)."""
         _check(self._L.lbm_vanse_set_drag(self._h, float(d0), float(d1), float(us_x), float(us_y)), self._h)
 
+    def set_solid_cells(self, enable: bool = True) -> None:
+        """Cells with phi = 0 are solid (lbm_vanse_set_solid_cells; kernel 1, before
+        init_fields)."""
+        _check(self._L.lbm_vanse_set_solid_cells(self._h, int(enable)), self._h)
+
     def set_moving_wall(self, uw_x: float = 0.0, uw_y: float = 0.0, enable: bool = True) -> None:
         """Row ny-1 as a wall moving at (uw_x, uw_y) by non-equilibrium extrapolation
         (lbm_vanse_set_moving_wall; bounce-back walls, kernel 1)."""

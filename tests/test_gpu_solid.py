@@ -1,0 +1,176 @@
+"""Solid cells (phi = 0; lbm_vanse_set_solid_cells, kernel 1) on the GPU against the
+FP64 oracle: random solid patterns (a block, isolated cells, diagonal pairs, cells at
+the periodic edge and next to the walls) on walled and periodic lattices with moving
+phi and force fields; solid frames against the built-in walls; the Eq. (24) block
+flow over many steps; mass conservation.
+
+Tolerances as in test_gpu_parity (FP64: 1e-12 of the fluid cells' largest deviation
+from rest; FP32: 32 * 2^-24 * max|f| per step)."""
+import numpy as np
+import pytest
+
+from gpu_cases import random_case, rest_populations, total_force
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_02964_gb300 as pkg
+    pkg.capi.load()
+    return pkg
+
+
+def _solids(nx, ny, seed, wall_y):
+    rng = np.random.default_rng(seed)
+    m = np.zeros((ny, nx), bool)
+    a, b = ny // 3, max(ny // 3 + 2, 2 * ny // 3)
+    c, d = nx // 3, max(nx // 3 + 2, nx // 2)
+    m[a:b, c:d] = True                                  # a block
+    for _ in range(max(2, nx * ny // 60)):              # scattered cells
+        m[rng.integers(ny), rng.integers(nx)] = True
+    m[1, 1] = m[2, 2] = True                            # a diagonal pair
+    m[ny // 2, 0] = m[ny // 2 + 1, nx - 1] = True       # across the periodic x edge
+    if wall_y:
+        m[0, nx // 2] = m[ny - 1, nx // 3] = True       # next to the walls
+    return m
+
+
+def _run(P, O, nx, ny, case, solid, steps, storage, wall_y, tau=0.8, eq_order=3, drag=None):
+    phi = np.where(solid, 0.0, case["phi"])
+    phin = np.where(solid, 0.0, case["phin"]) if case["phin"] is not None else None
+    case = dict(case, phi=phi, phin=phin)
+    lat = P.Lattice(nx, ny, tau, s_eps=1.2, s_q=1.4, bc_y="bounceback" if wall_y else "periodic", storage=storage,
+                    kernel=1, eq_order=eq_order)
+    lat.set_solid_cells()
+    if drag:
+        lat.set_drag(*drag)
+    lat.set_void_fraction(case["phi"], case["phin"])
+    lat.set_body_force(case["g"][0], case["g"][1], case["fb"])
+    lat.init_fields(case["rho"], case["ux"], case["uy"])
+    kw = dict(drag_d0=drag[0], drag_d1=drag[1], us_x=drag[2], us_y=drag[3]) if drag else {}
+    prm = O.Params(nx=nx, ny=ny, **O.rates_from_tau(tau, s_eps=1.2, s_q=1.4), kappa=0.5, bc_y=int(wall_y),
+                   eq_order=eq_order, **kw)
+    fb = total_force(case)
+    f = O.init(prm, case["rho"], case["ux"], case["uy"], case["phi"], fb)
+    f0g = lat.get_populations().cpu().numpy()
+    init_err = np.abs(f0g - f).max() / np.abs(f).max()
+    for k in range(steps):
+        pn = case["phin"] if k == 0 else None
+        if k == 1 and case["phin"] is not None:
+            case = dict(case, phi=case["phin"], phin=None)
+            fb = total_force(case)
+        f = O.step(prm, f, case["phi"], pn, fb)
+    lat.step(steps)
+    lat.sync()
+    fg = lat.get_populations().cpu().numpy()
+    m = {k: v.cpu().numpy() for k, v in lat.macros().items()}
+    lat.close()
+    return init_err, fg, f, case, m
+
+
+CASES = [
+    (37, 21, True, True, True, (2e-5, -1e-5)),
+    (64, 17, False, False, True, (0.0, 0.0)),
+    (130, 40, True, False, False, (1e-5, 0.0)),
+    (9, 7, False, True, False, (0.0, 3e-5)),
+]
+
+
+@pytest.mark.parametrize("nx,ny,wall_y,unsteady,field,g", CASES)
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_solid_cells_match_oracle(P, oracle_mod, nx, ny, wall_y, unsteady, field, g, storage):
+    steps = 6
+    case = random_case(nx, ny, seed=nx + 3 * ny, wall_y=wall_y, unsteady=unsteady, field=field, g=g)
+    solid = _solids(nx, ny, nx * ny, wall_y)
+    init_err, fg, fo, case, m = _run(P, oracle_mod, nx, ny, case, solid, steps, storage, wall_y)
+    fluid = ~solid
+    assert np.all(fg[:, solid] == 0.0) and np.all(m["rho"][solid] == 0.0) and np.all(m["ux"][solid] == 0.0)
+    if storage == "fp64":
+        assert init_err < 1e-14
+        scale = np.abs(fo - rest_populations(case["phi"]))[:, fluid].max()
+        assert np.abs(fg - fo).max() / scale <= 1e-12
+    else:
+        assert np.abs(fg - fo).max() <= steps * 32 * EPS32 * np.abs(fo).max()
+
+
+@pytest.mark.parametrize("variant", ["appb", "drag"])
+def test_solid_cells_with_variants_match_oracle(P, oracle_mod, variant):
+    nx, ny = 40, 19
+    case = random_case(nx, ny, seed=5, wall_y=True, unsteady=True, field=True, g=(1e-5, 0.0))
+    solid = _solids(nx, ny, 9, True)
+    kw = dict(eq_order=2) if variant == "appb" else dict(drag=(0.03, 0.4, 2e-3, -1e-3))
+    _, fg, fo, case, _ = _run(P, oracle_mod, nx, ny, case, solid, 5, "fp64", True, **kw)
+    scale = np.abs(fo - rest_populations(case["phi"]))[:, ~solid].max()
+    assert np.abs(fg - fo).max() / scale <= 1e-12
+
+
+def test_solid_rows_equal_builtin_walls(P):
+    """A periodic lattice framed by solid rows steps like the walled lattice (FP64)."""
+    nx, ny, steps = 50, 20, 30
+    case = random_case(nx, ny, seed=12, wall_y=True, unsteady=False, field=True, g=(1e-5, 0.0))
+    pad = lambda a, v=0.0: np.pad(a, ((1, 1), (0, 0)), constant_values=v)
+    walled = P.Lattice(nx, ny, 0.7, s_eps=1.2, s_q=1.4, bc_y="bounceback", storage="fp64", kernel=1)
+    framed = P.Lattice(nx, ny + 2, 0.7, s_eps=1.2, s_q=1.4, bc_y="periodic", storage="fp64", kernel=1)
+    framed.set_solid_cells()
+    walled.set_void_fraction(case["phi"])
+    framed.set_void_fraction(pad(case["phi"]))
+    walled.set_body_force(case["g"][0], 0.0, case["fb"])
+    framed.set_body_force(case["g"][0], 0.0, np.stack([pad(case["fb"][0]), pad(case["fb"][1])]))
+    walled.init_fields(case["rho"], case["ux"], case["uy"])
+    framed.init_fields(pad(case["rho"], 1.0), pad(case["ux"]), pad(case["uy"]))
+    walled.step(steps)
+    framed.step(steps)
+    fw = walled.get_populations().cpu().numpy()
+    ff = framed.get_populations().cpu().numpy()[:, 1:-1]
+    walled.close()
+    framed.close()
+    assert np.abs(ff - fw).max() <= 1e-14 * np.abs(fw).max()
+
+
+def test_eq24_solid_block_flow_matches_oracle(P, oracle_mod):
+    """The Eq. (24) geometry with an impermeable block, G = 1e-6 (scaled up to 1e-4 to
+    move the populations well above rounding), 400 steps, FP64."""
+    O = oracle_mod
+    n, steps, G = 32, 400, 1e-4
+    solid = np.zeros((n, n), bool)
+    a, b = int(round(0.4 * n)), int(round(0.6 * n))
+    solid[a:b, a:b] = True
+    phi = np.where(solid, 0.0, 1.0)
+    lat = P.Lattice(n, n, 0.8, s_eps=1.2, s_q=1.2, storage="fp64", kernel=1)
+    lat.set_solid_cells()
+    lat.set_void_fraction(phi)
+    lat.set_body_force(G, 0.0)
+    zeros = np.zeros((n, n))
+    lat.init_fields(np.ones((n, n)), zeros, zeros)
+    prm = O.Params(nx=n, ny=n, **O.rates_from_tau(0.8, s_eps=1.2, s_q=1.2), kappa=0.5)
+    fb = np.stack([phi * G, zeros])
+    f = O.init(prm, np.ones((n, n)), zeros, zeros, phi, fb)
+    m0 = f.sum()
+    for _ in range(steps):
+        f = O.step(prm, f, phi, None, fb)
+    lat.step(steps)
+    fg = lat.get_populations().cpu().numpy()
+    mass = lat.reduce()[0]
+    lat.close()
+    assert np.abs(fg - f).max() / np.abs(f - rest_populations(phi))[:, ~solid].max() <= 1e-12
+    assert abs(mass - m0) <= 1e-13 * m0
+
+
+def test_solid_cell_errors(P):
+    lat = P.Lattice(16, 8, 0.8, kernel=5)
+    with pytest.raises(P.LbmError):
+        lat.set_solid_cells()
+    lat.close()
+    lat = P.Lattice(16, 8, 0.8, storage="fp64")      # kernel 1, solid cells not enabled
+    phi = np.full((8, 16), 0.7)
+    phi[3, 4] = 0.0
+    lat.set_void_fraction(phi)
+    with pytest.raises(P.LbmError):
+        lat.sync()
+    lat.close()
