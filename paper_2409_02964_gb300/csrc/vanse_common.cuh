@@ -24,20 +24,20 @@ constexpr int kPadCols = 32;
 // deviations from the rest state; FP32/FP64 hold f itself.
 template <typename S> struct Prec;
 template <> struct Prec<double> { using R = double; static constexpr bool kDev = false; };
-template <> struct Prec<float> { using R = float; static constexpr bool kDev = false; };
+template <> struct Prec<float> { using R = float; static constexpr bool kDev = true; };
 template <> struct Prec<__half> { using R = float; static constexpr bool kDev = true; };
 template <> struct Prec<__nv_bfloat16> { using R = float; static constexpr bool kDev = true; };
 
 template <typename R> __device__ __forceinline__ R to_r(double v) { return (R)v; }
 
 __device__ __forceinline__ double dec(double s, double, double) { return s; }
-__device__ __forceinline__ float dec(float s, float, float) { return s; }
+__device__ __forceinline__ float dec(float s, float rest, float inv_scale) { return fmaf(s, inv_scale, rest); }
 __device__ __forceinline__ float dec(__half s, float rest, float inv_scale) { return fmaf(__half2float(s), inv_scale, rest); }
 __device__ __forceinline__ float dec(__nv_bfloat16 s, float rest, float inv_scale) { return fmaf(__bfloat162float(s), inv_scale, rest); }
 
 template <typename S, typename R> __device__ __forceinline__ S enc(R f, R rest, R scale);
 template <> __device__ __forceinline__ double enc<double, double>(double f, double, double) { return f; }
-template <> __device__ __forceinline__ float enc<float, float>(float f, float, float) { return f; }
+template <> __device__ __forceinline__ float enc<float, float>(float f, float rest, float scale) { return (f - rest) * scale; }
 template <> __device__ __forceinline__ __half enc<__half, float>(float f, float rest, float scale) { return __float2half_rn((f - rest) * scale); }
 template <> __device__ __forceinline__ __nv_bfloat16 enc<__nv_bfloat16, float>(float f, float rest, float scale) { return __float2bfloat16_rn((f - rest) * scale); }
 

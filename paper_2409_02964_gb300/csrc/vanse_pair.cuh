@@ -52,14 +52,16 @@ template <typename S> struct PairIO;
 template <> struct PairIO<float> {
     __device__ static V2 al(const float* p) { return V2{*reinterpret_cast<const float2*>(p)}; }
     __device__ static V2 un(const float* p) { return mk(p[0], p[1]); }
-    __device__ static V2 dec(V2 d, V2, float) { return d; }
+    __device__ static V2 dec(V2 d, V2 rest, float) { return d + rest; }
+    __device__ static V2 dev(V2 d, float) { return d; }
     __device__ static void st(float* p, V2 v) { *reinterpret_cast<float2*>(p) = v.v; }
-    __device__ static float enc1(float f, float, float) { return f; }
+    __device__ static float enc1(float f, float rest, float) { return f - rest; }
 };
 template <> struct PairIO<__half> {
     __device__ static V2 al(const __half* p) { return V2{__half22float2(*reinterpret_cast<const __half2*>(p))}; }
     __device__ static V2 un(const __half* p) { return V2{__half22float2(__halves2half2(p[0], p[1]))}; }
     __device__ static V2 dec(V2 d, V2 rest, float ia) { return fma2(ia, d, rest); }
+    __device__ static V2 dev(V2 d, float ia) { return ia * d; }
     __device__ static void st(__half* p, V2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
     __device__ static __half enc1(float f, float rest, float s) { return __float2half_rn((f - rest) * s); }
 };
@@ -69,6 +71,7 @@ template <> struct PairIO<__nv_bfloat16> {
     }
     __device__ static V2 un(const __nv_bfloat16* p) { return V2{__bfloat1622float2(__halves2bfloat162(p[0], p[1]))}; }
     __device__ static V2 dec(V2 d, V2 rest, float ia) { return fma2(ia, d, rest); }
+    __device__ static V2 dev(V2 d, float ia) { return ia * d; }
     __device__ static void st(__nv_bfloat16* p, V2 v) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
     }
@@ -374,11 +377,11 @@ __device__ __forceinline__ void pair_phase3(const PairCtx<S, T>& c, const PRow& 
     const bool va = xa0 < p.nx, vb = xa0 + 1 < p.nx;
     if (va && vb) {
         S* cell = row + xa0;
-        IO::st(cell, sizeof(S) == 4 ? fo[0] : p.scale * (fo[0] - r0));
+        IO::st(cell, sizeof(S) == 4 ? fo[0] - r0 : p.scale * (fo[0] - r0));
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const V2 ri = bc(i <= 4 ? p.rest.ax : p.rest.dg);
-            IO::st(cell + i * p.plane, sizeof(S) == 4 ? fo[i] : p.scale * (fo[i] - ri));
+            IO::st(cell + i * p.plane, sizeof(S) == 4 ? fo[i] - ri : p.scale * (fo[i] - ri));
         }
     } else if (va) {
         S* cell = row + xa0;

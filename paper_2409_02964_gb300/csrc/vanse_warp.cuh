@@ -193,32 +193,33 @@ __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
     c.row_setup(r, st);
     const V2 phi = c.phi2(r, st);
     const float ia = p.inv_scale;
-    const V2 rax = bc(p.rest.ax), rdg = bc(p.rest.dg);
-    const V2 r0 = fma2(p.rest.rho0, phi, bc(-p.rest.k59));
+    // the stored values are deviations from the rest state of Eq. (14) (times the
+    // storage scale); this kernel keeps them as deviations: f0..f8 below are
+    // f_i - f_i^rest, and the rest state's moments are added back analytically
     const S* cur = c.pop(r);
     V2 f0, f1, f2, f3, f4, f5, f6, f7, f8;
-    f0 = IO::dec(IO::al(cur), r0, ia);
-    f1 = IO::dec(IO::un(cur + 1 * RW - 1), rax, ia);
-    f3 = IO::dec(IO::un(cur + 3 * RW + 1), rax, ia);
+    f0 = IO::dev(IO::al(cur), ia);
+    f1 = IO::dev(IO::un(cur + 1 * RW - 1), ia);
+    f3 = IO::dev(IO::un(cur + 3 * RW + 1), ia);
     if (!FAST && p.wall_y && r == 0) {
-        f2 = IO::dec(IO::al(cur + 4 * RW), rax, ia);
-        f5 = IO::dec(IO::al(cur + 7 * RW), rdg, ia);
-        f6 = IO::dec(IO::al(cur + 8 * RW), rdg, ia);
+        f2 = IO::dev(IO::al(cur + 4 * RW), ia);
+        f5 = IO::dev(IO::al(cur + 7 * RW), ia);
+        f6 = IO::dev(IO::al(cur + 8 * RW), ia);
     } else {
         const S* lo = c.pop(r - 1);
-        f2 = IO::dec(IO::al(lo + 2 * RW), rax, ia);
-        f5 = IO::dec(IO::un(lo + 5 * RW - 1), rdg, ia);
-        f6 = IO::dec(IO::un(lo + 6 * RW + 1), rdg, ia);
+        f2 = IO::dev(IO::al(lo + 2 * RW), ia);
+        f5 = IO::dev(IO::un(lo + 5 * RW - 1), ia);
+        f6 = IO::dev(IO::un(lo + 6 * RW + 1), ia);
     }
     if (!FAST && p.wall_y && r == p.ny - 1) {
-        f4 = IO::dec(IO::al(cur + 2 * RW), rax, ia);
-        f7 = IO::dec(IO::al(cur + 5 * RW), rdg, ia);
-        f8 = IO::dec(IO::al(cur + 6 * RW), rdg, ia);
+        f4 = IO::dev(IO::al(cur + 2 * RW), ia);
+        f7 = IO::dev(IO::al(cur + 5 * RW), ia);
+        f8 = IO::dev(IO::al(cur + 6 * RW), ia);
     } else {
         const S* hi = c.pop(r + 1);
-        f4 = IO::dec(IO::al(hi + 4 * RW), rax, ia);
-        f7 = IO::dec(IO::un(hi + 7 * RW + 1), rdg, ia);
-        f8 = IO::dec(IO::un(hi + 8 * RW - 1), rdg, ia);
+        f4 = IO::dev(IO::al(hi + 4 * RW), ia);
+        f7 = IO::dev(IO::un(hi + 7 * RW + 1), ia);
+        f8 = IO::dev(IO::un(hi + 8 * RW - 1), ia);
     }
     const V2 a13 = f1 + f3, a24 = f2 + f4, b57 = f5 + f7, b68 = f6 + f8;
     const V2 sax = a13 + a24, sdg = b57 + b68;
@@ -234,6 +235,8 @@ __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
     st.m[6] = fma2(-2.f, d24, dy);
     st.m[7] = a13 - a24;
     st.m[8] = b57 - b68;
+    // m[0..2] are the deviations of sum f, e and eps from the rest state's phi rho0,
+    // rho0 (2 kappa - 4 phi) and rho0 (4 phi - 3 kappa); rho holds rho - rho0
     st.rho = st.m[0] * rcp2(phi);
 }
 
@@ -253,7 +256,7 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
     V2 Fx = fma2(kp, gx, p.gx * phi);
     V2 Fy = fma2(kp, gy, p.gy * phi);
     c.template add_field_force<FAST>(p2, Bs, Fx, Fy);
-    const V2 m0 = Bs.m[0];
+    const V2 m0 = fma2(p.rest.rho0, phi, Bs.m[0]);   // sum f = phi rho0 + its deviation
     V2 ux, uy;
     if (!FAST && p.has_drag) {
         // Eq. (7) with F^B += -beta (u - u_s): linear in u, solved exactly (never on the fast path)
@@ -270,7 +273,8 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
     }
     Bs.Fx = Fx; Bs.Fy = Fy; Bs.ux = ux; Bs.uy = uy;
     // the Eq. (10) x-differences / smoothed sums of rho u, u, phi rho u on row p2
-    const V2 Ax = Bs.rho * ux, Ay = Bs.rho * uy, Dx = m0 * ux, Dy = m0 * uy;
+    const V2 rho = Bs.rho + p.rest.rho0;
+    const V2 Ax = rho * ux, Ay = rho * uy, Dx = m0 * ux, Dy = m0 * uy;
     const float Axl = left_of(Ax), Axr = right_of(Ax);
     const float Ayl = left_of(Ay), Ayr = right_of(Ay);
     const float Bxl = left_of(ux), Bxr = right_of(ux);
@@ -322,7 +326,7 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     }
     const V2 phi = c.phi2(p3, Cs);
     const V2 phin = c.template phin2<FAST>(p3, Cs);
-    const V2 rho = Cs.rho;
+    const V2 rho = Cs.rho + p.rest.rho0;
     const V2 X = p.kappa * rcp2(phi);
     const V2 kp = p.model_b ? bc(p.kappa - 1.f) : bc(p.kappa) - phi;
     const V2 kr = kp * rho;
@@ -331,15 +335,21 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     if (!FAST || Ctx::kUnsteady) Ca = fma2(-2.f, (X * rho) * (phin - phi), Ca);
     const V2 Cb = tw * fma2(-p.kappa, xAx - yAy, fma2((2.f / 3.f) * kr, xBx - yBy, difD));
     const V2 Cc = (1.f / 36.f) * (kr * (xBy + yBx));
-    const V2 m0 = Cs.m[0], ux = Cs.ux, uy = Cs.uy, Fx = Cs.Fx, Fy = Cs.Fy;
+    // Eq. (18), (19), (16) on the deviations from the rest state: the rest state's
+    // moments (phi rho0, rho0 (2 kappa - 4 phi), rho0 (4 phi - 3 kappa), 0, ...) leave
+    // m_0, e and eps; the equilibria of e and eps then differ from them by
+    // dm0 (2X - 4) + 3 m0 |u|^2 and dm0 (4 - 3X) - 3 m0 |u|^2 (rho - rho0 = dm0 / phi)
+    const V2 dm0 = Cs.m[0], ux = Cs.ux, uy = Cs.uy, Fx = Cs.Fx, Fy = Cs.Fy;
+    const V2 m0 = fma2(p.rest.rho0, phi, dm0);
     const V2 uu = fma2(ux, ux, uy * uy);
     const V2 uF = fma2(ux, Fx, uy * Fy);
     const V2 jxe = m0 * ux, jye = m0 * uy;
     const V2 q = X - bc(2.f);
+    const V2 m0uu = m0 * uu;
     V2 a[9];
-    a[0] = m0;
-    const V2 me1 = m0 * fma2(3.f, uu, fma2(2.f, X, bc(-4.f)));
-    const V2 me2 = m0 * fma2(-3.f, uu, fma2(-3.f, X, bc(4.f)));
+    a[0] = dm0;
+    const V2 me1 = fma2(dm0, fma2(2.f, X, bc(-4.f)), 3.f * m0uu);
+    const V2 me2 = fma2(dm0, fma2(-3.f, X, bc(4.f)), -3.f * m0uu);
     a[1] = fma2(p.h_e, fma2(6.f, uF, Ca), fma2(p.s_e, me1 - Cs.m[1], Cs.m[1]));
     a[2] = fma2(-p.h_eps * 6.f, uF, fma2(p.s_eps, me2 - Cs.m[2], Cs.m[2]));
     a[3] = Cs.m[3] + Fx;
@@ -353,11 +363,11 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     a[8] = fma2(p.h_nu, S8 + Cc, fma2(p.s_nu, fma2(jxe, uy, -Cs.m[8]), Cs.m[8]));
     // f+ = M^-1 m+ (A1). The 1/9, 1/36, 1/6 and 1/12 of M^-1 round in FP32, and
     // written directly they scale the cell's mass and momentum by the same rounding
-    // factor every step (a steady drift of ~7e-9 of the mass per step). Instead f_0
-    // and the diagonal-link x/y parts are taken as what the lattice's m_0 and j leave
-    // after the other populations: with s = bax + bdg formed first and bdg = s - bax
-    // (exact near rest, where bax / s ~ 0.8), f_0 = m_0 - 4 s and xd = (j_x - 2 xa) / 4
-    // equal (A1)'s rows and keep both sums exact up to unbiased rounding.
+    // factor every step. Instead f_0 and the diagonal-link x/y parts are taken as what
+    // m_0 and j leave after the other populations: with s = bax + bdg formed first and
+    // bdg = s - bax, f_0 = m_0 - 4 s and xd = (j_x - 2 xa) / 4 equal (A1)'s rows and
+    // keep both sums exact up to rounding at the scale of the deviations.
+    // f+ - f^rest = M^-1 (m+ - m^rest), all nine outputs deviations
     V2 fo[9];
     const V2 bax = (1.f / 36.f) * fma2(4.f, a[0], -fma2(2.f, a[2], a[1]));
     const V2 sbd = (1.f / 36.f) * fma2(8.f, a[0], a[1] - a[2]);
@@ -381,7 +391,8 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     fo[6] = t68 - smm;
     fo[8] = t68 + smm;
 
-    const V2 r0 = fma2(p.rest.rho0, phin, bc(-p.rest.k59));
+    // f_0's rest value follows phi to t+1 (it is stored against phi(t+1))
+    if (!FAST || Ctx::kUnsteady) fo[0] = fma2(p.rest.rho0, phi - phin, fo[0]);
     // one 2-wide store per population for every lane whose first column is inside
     // the lattice; the second column may then be the first ghost column, which the
     // ghost refresh after the step overwrites (the one-warp kernels leave all ghost
@@ -391,17 +402,14 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
             // the second column of the pair may lie past nx (its store lands in the
             // first ghost column, overwritten by the ghost refresh): count it only when inside
             const V2 in = V2{make_float2(1.f, c.xa + 1 < p.nx ? 1.f : 0.f)};
-            c.sums.add(0, a[0] * in);
+            c.sums.add(0, m0 * in);
             c.sums.add(1, a[3] * in);
             c.sums.add(2, a[5] * in);
         }
         S* cell = reinterpret_cast<S*>(p.dst) + (long long)p3 * p.P + kPadCols + c.xa;
-        IO::st(cell, sizeof(S) == 4 ? fo[0] : p.scale * (fo[0] - r0));
+        IO::st(cell, sizeof(S) == 4 ? fo[0] : p.scale * fo[0]);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const V2 ri = bc(i <= 4 ? p.rest.ax : p.rest.dg);
-            IO::st(cell + i * p.plane, sizeof(S) == 4 ? fo[i] : p.scale * (fo[i] - ri));
-        }
+        for (int i = 1; i < 9; ++i) IO::st(cell + i * p.plane, sizeof(S) == 4 ? fo[i] : p.scale * fo[i]);
     }
 }
 
