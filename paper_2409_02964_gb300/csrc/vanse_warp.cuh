@@ -236,8 +236,11 @@ __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
     st.m[7] = a13 - a24;
     st.m[8] = b57 - b68;
     // m[0..2] are the deviations of sum f, e and eps from the rest state's phi rho0,
-    // rho0 (2 kappa - 4 phi) and rho0 (4 phi - 3 kappa); rho holds rho - rho0
-    st.rho = st.m[0] * rcp2(phi);
+    // rho0 (2 kappa - 4 phi) and rho0 (4 phi - 3 kappa); rho holds rho - rho0. 1/phi
+    // and the full sum f are kept for phases 2 and 3 (cheaper than forming them there)
+    st.iphi = rcp2(phi);
+    st.rho = st.m[0] * st.iphi;
+    st.mf = fma2(p.rest.rho0, phi, st.m[0]);
 }
 
 template <typename S, bool FAST, typename Ctx>
@@ -256,7 +259,7 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
     V2 Fx = fma2(kp, gx, p.gx * phi);
     V2 Fy = fma2(kp, gy, p.gy * phi);
     c.template add_field_force<FAST>(p2, Bs, Fx, Fy);
-    const V2 m0 = fma2(p.rest.rho0, phi, Bs.m[0]);   // sum f = phi rho0 + its deviation
+    const V2 m0 = Bs.mf;
     V2 ux, uy;
     if (!FAST && p.has_drag) {
         // Eq. (7) with F^B += -beta (u - u_s): linear in u, solved exactly (never on the fast path)
@@ -327,7 +330,7 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     const V2 phi = c.phi2(p3, Cs);
     const V2 phin = c.template phin2<FAST>(p3, Cs);
     const V2 rho = Cs.rho + p.rest.rho0;
-    const V2 X = p.kappa * rcp2(phi);
+    const V2 X = p.kappa * Cs.iphi;
     const V2 kp = p.model_b ? bc(p.kappa - 1.f) : bc(p.kappa) - phi;
     const V2 kr = kp * rho;
     const V2 divD = xDx + yDy, difD = xDx - yDy;
@@ -340,7 +343,7 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     // m_0, e and eps; the equilibria of e and eps then differ from them by
     // dm0 (2X - 4) + 3 m0 |u|^2 and dm0 (4 - 3X) - 3 m0 |u|^2 (rho - rho0 = dm0 / phi)
     const V2 dm0 = Cs.m[0], ux = Cs.ux, uy = Cs.uy, Fx = Cs.Fx, Fy = Cs.Fy;
-    const V2 m0 = fma2(p.rest.rho0, phi, dm0);
+    const V2 m0 = Cs.mf;
     const V2 uu = fma2(ux, ux, uy * uy);
     const V2 uF = fma2(ux, Fx, uy * Fy);
     const V2 jxe = m0 * ux, jye = m0 * uy;
