@@ -99,7 +99,7 @@ struct PRow {
     float sy, cy;   // sin, cos of k y of this row (analytic sources only)
     V2 m[9];
     V2 rho;
-    V2 iphi, mf;    // one-warp kernel: 1/phi and the full sum f, kept from phase 1
+    V2 iphi, mf, rf;   // one-warp kernel: 1/phi, the full sum f and the full rho, kept from phase 1
     V2 dr, wr;
     V2 Fx, Fy, ux, uy;
     V2 dAx, dBx, dBy, dDx;

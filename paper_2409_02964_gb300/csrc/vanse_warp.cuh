@@ -236,11 +236,13 @@ __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
     st.m[7] = a13 - a24;
     st.m[8] = b57 - b68;
     // m[0..2] are the deviations of sum f, e and eps from the rest state's phi rho0,
-    // rho0 (2 kappa - 4 phi) and rho0 (4 phi - 3 kappa); rho holds rho - rho0. 1/phi
-    // and the full sum f are kept for phases 2 and 3 (cheaper than forming them there)
+    // rho0 (2 kappa - 4 phi) and rho0 (4 phi - 3 kappa); rho holds rho - rho0. 1/phi,
+    // the full sum f and the full rho are kept for phases 2 and 3 (cheaper than
+    // forming them there)
     st.iphi = rcp2(phi);
     st.rho = st.m[0] * st.iphi;
     st.mf = fma2(p.rest.rho0, phi, st.m[0]);
+    st.rf = st.rho + p.rest.rho0;
 }
 
 template <typename S, bool FAST, typename Ctx>
@@ -276,7 +278,7 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
     }
     Bs.Fx = Fx; Bs.Fy = Fy; Bs.ux = ux; Bs.uy = uy;
     // the Eq. (10) x-differences / smoothed sums of rho u, u, phi rho u on row p2
-    const V2 rho = Bs.rho + p.rest.rho0;
+    const V2 rho = Bs.rf;
     const V2 Ax = rho * ux, Ay = rho * uy, Dx = m0 * ux, Dy = m0 * uy;
     const float Axl = left_of(Ax), Axr = right_of(Ax);
     const float Ayl = left_of(Ay), Ayr = right_of(Ay);
@@ -329,7 +331,7 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     }
     const V2 phi = c.phi2(p3, Cs);
     const V2 phin = c.template phin2<FAST>(p3, Cs);
-    const V2 rho = Cs.rho + p.rest.rho0;
+    const V2 rho = Cs.rf;
     const V2 X = p.kappa * Cs.iphi;
     const V2 kp = p.model_b ? bc(p.kappa - 1.f) : bc(p.kappa) - phi;
     const V2 kr = kp * rho;
@@ -348,11 +350,11 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     const V2 uF = fma2(ux, Fx, uy * Fy);
     const V2 jxe = m0 * ux, jye = m0 * uy;
     const V2 q = X - bc(2.f);
-    const V2 m0uu = m0 * uu;
+    const V2 m0uu3 = m0 * (3.f * uu);
     V2 a[9];
     a[0] = dm0;
-    const V2 me1 = fma2(dm0, fma2(2.f, X, bc(-4.f)), 3.f * m0uu);
-    const V2 me2 = fma2(dm0, fma2(-3.f, X, bc(4.f)), -3.f * m0uu);
+    const V2 me1 = fma2(dm0, fma2(2.f, X, bc(-4.f)), m0uu3);
+    const V2 me2 = fma2(dm0, fma2(-3.f, X, bc(4.f)), -m0uu3);
     a[1] = fma2(p.h_e, fma2(6.f, uF, Ca), fma2(p.s_e, me1 - Cs.m[1], Cs.m[1]));
     a[2] = fma2(-p.h_eps * 6.f, uF, fma2(p.s_eps, me2 - Cs.m[2], Cs.m[2]));
     a[3] = Cs.m[3] + Fx;
