@@ -312,6 +312,12 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
     p.h_eps = (R)(1.0 - 0.5 * h->prm.s_eps);
     p.h_q = (R)(1.0 - 0.5 * h->prm.s_q);
     p.h_nu = (R)(1.0 - 0.5 * h->s_nu);
+    p.hs_e = (R)((1.0 - 0.5 * h->s_e) * h->scale);
+    p.hs_eps = (R)((1.0 - 0.5 * h->prm.s_eps) * h->scale);
+    p.hs_q = (R)((1.0 - 0.5 * h->prm.s_q) * h->scale);
+    p.hs_nu = (R)((1.0 - 0.5 * h->s_nu) * h->scale);
+    p.rho0s = (R)(h->prm.rho0 * h->scale);
+    p.kp3 = (R)(h->inv_scale / 3.0);
     p.scale = (R)h->scale;
     p.inv_scale = (R)h->inv_scale;
     p.rest = make_rest<R>(h);

@@ -184,6 +184,10 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         p.h_e = Lt.h_e; p.h_eps = Lt.h_eps; p.h_q = Lt.h_q; p.h_nu = Lt.h_nu;
         p.scale = bp.scale;
         p.inv_scale = bp.inv_scale;
+        p.hs_e = Lt.h_e * bp.scale; p.hs_eps = Lt.h_eps * bp.scale;
+        p.hs_q = Lt.h_q * bp.scale; p.hs_nu = Lt.h_nu * bp.scale;
+        p.rho0s = Lt.rho0 * bp.scale;
+        p.kp3 = bp.inv_scale * (1.f / 3.f);
         p.rest.ax = Lt.kappa * Lt.rho0 * (1.f / 9.f);
         p.rest.dg = Lt.kappa * Lt.rho0 * (1.f / 36.f);
         p.rest.k59 = Lt.kappa * Lt.rho0 * (5.f / 9.f);
@@ -470,6 +474,10 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     p.h_e = Lt.h_e; p.h_eps = Lt.h_eps; p.h_q = Lt.h_q; p.h_nu = Lt.h_nu;
     p.scale = bp.scale;
     p.inv_scale = bp.inv_scale;
+    p.hs_e = Lt.h_e * bp.scale; p.hs_eps = Lt.h_eps * bp.scale;
+    p.hs_q = Lt.h_q * bp.scale; p.hs_nu = Lt.h_nu * bp.scale;
+    p.rho0s = Lt.rho0 * bp.scale;
+    p.kp3 = bp.inv_scale * (1.f / 3.f);
     p.rest.ax = Lt.kappa * Lt.rho0 * (1.f / 9.f);
     p.rest.dg = Lt.kappa * Lt.rho0 * (1.f / 36.f);
     p.rest.k59 = Lt.kappa * Lt.rho0 * (5.f / 9.f);

@@ -61,7 +61,7 @@ template <> struct PairIO<__half> {
     __device__ static V2 al(const __half* p) { return V2{__half22float2(*reinterpret_cast<const __half2*>(p))}; }
     __device__ static V2 un(const __half* p) { return V2{__half22float2(__halves2half2(p[0], p[1]))}; }
     __device__ static V2 dec(V2 d, V2 rest, float ia) { return fma2(ia, d, rest); }
-    __device__ static V2 dev(V2 d, float ia) { return ia * d; }
+    __device__ static V2 dev(V2 d, float) { return d; }   // the storage's scaled units
     __device__ static void st(__half* p, V2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
     __device__ static __half enc1(float f, float rest, float s) { return __float2half_rn((f - rest) * s); }
 };
@@ -71,7 +71,7 @@ template <> struct PairIO<__nv_bfloat16> {
     }
     __device__ static V2 un(const __nv_bfloat16* p) { return V2{__bfloat1622float2(__halves2bfloat162(p[0], p[1]))}; }
     __device__ static V2 dec(V2 d, V2 rest, float ia) { return fma2(ia, d, rest); }
-    __device__ static V2 dev(V2 d, float ia) { return ia * d; }
+    __device__ static V2 dev(V2 d, float) { return d; }   // the storage's scaled units
     __device__ static void st(__nv_bfloat16* p, V2 v) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
     }

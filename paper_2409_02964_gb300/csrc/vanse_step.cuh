@@ -84,6 +84,9 @@ struct StepParams {
     int nee_top;          // row ny-1 is a moving wall by non-equilibrium extrapolation (kernel 1 only)
     R uw_x, uw_y;         // its velocity
     int has_solid;        // cells with phi = 0 are solid (the SOLID variants of kernel 1; see solid_grad12)
+    // the one-warp kernel collides FP16/BF16 deviations in the storage's scaled units:
+    // h_* x scale, rho0 x scale and inv_scale / 3 (equal to h_*, rho0, 1/3 at scale 1)
+    R hs_e, hs_eps, hs_q, hs_nu, rho0s, kp3;
 };
 
 // Compensated (Kahan) sums of the post-collision m_0, j_x, j_y of the cells one

@@ -193,9 +193,11 @@ __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
     c.row_setup(r, st);
     const V2 phi = c.phi2(r, st);
     const float ia = p.inv_scale;
-    // the stored values are deviations from the rest state of Eq. (14) (times the
-    // storage scale); this kernel keeps them as deviations: f0..f8 below are
-    // f_i - f_i^rest, and the rest state's moments are added back analytically
+    // the stored values are deviations from the rest state of Eq. (14) times the
+    // storage scale (1 for FP32, a power of two for FP16/BF16); this kernel keeps them
+    // as they are: f0..f8 below are scale x (f_i - f_i^rest), the rest state's moments
+    // are added back analytically, and the collision runs in these scaled units (the
+    // scale is a power of two, so this changes no rounding)
     const S* cur = c.pop(r);
     V2 f0, f1, f2, f3, f4, f5, f6, f7, f8;
     f0 = IO::dev(IO::al(cur), ia);
@@ -240,9 +242,14 @@ __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
     // the full sum f and the full rho are kept for phases 2 and 3 (cheaper than
     // forming them there)
     st.iphi = rcp2(phi);
-    st.rho = st.m[0] * st.iphi;
-    st.mf = fma2(p.rest.rho0, phi, st.m[0]);
-    st.rf = st.rho + p.rest.rho0;
+    st.rho = st.m[0] * st.iphi;   // scale x (rho - rho0)
+    if constexpr (sizeof(S) == 4) {
+        st.mf = fma2(p.rest.rho0, phi, st.m[0]);
+        st.rf = st.rho + p.rest.rho0;
+    } else {
+        st.mf = fma2(p.rest.rho0, phi, ia * st.m[0]);
+        st.rf = fma2(ia, st.rho, bc(p.rest.rho0));
+    }
 }
 
 template <typename S, bool FAST, typename Ctx>
@@ -257,24 +264,28 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
     const V2 gx = tw * fma2(4.f, Bs.dr, dlo + dhi);
     const V2 gy = tw * (whi - wlo);
     const V2 phi = c.phi2(p2, Bs);
-    const V2 kp = p.model_b ? bc((p.kappa - 1.f) * (1.f / 3.f)) : (1.f / 3.f) * (bc(p.kappa) - phi);
+    // (kappa - phi) / 3 times 1/scale: the rho differences are in scaled units
+    const float k3 = sizeof(S) == 4 ? 1.f / 3.f : p.kp3;
+    const V2 kp = p.model_b ? bc((p.kappa - 1.f) * k3) : k3 * (bc(p.kappa) - phi);
     V2 Fx = fma2(kp, gx, p.gx * phi);
     V2 Fy = fma2(kp, gy, p.gy * phi);
     c.template add_field_force<FAST>(p2, Bs, Fx, Fy);
     const V2 m0 = Bs.mf;
+    const V2 jx = sizeof(S) == 4 ? Bs.m[3] : p.inv_scale * Bs.m[3];
+    const V2 jy = sizeof(S) == 4 ? Bs.m[5] : p.inv_scale * Bs.m[5];
     V2 ux, uy;
     if (!FAST && p.has_drag) {
         // Eq. (7) with F^B += -beta (u - u_s): linear in u, solved exactly (never on the fast path)
         const V2 beta = (phi * phi) * fma2(-p.drag_d1, phi, bc(p.drag_d0 + p.drag_d1));
         const V2 inv = rcp2(fma2(0.5f, beta, m0));
-        ux = fma2(0.5f, fma2(p.us_x, beta, Fx), Bs.m[3]) * inv;
-        uy = fma2(0.5f, fma2(p.us_y, beta, Fy), Bs.m[5]) * inv;
+        ux = fma2(0.5f, fma2(p.us_x, beta, Fx), jx) * inv;
+        uy = fma2(0.5f, fma2(p.us_y, beta, Fy), jy) * inv;
         Fx = Fx - beta * (ux + (-p.us_x));
         Fy = Fy - beta * (uy + (-p.us_y));
     } else {
         const V2 inv = rcp2(m0);
-        ux = fma2(0.5f, Fx, Bs.m[3]) * inv;
-        uy = fma2(0.5f, Fy, Bs.m[5]) * inv;
+        ux = fma2(0.5f, Fx, jx) * inv;
+        uy = fma2(0.5f, Fy, jy) * inv;
     }
     Bs.Fx = Fx; Bs.Fy = Fy; Bs.ux = ux; Bs.uy = uy;
     // the Eq. (10) x-differences / smoothed sums of rho u, u, phi rho u on row p2
@@ -348,24 +359,29 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     const V2 m0 = Cs.mf;
     const V2 uu = fma2(ux, ux, uy * uy);
     const V2 uF = fma2(ux, Fx, uy * Fy);
-    const V2 jxe = m0 * ux, jye = m0 * uy;
+    // equilibrium and source terms in the storage's scaled units
+    const V2 m0s = sizeof(S) == 4 ? m0 : p.scale * m0;
+    const V2 jxe = m0s * ux, jye = m0s * uy;
     const V2 q = X - bc(2.f);
-    const V2 m0uu3 = m0 * (3.f * uu);
+    const V2 m0uu3 = m0s * (3.f * uu);
     V2 a[9];
     a[0] = dm0;
     const V2 me1 = fma2(dm0, fma2(2.f, X, bc(-4.f)), m0uu3);
     const V2 me2 = fma2(dm0, fma2(-3.f, X, bc(4.f)), -m0uu3);
-    a[1] = fma2(p.h_e, fma2(6.f, uF, Ca), fma2(p.s_e, me1 - Cs.m[1], Cs.m[1]));
-    a[2] = fma2(-p.h_eps * 6.f, uF, fma2(p.s_eps, me2 - Cs.m[2], Cs.m[2]));
-    a[3] = Cs.m[3] + Fx;
-    a[4] = fma2(-p.h_q, Fx, fma2(p.s_q, fma2(q, jxe, -Cs.m[4]), Cs.m[4]));
-    a[5] = Cs.m[5] + Fy;
-    a[6] = fma2(-p.h_q, Fy, fma2(p.s_q, fma2(q, jye, -Cs.m[6]), Cs.m[6]));
-    const V2 me7 = m0 * fma2(ux, ux, -(uy * uy));
+    constexpr bool kUnit = sizeof(S) == 4;   // FP32: scale 1, the plain coefficients
+    const float hs_e = kUnit ? p.h_e : p.hs_e, hs_eps = kUnit ? p.h_eps : p.hs_eps;
+    const float hs_q = kUnit ? p.h_q : p.hs_q, hs_nu = kUnit ? p.h_nu : p.hs_nu;
+    a[1] = fma2(hs_e, fma2(6.f, uF, Ca), fma2(p.s_e, me1 - Cs.m[1], Cs.m[1]));
+    a[2] = fma2(-hs_eps * 6.f, uF, fma2(p.s_eps, me2 - Cs.m[2], Cs.m[2]));
+    a[3] = sizeof(S) == 4 ? Cs.m[3] + Fx : fma2(p.scale, Fx, Cs.m[3]);
+    a[4] = fma2(-hs_q, Fx, fma2(p.s_q, fma2(q, jxe, -Cs.m[4]), Cs.m[4]));
+    a[5] = sizeof(S) == 4 ? Cs.m[5] + Fy : fma2(p.scale, Fy, Cs.m[5]);
+    a[6] = fma2(-hs_q, Fy, fma2(p.s_q, fma2(q, jye, -Cs.m[6]), Cs.m[6]));
+    const V2 me7 = m0s * fma2(ux, ux, -(uy * uy));
     const V2 S7 = 2.f * fma2(ux, Fx, -(uy * Fy));
-    a[7] = fma2(p.h_nu, S7 + Cb, fma2(p.s_nu, me7 - Cs.m[7], Cs.m[7]));
+    a[7] = fma2(hs_nu, S7 + Cb, fma2(p.s_nu, me7 - Cs.m[7], Cs.m[7]));
     const V2 S8 = fma2(ux, Fy, uy * Fx);
-    a[8] = fma2(p.h_nu, S8 + Cc, fma2(p.s_nu, fma2(jxe, uy, -Cs.m[8]), Cs.m[8]));
+    a[8] = fma2(hs_nu, S8 + Cc, fma2(p.s_nu, fma2(jxe, uy, -Cs.m[8]), Cs.m[8]));
     // f+ = M^-1 m+ (A1). The 1/9, 1/36, 1/6 and 1/12 of M^-1 round in FP32, and
     // written directly they scale the cell's mass and momentum by the same rounding
     // factor every step. Instead f_0 and the diagonal-link x/y parts are taken as what
@@ -397,7 +413,7 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     fo[8] = t68 + smm;
 
     // f_0's rest value follows phi to t+1 (it is stored against phi(t+1))
-    if (!FAST || Ctx::kUnsteady) fo[0] = fma2(p.rest.rho0, phi - phin, fo[0]);
+    if (!FAST || Ctx::kUnsteady) fo[0] = fma2(sizeof(S) == 4 ? p.rest.rho0 : p.rho0s, phi - phin, fo[0]);
     // one 2-wide store per population for every lane whose first column is inside
     // the lattice; the second column may then be the first ghost column, which the
     // ghost refresh after the step overwrites (the one-warp kernels leave all ghost
@@ -408,13 +424,14 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
             // first ghost column, overwritten by the ghost refresh): count it only when inside
             const V2 in = V2{make_float2(1.f, c.xa + 1 < p.nx ? 1.f : 0.f)};
             c.sums.add(0, m0 * in);
-            c.sums.add(1, a[3] * in);
-            c.sums.add(2, a[5] * in);
+            const V2 ins = sizeof(S) == 4 ? in : p.inv_scale * in;
+            c.sums.add(1, a[3] * ins);
+            c.sums.add(2, a[5] * ins);
         }
         S* cell = reinterpret_cast<S*>(p.dst) + (long long)p3 * p.P + kPadCols + c.xa;
-        IO::st(cell, sizeof(S) == 4 ? fo[0] : p.scale * fo[0]);
+        IO::st(cell, fo[0]);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) IO::st(cell + i * p.plane, sizeof(S) == 4 ? fo[i] : p.scale * fo[i]);
+        for (int i = 1; i < 9; ++i) IO::st(cell + i * p.plane, fo[i]);
     }
 }
 
