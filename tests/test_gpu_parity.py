@@ -498,3 +498,24 @@ def test_invalid_arguments_are_reported(P):
         lat.init_fields(np.ones((8, 8)), np.zeros((8, 8)), np.zeros((8, 8)))
     assert e.value.status == P.capi.LBM_ERR_STATE
     lat.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_step_sums_full_size_channel(P, storage):
+    """lbm_vanse_step_sums on the 4096 x 4096 channel in the benchmark's launch
+    configuration: the step's mass equals the mass reduce() sees before it (both FP64
+    sums of the same populations, per-cell sums in FP32) and the momentum is finite
+    and points along the forcing."""
+    import torch
+    nx = ny = 4096
+    case = channel_case(nx, ny)
+    lat = _gpu_lattice(P, nx, ny, 0.6, True, storage, case, **CHANNEL_RATES)
+    lat.step(20)
+    m_before, _, _ = lat.reduce()
+    out = torch.full((3,), float("nan"), dtype=torch.float64).pin_memory()
+    lat.step_sums(out)
+    lat.sync()
+    got = out.numpy()
+    lat.close()
+    assert abs(got[0] - m_before) <= 1e-8 * m_before, (got, m_before)
+    assert np.isfinite(got).all() and got[1] > 0

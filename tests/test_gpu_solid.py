@@ -174,3 +174,44 @@ def test_solid_cell_errors(P):
     with pytest.raises(P.LbmError):
         lat.sync()
     lat.close()
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_large_lattice_with_solids_and_moving_wall_matches_oracle(P, oracle_mod, storage):
+    """A 192 x 160 walled lattice (strips much taller than the 8-row staging ring)
+    with a solid block, scattered solid cells and the moving top wall, moving phi and
+    a force field, 12 steps against the oracle."""
+    O = oracle_mod
+    nx, ny, steps, uw = 192, 160, 12, (1e-3, 0.0)
+    case = random_case(nx, ny, seed=77, wall_y=True, unsteady=True, field=True, g=(1e-5, 0.0))
+    solid = _solids(nx, ny, 5, False)
+    solid[ny - 3:, :] = False                          # keep the rows next to the moving wall fluid
+    phi = np.where(solid, 0.0, case["phi"])
+    phin = np.where(solid, 0.0, case["phin"])
+    case = dict(case, phi=phi, phin=phin)
+    lat = P.Lattice(nx, ny, 0.8, s_eps=1.2, s_q=1.4, bc_y="bounceback", storage=storage, kernel=1)
+    lat.set_solid_cells()
+    lat.set_moving_wall(*uw)
+    lat.set_void_fraction(case["phi"], case["phin"])
+    lat.set_body_force(case["g"][0], case["g"][1], case["fb"])
+    lat.init_fields(case["rho"], case["ux"], case["uy"])
+    shape = lat.launch_shape()
+    assert shape["rows"] > 8
+    prm = O.Params(nx=nx, ny=ny, **O.rates_from_tau(0.8, s_eps=1.2, s_q=1.4), kappa=0.5, bc_y=1, nee_top=1,
+                   uw_x=uw[0], uw_y=uw[1], nthreads=0)
+    fb = total_force(case)
+    f = O.init(prm, case["rho"], case["ux"], case["uy"], case["phi"], fb)
+    for k in range(steps):
+        pn = case["phin"] if k == 0 else None
+        if k == 1:
+            case = dict(case, phi=case["phin"], phin=None)
+            fb = total_force(case)
+        f = O.step(prm, f, case["phi"], pn, fb)
+    lat.step(steps)
+    fg = lat.get_populations().cpu().numpy()
+    lat.close()
+    if storage == "fp64":
+        scale = np.abs(f - rest_populations(case["phi"]))[:, ~solid].max()
+        assert np.abs(fg - f).max() / scale <= 1e-12
+    else:
+        assert np.abs(fg - f).max() <= steps * 32 * EPS32 * np.abs(f).max()
