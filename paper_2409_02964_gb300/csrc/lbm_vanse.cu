@@ -250,8 +250,7 @@ const void* step_sums_kernel_ptr(const lbm_vanse* h) {
         if (h->kernel == 5) return (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB, true>;
         if (h->kernel != 1) return nullptr;
     }
-    return h->has_solid ? (const void*)vanse_step_kernel<S, R, kThreads, true, true>
-                        : (const void*)vanse_step_kernel<S, R, kThreads, true>;
+    return (const void*)vanse_step_kernel<S, R, kThreads, true>;   // (solid cells: launch_solid_step)
 }
 
 // Kernel 1 with solid cells: a variant of its own (the neighbour-by-neighbour stencil
@@ -261,8 +260,6 @@ template <typename S>
 lbm_status launch_solid_step(lbm_vanse* h, const StepParams<typename Prec<S>::R>& p, dim3 grid, size_t smem,
                              cudaStream_t stream, bool sums) {
     using R = typename Prec<S>::R;
-    const void* kern = sums ? (const void*)vanse_step_kernel<S, R, kThreads, true, true>
-                            : (const void*)vanse_step_kernel<S, R, kThreads, false, true>;
     if (!h->solid_configured) {
         for (const void* k : {(const void*)vanse_step_kernel<S, R, kThreads, true, true>,
                               (const void*)vanse_step_kernel<S, R, kThreads, false, true>}) {
@@ -272,7 +269,6 @@ lbm_status launch_solid_step(lbm_vanse* h, const StepParams<typename Prec<S>::R>
         }
         h->solid_configured = true;
     }
-    (void)kern;
     if (sums) vanse_step_kernel<S, R, kThreads, true, true><<<grid, kThreads, smem, stream>>>(p);
     else vanse_step_kernel<S, R, kThreads, false, true><<<grid, kThreads, smem, stream>>>(p);
     CK(h, cudaGetLastError());
