@@ -74,6 +74,7 @@ struct lbm_vanse {
     double uw_x = 0, uw_y = 0;
     bool has_solid = false;       // phi = 0 marks solid cells (kernel 1)
     int* zero_phi = nullptr;      // device flag: the last phi upload held a zero
+    unsigned* step_ctr = nullptr; // device step count of the one-warp kernel (seeds stochastic rounding)
     double s_nu = 0, s_e = 0;
     double scale = 1, inv_scale = 1;
     int* err = nullptr;           // device flag set by bounded waits
@@ -329,6 +330,7 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
     p.uw_x = (R)h->uw_x;
     p.uw_y = (R)h->uw_y;
     p.has_solid = h->has_solid;
+    p.step_ctr = h->step_ctr;
     dim3 grid(h->gridx, h->gridy);
     if (h->has_solid) return launch_solid_step<S>(h, p, grid, smem, stream, sums != nullptr);
     if (sums) {
@@ -347,7 +349,7 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
                 CK(h, cudaGetLastError());
                 const long long ng = 9LL * h->prm.ny * 2 * kGhost;
                 ghost_fill_kernel<S><<<(int)std::min<long long>((ng + 255) / 256, 4096), 256, 0, stream>>>(
-                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P);
+                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P, h->step_ctr);
                 CK(h, cudaGetLastError());
                 return LBM_OK;
             }
@@ -367,7 +369,7 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
                 // the one-warp kernel writes columns 0 .. nx-1 only
                 const long long ng = 9LL * h->prm.ny * 2 * kGhost;
                 ghost_fill_kernel<S><<<(int)std::min<long long>((ng + 255) / 256, 4096), 256, 0, stream>>>(
-                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P);
+                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P, h->step_ctr);
                 CK(h, cudaGetLastError());
                 return LBM_OK;
             }
@@ -759,6 +761,7 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
     const size_t fldb = (size_t)h->plane * h->rbytes;
     bool ok = alloc(&h->f[0], popb) && alloc(&h->f[1], popb) && alloc(&h->phi, fldb) && alloc(&h->phin, fldb) &&
               alloc((void**)&h->err, sizeof(int)) && alloc((void**)&h->zero_phi, sizeof(int)) &&
+              alloc((void**)&h->step_ctr, sizeof(unsigned)) &&
               alloc((void**)&h->partial, kReduceBlocks * 3 * sizeof(double)) &&
               alloc((void**)&h->red_out, 4 * sizeof(double));
     if (ok) st = DISPATCH(h, configure);
@@ -1086,7 +1089,7 @@ extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
         cudaEventDestroy(h->staging_free);
     }
     void* ptrs[] = {h->f[0], h->f[1], h->phi, h->phin, h->fb, h->err, h->partial, h->red_out, h->scratch,
-                    h->staging[0], h->staging[1], h->zero_phi};
+                    h->staging[0], h->staging[1], h->zero_phi, h->step_ctr};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete h;

@@ -59,11 +59,15 @@ __device__ __forceinline__ void fill_ghosts(S* __restrict__ buf, long long plane
     row[g] = row[sx];
 }
 
+// step_ctr (optional): the one-warp kernel's step count, advanced here once per step
+// (it seeds the stochastic rounding of FP16/BF16 stores).
 template <typename S>
-__global__ void ghost_fill_kernel(S* __restrict__ buf, long long plane, int nx, int ny, int P) {
+__global__ void ghost_fill_kernel(S* __restrict__ buf, long long plane, int nx, int ny, int P,
+                                  unsigned* __restrict__ step_ctr = nullptr) {
     const long long n = 9LL * ny * 2 * kGhost;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
         fill_ghosts<S>(buf, plane, nx, ny, P, k);
+    if (step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1u;
 }
 
 // Copy a dense [ny][nx] field (double or float) into a padded R field (with

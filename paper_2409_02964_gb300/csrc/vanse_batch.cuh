@@ -77,6 +77,7 @@ struct BatchCtx {
     uint32_t phase;            // parity of the next completion of each ring slot
     RowCopy cp;
     bool st_pair;              // this lane stores its pair (lanes 1..30, first column inside)
+    uint32_t step = 0, salt = 0;   // seed of the stochastic rounding of FP16/BF16 stores
     // manufactured solution at this step
     V2 sx2, cx2;               // sin, cos of k x of the lane's two columns
     float k, w, A, U0, phi0, nu, rho0;
@@ -161,6 +162,8 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         BatchCtx<S> c;
         c.smem = smem;
         c.lane = lane;
+        c.step = (uint32_t)t;
+        c.salt = (uint32_t)bp.unit_lattice[u] * 0x27d4eb2fu;
         c.aborted = false;
         c.phase = phase;
         StepParams<float>& p = c.p;
@@ -451,6 +454,8 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     BatchCtx<S> c;
     c.smem = smem;
     c.lane = lane;
+    c.step = (uint32_t)t;
+    c.salt = (uint32_t)index * 0x27d4eb2fu;
     c.aborted = false;
     c.phase = 0;
     StepParams<float>& p = c.p;

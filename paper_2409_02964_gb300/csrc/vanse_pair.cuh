@@ -63,6 +63,12 @@ template <> struct PairIO<__half> {
     __device__ static V2 dec(V2 d, V2 rest, float ia) { return fma2(ia, d, rest); }
     __device__ static V2 dev(V2 d, float) { return d; }   // the storage's scaled units
     __device__ static void st(__half* p, V2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v.v); }
+    // stochastic rounding (the conversion's .rs mode) with 32 random bits r
+    __device__ static void st_sr(__half* p, V2 v, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x), "r"(r));
+        *reinterpret_cast<uint32_t*>(p) = d;
+    }
     __device__ static __half enc1(float f, float rest, float s) { return __float2half_rn((f - rest) * s); }
 };
 template <> struct PairIO<__nv_bfloat16> {
@@ -74,6 +80,11 @@ template <> struct PairIO<__nv_bfloat16> {
     __device__ static V2 dev(V2 d, float) { return d; }   // the storage's scaled units
     __device__ static void st(__nv_bfloat16* p, V2 v) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v.v);
+    }
+    __device__ static void st_sr(__nv_bfloat16* p, V2 v, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.v.y), "f"(v.v.x), "r"(r));
+        *reinterpret_cast<uint32_t*>(p) = d;
     }
     __device__ static __nv_bfloat16 enc1(float f, float rest, float s) { return __float2bfloat16_rn((f - rest) * s); }
 };

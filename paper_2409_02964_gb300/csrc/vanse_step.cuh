@@ -87,6 +87,7 @@ struct StepParams {
     // the one-warp kernel collides FP16/BF16 deviations in the storage's scaled units:
     // h_* x scale, rho0 x scale and inv_scale / 3 (equal to h_*, rho0, 1/3 at scale 1)
     R hs_e, hs_eps, hs_q, hs_nu, rho0s, kp3;
+    const unsigned* step_ctr;   // one-warp kernel: steps taken (seeds the stochastic rounding), or nullptr
 };
 
 // Compensated (Kahan) sums of the post-collision m_0, j_x, j_y of the cells one

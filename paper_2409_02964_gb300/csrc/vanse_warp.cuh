@@ -107,6 +107,7 @@ struct WarpCtx {
     RowCopy cp;
     bool st_pair;              // this lane stores its pair (lanes 1..30, first column inside)
     mutable PairSums sums;     // used when kSums
+    uint32_t step = 0, salt = 0;   // seed of the stochastic rounding of FP16/BF16 stores
 
     __device__ __forceinline__ uint64_t* bar(int r) const { return reinterpret_cast<uint64_t*>(smem) + wslot(r); }
     __device__ __forceinline__ const S* pop(int r) const {
@@ -179,6 +180,16 @@ struct WarpCtx {
         }
     }
 };
+
+// 32-bit integer mixer (xor-shift / multiply rounds); seeds the stochastic rounding
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
 
 // neighbour values across lanes: the left neighbour of xa is lane-1's xb, the right
 // neighbour of xb is lane+1's xa
@@ -429,9 +440,23 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
             c.sums.add(2, a[5] * ins);
         }
         S* cell = reinterpret_cast<S*>(p.dst) + (long long)p3 * p.P + kPadCols + c.xa;
-        IO::st(cell, fo[0]);
+        if constexpr (sizeof(S) == 4) {
+            IO::st(cell, fo[0]);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) IO::st(cell + i * p.plane, fo[i]);
+            for (int i = 1; i < 9; ++i) IO::st(cell + i * p.plane, fo[i]);
+        } else {
+            // FP16/BF16: stochastic rounding. Round-to-nearest loses every increment
+            // below half a unit of the stored deviation (a slowly forced flow then
+            // stalls); rounding up with probability equal to the discarded fraction
+            // keeps each stored value unbiased. One hashed 32-bit word per column pair
+            // (its column, row and step); population i takes it times an odd constant,
+            // a bijection of 32-bit words, so every population's bits are uniform too.
+            const uint32_t h0 = mix32(((uint32_t)c.xa * 0x9E3779B1u) ^ ((uint32_t)p3 * 0x85EBCA77u) ^
+                                      ((c.step ^ c.salt) * 0xC2B2AE3Du));
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                IO::st_sr(cell + i * p.plane, fo[i], h0 * (0x2545F491u + 0x9E3779B8u * (uint32_t)i));
+        }
     }
 }
 
@@ -518,6 +543,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     const int y1 = min(y0 + p.H, p.ny);
 
     WarpCtx<S, SUMS> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
+    if constexpr (sizeof(S) == 2) c.step = p.step_ctr ? *p.step_ctr : 0u;
     c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
     c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
     c.xa = x0 - 2 + 2 * lane;

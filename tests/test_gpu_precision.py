@@ -5,7 +5,7 @@ with FP64, FP32, FP16 and BF16 population storage. Each run's velocity error E_u
 (Eq. 26) against the manufactured velocity is compared with the FP64 run's, which
 is the scheme's discretisation error: FP32 and FP16 storage must stay within 1.5x
 of it. BF16 (8 significant bits) is reported; its bound is checked separately
-with the looser factor its rounding allows.
+with the looser factor its rounding allows (3x).
 """
 import numpy as np
 import pytest
@@ -78,9 +78,11 @@ def test_reduced_storage_within_1p5x_of_fp64(errors, storage):
 
 
 def test_bf16_error_reported(errors):
-    # BF16 keeps 8 significant bits of the deviation from rest: recorded, bounded loosely
+    # BF16 keeps 8 significant bits of the deviation from rest; with stochastic
+    # rounding of its stores the error is twice the discretisation error (measured
+    # 3.4e-3 against 1.76e-3; 5.9e-3 with round-to-nearest)
     assert np.isfinite(errors["bf16"][0])
-    assert errors["bf16"][0] <= 10 * errors["fp64"][0]
+    assert errors["bf16"][0] <= 3 * errors["fp64"][0]
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
