@@ -1,0 +1,222 @@
+"""Pins of the 3-D (D3Q19) oracle against what the lattice, the paper's construction
+and the mathematics fix: isotropy of the lattice, the moment basis, the velocity
+moments the equilibrium is built to have (the Eq. (15) pattern), Guo forcing,
+reduction to a textbook D3Q19 BGK when phi = kappa, the rest state, mass and
+momentum balance, exact Poiseuille flow at the "magic" rates, and second-order
+convergence on a 3-D manufactured solution (which fails without the penalty
+source)."""
+import numpy as np
+import pytest
+
+from oracle import d3q19 as D
+from synth.mms3 import Config3
+
+E_REF = np.array([(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+                  (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1),
+                  (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)])
+
+
+def test_lattice_is_d3q19_and_isotropic_to_fourth_order():
+    e, w = D.lattice()
+    assert np.array_equal(e, E_REF)
+    c2 = (e ** 2).sum(1)
+    assert np.allclose(w, np.where(c2 == 0, 1 / 3, np.where(c2 == 1, 1 / 18, 1 / 36)), rtol=0, atol=1e-16)
+    d = np.eye(3)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.abs(np.einsum("i,ia->a", w, e)).max() < 1e-16
+    assert np.abs(np.einsum("i,ia,ib->ab", w, e, e) - d / 3).max() < 1e-15
+    four = np.einsum("i,ia,ib,ic,id->abcd", w, e, e, e, e)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)) / 9
+    assert np.abs(four - iso).max() < 1e-15
+
+
+def _basis_rows():
+    x, y, z = E_REF.T.astype(float)
+    c2 = x * x + y * y + z * z
+    return np.array([np.ones(19), 19 * c2 - 30, (21 * c2 ** 2 - 53 * c2 + 24) / 2,
+                     x, (5 * c2 - 9) * x, y, (5 * c2 - 9) * y, z, (5 * c2 - 9) * z,
+                     3 * x * x - c2, (3 * c2 - 5) * (3 * x * x - c2), y * y - z * z,
+                     (3 * c2 - 5) * (y * y - z * z), x * y, y * z, x * z,
+                     (y * y - z * z) * x, (z * z - x * x) * y, (x * x - y * y) * z])
+
+
+def test_moment_basis_and_inverse():
+    M = D.M()
+    assert np.array_equal(M, _basis_rows())
+    G = M @ M.T
+    assert np.abs(G - np.diag(np.diag(G))).max() == 0          # orthogonal rows
+    assert np.abs(M @ D.Minv() - np.eye(19)).max() < 1e-15
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_equilibrium_velocity_moments(seed):
+    rng = np.random.default_rng(seed)
+    kappa, phi, rho = rng.uniform(0.3, 1.0), rng.uniform(0.3, 1.0), rng.uniform(0.9, 1.1)
+    u = rng.normal(0, 0.05, 3)
+    f = D.feq(kappa, phi, rho, u)
+    e = E_REF.astype(float)
+    m0 = phi * rho
+    assert abs(f.sum() - m0) < 1e-15
+    assert np.abs(e.T @ f - m0 * u).max() < 1e-16
+    P = np.einsum("ia,ib,i->ab", e, e, f)
+    assert np.abs(P - (m0 * np.outer(u, u) + kappa * rho / 3 * np.eye(3))).max() < 1e-15
+    Qt = np.einsum("ia,ib,ic,i->abc", e, e, e, f)
+    for a in range(3):
+        assert abs(Qt[a, a, a] - m0 * u[a]) < 1e-16                   # e_a^3 = e_a: phi rho u_a
+        for b in range(3):
+            if b != a:
+                assert abs(Qt[a, b, b] - kappa * rho / 3 * u[a]) < 1e-16   # kappa rho cs^2 u_a
+    assert abs(Qt[0, 1, 2]) < 1e-16
+    assert np.abs(D.M() @ f - D.meq(kappa, phi, rho, u)).max() < 1e-14
+
+
+def test_guo_force_moments():
+    rng = np.random.default_rng(4)
+    u, F = rng.normal(0, 0.05, 3), rng.normal(0, 1e-3, 3)
+    Fi = D.guo_force(u, F)
+    e = E_REF.astype(float)
+    assert abs(Fi.sum()) < 1e-18
+    assert np.abs(e.T @ Fi - F).max() < 1e-18
+    assert np.abs(np.einsum("ia,ib,i->ab", e, e, Fi) - (np.outer(u, F) + np.outer(F, u))).max() < 1e-18
+    assert np.abs(D.M() @ Fi - D.force_moments(u, F)).max() < 1e-16
+
+
+def test_penalty_vanishes_for_standard_mrt_and_has_the_2d_structure():
+    rng = np.random.default_rng(5)
+    dA, dD, dB = rng.normal(size=3), rng.normal(size=3), rng.normal(size=(3, 3))
+    # phi = kappa uniform and steady (so d(phi rho u) = kappa d(rho u)): C = 0, the
+    # scheme is then the standard D3Q19 MRT
+    assert np.abs(D.penalty(0.6, 0.6, 1.0, dA, dB, 0.6 * dA, 0.0)).max() < 1e-15
+    kappa, phi, rho = 0.5, 0.8, 1.03
+    C = D.penalty(kappa, phi, rho, dA, dB, dD, 0.01)
+    X, kp = kappa / phi, kappa - phi
+    assert abs(C[1] - 19 * ((1 - X) * dD.sum() - X * rho * 0.01 + 2 / 3 * kp * rho * np.trace(dB))) < 1e-14
+    diag = -kappa * dA + 2 / 3 * kp * rho * np.diag(dB) + dD
+    assert abs(C[9] - (2 * diag[0] - diag[1] - diag[2])) < 1e-14
+    assert abs(C[11] - (diag[1] - diag[2])) < 1e-14
+    assert abs(C[13] - kp * rho * (dB[0, 1] + dB[1, 0]) / 3) < 1e-15
+    assert abs(C[14] - kp * rho * (dB[1, 2] + dB[2, 1]) / 3) < 1e-15
+    assert abs(C[15] - kp * rho * (dB[0, 2] + dB[2, 0]) / 3) < 1e-15
+    assert np.all(C[[0, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 17, 18]] == 0)
+
+
+def _bgk_step(f, s, F):
+    """Textbook D3Q19 BGK with Guo forcing, periodic (independent of the oracle)."""
+    e = E_REF
+    w = np.where((e ** 2).sum(1) == 0, 1 / 3, np.where((e ** 2).sum(1) == 1, 1 / 18, 1 / 36))
+    rho = f.sum(0)
+    u = (np.einsum("ia,i...->a...", e, f) + 0.5 * F) / rho
+    out = np.empty_like(f)
+    for i in range(19):
+        eu = sum(e[i, a] * u[a] for a in range(3))
+        uu = (u ** 2).sum(0)
+        feq = w[i] * rho * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * uu)
+        Fi = w[i] * sum((3 * (e[i, a] - u[a]) + 9 * eu * e[i, a]) * F[a] for a in range(3))
+        post = f[i] - s * (f[i] - feq) + (1 - s / 2) * Fi
+        out[i] = np.roll(post, shift=(e[i, 2], e[i, 1], e[i, 0]), axis=(0, 1, 2))
+    return out
+
+
+def test_reduces_to_textbook_bgk_when_phi_is_kappa_and_rates_are_equal():
+    nx, ny, nz, s = 7, 5, 6, 1.3
+    rng = np.random.default_rng(6)
+    kappa = 0.6
+    p = D.Params(nx, ny, nz, s_nu=s, s_e=s, s_eps=s, s_q=s, s_pi=s, s_m=s, s_c=s, kappa=kappa)
+    phi = np.full((nz, ny, nx), kappa)
+    rho = 1 + 0.01 * rng.normal(size=(nz, ny, nx))
+    u = 0.03 * rng.normal(size=(3, nz, ny, nx))
+    fb = 1e-4 * rng.normal(size=(3, nz, ny, nx))
+    f = D.init(p, rho, u, phi, fb)
+    # the oracle's F^p = (kappa - phi) grad rho / 3 vanishes, so F = F^B
+    g = f.copy()
+    for _ in range(3):
+        f = D.step(p, f, phi, None, fb)
+        g = _bgk_step(g, s, fb)
+    assert np.abs(f - g).max() < 1e-14
+
+
+def test_rest_state_is_a_fixed_point_with_a_varying_phi():
+    nx, ny, nz = 6, 7, 5
+    rng = np.random.default_rng(7)
+    phi = rng.uniform(0.4, 1.0, size=(nz, ny, nx))
+    p = D.Params(nx, ny, nz, s_nu=1.25, kappa=0.5)
+    f0 = D.init(p, np.ones_like(phi), np.zeros((3, nz, ny, nx)), phi)
+    f = f0
+    for _ in range(4):
+        f = D.step(p, f, phi)
+    assert np.abs(f - f0).max() < 1e-15
+
+
+@pytest.mark.parametrize("bc_y", [0, 1])
+def test_mass_and_momentum_balance(bc_y):
+    nx, ny, nz = 8, 6, 5
+    rng = np.random.default_rng(8 + bc_y)
+    phi = rng.uniform(0.5, 1.0, size=(nz, ny, nx))
+    phin = phi + 0.01 * rng.normal(size=phi.shape)
+    p = D.Params(nx, ny, nz, s_nu=1.4, kappa=0.5, bc_y=bc_y)
+    rho = 1 + 0.01 * rng.normal(size=phi.shape)
+    u = 0.02 * rng.normal(size=(3,) + phi.shape)
+    fb = 1e-4 * rng.normal(size=(3,) + phi.shape)
+    f = D.init(p, rho, u, phi, fb)
+    f1 = D.step(p, f, phi, phin, fb)
+    assert abs(f1.sum() - f.sum()) < 1e-13 * f.sum()
+    if bc_y == 0:
+        F = D.macros(p, f, phi, fb)["F"]
+        e = E_REF.astype(float)
+        j0 = e.T @ f.reshape(19, -1).sum(1)
+        j1 = e.T @ f1.reshape(19, -1).sum(1)
+        assert np.abs(j1 - j0 - F.reshape(3, -1).sum(1)).max() < 1e-14
+
+
+def test_poiseuille_is_exact_at_the_magic_rates():
+    """phi = kappa = 1, walls in y, force along x: the parabola G y(H - y)/(2 nu) with
+    H = ny at the half-way walls, exact when the even moments relax at s_nu, the odd
+    ghosts (q and m) at s_q, and (1/s_nu - 1/2)(1/s_q - 1/2) = 3/16 (measured 1.5e-12;
+    5e-9 with the even ghosts at 1.2 and 1.67)."""
+    nx, ny, nz, g = 3, 12, 3, 1e-5
+    s_nu = 1 / 0.8
+    s_q = 1 / (3 / 16 / (1 / s_nu - 0.5) + 0.5)
+    p = D.Params(nx, ny, nz, s_nu=s_nu, s_e=s_nu, s_eps=s_nu, s_pi=s_nu, s_q=s_q, s_m=s_q, kappa=1.0, bc_y=1)
+    phi = np.ones((nz, ny, nx))
+    fb = np.zeros((3, nz, ny, nx))
+    fb[0] = g
+    f = D.init(p, np.ones_like(phi), np.zeros((3, nz, ny, nx)), phi, fb)
+    for _ in range(6000):
+        f = D.step(p, f, phi, None, fb)
+    u = D.macros(p, f, phi, fb)["u"][0][0, :, 0]
+    nu = (1 / s_nu - 0.5) / 3
+    y = np.arange(ny) + 0.5
+    want = g * y * (ny - y) / (2 * nu)
+    assert np.abs(u - want).max() < 1e-9 * want.max(), np.abs(u - want).max() / want.max()
+
+
+def _mms_error(n, T, U0, no_penalty=0, tau=0.8):
+    M = Config3(n=n, T=float(T), U0=U0)
+    r = D.rates_from_tau(tau)
+    nu, nu_e = (tau - 0.5) / 3, (1 / r["s_e"] - 0.5) / 3
+    p = D.Params(n, n, n, nthreads=8, no_penalty=no_penalty, **r)
+    f = D.init(p, np.ones((n, n, n)), M.velocity(0), M.phi(0), M.force(0, nu, nu_e))
+    for t in range(T):
+        f = D.step(p, f, M.phi(t), M.phi(t + 1), M.force(t, nu, nu_e))
+    u = D.macros(p, f, M.phi(T), M.force(T, nu, nu_e))["u"]
+    ur = M.velocity(T)
+    return float(np.sqrt(((u - ur) ** 2).sum() / (ur ** 2).sum()))
+
+
+def test_manufactured_solution_converges_at_second_order():
+    """Diffusive scaling (T ~ n^2, U0 ~ 1/n), one period of the moving phi: the error
+    falls by 4 from 12^3 to 24^3 (measured 1.19e-2 -> 3.01e-3)."""
+    assert Config3(n=12).continuity_residual(5.0).__abs__().max() < 1e-16
+    e12 = _mms_error(12, 64, 0.02)
+    e24 = _mms_error(24, 256, 0.01)
+    print(f"E_u 12^3 {e12:.3e}, 24^3 {e24:.3e}, ratio {e12 / e24:.3f}")
+    assert 3.5 < e12 / e24 < 4.5
+    assert e24 < 5e-3
+
+
+def test_manufactured_solution_fails_without_the_penalty_source():
+    """A planted mistake: without C the scheme's viscous stress is wrong at O(1) and the
+    error sits at 0.25 (20x the consistent scheme's at 12^3, and it does not fall with n)."""
+    e_ok = _mms_error(12, 64, 0.02)
+    e_bad = _mms_error(12, 64, 0.02, no_penalty=1)
+    assert e_bad > 10 * e_ok, (e_ok, e_bad)
