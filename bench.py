@@ -286,6 +286,48 @@ ADJOINT_WORKLOAD = ("1024x1024 porous channel (the 4096^2 channel recipe regener
                     "100 of 4000 steps from rest; dJ/dphi for every cell; FP64; checkpoint every 200 steps")
 
 
+def d3q19_run(n: int = 256, steps: int = 200, warmup: int = 5):
+    """The 3-D (D3Q19) form of the scheme on an n^3 porous channel (walls in y,
+    periodic x and z, g_x = 1e-6, tau = 0.6, the other rates 1.2 as in the 2-D channel,
+    from rest), FP32 storage: MLUPS over
+    ``steps`` steps timed with CUDA events on the lattice's stream (populations 2 x
+    19 x n^3 x 4 B, larger than L2), algorithmic HBM bytes 19 x 4 x 2 + 4 = 156 per
+    cell (populations read and written once, phi read once), and the FP64 rate on a
+    smaller lattice."""
+    import torch
+    import paper_2409_02964_gb300 as P
+    from synth.fields3d import channel3d_fields
+    phi, g = channel3d_fields(n)
+    out = {"workload": f"3-D porous channel {n}^3, D3Q19 MRT-VANSE, bounce-back walls in y, periodic x and z, "
+                       "g_x=1e-6, tau=0.6, s_e=s_eps=s_q=s_pi=s_m=1.2, kappa=0.5, GRF void "
+                       "fraction [0.35,1] (l=16, seed 2409) with a cube block",
+           "kernels_per_step": 3}
+    peak, _ = _peaks()
+    for storage, size, k in (("fp32", n, steps), ("fp64", n // 2, max(10, steps // 10))):
+        ph = phi if size == n else channel3d_fields(size)[0]
+        lat = P.Lattice3D(size, size, size, 0.6, s_e=1.2, bc_y="bounceback", storage=storage)
+        lat.set_void_fraction(ph)
+        lat.set_body_force(g, 0.0, 0.0)
+        lat.init_fields(np.ones((size,) * 3), np.zeros((3,) + (size,) * 3))
+        lat.step(warmup)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0, _ = lat.reduce()
+        e0.record(lat.stream)
+        lat.step(k)
+        e1.record(lat.stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        m1, _ = lat.reduce()
+        lat.close()
+        mlups = size ** 3 * k / sec / 1e6
+        bpc = 19 * 2 * (4 if storage == "fp32" else 8) + (4 if storage == "fp32" else 8)
+        out[storage] = {"n": size, "steps": k, "MLUPS": round(mlups, 1), "bytes_per_cell": bpc,
+                        "GB_s": round(mlups * bpc / 1e3, 1), "hbm_frac": round(mlups * bpc / 1e3 / peak, 4),
+                        "mass_drift": (m1 - m0) / m0}
+    return out
+
+
 def adjoint_run(n: int = 1024, nsteps: int = 4000, avg: int = 100, ckpt: int = 200):
     """The differentiation workload: J and dJ/dphi through the C ABI; forward and
     backward device time from CUDA events inside the call."""
@@ -395,6 +437,9 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=4000)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3-D (D3Q19) workload")
+    ap.add_argument("--d3q19-only", action="store_true", help="run only the 3-D (D3Q19) workload")
+    ap.add_argument("--d3q19-n", type=int, default=256, help="edge of the 3-D channel")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -406,6 +451,9 @@ def main():
         return 0
     if args.batch_only:
         print(json.dumps({"batch": batch_run(args.batch_steps, args.batch_count)}), flush=True)
+        return 0
+    if args.d3q19_only:
+        print(json.dumps({"d3q19": d3q19_run(args.d3q19_n)}), flush=True)
         return 0
 
     import torch
@@ -501,6 +549,8 @@ def main():
             out["batch"] = batch_run(args.batch_steps, args.batch_count)
         if not args.no_adjoint:
             out["adjoint"] = adjoint_run()
+        if not args.no_3d:
+            out["d3q19"] = d3q19_run(args.d3q19_n)
         out["cpu_baseline"] = cpu_baseline(args.n)
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -1,8 +1,9 @@
 """Compile the CUDA library ``liblbm_vanse.so`` for sm_103a, in-tree.
 
-One translation unit (``csrc/lbm_vanse.cu``) holds the C ABI of
-``include/lbm_vanse.h`` and every kernel; it is built with nvcc for
-``arch=compute_103a,code=sm_103a`` into ``paper_2409_02964_gb300/_build/``.
+Two translation units, compiled in parallel and linked into one shared library in
+``paper_2409_02964_gb300/_build/`` with nvcc for ``arch=compute_103a,code=sm_103a``:
+``csrc/lbm_vanse.cu`` (the C ABI of ``include/lbm_vanse.h`` and the D2Q9 kernels) and
+``csrc/lbm_vanse3d.cu`` (``include/lbm_vanse3d.h``, the D3Q19 step).
 """
 from __future__ import annotations
 
@@ -16,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_vanse.so")
-SOURCES = ["lbm_vanse.cu"]
+SOURCES = ["lbm_vanse.cu", "lbm_vanse3d.cu"]
 HEADERS = ["vanse_common.cuh", "vanse_step.cuh", "vanse_aux.cuh", "vanse_pair.cuh", "vanse_warp.cuh",
            "vanse_batch.cuh", "mms_force.cuh", "vanse_adjoint.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -33,7 +34,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "lbm_vanse.h")]
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, h)
+                                                                for h in ("lbm_vanse.h", "lbm_vanse3d.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -48,16 +50,28 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None, out: str
         return LIB
     os.makedirs(os.path.dirname(lib), exist_ok=True)
     tmp = lib + ".tmp"
-    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           f"-I{INCLUDE}", "-o", tmp] + flags + [os.path.join(CSRC, s) for s in SOURCES]
+    common = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"] + flags
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+        common.insert(1, "-Xptxas=-v")
+    objs, procs = [], []
+    for s in SOURCES:
+        obj = os.path.join(os.path.dirname(lib), os.path.splitext(s)[0] + ".o")
+        cmd = common + ["-c", "-o", obj, os.path.join(CSRC, s)]
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)))
+        objs.append(obj)
+    logs = []
+    for cmd, pr in procs:
+        _, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(f"nvcc failed ({' '.join(cmd)}):\n{err}")
+        logs.append(err)
+    link = [nvcc(), ARCH, "-shared", "-o", tmp] + objs
+    r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed ({' '.join(cmd)}):\n{r.stderr}")
+        raise RuntimeError(f"nvcc link failed ({' '.join(link)}):\n{r.stderr}")
     os.replace(tmp, lib)
     if verbose:
-        print(r.stderr)
+        print("".join(logs))
     return lib
 
 

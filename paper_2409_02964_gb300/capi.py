@@ -34,6 +34,11 @@ EXPORTS = [
     "lbm_vanse_batch_velocity_error", "lbm_vanse_batch_get_populations", "lbm_vanse_batch_cells",
     "lbm_vanse_batch_step_count", "lbm_vanse_batch_last_error", "lbm_vanse_batch_destroy",
     "lbm_vanse_outlet_momentum_grad",
+    # include/lbm_vanse3d.h
+    "lbm_vanse3d_default_params", "lbm_vanse3d_create", "lbm_vanse3d_destroy", "lbm_vanse3d_set_void_fraction",
+    "lbm_vanse3d_set_body_force", "lbm_vanse3d_init_fields", "lbm_vanse3d_step", "lbm_vanse3d_sync",
+    "lbm_vanse3d_get_populations", "lbm_vanse3d_set_populations", "lbm_vanse3d_macros", "lbm_vanse3d_reduce",
+    "lbm_vanse3d_step_count", "lbm_vanse3d_last_error",
 ]
 
 
@@ -48,6 +53,17 @@ class lbm_vanse_params(ctypes.Structure):
         ("storage", ctypes.c_int), ("model_b", ctypes.c_int),
         ("storage_scale_log2", ctypes.c_int), ("strip_rows", ctypes.c_int),
         ("eager", ctypes.c_int), ("kernel", ctypes.c_int), ("eq_order", ctypes.c_int),
+    ]
+
+
+class lbm_vanse3d_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("tau_nu", ctypes.c_double),
+        ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
+        ("s_pi", ctypes.c_double), ("s_m", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("bc_y", ctypes.c_int), ("storage", ctypes.c_int),
     ]
 
 
@@ -138,6 +154,20 @@ def load(path: str | None = None):
         "lbm_vanse_batch_destroy": (None, [vp]),
         "lbm_vanse_outlet_momentum_grad": (i, [pp, ctypes.POINTER(lbm_vanse_adjoint_params), vp, i, vp, dp, vp,
                                                ctypes.POINTER(lbm_vanse_adjoint_stats)]),
+        "lbm_vanse3d_default_params": (None, [ctypes.POINTER(lbm_vanse3d_params)]),
+        "lbm_vanse3d_create": (i, [ctypes.POINTER(lbm_vanse3d_params), vp, ctypes.POINTER(vp)]),
+        "lbm_vanse3d_destroy": (None, [vp]),
+        "lbm_vanse3d_set_void_fraction": (i, [vp, vp, vp, i]),
+        "lbm_vanse3d_set_body_force": (i, [vp, d, d, d, vp, i]),
+        "lbm_vanse3d_init_fields": (i, [vp, vp, vp, vp, vp, i]),
+        "lbm_vanse3d_step": (i, [vp, i]),
+        "lbm_vanse3d_sync": (i, [vp]),
+        "lbm_vanse3d_get_populations": (i, [vp, vp, i]),
+        "lbm_vanse3d_set_populations": (i, [vp, vp, i]),
+        "lbm_vanse3d_macros": (i, [vp, vp, vp, i]),
+        "lbm_vanse3d_reduce": (i, [vp, dp, dp]),
+        "lbm_vanse3d_step_count": (ctypes.c_longlong, [vp]),
+        "lbm_vanse3d_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -156,4 +186,10 @@ def default_params() -> lbm_vanse_params:
 def batch_default_params() -> lbm_vanse_batch_params:
     p = lbm_vanse_batch_params()
     load().lbm_vanse_batch_default_params(ctypes.byref(p))
+    return p
+
+
+def default_params3d() -> lbm_vanse3d_params:
+    p = lbm_vanse3d_params()
+    load().lbm_vanse3d_default_params(ctypes.byref(p))
     return p

@@ -1,0 +1,748 @@
+// The three-dimensional (D3Q19) MRTLB-VANSE step and the C ABI of
+// include/lbm_vanse3d.h.
+//
+// One step is three kernels over the cells (x fastest, one thread per cell):
+//   v3_moments   sum f and sum e f of the post-streaming populations, rho = sum f / phi
+//                (Eq. 7);
+//   v3_velocity  grad rho by Eq. (10) with the D3Q19 weights, F = (kappa - phi)/3 grad rho
+//                + F^B (Eq. 13), u = (j + F/2) / sum f (Eq. 7);
+//   v3_collide   the gradients of rho u, u and phi rho u (Eq. 10), the D3Q19 penalty
+//                source, m = M f, the relaxation of Eq. (16) with the equilibrium and
+//                Guo force moments, f+ = M^-1 m+, and push streaming (periodic x, z;
+//                periodic or half-way bounce-back in y).
+// The population buffers hold post-streaming values, [19][nz][ny][nx] planes in the
+// storage type T (double or float), which is also the compute type. Next to a wall
+// the gradient stencils read a ghost cell mirrored about it (scalars keep the mirror
+// value, vector components change sign).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <utility>
+
+#include "lbm_vanse3d.h"
+
+namespace lbmv3 {
+
+constexpr int Q = 19;
+
+// D3Q19 velocities (the order of the ABI)
+constexpr int kE[Q][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                          {0, 0, 1},   {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                          {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                          {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+__constant__ int cE[Q][3];
+__constant__ int cOpp[Q];
+__constant__ double cWd[Q];
+__constant__ float cWf[Q];
+__constant__ double cMd[Q * Q], cMid[Q * Q];
+__constant__ float cMf[Q * Q], cMif[Q * Q];
+
+// the moment basis (d'Humieres et al. 2002) at velocity c: one row per moment
+static double host_basis(int k, int x, int y, int z) {
+    const double c2 = x * x + y * y + z * z;
+    const double X = x, Y = y, Z = z;
+    switch (k) {
+        case 0: return 1.0;
+        case 1: return 19.0 * c2 - 30.0;
+        case 2: return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;
+        case 3: return X;
+        case 4: return (5.0 * c2 - 9.0) * X;
+        case 5: return Y;
+        case 6: return (5.0 * c2 - 9.0) * Y;
+        case 7: return Z;
+        case 8: return (5.0 * c2 - 9.0) * Z;
+        case 9: return 3.0 * X * X - c2;
+        case 10: return (3.0 * c2 - 5.0) * (3.0 * X * X - c2);
+        case 11: return Y * Y - Z * Z;
+        case 12: return (3.0 * c2 - 5.0) * (Y * Y - Z * Z);
+        case 13: return X * Y;
+        case 14: return Y * Z;
+        case 15: return X * Z;
+        case 16: return (Y * Y - Z * Z) * X;
+        case 17: return (Z * Z - X * X) * Y;
+        default: return (X * X - Y * Y) * Z;
+    }
+}
+
+static cudaError_t upload_tables() {
+    double M[Q * Q], Mi[Q * Q], w[Q];
+    float Mf[Q * Q], Mif[Q * Q], wf[Q];
+    int opp[Q];
+    for (int k = 0; k < Q; ++k) {
+        double n2 = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            M[k * Q + i] = host_basis(k, kE[i][0], kE[i][1], kE[i][2]);
+            n2 += M[k * Q + i] * M[k * Q + i];
+        }
+        for (int i = 0; i < Q; ++i) Mi[i * Q + k] = M[k * Q + i] / n2;   // rows are orthogonal
+    }
+    for (int i = 0; i < Q; ++i) {
+        const int c2 = kE[i][0] * kE[i][0] + kE[i][1] * kE[i][1] + kE[i][2] * kE[i][2];
+        w[i] = c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        wf[i] = (float)w[i];
+        for (int k = 0; k < Q; ++k)
+            if (kE[k][0] == -kE[i][0] && kE[k][1] == -kE[i][1] && kE[k][2] == -kE[i][2]) opp[i] = k;
+    }
+    for (int k = 0; k < Q * Q; ++k) {
+        Mf[k] = (float)M[k];
+        Mif[k] = (float)Mi[k];
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(cE, kE, sizeof(kE))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cOpp, opp, sizeof(opp))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cWd, w, sizeof(w))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cWf, wf, sizeof(wf))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cMd, M, sizeof(M))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cMid, Mi, sizeof(Mi))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cMf, Mf, sizeof(Mf))) != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(cMif, Mif, sizeof(Mif));
+}
+
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+    __device__ static double w(int i) { return cWd[i]; }
+    __device__ static double M(int k) { return cMd[k]; }
+    __device__ static double Mi(int k) { return cMid[k]; }
+};
+template <> struct Tab<float> {
+    __device__ static float w(int i) { return cWf[i]; }
+    __device__ static float M(int k) { return cMf[k]; }
+    __device__ static float Mi(int k) { return cMif[k]; }
+};
+
+struct Geo {
+    int nx, ny, nz;
+    long long N;
+    int walls;   // 1: half-way bounce-back walls in y
+};
+
+template <typename T> struct Rates {
+    T s[Q];
+    T kappa;
+};
+
+__device__ __forceinline__ void decode(const Geo& g, long long c, int& x, int& y, int& z) {
+    x = (int)(c % g.nx);
+    const long long r = c / g.nx;
+    y = (int)(r % g.ny);
+    z = (int)(r / g.ny);
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// neighbour (x + e) for the gradient stencils: periodic x, z; y periodic or mirrored
+// about the wall (mirror = true when the ghost is a mirror image)
+__device__ __forceinline__ long long neighbour(const Geo& g, int x, int y, int z, int i, bool& mirror) {
+    const int xn = wrapi(x + cE[i][0], g.nx), zn = wrapi(z + cE[i][2], g.nz);
+    int yn = y + cE[i][1];
+    mirror = false;
+    if (g.walls) {
+        if (yn < 0) { yn = -1 - yn; mirror = true; }
+        else if (yn >= g.ny) { yn = 2 * g.ny - 1 - yn; mirror = true; }
+    } else {
+        yn = wrapi(yn, g.ny);
+    }
+    return ((long long)zn * g.ny + yn) * g.nx + xn;
+}
+
+template <typename T>
+__global__ void v3_moments(const T* __restrict__ f, const T* __restrict__ phi, T* __restrict__ rho,
+                           T* __restrict__ j, Geo g) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    T m0 = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T v = f[i * g.N + c];
+        m0 += v;
+        jx += (T)cE[i][0] * v;
+        jy += (T)cE[i][1] * v;
+        jz += (T)cE[i][2] * v;
+    }
+    rho[c] = m0 / phi[c];
+    j[c] = jx;
+    j[g.N + c] = jy;
+    j[2 * g.N + c] = jz;
+}
+
+// F = (kappa - phi)/3 grad rho + phi G + field, u = (j + F/2) / (phi rho)
+template <typename T>
+__global__ void v3_velocity(const T* __restrict__ rho, const T* __restrict__ j, const T* __restrict__ phi,
+                            const T* __restrict__ fb, T gx, T gy, T gz, T kappa, T* __restrict__ u,
+                            T* __restrict__ F, Geo g) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int x, y, z;
+    decode(g, c, x, y, z);
+    T gr[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        bool mir;
+        const T v = (T)3 * Tab<T>::w(i) * rho[neighbour(g, x, y, z, i, mir)];
+        gr[0] += (T)cE[i][0] * v;
+        gr[1] += (T)cE[i][1] * v;
+        gr[2] += (T)cE[i][2] * v;
+    }
+    const T ph = phi[c], r = rho[c];
+    const T G[3] = {gx, gy, gz};
+    const T m0 = ph * r;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T Fa = (kappa - ph) / (T)3 * gr[a] + ph * G[a];
+        if (fb) Fa += fb[a * g.N + c];
+        F[a * g.N + c] = Fa;
+        u[a * g.N + c] = (j[a * g.N + c] + (T)0.5 * Fa) / m0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void equilibrium_moments(T kappa, T phi, T rho, const T* u, T* m) {
+    const T m0 = phi * rho, X = kappa / phi;
+    const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T pxx3 = m0 * ((T)3 * u[0] * u[0] - u2), pww = m0 * (u[1] * u[1] - u[2] * u[2]);
+    const T qf = (T)10 * X / (T)3 - (T)4;
+    m[0] = m0;
+    m[1] = (T)19 * (kappa * rho + m0 * u2) - (T)30 * m0;
+    m[2] = (T)12 * m0 - (T)9 * kappa * rho - (T)5.5 * m0 * u2;
+    m[3] = m0 * u[0];
+    m[4] = qf * m0 * u[0];
+    m[5] = m0 * u[1];
+    m[6] = qf * m0 * u[1];
+    m[7] = m0 * u[2];
+    m[8] = qf * m0 * u[2];
+    m[9] = pxx3;
+    m[10] = (T)-0.5 * pxx3;
+    m[11] = pww;
+    m[12] = (T)-0.5 * pww;
+    m[13] = m0 * u[0] * u[1];
+    m[14] = m0 * u[1] * u[2];
+    m[15] = m0 * u[0] * u[2];
+    m[16] = 0;
+    m[17] = 0;
+    m[18] = 0;
+}
+
+// Eq. (6): F_i = w_i [3 (e_i - u) + 9 (e_i . u) e_i] . F
+template <typename T>
+__device__ __forceinline__ T guo(int i, const T* u, const T* F) {
+    const T eu = (T)cE[i][0] * u[0] + (T)cE[i][1] * u[1] + (T)cE[i][2] * u[2];
+    T s = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s += ((T)3 * ((T)cE[i][a] - u[a]) + (T)9 * eu * (T)cE[i][a]) * F[a];
+    return Tab<T>::w(i) * s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) v3_collide(const T* __restrict__ f, T* __restrict__ fo,
+                                                   const T* __restrict__ rho, const T* __restrict__ u,
+                                                   const T* __restrict__ F, const T* __restrict__ phi,
+                                                   const T* __restrict__ phin, Rates<T> R, Geo g) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int x, y, z;
+    decode(g, c, x, y, z);
+    const T kappa = R.kappa;
+    // gradients of A = rho u (diagonal), B = u (all nine), D = phi rho u (diagonal)
+    T dA[3] = {0, 0, 0}, dD[3] = {0, 0, 0}, dB[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll 2
+    for (int i = 1; i < Q; ++i) {
+        bool mir;
+        const long long n = neighbour(g, x, y, z, i, mir);
+        const T sg = mir ? (T)-1 : (T)1;
+        const T rn = rho[n], pn = phi[n];
+        const T un[3] = {sg * u[n], sg * u[g.N + n], sg * u[2 * g.N + n]};
+        const T wv = (T)3 * Tab<T>::w(i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T ca = wv * (T)cE[i][a];
+            dA[a] += ca * rn * un[a];
+            dD[a] += ca * pn * rn * un[a];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) dB[3 * a + b] += ca * un[b];
+        }
+    }
+    const T ph = phi[c], r = rho[c];
+    const T uc[3] = {u[c], u[g.N + c], u[2 * g.N + c]};
+    const T Fc[3] = {F[c], F[g.N + c], F[2 * g.N + c]};
+    const T X = kappa / ph, kp = kappa - ph;
+    const T dtphi = phin ? phin[c] - ph : (T)0;
+    T C[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) C[k] = 0;
+    {
+        const T divB = dB[0] + dB[4] + dB[8], divD = dD[0] + dD[1] + dD[2];
+        C[1] = (T)19 * (((T)1 - X) * divD - X * r * dtphi + (T)2 / (T)3 * kp * r * divB);
+        T dg[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dg[a] = -kappa * dA[a] + (T)2 / (T)3 * kp * r * dB[4 * a] + dD[a];
+        C[9] = (T)2 * dg[0] - dg[1] - dg[2];
+        C[11] = dg[1] - dg[2];
+        C[13] = kp * r * (dB[1] + dB[3]) / (T)3;
+        C[14] = kp * r * (dB[5] + dB[7]) / (T)3;
+        C[15] = kp * r * (dB[2] + dB[6]) / (T)3;
+    }
+    T fl[Q], Fi[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        fl[i] = f[i * g.N + c];
+        Fi[i] = guo<T>(i, uc, Fc);
+    }
+    T meq[Q];
+    equilibrium_moments<T>(kappa, ph, r, uc, meq);
+    T mp[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        T m = 0, S = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            m += Tab<T>::M(k * Q + i) * fl[i];
+            S += Tab<T>::M(k * Q + i) * Fi[i];
+        }
+        const T s = R.s[k];
+        mp[k] = m - s * (m - meq[k]) + ((T)1 - (T)0.5 * s) * (S + C[k]);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T v = 0;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) v += Tab<T>::Mi(i * Q + k) * mp[k];
+        // push: f+_i(x) -> f_i(x + e_i); a link into a y wall returns as f_opp(x)
+        const int yd = y + cE[i][1];
+        if (g.walls && (yd < 0 || yd >= g.ny)) {
+            fo[cOpp[i] * g.N + c] = v;
+        } else {
+            const int xd = wrapi(x + cE[i][0], g.nx), zd = wrapi(z + cE[i][2], g.nz);
+            fo[i * g.N + ((long long)zd * g.ny + wrapi(yd, g.ny)) * g.nx + xd] = v;
+        }
+    }
+}
+
+// f = f^eq(rho, u, phi) - F_i/2 (F from v3_velocity's force part)
+template <typename T>
+__global__ void v3_init(T* __restrict__ f, const T* __restrict__ rho, const T* __restrict__ u,
+                        const T* __restrict__ F, const T* __restrict__ phi, T kappa, Geo g) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    const T uc[3] = {u[c], u[g.N + c], u[2 * g.N + c]};
+    const T Fc[3] = {F[c], F[g.N + c], F[2 * g.N + c]};
+    T meq[Q];
+    equilibrium_moments<T>(kappa, phi[c], rho[c], uc, meq);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T v = 0;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) v += Tab<T>::Mi(i * Q + k) * meq[k];
+        f[i * g.N + c] = v - (T)0.5 * guo<T>(i, uc, Fc);
+    }
+}
+
+// F only (init: the velocity is given)
+template <typename T>
+__global__ void v3_force(const T* __restrict__ rho, const T* __restrict__ phi, const T* __restrict__ fb, T gx,
+                         T gy, T gz, T kappa, T* __restrict__ F, Geo g) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.N) return;
+    int x, y, z;
+    decode(g, c, x, y, z);
+    T gr[3] = {0, 0, 0};
+    for (int i = 1; i < Q; ++i) {
+        bool mir;
+        const T v = (T)3 * Tab<T>::w(i) * rho[neighbour(g, x, y, z, i, mir)];
+        for (int a = 0; a < 3; ++a) gr[a] += (T)cE[i][a] * v;
+    }
+    const T ph = phi[c], G[3] = {gx, gy, gz};
+    for (int a = 0; a < 3; ++a) F[a * g.N + c] = (kappa - ph) / (T)3 * gr[a] + ph * G[a] + (fb ? fb[a * g.N + c] : (T)0);
+}
+
+template <typename Tin, typename Tout>
+__global__ void v3_convert(const Tin* __restrict__ a, Tout* __restrict__ b, long long n) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        b[k] = (Tout)a[k];
+}
+
+// FP64 mass and momentum sums: out[0..3] += per-block partials
+template <typename T>
+__global__ void v3_reduce(const T* __restrict__ f, long long N, double* __restrict__ out) {
+    __shared__ double sh[4][256];
+    double s[4] = {0, 0, 0, 0};
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        for (int i = 0; i < Q; ++i) {
+            const double v = (double)f[i * N + c];
+            s[0] += v;
+            s[1] += cE[i][0] * v;
+            s[2] += cE[i][1] * v;
+            s[3] += cE[i][2] * v;
+        }
+    for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 4; ++q) atomicAdd(out + q, sh[q][0]);
+}
+
+__global__ void v3_check_phi(const double* __restrict__ phi, long long n, int* __restrict__ bad) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        if (!(phi[k] > 0.0 && phi[k] <= 1.0)) atomicExch(bad, 1);
+}
+
+}  // namespace lbmv3
+
+using namespace lbmv3;
+
+namespace {
+thread_local std::string g_err3;
+}
+
+struct lbm_vanse3d {
+    lbm_vanse3d_params prm{};
+    cudaStream_t stream = nullptr;
+    Geo geo{};
+    int fp64 = 0;
+    size_t tb = 4;               // bytes of T
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *phi = nullptr, *phin = nullptr, *fb = nullptr;
+    void *rho = nullptr, *j = nullptr, *u = nullptr, *F = nullptr;
+    double* red = nullptr;
+    int* bad = nullptr;
+    double g[3] = {0, 0, 0};
+    bool phi_set = false, phin_set = false, fb_set = false, initialised = false;
+    long long steps = 0;
+    double s[Q];
+    std::string msg;
+};
+
+static lbm_status fail3(lbm_vanse3d* h, lbm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->msg = buf; else g_err3 = buf;
+    return st;
+}
+
+#define CK3(h, call)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return fail3((h), LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// stage n doubles from the caller into device memory (a device copy when on the host)
+static lbm_status stage_in3(lbm_vanse3d* h, const double* src, long long n, int on_device, const double** out,
+                            double** owned) {
+    *owned = nullptr;
+    if (on_device) { *out = src; return LBM_OK; }
+    double* d = nullptr;
+    CK3(h, cudaMallocAsync((void**)&d, n * sizeof(double), h->stream));
+    CK3(h, cudaMemcpyAsync(d, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    *out = d;
+    *owned = d;
+    return LBM_OK;
+}
+
+static void convert_in(lbm_vanse3d* h, const double* d, void* dst, long long n) {
+    const unsigned nb = blocks_for(n, 256) < 4096 ? blocks_for(n, 256) : 4096;
+    if (h->fp64) v3_convert<double, double><<<nb, 256, 0, h->stream>>>(d, (double*)dst, n);
+    else v3_convert<double, float><<<nb, 256, 0, h->stream>>>(d, (float*)dst, n);
+}
+
+template <typename T>
+static Rates<T> rates(const lbm_vanse3d* h) {
+    Rates<T> R;
+    for (int k = 0; k < Q; ++k) R.s[k] = (T)h->s[k];
+    R.kappa = (T)h->prm.kappa;
+    return R;
+}
+
+template <typename T>
+static void enqueue_step(lbm_vanse3d* h) {
+    const Geo& g = h->geo;
+    const unsigned nb = blocks_for(g.N, 128);
+    const T* src = (const T*)h->f[h->cur];
+    T* dst = (T*)h->f[1 - h->cur];
+    v3_moments<T><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(src, (const T*)h->phi, (T*)h->rho, (T*)h->j, g);
+    v3_velocity<T><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(
+        (const T*)h->rho, (const T*)h->j, (const T*)h->phi, h->fb_set ? (const T*)h->fb : nullptr, (T)h->g[0],
+        (T)h->g[1], (T)h->g[2], (T)h->prm.kappa, (T*)h->u, (T*)h->F, g);
+    v3_collide<T><<<nb, 128, 0, h->stream>>>(src, dst, (const T*)h->rho, (const T*)h->u, (const T*)h->F,
+                                               (const T*)h->phi, h->phin_set ? (const T*)h->phin : nullptr,
+                                               rates<T>(h), g);
+}
+
+extern "C" void lbm_vanse3d_default_params(lbm_vanse3d_params* p) {
+    if (!p) return;
+    *p = lbm_vanse3d_params{};
+    p->tau_nu = 0.8;
+    p->s_e = 0.0;
+    p->s_eps = p->s_q = p->s_pi = p->s_m = 1.2;
+    p->kappa = 0.5;
+    p->rho0 = 1.0;
+    p->bc_y = LBM_BC_PERIODIC;
+    p->storage = LBM_FP32;
+}
+
+extern "C" const char* lbm_vanse3d_last_error(lbm_vanse3d_t h) { return h ? h->msg.c_str() : g_err3.c_str(); }
+
+extern "C" void lbm_vanse3d_destroy(lbm_vanse3d_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    void* ptrs[] = {h->f[0], h->f[1], h->phi, h->phin, h->fb, h->rho, h->j, h->u, h->F, h->red, h->bad};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete h;
+}
+
+extern "C" lbm_status lbm_vanse3d_create(const lbm_vanse3d_params* p, void* stream, lbm_vanse3d_t* out) {
+    if (!out) return fail3(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail3(nullptr, LBM_ERR_ARG, "params is NULL");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail3(nullptr, LBM_ERR_ARG, "lattice size must be >= 1");
+    const long long N = (long long)p->nx * p->ny * p->nz;
+    if (N > (1LL << 40)) return fail3(nullptr, LBM_ERR_ARG, "lattice too large");
+    if (!(p->tau_nu > 0.5)) return fail3(nullptr, LBM_ERR_ARG, "tau_nu must exceed 1/2");
+    const double rates_in[] = {p->s_eps, p->s_q, p->s_pi, p->s_m};
+    for (double r : rates_in)
+        if (!(r > 0.0 && r <= 2.0)) return fail3(nullptr, LBM_ERR_ARG, "rates must lie in (0, 2]");
+    if (p->s_e > 2.0) return fail3(nullptr, LBM_ERR_ARG, "s_e must lie in (0, 2] (or <= 0: derived)");
+    if (!(p->rho0 > 0.0)) return fail3(nullptr, LBM_ERR_ARG, "rho0 must be positive");
+    if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_BOUNCEBACK) return fail3(nullptr, LBM_ERR_ARG, "bad bc_y");
+    if (p->storage != LBM_FP64 && p->storage != LBM_FP32)
+        return fail3(nullptr, LBM_ERR_ARG, "3-D storage must be LBM_FP64 or LBM_FP32");
+    lbm_vanse3d* h = new lbm_vanse3d();
+    h->prm = *p;
+    h->stream = (cudaStream_t)stream;
+    h->geo = Geo{p->nx, p->ny, p->nz, N, p->bc_y == LBM_BC_BOUNCEBACK ? 1 : 0};
+    h->fp64 = p->storage == LBM_FP64;
+    h->tb = h->fp64 ? sizeof(double) : sizeof(float);
+    const double s_nu = 1.0 / p->tau_nu, nu = (p->tau_nu - 0.5) / 3.0;
+    const double s_e = p->s_e > 0.0 ? p->s_e : 1.0 / (nu + 0.5);   // nu_e = nu/3
+    const double s[Q] = {1.0, s_e, p->s_eps, 1.0, p->s_q, 1.0, p->s_q, 1.0, p->s_q, s_nu,
+                         p->s_pi, s_nu, p->s_pi, s_nu, s_nu, s_nu, p->s_m, p->s_m, p->s_m};
+    for (int k = 0; k < Q; ++k) h->s[k] = s[k];
+    cudaError_t e = upload_tables();
+    if (e != cudaSuccess) {
+        fail3(nullptr, LBM_ERR_CUDA, "constant tables: %s", cudaGetErrorString(e));
+        delete h;
+        return LBM_ERR_CUDA;
+    }
+    struct A { void** p; size_t b; } allocs[] = {
+        {&h->f[0], Q * N * h->tb}, {&h->f[1], Q * N * h->tb}, {&h->phi, N * h->tb}, {&h->phin, N * h->tb},
+        {&h->fb, 3 * N * h->tb}, {&h->rho, N * h->tb}, {&h->j, 3 * N * h->tb}, {&h->u, 3 * N * h->tb},
+        {&h->F, 3 * N * h->tb}, {(void**)&h->red, 4 * sizeof(double)}, {(void**)&h->bad, sizeof(int)}};
+    for (auto& a : allocs) {
+        e = cudaMalloc(a.p, a.b);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g_err3 = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+            lbm_vanse3d_destroy(h);
+            return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+        }
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse3d_set_void_fraction(lbm_vanse3d_t h, const double* phi_t, const double* phi_next,
+                                                    int on_device) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!phi_t) return fail3(h, LBM_ERR_ARG, "phi_t is NULL");
+    const long long N = h->geo.N;
+    const double* srcs[2] = {phi_t, phi_next};
+    void* dsts[2] = {h->phi, h->phin};
+    CK3(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
+    for (int k = 0; k < 2; ++k) {
+        if (!srcs[k]) continue;
+        const double* d;
+        double* owned;
+        lbm_status st = stage_in3(h, srcs[k], N, on_device, &d, &owned);
+        if (st != LBM_OK) return st;
+        v3_check_phi<<<blocks_for(N, 256) < 2048 ? blocks_for(N, 256) : 2048, 256, 0, h->stream>>>(d, N, h->bad);
+        convert_in(h, d, dsts[k], N);
+        if (owned) CK3(h, cudaFreeAsync(owned, h->stream));
+    }
+    int bad = 0;
+    CK3(h, cudaMemcpyAsync(&bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK3(h, cudaStreamSynchronize(h->stream));
+    CK3(h, cudaGetLastError());
+    if (bad) return fail3(h, LBM_ERR_ARG, "void fraction outside (0, 1]");
+    h->phi_set = true;
+    h->phin_set = phi_next != nullptr;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse3d_set_body_force(lbm_vanse3d_t h, double gx, double gy, double gz,
+                                                 const double* field, int on_device) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+    h->g[0] = gx;
+    h->g[1] = gy;
+    h->g[2] = gz;
+    h->fb_set = false;
+    if (field) {
+        const double* d;
+        double* owned;
+        lbm_status st = stage_in3(h, field, 3 * h->geo.N, on_device, &d, &owned);
+        if (st != LBM_OK) return st;
+        convert_in(h, d, h->fb, 3 * h->geo.N);
+        if (owned) CK3(h, cudaFreeAsync(owned, h->stream));
+        CK3(h, cudaGetLastError());
+        h->fb_set = true;
+    }
+    return LBM_OK;
+}
+
+template <typename T>
+static void enqueue_init(lbm_vanse3d* h) {
+    const Geo& g = h->geo;
+    v3_force<T><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(
+        (const T*)h->rho, (const T*)h->phi, h->fb_set ? (const T*)h->fb : nullptr, (T)h->g[0], (T)h->g[1],
+        (T)h->g[2], (T)h->prm.kappa, (T*)h->F, g);
+    v3_init<T><<<blocks_for(g.N, 128), 128, 0, h->stream>>>((T*)h->f[h->cur], (const T*)h->rho, (const T*)h->u,
+                                                            (const T*)h->F, (const T*)h->phi, (T)h->prm.kappa, g);
+}
+
+extern "C" lbm_status lbm_vanse3d_init_fields(lbm_vanse3d_t h, const double* rho, const double* ux,
+                                              const double* uy, const double* uz, int on_device) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!rho || !ux || !uy || !uz) return fail3(h, LBM_ERR_ARG, "a field is NULL");
+    if (!h->phi_set) return fail3(h, LBM_ERR_STATE, "set the void fraction before init_fields");
+    const long long N = h->geo.N;
+    const double* srcs[4] = {rho, ux, uy, uz};
+    char* ub = (char*)h->u;
+    void* dsts[4] = {h->rho, ub, ub + N * h->tb, ub + 2 * N * h->tb};
+    for (int k = 0; k < 4; ++k) {
+        const double* d;
+        double* owned;
+        lbm_status st = stage_in3(h, srcs[k], N, on_device, &d, &owned);
+        if (st != LBM_OK) return st;
+        convert_in(h, d, dsts[k], N);
+        if (owned) CK3(h, cudaFreeAsync(owned, h->stream));
+    }
+    h->cur = 0;
+    if (h->fp64) enqueue_init<double>(h); else enqueue_init<float>(h);
+    CK3(h, cudaGetLastError());
+    h->initialised = true;
+    h->steps = 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse3d_step(lbm_vanse3d_t h, int nsteps) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail3(h, LBM_ERR_ARG, "nsteps must be >= 0");
+    if (!h->initialised) return fail3(h, LBM_ERR_STATE, "lattice not initialised");
+    for (int s = 0; s < nsteps; ++s) {
+        if (h->fp64) enqueue_step<double>(h); else enqueue_step<float>(h);
+        CK3(h, cudaGetLastError());
+        h->cur = 1 - h->cur;
+        ++h->steps;
+        if (h->phin_set) {   // phi(t) <- phi(t+1); steady afterwards
+            std::swap(h->phi, h->phin);
+            h->phin_set = false;
+        }
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse3d_sync(lbm_vanse3d_t h) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+    CK3(h, cudaStreamSynchronize(h->stream));
+    CK3(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+static lbm_status copy_out(lbm_vanse3d* h, const void* src, double* dst, long long n, int on_device) {
+    double* d = dst;
+    if (!on_device) CK3(h, cudaMallocAsync((void**)&d, n * sizeof(double), h->stream));
+    const unsigned nb = blocks_for(n, 256) < 4096 ? blocks_for(n, 256) : 4096;
+    if (h->fp64) v3_convert<double, double><<<nb, 256, 0, h->stream>>>((const double*)src, d, n);
+    else v3_convert<float, double><<<nb, 256, 0, h->stream>>>((const float*)src, d, n);
+    CK3(h, cudaGetLastError());
+    if (!on_device) {
+        CK3(h, cudaMemcpyAsync(dst, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK3(h, cudaFreeAsync(d, h->stream));
+        CK3(h, cudaStreamSynchronize(h->stream));
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse3d_get_populations(lbm_vanse3d_t h, double* f, int on_device) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!f) return fail3(h, LBM_ERR_ARG, "f is NULL");
+    if (!h->initialised) return fail3(h, LBM_ERR_STATE, "lattice not initialised");
+    return copy_out(h, h->f[h->cur], f, Q * h->geo.N, on_device);
+}
+
+extern "C" lbm_status lbm_vanse3d_set_populations(lbm_vanse3d_t h, const double* f, int on_device) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!f) return fail3(h, LBM_ERR_ARG, "f is NULL");
+    if (!h->phi_set) return fail3(h, LBM_ERR_STATE, "set the void fraction before set_populations");
+    const double* d;
+    double* owned;
+    lbm_status st = stage_in3(h, f, Q * h->geo.N, on_device, &d, &owned);
+    if (st != LBM_OK) return st;
+    h->cur = 0;
+    convert_in(h, d, h->f[0], Q * h->geo.N);
+    if (owned) CK3(h, cudaFreeAsync(owned, h->stream));
+    CK3(h, cudaGetLastError());
+    h->initialised = true;
+    h->steps = 0;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse3d_macros(lbm_vanse3d_t h, double* rho, double* u, int on_device) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!h->initialised) return fail3(h, LBM_ERR_STATE, "lattice not initialised");
+    const Geo& g = h->geo;
+    if (h->fp64) {
+        v3_moments<double><<<blocks_for(g.N, 256), 256, 0, h->stream>>>((const double*)h->f[h->cur],
+                                                                         (const double*)h->phi, (double*)h->rho,
+                                                                         (double*)h->j, g);
+        v3_velocity<double><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(
+            (const double*)h->rho, (const double*)h->j, (const double*)h->phi,
+            h->fb_set ? (const double*)h->fb : nullptr, h->g[0], h->g[1], h->g[2], h->prm.kappa, (double*)h->u,
+            (double*)h->F, g);
+    } else {
+        v3_moments<float><<<blocks_for(g.N, 256), 256, 0, h->stream>>>((const float*)h->f[h->cur],
+                                                                        (const float*)h->phi, (float*)h->rho,
+                                                                        (float*)h->j, g);
+        v3_velocity<float><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(
+            (const float*)h->rho, (const float*)h->j, (const float*)h->phi,
+            h->fb_set ? (const float*)h->fb : nullptr, (float)h->g[0], (float)h->g[1], (float)h->g[2],
+            (float)h->prm.kappa, (float*)h->u, (float*)h->F, g);
+    }
+    CK3(h, cudaGetLastError());
+    lbm_status st = LBM_OK;
+    if (rho) st = copy_out(h, h->rho, rho, g.N, on_device);
+    if (st == LBM_OK && u) st = copy_out(h, h->u, u, 3 * g.N, on_device);
+    return st;
+}
+
+extern "C" lbm_status lbm_vanse3d_reduce(lbm_vanse3d_t h, double* mass, double* mom) {
+    if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!h->initialised) return fail3(h, LBM_ERR_STATE, "lattice not initialised");
+    CK3(h, cudaMemsetAsync(h->red, 0, 4 * sizeof(double), h->stream));
+    const unsigned nb = blocks_for(h->geo.N, 256) < 1024 ? blocks_for(h->geo.N, 256) : 1024;
+    if (h->fp64) v3_reduce<double><<<nb, 256, 0, h->stream>>>((const double*)h->f[h->cur], h->geo.N, h->red);
+    else v3_reduce<float><<<nb, 256, 0, h->stream>>>((const float*)h->f[h->cur], h->geo.N, h->red);
+    CK3(h, cudaGetLastError());
+    double r[4];
+    CK3(h, cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    CK3(h, cudaStreamSynchronize(h->stream));
+    if (mass) *mass = r[0];
+    if (mom) { mom[0] = r[1]; mom[1] = r[2]; mom[2] = r[3]; }
+    for (double v : r)
+        if (!std::isfinite(v)) return fail3(h, LBM_ERR_DIVERGED, "non-finite populations (mass %g)", r[0]);
+    return LBM_OK;
+}
+
+extern "C" long long lbm_vanse3d_step_count(lbm_vanse3d_t h) { return h ? h->steps : -1; }

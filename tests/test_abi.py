@@ -1,5 +1,5 @@
 """CPU checks of the boundary: the library builds, loads without a GPU and exports
-every entry point that include/lbm_vanse.h declares."""
+every entry point that include/lbm_vanse.h and include/lbm_vanse3d.h declare."""
 import ctypes
 import os
 import re
@@ -8,9 +8,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "lbm_vanse.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_vanse_\w+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_vanse(?:3d)?_\w+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -45,6 +49,24 @@ def test_default_params_and_create_errors_without_gpu():
     assert L.lbm_vanse_create(ctypes.byref(p), None, ctypes.byref(h)) == capi.LBM_ERR_ARG
     assert L.lbm_vanse_step(None, 1) == capi.LBM_ERR_ARG
     L.lbm_vanse_destroy(None)
+
+
+def test_3d_create_checks_arguments_without_gpu():
+    from paper_2409_02964_gb300 import capi
+    L = capi.load()
+    p = capi.default_params3d()
+    assert (p.tau_nu, p.s_e, p.s_eps, p.s_q, p.s_pi, p.s_m, p.kappa, p.rho0, p.storage) == \
+        (0.8, 0.0, 1.2, 1.2, 1.2, 1.2, 0.5, 1.0, capi.LBM_FP32)
+    h = ctypes.c_void_p()
+    assert L.lbm_vanse3d_create(ctypes.byref(p), None, ctypes.byref(h)) == capi.LBM_ERR_ARG   # nx = 0
+    assert b"size" in L.lbm_vanse3d_last_error(None)
+    p.nx = p.ny = p.nz = 4
+    p.storage = capi.LBM_FP16
+    assert L.lbm_vanse3d_create(ctypes.byref(p), None, ctypes.byref(h)) == capi.LBM_ERR_ARG
+    p.storage, p.s_q = capi.LBM_FP32, 2.5
+    assert L.lbm_vanse3d_create(ctypes.byref(p), None, ctypes.byref(h)) == capi.LBM_ERR_ARG
+    assert L.lbm_vanse3d_step(None, 1) == capi.LBM_ERR_ARG
+    L.lbm_vanse3d_destroy(None)
 
 
 def test_graft_entry_build_compiles_everything():
