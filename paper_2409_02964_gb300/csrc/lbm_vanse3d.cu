@@ -34,85 +34,132 @@ constexpr int kE[Q][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, 
                           {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
                           {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
 
-__constant__ int cE[Q][3];
-__constant__ int cOpp[Q];
-__constant__ double cWd[Q];
-__constant__ float cWf[Q];
-__constant__ double cMd[Q * Q], cMid[Q * Q];
-__constant__ float cMf[Q * Q], cMif[Q * Q];
+// The same velocities, the opposite directions, the weights and the integer moment
+// basis as compile-time functions: inside fully unrolled loops they fold into
+// immediates, so the 19 x 19 transforms drop their zero products and turn the +-1
+// entries into adds.
+__host__ __device__ constexpr int vel(int i, int a) {
+    return a == 0 ? ((i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+                     : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0)
+         : a == 1 ? ((i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+                     : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0)
+                  : ((i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+                     : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+}
 
-// the moment basis (d'Humieres et al. 2002) at velocity c: one row per moment
-static double host_basis(int k, int x, int y, int z) {
-    const double c2 = x * x + y * y + z * z;
-    const double X = x, Y = y, Z = z;
+__host__ __device__ constexpr int opp(int i) {
+    int r = 0;
+    for (int k = 0; k < Q; ++k)
+        if (vel(k, 0) == -vel(i, 0) && vel(k, 1) == -vel(i, 1) && vel(k, 2) == -vel(i, 2)) r = k;
+    return r;
+}
+
+// the basis polynomial of moment k at e_i (d'Humieres et al. 2002); all integers
+__host__ __device__ constexpr int mcoef(int k, int i) {
+    const int x = vel(i, 0), y = vel(i, 1), z = vel(i, 2), c2 = x * x + y * y + z * z;
     switch (k) {
-        case 0: return 1.0;
-        case 1: return 19.0 * c2 - 30.0;
-        case 2: return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;
-        case 3: return X;
-        case 4: return (5.0 * c2 - 9.0) * X;
-        case 5: return Y;
-        case 6: return (5.0 * c2 - 9.0) * Y;
-        case 7: return Z;
-        case 8: return (5.0 * c2 - 9.0) * Z;
-        case 9: return 3.0 * X * X - c2;
-        case 10: return (3.0 * c2 - 5.0) * (3.0 * X * X - c2);
-        case 11: return Y * Y - Z * Z;
-        case 12: return (3.0 * c2 - 5.0) * (Y * Y - Z * Z);
-        case 13: return X * Y;
-        case 14: return Y * Z;
-        case 15: return X * Z;
-        case 16: return (Y * Y - Z * Z) * X;
-        case 17: return (Z * Z - X * X) * Y;
-        default: return (X * X - Y * Y) * Z;
+        case 0: return 1;
+        case 1: return 19 * c2 - 30;
+        case 2: return (21 * c2 * c2 - 53 * c2 + 24) / 2;
+        case 3: return x;
+        case 4: return (5 * c2 - 9) * x;
+        case 5: return y;
+        case 6: return (5 * c2 - 9) * y;
+        case 7: return z;
+        case 8: return (5 * c2 - 9) * z;
+        case 9: return 3 * x * x - c2;
+        case 10: return (3 * c2 - 5) * (3 * x * x - c2);
+        case 11: return y * y - z * z;
+        case 12: return (3 * c2 - 5) * (y * y - z * z);
+        case 13: return x * y;
+        case 14: return y * z;
+        case 15: return x * z;
+        case 16: return (y * y - z * z) * x;
+        case 17: return (z * z - x * x) * y;
+        default: return (x * x - y * y) * z;
     }
 }
 
-static cudaError_t upload_tables() {
-    double M[Q * Q], Mi[Q * Q], w[Q];
-    float Mf[Q * Q], Mif[Q * Q], wf[Q];
-    int opp[Q];
-    for (int k = 0; k < Q; ++k) {
-        double n2 = 0.0;
-        for (int i = 0; i < Q; ++i) {
-            M[k * Q + i] = host_basis(k, kE[i][0], kE[i][1], kE[i][2]);
-            n2 += M[k * Q + i] * M[k * Q + i];
+__host__ __device__ constexpr int mnorm2(int k) {
+    int s = 0;
+    for (int i = 0; i < Q; ++i) s += mcoef(k, i) * mcoef(k, i);
+    return s;
+}
+
+constexpr bool tables_agree() {
+    for (int i = 0; i < Q; ++i)
+        for (int a = 0; a < 3; ++a)
+            if (vel(i, a) != kE[i][a]) return false;
+    for (int k = 0; k < Q; ++k)            // orthogonal rows
+        for (int l = 0; l < k; ++l) {
+            int d = 0;
+            for (int i = 0; i < Q; ++i) d += mcoef(k, i) * mcoef(l, i);
+            if (d != 0) return false;
         }
-        for (int i = 0; i < Q; ++i) Mi[i * Q + k] = M[k * Q + i] / n2;   // rows are orthogonal
-    }
-    for (int i = 0; i < Q; ++i) {
-        const int c2 = kE[i][0] * kE[i][0] + kE[i][1] * kE[i][1] + kE[i][2] * kE[i][2];
-        w[i] = c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
-        wf[i] = (float)w[i];
-        for (int k = 0; k < Q; ++k)
-            if (kE[k][0] == -kE[i][0] && kE[k][1] == -kE[i][1] && kE[k][2] == -kE[i][2]) opp[i] = k;
-    }
-    for (int k = 0; k < Q * Q; ++k) {
-        Mf[k] = (float)M[k];
-        Mif[k] = (float)Mi[k];
-    }
-    cudaError_t e;
-    if ((e = cudaMemcpyToSymbol(cE, kE, sizeof(kE))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(cOpp, opp, sizeof(opp))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(cWd, w, sizeof(w))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(cWf, wf, sizeof(wf))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(cMd, M, sizeof(M))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(cMid, Mi, sizeof(Mi))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(cMf, Mf, sizeof(Mf))) != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(cMif, Mif, sizeof(Mif));
+    return true;
+}
+static_assert(tables_agree(), "velocity table and moment basis disagree");
+
+template <typename T>
+__host__ __device__ constexpr T weight(int i) {
+    return i == 0 ? (T)1 / (T)3 : (i <= 6 ? (T)1 / (T)18 : (T)1 / (T)36);
 }
 
-template <typename T> struct Tab;
-template <> struct Tab<double> {
-    __device__ static double w(int i) { return cWd[i]; }
-    __device__ static double M(int k) { return cMd[k]; }
-    __device__ static double Mi(int k) { return cMid[k]; }
-};
-template <> struct Tab<float> {
-    __device__ static float w(int i) { return cWf[i]; }
-    __device__ static float M(int k) { return cMf[k]; }
-    __device__ static float Mi(int k) { return cMif[k]; }
-};
+// Transforms with compile-time coefficients: index sequences over the rows and the
+// columns, `if constexpr` on each coefficient (zeros skipped, +-1 as adds), so no
+// coefficient is looked up or tested while the kernel runs.
+template <int K, int I, typename T>
+__device__ __forceinline__ void row_acc(T& a, const T* v) {
+    if constexpr (I < Q) {
+        constexpr int c = mcoef(K, I);
+        if constexpr (c == 1) a += v[I];
+        else if constexpr (c == -1) a -= v[I];
+        else if constexpr (c != 0) a += (T)c * v[I];
+        row_acc<K, I + 1>(a, v);
+    }
+}
+
+template <int I, int K, typename T>
+__device__ __forceinline__ void col_acc(T& a, const T* v) {
+    if constexpr (K < Q) {
+        constexpr int c = mcoef(K, I);
+        if constexpr (c == 1) a += v[K];
+        else if constexpr (c == -1) a -= v[K];
+        else if constexpr (c != 0) a += (T)c * v[K];
+        col_acc<I, K + 1>(a, v);
+    }
+}
+
+// out_k = sum_i M_ki v_i
+template <typename T, int... K>
+__device__ __forceinline__ void to_moments(const T* v, T* out, std::integer_sequence<int, K...>) {
+    ((out[K] = (T)0, row_acc<K, 0>(out[K], v)), ...);
+}
+
+// out_i = sum_k M_ki v_k / |row k|^2 (v is scaled in place first)
+template <typename T, int... K>
+__device__ __forceinline__ void from_moments(T* v, T* out, std::integer_sequence<int, K...>) {
+    ((v[K] *= (T)1 / (T)mnorm2(K)), ...);
+    ((out[K] = (T)0, col_acc<K, 0>(out[K], v)), ...);
+}
+
+// Eq. (6) for every direction: F_i = w_i [3 (e_i - u) + 9 (e_i . u) e_i] . F
+template <int I, typename T>
+__device__ __forceinline__ T guo_one(const T* u, const T* F) {
+    constexpr int ex = vel(I, 0), ey = vel(I, 1), ez = vel(I, 2);
+    const T eu = (T)ex * u[0] + (T)ey * u[1] + (T)ez * u[2];
+    const T s = ((T)3 * ((T)ex - u[0]) + (T)9 * eu * (T)ex) * F[0] +
+                ((T)3 * ((T)ey - u[1]) + (T)9 * eu * (T)ey) * F[1] +
+                ((T)3 * ((T)ez - u[2]) + (T)9 * eu * (T)ez) * F[2];
+    return weight<T>(I) * s;
+}
+
+template <typename T, int... I>
+__device__ __forceinline__ void guo_all(const T* u, const T* F, T* out, std::integer_sequence<int, I...>) {
+    ((out[I] = guo_one<I>(u, F)), ...);
+}
+
+using Seq = std::make_integer_sequence<int, 19>;
 
 struct Geo {
     int nx, ny, nz;
@@ -137,8 +184,8 @@ __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >
 // neighbour (x + e) for the gradient stencils: periodic x, z; y periodic or mirrored
 // about the wall (mirror = true when the ghost is a mirror image)
 __device__ __forceinline__ long long neighbour(const Geo& g, int x, int y, int z, int i, bool& mirror) {
-    const int xn = wrapi(x + cE[i][0], g.nx), zn = wrapi(z + cE[i][2], g.nz);
-    int yn = y + cE[i][1];
+    const int xn = wrapi(x + vel(i, 0), g.nx), zn = wrapi(z + vel(i, 2), g.nz);
+    int yn = y + vel(i, 1);
     mirror = false;
     if (g.walls) {
         if (yn < 0) { yn = -1 - yn; mirror = true; }
@@ -159,9 +206,9 @@ __global__ void v3_moments(const T* __restrict__ f, const T* __restrict__ phi, T
     for (int i = 0; i < Q; ++i) {
         const T v = f[i * g.N + c];
         m0 += v;
-        jx += (T)cE[i][0] * v;
-        jy += (T)cE[i][1] * v;
-        jz += (T)cE[i][2] * v;
+        jx += (T)vel(i, 0) * v;
+        jy += (T)vel(i, 1) * v;
+        jz += (T)vel(i, 2) * v;
     }
     rho[c] = m0 / phi[c];
     j[c] = jx;
@@ -182,10 +229,10 @@ __global__ void v3_velocity(const T* __restrict__ rho, const T* __restrict__ j, 
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         bool mir;
-        const T v = (T)3 * Tab<T>::w(i) * rho[neighbour(g, x, y, z, i, mir)];
-        gr[0] += (T)cE[i][0] * v;
-        gr[1] += (T)cE[i][1] * v;
-        gr[2] += (T)cE[i][2] * v;
+        const T v = (T)3 * weight<T>(i) * rho[neighbour(g, x, y, z, i, mir)];
+        gr[0] += (T)vel(i, 0) * v;
+        gr[1] += (T)vel(i, 1) * v;
+        gr[2] += (T)vel(i, 2) * v;
     }
     const T ph = phi[c], r = rho[c];
     const T G[3] = {gx, gy, gz};
@@ -226,16 +273,6 @@ __device__ __forceinline__ void equilibrium_moments(T kappa, T phi, T rho, const
     m[18] = 0;
 }
 
-// Eq. (6): F_i = w_i [3 (e_i - u) + 9 (e_i . u) e_i] . F
-template <typename T>
-__device__ __forceinline__ T guo(int i, const T* u, const T* F) {
-    const T eu = (T)cE[i][0] * u[0] + (T)cE[i][1] * u[1] + (T)cE[i][2] * u[2];
-    T s = 0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) s += ((T)3 * ((T)cE[i][a] - u[a]) + (T)9 * eu * (T)cE[i][a]) * F[a];
-    return Tab<T>::w(i) * s;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(128) v3_collide(const T* __restrict__ f, T* __restrict__ fo,
                                                    const T* __restrict__ rho, const T* __restrict__ u,
@@ -248,17 +285,17 @@ __global__ void __launch_bounds__(128) v3_collide(const T* __restrict__ f, T* __
     const T kappa = R.kappa;
     // gradients of A = rho u (diagonal), B = u (all nine), D = phi rho u (diagonal)
     T dA[3] = {0, 0, 0}, dD[3] = {0, 0, 0}, dB[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll 2
+#pragma unroll
     for (int i = 1; i < Q; ++i) {
         bool mir;
         const long long n = neighbour(g, x, y, z, i, mir);
         const T sg = mir ? (T)-1 : (T)1;
         const T rn = rho[n], pn = phi[n];
         const T un[3] = {sg * u[n], sg * u[g.N + n], sg * u[2 * g.N + n]};
-        const T wv = (T)3 * Tab<T>::w(i);
+        const T wv = (T)3 * weight<T>(i);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const T ca = wv * (T)cE[i][a];
+            const T ca = wv * (T)vel(i, a);
             dA[a] += ca * rn * un[a];
             dD[a] += ca * pn * rn * un[a];
 #pragma unroll
@@ -287,35 +324,29 @@ __global__ void __launch_bounds__(128) v3_collide(const T* __restrict__ f, T* __
     }
     T fl[Q], Fi[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        fl[i] = f[i * g.N + c];
-        Fi[i] = guo<T>(i, uc, Fc);
-    }
-    T meq[Q];
+    for (int i = 0; i < Q; ++i) fl[i] = f[i * g.N + c];
+    guo_all<T>(uc, Fc, Fi, Seq{});
+    T meq[Q], m[Q], S[Q];
     equilibrium_moments<T>(kappa, ph, r, uc, meq);
+    to_moments<T>(fl, m, Seq{});
+    to_moments<T>(Fi, S, Seq{});
     T mp[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        T m = 0, S = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            m += Tab<T>::M(k * Q + i) * fl[i];
-            S += Tab<T>::M(k * Q + i) * Fi[i];
-        }
         const T s = R.s[k];
-        mp[k] = m - s * (m - meq[k]) + ((T)1 - (T)0.5 * s) * (S + C[k]);
+        mp[k] = m[k] - s * (m[k] - meq[k]) + ((T)1 - (T)0.5 * s) * (S[k] + C[k]);
     }
+    T fp[Q];
+    from_moments<T>(mp, fp, Seq{});
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        T v = 0;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) v += Tab<T>::Mi(i * Q + k) * mp[k];
+        const T v = fp[i];
         // push: f+_i(x) -> f_i(x + e_i); a link into a y wall returns as f_opp(x)
-        const int yd = y + cE[i][1];
+        const int yd = y + vel(i, 1);
         if (g.walls && (yd < 0 || yd >= g.ny)) {
-            fo[cOpp[i] * g.N + c] = v;
+            fo[opp(i) * g.N + c] = v;
         } else {
-            const int xd = wrapi(x + cE[i][0], g.nx), zd = wrapi(z + cE[i][2], g.nz);
+            const int xd = wrapi(x + vel(i, 0), g.nx), zd = wrapi(z + vel(i, 2), g.nz);
             fo[i * g.N + ((long long)zd * g.ny + wrapi(yd, g.ny)) * g.nx + xd] = v;
         }
     }
@@ -329,14 +360,13 @@ __global__ void v3_init(T* __restrict__ f, const T* __restrict__ rho, const T* _
     if (c >= g.N) return;
     const T uc[3] = {u[c], u[g.N + c], u[2 * g.N + c]};
     const T Fc[3] = {F[c], F[g.N + c], F[2 * g.N + c]};
-    T meq[Q];
+    T meq[Q], fe[Q], Fi[Q];
     equilibrium_moments<T>(kappa, phi[c], rho[c], uc, meq);
+    from_moments<T>(meq, fe, Seq{});
+    guo_all<T>(uc, Fc, Fi, Seq{});
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        T v = 0;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) v += Tab<T>::Mi(i * Q + k) * meq[k];
-        f[i * g.N + c] = v - (T)0.5 * guo<T>(i, uc, Fc);
+        f[i * g.N + c] = fe[i] - (T)0.5 * Fi[i];
     }
 }
 
@@ -349,10 +379,12 @@ __global__ void v3_force(const T* __restrict__ rho, const T* __restrict__ phi, c
     int x, y, z;
     decode(g, c, x, y, z);
     T gr[3] = {0, 0, 0};
+#pragma unroll
     for (int i = 1; i < Q; ++i) {
         bool mir;
-        const T v = (T)3 * Tab<T>::w(i) * rho[neighbour(g, x, y, z, i, mir)];
-        for (int a = 0; a < 3; ++a) gr[a] += (T)cE[i][a] * v;
+        const T v = (T)3 * weight<T>(i) * rho[neighbour(g, x, y, z, i, mir)];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gr[a] += (T)vel(i, a) * v;
     }
     const T ph = phi[c], G[3] = {gx, gy, gz};
     for (int a = 0; a < 3; ++a) F[a * g.N + c] = (kappa - ph) / (T)3 * gr[a] + ph * G[a] + (fb ? fb[a * g.N + c] : (T)0);
@@ -370,12 +402,13 @@ __global__ void v3_reduce(const T* __restrict__ f, long long N, double* __restri
     __shared__ double sh[4][256];
     double s[4] = {0, 0, 0, 0};
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+#pragma unroll
         for (int i = 0; i < Q; ++i) {
             const double v = (double)f[i * N + c];
             s[0] += v;
-            s[1] += cE[i][0] * v;
-            s[2] += cE[i][1] * v;
-            s[3] += cE[i][2] * v;
+            s[1] += vel(i, 0) * v;
+            s[2] += vel(i, 1) * v;
+            s[3] += vel(i, 2) * v;
         }
     for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = s[q];
     __syncthreads();
@@ -530,12 +563,7 @@ extern "C" lbm_status lbm_vanse3d_create(const lbm_vanse3d_params* p, void* stre
     const double s[Q] = {1.0, s_e, p->s_eps, 1.0, p->s_q, 1.0, p->s_q, 1.0, p->s_q, s_nu,
                          p->s_pi, s_nu, p->s_pi, s_nu, s_nu, s_nu, p->s_m, p->s_m, p->s_m};
     for (int k = 0; k < Q; ++k) h->s[k] = s[k];
-    cudaError_t e = upload_tables();
-    if (e != cudaSuccess) {
-        fail3(nullptr, LBM_ERR_CUDA, "constant tables: %s", cudaGetErrorString(e));
-        delete h;
-        return LBM_ERR_CUDA;
-    }
+    cudaError_t e;
     struct A { void** p; size_t b; } allocs[] = {
         {&h->f[0], Q * N * h->tb}, {&h->f[1], Q * N * h->tb}, {&h->phi, N * h->tb}, {&h->phin, N * h->tb},
         {&h->fb, 3 * N * h->tb}, {&h->rho, N * h->tb}, {&h->j, 3 * N * h->tb}, {&h->u, 3 * N * h->tb},
