@@ -273,25 +273,58 @@ __device__ __forceinline__ void equilibrium_moments(T kappa, T phi, T rho, const
     m[18] = 0;
 }
 
+// the collision's tile: 32 x 2 x 2 cells (one thread each) and a one-cell halo
+constexpr int TX = 32, TY = 2, TZ = 2, HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HN = HX * HY * HZ;
+
+__device__ __forceinline__ int modp(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(128) v3_collide(const T* __restrict__ f, T* __restrict__ fo,
-                                                   const T* __restrict__ rho, const T* __restrict__ u,
-                                                   const T* __restrict__ F, const T* __restrict__ phi,
-                                                   const T* __restrict__ phin, Rates<T> R, Geo g) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.N) return;
-    int x, y, z;
-    decode(g, c, x, y, z);
+__global__ void __launch_bounds__(TX * TY * TZ) v3_collide(const T* __restrict__ f, T* __restrict__ fo,
+                                                           const T* __restrict__ rho, const T* __restrict__ u,
+                                                           const T* __restrict__ F, const T* __restrict__ phi,
+                                                           const T* __restrict__ phin, Rates<T> R, Geo g) {
+    // rho, phi and u of the tile and its halo, staged once: the wall ghosts are
+    // mirrored here (u with its sign changed), periodic axes wrap
+    __shared__ T s_r[HN], s_p[HN], s_u[3][HN];
+    const int nbx = (g.nx + TX - 1) / TX, nby = (g.ny + TY - 1) / TY;
+    const int bx = (int)(blockIdx.x % nbx), by = (int)((blockIdx.x / nbx) % nby), bz = (int)(blockIdx.x / (nbx * nby));
+    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+    for (int q = threadIdx.x; q < HN; q += TX * TY * TZ) {
+        const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
+        const int gx = modp(x0 - 1 + hx, g.nx), gz = modp(z0 - 1 + hz, g.nz);
+        int gy = y0 - 1 + hy;
+        T sg = 1;
+        if (g.walls) {
+            if (gy < 0) { gy = -1 - gy; sg = -1; }
+            else if (gy >= g.ny) { gy = 2 * g.ny - 1 - gy; sg = -1; }
+            gy = gy < 0 ? 0 : (gy >= g.ny ? g.ny - 1 : gy);   // beyond one ghost: only idle threads read it
+        } else {
+            gy = modp(gy, g.ny);
+        }
+        const long long n = ((long long)gz * g.ny + gy) * g.nx + gx;
+        s_r[q] = rho[n];
+        s_p[q] = phi[n];
+        s_u[0][q] = sg * u[n];
+        s_u[1][q] = sg * u[g.N + n];
+        s_u[2][q] = sg * u[2 * g.N + n];
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+    if (x >= g.nx || y >= g.ny || z >= g.nz) return;
+    const long long c = ((long long)z * g.ny + y) * g.nx + x;
+    const int hc = ((tz + 1) * HY + (ty + 1)) * HX + (tx + 1);
     const T kappa = R.kappa;
     // gradients of A = rho u (diagonal), B = u (all nine), D = phi rho u (diagonal)
     T dA[3] = {0, 0, 0}, dD[3] = {0, 0, 0}, dB[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        bool mir;
-        const long long n = neighbour(g, x, y, z, i, mir);
-        const T sg = mir ? (T)-1 : (T)1;
-        const T rn = rho[n], pn = phi[n];
-        const T un[3] = {sg * u[n], sg * u[g.N + n], sg * u[2 * g.N + n]};
+        const int hn = hc + (vel(i, 2) * HY + vel(i, 1)) * HX + vel(i, 0);
+        const T rn = s_r[hn], pn = s_p[hn];
+        const T un[3] = {s_u[0][hn], s_u[1][hn], s_u[2][hn]};
         const T wv = (T)3 * weight<T>(i);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -302,8 +335,8 @@ __global__ void __launch_bounds__(128) v3_collide(const T* __restrict__ f, T* __
             for (int b = 0; b < 3; ++b) dB[3 * a + b] += ca * un[b];
         }
     }
-    const T ph = phi[c], r = rho[c];
-    const T uc[3] = {u[c], u[g.N + c], u[2 * g.N + c]};
+    const T ph = s_p[hc], r = s_r[hc];
+    const T uc[3] = {s_u[0][hc], s_u[1][hc], s_u[2][hc]};
     const T Fc[3] = {F[c], F[g.N + c], F[2 * g.N + c]};
     const T X = kappa / ph, kp = kappa - ph;
     const T dtphi = phin ? phin[c] - ph : (T)0;
@@ -501,14 +534,14 @@ static Rates<T> rates(const lbm_vanse3d* h) {
 template <typename T>
 static void enqueue_step(lbm_vanse3d* h) {
     const Geo& g = h->geo;
-    const unsigned nb = blocks_for(g.N, 128);
+    const unsigned nb = (unsigned)(((g.nx + TX - 1) / TX) * (long long)((g.ny + TY - 1) / TY) * ((g.nz + TZ - 1) / TZ));
     const T* src = (const T*)h->f[h->cur];
     T* dst = (T*)h->f[1 - h->cur];
     v3_moments<T><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(src, (const T*)h->phi, (T*)h->rho, (T*)h->j, g);
     v3_velocity<T><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(
         (const T*)h->rho, (const T*)h->j, (const T*)h->phi, h->fb_set ? (const T*)h->fb : nullptr, (T)h->g[0],
         (T)h->g[1], (T)h->g[2], (T)h->prm.kappa, (T*)h->u, (T*)h->F, g);
-    v3_collide<T><<<nb, 128, 0, h->stream>>>(src, dst, (const T*)h->rho, (const T*)h->u, (const T*)h->F,
+    v3_collide<T><<<nb, TX * TY * TZ, 0, h->stream>>>(src, dst, (const T*)h->rho, (const T*)h->u, (const T*)h->F,
                                                (const T*)h->phi, h->phin_set ? (const T*)h->phin : nullptr,
                                                rates<T>(h), g);
 }
@@ -587,23 +620,34 @@ extern "C" lbm_status lbm_vanse3d_set_void_fraction(lbm_vanse3d_t h, const doubl
     if (!phi_t) return fail3(h, LBM_ERR_ARG, "phi_t is NULL");
     const long long N = h->geo.N;
     const double* srcs[2] = {phi_t, phi_next};
-    void* dsts[2] = {h->phi, h->phin};
+    const double* staged[2] = {nullptr, nullptr};
+    double* owned[2] = {nullptr, nullptr};
+    // stage and check both fields before either replaces the lattice's own
+    lbm_status st = LBM_OK;
     CK3(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->stream));
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 2 && st == LBM_OK; ++k) {
         if (!srcs[k]) continue;
-        const double* d;
-        double* owned;
-        lbm_status st = stage_in3(h, srcs[k], N, on_device, &d, &owned);
-        if (st != LBM_OK) return st;
-        v3_check_phi<<<blocks_for(N, 256) < 2048 ? blocks_for(N, 256) : 2048, 256, 0, h->stream>>>(d, N, h->bad);
-        convert_in(h, d, dsts[k], N);
-        if (owned) CK3(h, cudaFreeAsync(owned, h->stream));
+        st = stage_in3(h, srcs[k], N, on_device, &staged[k], &owned[k]);
+        if (st == LBM_OK)
+            v3_check_phi<<<blocks_for(N, 256) < 2048 ? blocks_for(N, 256) : 2048, 256, 0, h->stream>>>(staged[k], N,
+                                                                                                     h->bad);
     }
     int bad = 0;
-    CK3(h, cudaMemcpyAsync(&bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK3(h, cudaStreamSynchronize(h->stream));
+    if (st == LBM_OK) {
+        cudaError_t e = cudaMemcpyAsync(&bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) st = fail3(h, LBM_ERR_CUDA, "void fraction check: %s", cudaGetErrorString(e));
+        else if (bad) st = fail3(h, LBM_ERR_ARG, "void fraction outside (0, 1]");
+    }
+    if (st == LBM_OK) {
+        convert_in(h, staged[0], h->phi, N);
+        if (staged[1]) convert_in(h, staged[1], h->phin, N);
+    }
+    for (double* o : owned)
+        if (o) cudaFreeAsync(o, h->stream);
+    if (st != LBM_OK) return st;
     CK3(h, cudaGetLastError());
-    if (bad) return fail3(h, LBM_ERR_ARG, "void fraction outside (0, 1]");
     h->phi_set = true;
     h->phin_set = phi_next != nullptr;
     return LBM_OK;

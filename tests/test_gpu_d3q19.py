@@ -177,3 +177,33 @@ def test_full_size_channel_step_on_sampled_windows(P):
     m0, _ = lat.reduce()
     assert np.isfinite(m0)
     lat.close()
+
+
+def test_error_paths(P):
+    """Invalid calls return an error status and leave the handle usable."""
+    from paper_2409_02964_gb300.lattice import LbmError
+    n = 4
+    lat = P.Lattice3D(n, n, n, storage="fp64")
+    with pytest.raises(LbmError, match="STATE"):
+        lat.step(1)                                   # before init
+    with pytest.raises(LbmError, match="STATE"):
+        lat.init_fields(np.ones((n, n, n)), np.zeros((3, n, n, n)))   # before phi
+    bad = np.full((n, n, n), 0.8)
+    bad[1, 2, 3] = 0.0
+    with pytest.raises(LbmError, match="ARG"):
+        lat.set_void_fraction(bad)
+    bad[1, 2, 3] = 1.5
+    with pytest.raises(LbmError, match="ARG"):
+        lat.set_void_fraction(bad)
+    lat.set_void_fraction(np.full((n, n, n), 0.8))
+    lat.init_fields(np.ones((n, n, n)), np.zeros((3, n, n, n)))
+    with pytest.raises(LbmError, match="ARG"):
+        lat.set_void_fraction(bad)                     # rejected: the lattice keeps phi = 0.8
+    with pytest.raises(LbmError, match="ARG"):
+        lat.step(-1)
+    lat.step(0)
+    lat.step(3)
+    m, j = lat.reduce()
+    assert abs(m - 0.8 * n ** 3) < 1e-12 and max(abs(x) for x in j) < 1e-14
+    assert lat.step_count == 3
+    lat.close()
