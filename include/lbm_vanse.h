@@ -92,6 +92,8 @@ lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_va
  * d_t phi = phi(t+1) - phi(t), Sec. 2.3). phi_next = NULL means steady. After a
  * step, phi(t) takes the value of phi(t+1) and the field is steady until the next
  * call. Values must lie in (0, 1]. Must be called before lbm_vanse_init_fields.
+ * A new phi(t) keeps the populations the steps left (FP32/FP16/BF16 move their
+ * stored f_0 deviation to the new rest value; FP16/BF16 round it again).
  * Host arrays in pinned (page-locked) memory are copied on a stream of the
  * library's own, so the copy overlaps the steps still queued on the lattice's
  * stream; the call returns once the arrays have been read, as for any host array. */

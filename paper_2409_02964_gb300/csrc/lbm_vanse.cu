@@ -533,6 +533,29 @@ lbm_status pad_into(lbm_vanse* h, const T* dev_src, void* dst, int* zero_seen = 
     return LBM_OK;
 }
 
+template <typename T, typename S>
+lbm_status rebase_pad(lbm_vanse* h, const T* dev_src) {
+    using R = typename Prec<S>::R;
+    const int blocks = std::min(h->prm.ny, 65535);
+    pad_phi_rebase_kernel<T, R, S><<<blocks, kAuxThreads, 0, h->stream>>>(
+        dev_src, (R*)h->phi, (S*)h->f[h->cur], h->prm.nx, h->prm.ny, h->P, (R)(h->prm.rho0 * h->scale), h->zero_phi);
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
+// phi(t) into the lattice: a plain copy while no populations are stored (or they are
+// FP64, stored as they are); otherwise the copy that also keeps the populations
+// (pad_phi_rebase_kernel).
+template <typename T>
+lbm_status put_phi_t(lbm_vanse* h, const T* dev_src) {
+    if (!h->initialised || h->prm.storage == LBM_FP64) return pad_into<T>(h, dev_src, h->phi, h->zero_phi);
+    switch (h->prm.storage) {
+        case LBM_FP32: return rebase_pad<T, float>(h, dev_src);
+        case LBM_FP16: return rebase_pad<T, __half>(h, dev_src);
+        default: return rebase_pad<T, __nv_bfloat16>(h, dev_src);
+    }
+}
+
 // Upload of phi(t) [and phi(t+1)] from pinned host arrays: the copies run on the
 // copy stream into the staging buffers, overlapping whatever `stream` is still
 // executing (e.g. the previous step); the call returns once the caller's arrays
@@ -556,7 +579,7 @@ lbm_status upload_void_fraction_pinned(lbm_vanse* h, const T* phi_t, const T* ph
     CK(h, cudaEventSynchronize(h->copy_done));
     CK(h, cudaStreamWaitEvent(h->stream, h->copy_done, 0));
     CK(h, cudaMemsetAsync(h->zero_phi, 0, sizeof(int), h->stream));
-    lbm_status st = pad_into<T>(h, (const T*)h->staging[0], h->phi, h->zero_phi);
+    lbm_status st = put_phi_t<T>(h, (const T*)h->staging[0]);
     if (st == LBM_OK && phi_next) st = pad_into<T>(h, (const T*)h->staging[1], h->phin, h->zero_phi);
     if (st != LBM_OK) return st;
     CK(h, cudaEventRecord(h->staging_free, h->stream));
@@ -581,7 +604,7 @@ lbm_status set_void_fraction_impl(lbm_vanse* h, const T* phi_t, const T* phi_nex
     CK(h, cudaMemsetAsync(h->zero_phi, 0, sizeof(int), h->stream));
     lbm_status st = stage_in<T>(h, phi_t, n, on_device, &d, &owned);
     if (st != LBM_OK) return st;
-    st = pad_into<T>(h, d, h->phi, h->zero_phi);
+    st = put_phi_t<T>(h, d);
     if (owned) cudaFreeAsync(d, h->stream);
     if (st != LBM_OK) return st;
     h->unsteady = false;

@@ -88,6 +88,34 @@ __global__ void pad_field_kernel(const Tin* __restrict__ src, R* __restrict__ ds
     if (zero_seen && zero) *zero_seen = 1;
 }
 
+// Replace phi(t) of a lattice that already holds FP32/FP16/BF16 populations. Those
+// store f_0 as a deviation from the rest value (phi - 5 kappa / 9) rho0 of the
+// lattice's current phi, so where phi changes the stored deviation moves by
+// (phi_old - phi_new) rho0 (times the storage scale) and the populations themselves
+// stay as they are, as with FP64 storage. Cells whose phi is unchanged are not
+// written. Each thread reads only its interior cell and writes that cell and its
+// ghost images.
+template <typename Tin, typename R, typename S>
+__global__ void pad_phi_rebase_kernel(const Tin* __restrict__ src, R* __restrict__ phi, S* __restrict__ plane0,
+                                      int nx, int ny, int P, R rho0_scaled, int* __restrict__ zero_seen) {
+    bool zero = false;
+    for (int y = blockIdx.x; y < ny; y += gridDim.x) {
+        const Tin* row = src + (long long)y * nx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const R v = (R)row[x];
+            zero = zero || v == (R)0;
+            const long long o = cell_off(P, x, y);
+            const R old = phi[o];
+            if (old != v) {
+                const R d = dec(plane0[o], (R)0, (R)1) + (old - v) * rho0_scaled;
+                put_with_ghosts<S>(plane0, P, nx, x, y, enc<S, R>(d, (R)0, (R)1));
+                put_with_ghosts<R>(phi, P, nx, x, y, v);
+            }
+        }
+    }
+    if (zero_seen && zero) *zero_seen = 1;
+}
+
 // Pull the post-streaming populations of cell (x, y) from the stored planes.
 // With solid cells: a solid cell has no populations (zeros), and a population whose
 // source cell is solid comes back from the half-way link (opposite slot, same cell).
