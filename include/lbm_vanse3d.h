@@ -41,7 +41,9 @@
  * order e_0 = 0; e_1..e_6 = +x, -x, +y, -y, +z, -z; e_7..e_10 = (1,1,0), (-1,-1,0),
  * (1,-1,0), (-1,1,0); e_11..e_14 = (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1);
  * e_15..e_18 = (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1). The library stores the
- * populations as the same SoA planes in the precision chosen at creation.
+ * populations as the same SoA planes in the precision chosen at creation, as
+ * deviations from the rest state (w_i kappa rho0 for i >= 1, (phi - 2 kappa / 3) rho0
+ * for i = 0); callers always see the populations themselves.
  */
 #ifndef LBM_VANSE3D_H
 #define LBM_VANSE3D_H
@@ -92,7 +94,8 @@ void lbm_vanse3d_destroy(lbm_vanse3d_t h);
 /* phi(x, t) and optionally phi(x, t+1) (each nx ny nz doubles, every value in (0, 1]).
  * With phi_next the next step takes d_t phi = phi_next - phi_t and afterwards
  * phi(t) <- phi_next (steady again); NULL phi_next means steady. Required before
- * init_fields. LBM_ERR_ARG for a NULL phi_t or a value outside (0, 1]. */
+ * init_fields. A new phi(t) keeps the populations the steps left. LBM_ERR_ARG for a
+ * NULL phi_t or a value outside (0, 1] (the lattice keeps its previous phi). */
 lbm_status lbm_vanse3d_set_void_fraction(lbm_vanse3d_t h, const double* phi_t, const double* phi_next,
                                          int on_device);
 

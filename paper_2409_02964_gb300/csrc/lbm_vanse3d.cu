@@ -10,8 +10,12 @@
 //                source, m = M f, the relaxation of Eq. (16) with the equilibrium and
 //                Guo force moments, f+ = M^-1 m+, and push streaming (periodic x, z;
 //                periodic or half-way bounce-back in y).
-// The population buffers hold post-streaming values, [19][nz][ny][nx] planes in the
-// storage type T (double or float), which is also the compute type. Next to a wall
+// The population buffers hold post-streaming deviations from the rest state,
+// d_i = f_i - f_i^rest with f_i^rest = w_i kappa rho0 (i >= 1) and (phi - 2 kappa / 3) rho0
+// (i = 0, phi of the lattice's current time level: the rest equilibrium of Eq. (14) on
+// D3Q19), as [19][nz][ny][nx] planes in the storage type T (double or float), which is
+// also the compute type; the density scratch holds rho - rho0. Every rounding then
+// sits at the scale of the deviations rather than of the populations. Next to a wall
 // the gradient stencils read a ghost cell mirrored about it (scalars keep the mirror
 // value, vector components change sign).
 #include <cuda_runtime.h>
@@ -169,7 +173,7 @@ struct Geo {
 
 template <typename T> struct Rates {
     T s[Q];
-    T kappa;
+    T kappa, rho0;
 };
 
 __device__ __forceinline__ void decode(const Geo& g, long long c, int& x, int& y, int& z) {
@@ -219,7 +223,7 @@ __global__ void v3_moments(const T* __restrict__ f, const T* __restrict__ phi, T
 // F = (kappa - phi)/3 grad rho + phi G + field, u = (j + F/2) / (phi rho)
 template <typename T>
 __global__ void v3_velocity(const T* __restrict__ rho, const T* __restrict__ j, const T* __restrict__ phi,
-                            const T* __restrict__ fb, T gx, T gy, T gz, T kappa, T* __restrict__ u,
+                            const T* __restrict__ fb, T gx, T gy, T gz, T kappa, T rho0, T* __restrict__ u,
                             T* __restrict__ F, Geo g) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
@@ -236,7 +240,7 @@ __global__ void v3_velocity(const T* __restrict__ rho, const T* __restrict__ j, 
     }
     const T ph = phi[c], r = rho[c];
     const T G[3] = {gx, gy, gz};
-    const T m0 = ph * r;
+    const T m0 = ph * (rho0 + r);   // r = rho - rho0
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         T Fa = (kappa - ph) / (T)3 * gr[a] + ph * G[a];
@@ -271,6 +275,17 @@ __device__ __forceinline__ void equilibrium_moments(T kappa, T phi, T rho, const
     m[16] = 0;
     m[17] = 0;
     m[18] = 0;
+}
+
+// m^eq minus the rest state's moments (rho0, u = 0): only m_0, e and eps carry a rest
+// part; drho = rho - rho0
+template <typename T>
+__device__ __forceinline__ void equilibrium_deviation(T kappa, T phi, T rho, T drho, const T* u, T* m) {
+    equilibrium_moments<T>(kappa, phi, rho, u, m);
+    const T m0u2 = phi * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    m[0] = phi * drho;
+    m[1] = (T)19 * (kappa * drho + m0u2) - (T)30 * phi * drho;
+    m[2] = (T)12 * phi * drho - (T)9 * kappa * drho - (T)5.5 * m0u2;
 }
 
 // the collision's tile: 32 x 2 x 2 cells (one thread each) and a one-cell halo
@@ -323,7 +338,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) v3_collide(const T* __restrict__
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int hn = hc + (vel(i, 2) * HY + vel(i, 1)) * HX + vel(i, 0);
-        const T rn = s_r[hn], pn = s_p[hn];
+        const T rn = R.rho0 + s_r[hn], pn = s_p[hn];
         const T un[3] = {s_u[0][hn], s_u[1][hn], s_u[2][hn]};
         const T wv = (T)3 * weight<T>(i);
 #pragma unroll
@@ -335,7 +350,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) v3_collide(const T* __restrict__
             for (int b = 0; b < 3; ++b) dB[3 * a + b] += ca * un[b];
         }
     }
-    const T ph = s_p[hc], r = s_r[hc];
+    const T ph = s_p[hc], dr = s_r[hc], r = R.rho0 + dr;
     const T uc[3] = {s_u[0][hc], s_u[1][hc], s_u[2][hc]};
     const T Fc[3] = {F[c], F[g.N + c], F[2 * g.N + c]};
     const T X = kappa / ph, kp = kappa - ph;
@@ -360,7 +375,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) v3_collide(const T* __restrict__
     for (int i = 0; i < Q; ++i) fl[i] = f[i * g.N + c];
     guo_all<T>(uc, Fc, Fi, Seq{});
     T meq[Q], m[Q], S[Q];
-    equilibrium_moments<T>(kappa, ph, r, uc, meq);
+    equilibrium_deviation<T>(kappa, ph, r, dr, uc, meq);
     to_moments<T>(fl, m, Seq{});
     to_moments<T>(Fi, S, Seq{});
     T mp[Q];
@@ -371,6 +386,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) v3_collide(const T* __restrict__
     }
     T fp[Q];
     from_moments<T>(mp, fp, Seq{});
+    fp[0] -= dtphi * R.rho0;   // f_0's rest value moves to phi(t+1)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T v = fp[i];
@@ -388,13 +404,13 @@ __global__ void __launch_bounds__(TX * TY * TZ) v3_collide(const T* __restrict__
 // f = f^eq(rho, u, phi) - F_i/2 (F from v3_velocity's force part)
 template <typename T>
 __global__ void v3_init(T* __restrict__ f, const T* __restrict__ rho, const T* __restrict__ u,
-                        const T* __restrict__ F, const T* __restrict__ phi, T kappa, Geo g) {
+                        const T* __restrict__ F, const T* __restrict__ phi, T kappa, T rho0, Geo g) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.N) return;
     const T uc[3] = {u[c], u[g.N + c], u[2 * g.N + c]};
     const T Fc[3] = {F[c], F[g.N + c], F[2 * g.N + c]};
     T meq[Q], fe[Q], Fi[Q];
-    equilibrium_moments<T>(kappa, phi[c], rho[c], uc, meq);
+    equilibrium_deviation<T>(kappa, phi[c], rho[c], rho[c] - rho0, uc, meq);
     from_moments<T>(meq, fe, Seq{});
     guo_all<T>(uc, Fc, Fi, Seq{});
 #pragma unroll
@@ -423,18 +439,47 @@ __global__ void v3_force(const T* __restrict__ rho, const T* __restrict__ phi, c
     for (int a = 0; a < 3; ++a) F[a * g.N + c] = (kappa - ph) / (T)3 * gr[a] + ph * G[a] + (fb ? fb[a * g.N + c] : (T)0);
 }
 
+// populations to / from the caller's f: out = in + sign * f_i^rest, in FP64
+template <typename Tin, typename Tout, typename T>
+__global__ void v3_pop_io(const Tin* __restrict__ a, Tout* __restrict__ b, const T* __restrict__ phi, double kappa,
+                          double rho0, double sign, long long N) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < (long long)Q * N;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k / N);
+        const double rest = i == 0 ? ((double)phi[k] - 2.0 * kappa / 3.0) * rho0
+                                   : (i <= 6 ? kappa * rho0 / 18.0 : kappa * rho0 / 36.0);
+        b[k] = (Tout)((double)a[k] + sign * rest);
+    }
+}
+
+// a new phi(t) where the lattice holds populations: f_0's rest value follows phi, so the
+// stored d_0 moves by (phi_old - phi_new) rho0 where phi changes
+template <typename T>
+__global__ void v3_rebase(const double* __restrict__ phin_src, T* __restrict__ phi, T* __restrict__ d0, T rho0,
+                          long long N) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (long long)gridDim.x * blockDim.x) {
+        const T v = (T)phin_src[k], old = phi[k];
+        if (v != old) {
+            d0[k] += (old - v) * rho0;
+            phi[k] = v;
+        }
+    }
+}
+
 template <typename Tin, typename Tout>
-__global__ void v3_convert(const Tin* __restrict__ a, Tout* __restrict__ b, long long n) {
+__global__ void v3_convert(const Tin* __restrict__ a, Tout* __restrict__ b, long long n, double offset = 0.0) {
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        b[k] = (Tout)a[k];
+        b[k] = (Tout)((double)a[k] + offset);
 }
 
 // FP64 mass and momentum sums: out[0..3] += per-block partials
 template <typename T>
-__global__ void v3_reduce(const T* __restrict__ f, long long N, double* __restrict__ out) {
+__global__ void v3_reduce(const T* __restrict__ f, const T* __restrict__ phi, double rho0, long long N,
+                          double* __restrict__ out) {
     __shared__ double sh[4][256];
     double s[4] = {0, 0, 0, 0};
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        s[0] += (double)phi[c] * rho0;   // the rest state's mass
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const double v = (double)f[i * N + c];
@@ -443,6 +488,7 @@ __global__ void v3_reduce(const T* __restrict__ f, long long N, double* __restri
             s[2] += vel(i, 1) * v;
             s[3] += vel(i, 2) * v;
         }
+    }
     for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = s[q];
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -528,6 +574,7 @@ static Rates<T> rates(const lbm_vanse3d* h) {
     Rates<T> R;
     for (int k = 0; k < Q; ++k) R.s[k] = (T)h->s[k];
     R.kappa = (T)h->prm.kappa;
+    R.rho0 = (T)h->prm.rho0;
     return R;
 }
 
@@ -540,7 +587,7 @@ static void enqueue_step(lbm_vanse3d* h) {
     v3_moments<T><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(src, (const T*)h->phi, (T*)h->rho, (T*)h->j, g);
     v3_velocity<T><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(
         (const T*)h->rho, (const T*)h->j, (const T*)h->phi, h->fb_set ? (const T*)h->fb : nullptr, (T)h->g[0],
-        (T)h->g[1], (T)h->g[2], (T)h->prm.kappa, (T*)h->u, (T*)h->F, g);
+        (T)h->g[1], (T)h->g[2], (T)h->prm.kappa, (T)h->prm.rho0, (T*)h->u, (T*)h->F, g);
     v3_collide<T><<<nb, TX * TY * TZ, 0, h->stream>>>(src, dst, (const T*)h->rho, (const T*)h->u, (const T*)h->F,
                                                (const T*)h->phi, h->phin_set ? (const T*)h->phin : nullptr,
                                                rates<T>(h), g);
@@ -641,7 +688,17 @@ extern "C" lbm_status lbm_vanse3d_set_void_fraction(lbm_vanse3d_t h, const doubl
         else if (bad) st = fail3(h, LBM_ERR_ARG, "void fraction outside (0, 1]");
     }
     if (st == LBM_OK) {
-        convert_in(h, staged[0], h->phi, N);
+        if (h->initialised) {   // keep the populations: d_0 follows the new rest value
+            const unsigned nb = blocks_for(N, 256) < 4096 ? blocks_for(N, 256) : 4096;
+            if (h->fp64)
+                v3_rebase<double><<<nb, 256, 0, h->stream>>>(staged[0], (double*)h->phi, (double*)h->f[h->cur],
+                                                             h->prm.rho0, N);
+            else
+                v3_rebase<float><<<nb, 256, 0, h->stream>>>(staged[0], (float*)h->phi, (float*)h->f[h->cur],
+                                                            (float)h->prm.rho0, N);
+        } else {
+            convert_in(h, staged[0], h->phi, N);
+        }
         if (staged[1]) convert_in(h, staged[1], h->phin, N);
     }
     for (double* o : owned)
@@ -680,7 +737,8 @@ static void enqueue_init(lbm_vanse3d* h) {
         (const T*)h->rho, (const T*)h->phi, h->fb_set ? (const T*)h->fb : nullptr, (T)h->g[0], (T)h->g[1],
         (T)h->g[2], (T)h->prm.kappa, (T*)h->F, g);
     v3_init<T><<<blocks_for(g.N, 128), 128, 0, h->stream>>>((T*)h->f[h->cur], (const T*)h->rho, (const T*)h->u,
-                                                            (const T*)h->F, (const T*)h->phi, (T)h->prm.kappa, g);
+                                                            (const T*)h->F, (const T*)h->phi, (T)h->prm.kappa,
+                                                            (T)h->prm.rho0, g);
 }
 
 extern "C" lbm_status lbm_vanse3d_init_fields(lbm_vanse3d_t h, const double* rho, const double* ux,
@@ -732,12 +790,26 @@ extern "C" lbm_status lbm_vanse3d_sync(lbm_vanse3d_t h) {
     return LBM_OK;
 }
 
-static lbm_status copy_out(lbm_vanse3d* h, const void* src, double* dst, long long n, int on_device) {
+// device values out to the caller as doubles: plus `offset`, or, for the populations
+// (pops = true), plus their rest state
+static lbm_status copy_out(lbm_vanse3d* h, const void* src, double* dst, long long n, int on_device,
+                           double offset = 0.0, bool pops = false) {
     double* d = dst;
     if (!on_device) CK3(h, cudaMallocAsync((void**)&d, n * sizeof(double), h->stream));
     const unsigned nb = blocks_for(n, 256) < 4096 ? blocks_for(n, 256) : 4096;
-    if (h->fp64) v3_convert<double, double><<<nb, 256, 0, h->stream>>>((const double*)src, d, n);
-    else v3_convert<float, double><<<nb, 256, 0, h->stream>>>((const float*)src, d, n);
+    const double k = h->prm.kappa, r0 = h->prm.rho0;
+    if (pops) {
+        if (h->fp64)
+            v3_pop_io<double, double, double><<<nb, 256, 0, h->stream>>>((const double*)src, d, (const double*)h->phi,
+                                                                         k, r0, 1.0, h->geo.N);
+        else
+            v3_pop_io<float, double, float><<<nb, 256, 0, h->stream>>>((const float*)src, d, (const float*)h->phi, k,
+                                                                       r0, 1.0, h->geo.N);
+    } else if (h->fp64) {
+        v3_convert<double, double><<<nb, 256, 0, h->stream>>>((const double*)src, d, n, offset);
+    } else {
+        v3_convert<float, double><<<nb, 256, 0, h->stream>>>((const float*)src, d, n, offset);
+    }
     CK3(h, cudaGetLastError());
     if (!on_device) {
         CK3(h, cudaMemcpyAsync(dst, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -751,7 +823,7 @@ extern "C" lbm_status lbm_vanse3d_get_populations(lbm_vanse3d_t h, double* f, in
     if (!h) return fail3(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (!f) return fail3(h, LBM_ERR_ARG, "f is NULL");
     if (!h->initialised) return fail3(h, LBM_ERR_STATE, "lattice not initialised");
-    return copy_out(h, h->f[h->cur], f, Q * h->geo.N, on_device);
+    return copy_out(h, h->f[h->cur], f, Q * h->geo.N, on_device, 0.0, true);
 }
 
 extern "C" lbm_status lbm_vanse3d_set_populations(lbm_vanse3d_t h, const double* f, int on_device) {
@@ -763,7 +835,17 @@ extern "C" lbm_status lbm_vanse3d_set_populations(lbm_vanse3d_t h, const double*
     lbm_status st = stage_in3(h, f, Q * h->geo.N, on_device, &d, &owned);
     if (st != LBM_OK) return st;
     h->cur = 0;
-    convert_in(h, d, h->f[0], Q * h->geo.N);
+    {
+        const long long n = Q * h->geo.N;
+        const unsigned nb = blocks_for(n, 256) < 4096 ? blocks_for(n, 256) : 4096;
+        const double k = h->prm.kappa, r0 = h->prm.rho0;
+        if (h->fp64)
+            v3_pop_io<double, double, double><<<nb, 256, 0, h->stream>>>(d, (double*)h->f[0], (const double*)h->phi, k,
+                                                                         r0, -1.0, h->geo.N);
+        else
+            v3_pop_io<double, float, float><<<nb, 256, 0, h->stream>>>(d, (float*)h->f[0], (const float*)h->phi, k, r0,
+                                                                       -1.0, h->geo.N);
+    }
     if (owned) CK3(h, cudaFreeAsync(owned, h->stream));
     CK3(h, cudaGetLastError());
     h->initialised = true;
@@ -781,8 +863,8 @@ extern "C" lbm_status lbm_vanse3d_macros(lbm_vanse3d_t h, double* rho, double* u
                                                                          (double*)h->j, g);
         v3_velocity<double><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(
             (const double*)h->rho, (const double*)h->j, (const double*)h->phi,
-            h->fb_set ? (const double*)h->fb : nullptr, h->g[0], h->g[1], h->g[2], h->prm.kappa, (double*)h->u,
-            (double*)h->F, g);
+            h->fb_set ? (const double*)h->fb : nullptr, h->g[0], h->g[1], h->g[2], h->prm.kappa, h->prm.rho0,
+            (double*)h->u, (double*)h->F, g);
     } else {
         v3_moments<float><<<blocks_for(g.N, 256), 256, 0, h->stream>>>((const float*)h->f[h->cur],
                                                                         (const float*)h->phi, (float*)h->rho,
@@ -790,11 +872,11 @@ extern "C" lbm_status lbm_vanse3d_macros(lbm_vanse3d_t h, double* rho, double* u
         v3_velocity<float><<<blocks_for(g.N, 256), 256, 0, h->stream>>>(
             (const float*)h->rho, (const float*)h->j, (const float*)h->phi,
             h->fb_set ? (const float*)h->fb : nullptr, (float)h->g[0], (float)h->g[1], (float)h->g[2],
-            (float)h->prm.kappa, (float*)h->u, (float*)h->F, g);
+            (float)h->prm.kappa, (float)h->prm.rho0, (float*)h->u, (float*)h->F, g);
     }
     CK3(h, cudaGetLastError());
     lbm_status st = LBM_OK;
-    if (rho) st = copy_out(h, h->rho, rho, g.N, on_device);
+    if (rho) st = copy_out(h, h->rho, rho, g.N, on_device, h->prm.rho0);   // the scratch holds rho - rho0
     if (st == LBM_OK && u) st = copy_out(h, h->u, u, 3 * g.N, on_device);
     return st;
 }
@@ -804,8 +886,12 @@ extern "C" lbm_status lbm_vanse3d_reduce(lbm_vanse3d_t h, double* mass, double* 
     if (!h->initialised) return fail3(h, LBM_ERR_STATE, "lattice not initialised");
     CK3(h, cudaMemsetAsync(h->red, 0, 4 * sizeof(double), h->stream));
     const unsigned nb = blocks_for(h->geo.N, 256) < 1024 ? blocks_for(h->geo.N, 256) : 1024;
-    if (h->fp64) v3_reduce<double><<<nb, 256, 0, h->stream>>>((const double*)h->f[h->cur], h->geo.N, h->red);
-    else v3_reduce<float><<<nb, 256, 0, h->stream>>>((const float*)h->f[h->cur], h->geo.N, h->red);
+    if (h->fp64)
+        v3_reduce<double><<<nb, 256, 0, h->stream>>>((const double*)h->f[h->cur], (const double*)h->phi, h->prm.rho0,
+                                                     h->geo.N, h->red);
+    else
+        v3_reduce<float><<<nb, 256, 0, h->stream>>>((const float*)h->f[h->cur], (const float*)h->phi, h->prm.rho0,
+                                                    h->geo.N, h->red);
     CK3(h, cudaGetLastError());
     double r[4];
     CK3(h, cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, h->stream));

@@ -207,3 +207,36 @@ def test_error_paths(P):
     assert abs(m - 0.8 * n ** 3) < 1e-12 and max(abs(x) for x in j) < 1e-14
     assert lat.step_count == 3
     lat.close()
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_new_phi_keeps_populations_and_steps_match_oracle(P, storage):
+    """The populations are stored as deviations from the rest state of the lattice's
+    current phi; a new phi(t) moves f_0's stored deviation so that the populations
+    (and the mass) stay those the steps left, as in the oracle, and the following
+    steps agree with it."""
+    nx, ny, nz = 10, 7, 6
+    c = _case(nx, ny, nz, seed=77)
+    c["phin"] = None
+    lat = _gpu(P, nx, ny, nz, c, storage, True)
+    p = _params(nx, ny, nz, True)
+    f = D.init(p, c["rho"], c["u"], c["phi"], _total_force(c))
+    for _ in range(2):
+        f = D.step(p, f, c["phi"], None, _total_force(c))
+    lat.step(2)
+    before = lat.get_populations().cpu().numpy()
+    m0, _ = lat.reduce()
+    phi2 = np.clip(c["phi"] + np.random.default_rng(1).uniform(0.0, 0.1, size=c["phi"].shape), 0.3, 1.0)
+    lat.set_void_fraction(phi2)
+    after = lat.get_populations().cpu().numpy()
+    m1, _ = lat.reduce()
+    tol = 1e-15 if storage == "fp64" else 1e-7
+    assert np.abs(after - before).max() < tol
+    assert abs(m1 - m0) < (1e-13 if storage == "fp64" else 1e-5)
+    c2 = dict(c, phi=phi2)
+    for _ in range(2):
+        f = D.step(p, f, phi2, None, _total_force(c2))
+    lat.step(2)
+    g = lat.get_populations().cpu().numpy()
+    lat.close()
+    assert np.abs(g - f).max() < (1e-13 if storage == "fp64" else 4e-6)
