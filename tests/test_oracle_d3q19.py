@@ -220,3 +220,35 @@ def test_manufactured_solution_fails_without_the_penalty_source():
     e_ok = _mms_error(12, 64, 0.02)
     e_bad = _mms_error(12, 64, 0.02, no_penalty=1)
     assert e_bad > 10 * e_ok, (e_ok, e_bad)
+
+
+@pytest.mark.parametrize("s_e", [None, 1.0])
+def test_sound_wave_damping_pins_the_3d_stress(s_e):
+    """The 3-D scheme recovers tau = rho nu (grad u + grad u^T - 2/3 div u I)
+    + 2/3 rho nu_e div u I, so a standing sound wave along x decays at
+    (4/3 nu + 2/3 nu_e) k^2 / 2 (uniform phi = 0.7 != kappa = 0.5: the penalty source
+    and F^p enter). s_e from nu_e = nu/3 (the nu_e part 14 % of the rate) and s_e = 1
+    (45 %)."""
+    n, tau = 64, 0.8
+    nu = (tau - 0.5) / 3
+    r = D.rates_from_tau(tau)
+    if s_e is not None:
+        r["s_e"] = s_e
+    nu_e = (1 / r["s_e"] - 0.5) / 3
+    p = D.Params(n, 1, 1, kappa=0.5, **r)
+    x = np.arange(n, dtype=float)[None, None, :]
+    k = 2 * np.pi / n
+    phi = np.full((1, 1, n), 0.7)
+    f = D.init(p, 1 + 1e-4 * np.cos(k * x), np.zeros((3, 1, 1, n)), phi)
+    amps, steps = [], [0, 800, 1600, 2400]
+    for t in range(steps[-1] + 1):
+        if t in steps:
+            m = D.macros(p, f, phi)
+            a_rho = 2 / n * np.sum((m["rho"] - 1) * np.cos(k * x))
+            a_u = 2 / n * np.sum(m["u"][0] * np.sin(k * x))
+            amps.append(np.sqrt(a_rho ** 2 + 3 * a_u ** 2))
+        f = D.step(p, f, phi)
+    rate = -np.polyfit(steps, np.log(amps), 1)[0]
+    expect = (4 / 3 * nu + 2 / 3 * nu_e) * k * k / 2
+    print(f"s_e {r['s_e']:.3f}: decay rate {rate:.4e}, expected {expect:.4e} ({rate / expect - 1:+.2%})")
+    assert abs(rate / expect - 1) < 0.01, (rate, expect)   # measured 0.1 %
