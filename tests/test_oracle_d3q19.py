@@ -252,3 +252,29 @@ def test_sound_wave_damping_pins_the_3d_stress(s_e):
     expect = (4 / 3 * nu + 2 / 3 * nu_e) * k * k / 2
     print(f"s_e {r['s_e']:.3f}: decay rate {rate:.4e}, expected {expect:.4e} ({rate / expect - 1:+.2%})")
     assert abs(rate / expect - 1) < 0.01, (rate, expect)   # measured 0.1 %
+
+
+def _poiseuille_error(ny, no_penalty=0, phi0=0.8, kappa=0.5, tau=0.8, g=1e-6):
+    nu = (tau - 0.5) / 3
+    p = D.Params(3, ny, 3, kappa=kappa, bc_y=1, no_penalty=no_penalty, **D.rates_from_tau(tau))
+    phi = np.full((3, ny, 3), phi0)
+    fb = np.zeros((3, 3, ny, 3))
+    fb[0] = phi0 * g
+    f = D.init(p, np.ones_like(phi), np.zeros((3, 3, ny, 3)), phi, fb)
+    for _ in range(int(8 * ny * ny / nu)):
+        f = D.step(p, f, phi, None, fb)
+    u = D.macros(p, f, phi, fb)["u"][0][0, :, 0]
+    y = np.arange(ny) + 0.5
+    want = g * y * (ny - y) / (2 * nu)
+    return float(np.abs(u - want).max() / want.max())
+
+
+def test_poiseuille_at_phi_not_kappa_converges_at_second_order():
+    """Uniform phi = 0.8 != kappa = 0.5 between the walls, F^B = phi g: Eq. (1) gives
+    the parabola g y (H - y) / (2 nu) (phi cancels); the shear penalty and the wall
+    ghost rule are active. Measured 4.8e-3 -> 1.2e-3 from ny = 8 to 16; without the
+    penalty source the profile is off by O(1)."""
+    e8, e16 = _poiseuille_error(8), _poiseuille_error(16)
+    print(f"Poiseuille phi != kappa: {e8:.3e} (ny 8), {e16:.3e} (ny 16), ratio {e8 / e16:.2f}")
+    assert 3.5 < e8 / e16 < 4.6
+    assert _poiseuille_error(8, no_penalty=1) > 10 * e8
