@@ -12,8 +12,8 @@ O(|u|^2) terms the analysis neglects. This test evaluates the right-hand side at
 point from smooth analytic fields, with the oracle's equilibrium (f^eq, m^eq) and
 force moments as the only scheme ingredients and every derivative a central
 difference, and compares it with the oracle's penalty. On D2Q9 the same machinery
-must return the printed Eq. (20); on D3Q19 it checks the penalty derived for that
-lattice. Measured residuals are 1e-14 to 2e-12 against terms of 1e-7 to 2e-2 (the
+must return the printed Eq. (20) (and, with App. B's equilibrium, the printed (B3));
+on D3Q19 it checks the penalty derived for that lattice. Measured residuals are 1e-14 to 2e-12 against terms of 1e-7 to 2e-2 (the
 smallest, the shear term, is 3e-7), so a wrong coefficient or a dropped term in any
 of them fails by orders of magnitude.
 """
@@ -91,8 +91,18 @@ def _gradients(d, x0):
     return dA, dD
 
 
+def _full_gradient(d, x0, fn_of_fields):
+    """g[a, b] = d_a V_b for the vector field V = fn_of_fields(phi, rho, u) at x0."""
+    phi, rho, u = _fields(d)
+    return np.array([_grad(lambda x, b=b: fn_of_fields(phi(x), rho(x), u(x))[b], x0, d) for b in range(d)]).T
+
+
+@pytest.mark.parametrize("order", [3, 2])
 @pytest.mark.parametrize("x0", [(0.3, -1.2), (2.0, 0.7)])
-def test_d2q9_bookkeeping_returns_eq_20(x0):
+def test_d2q9_bookkeeping_returns_eq_20_and_b3(x0, order):
+    """order 3: the equilibrium of Eq. (14) and the printed Eq. (20); order 2: App. B's
+    equilibrium (B1) and the printed (B3), which also reads the cross derivatives of
+    rho u and phi rho u."""
     d = 2
     x0 = np.array(x0)
     e, _ = O2.lattice()
@@ -101,13 +111,14 @@ def test_d2q9_bookkeeping_returns_eq_20(x0):
     F_of = lambda x: (KAPPA - phi(x)) / 3 * _grad(rho, x, d)      # noqa: E731  F^p, no F^B
     stress = {1: 3 * np.eye(2), 7: np.diag([1.0, -1.0]), 8: np.array([[0, 0.5], [0.5, 0]])}
     ce, gu = _ce_penalty(d, x0, e.astype(float), M,
-                         lambda p, r, v: O2.meq(KAPPA, p, r, v[0], v[1]),
-                         lambda p, r, v: O2.feq(KAPPA, p, r, v[0], v[1]),
+                         lambda p, r, v: O2.meq(KAPPA, p, r, v[0], v[1], order=order),
+                         lambda p, r, v: O2.feq(KAPPA, p, r, v[0], v[1], order=order),
                          lambda v, F: O2.force_moments(v[0], v[1], F[0], F[1]), F_of, stress)
-    dA, dD = _gradients(d, x0)
-    # the oracle's Eq. (20): dX = (d_x X_x, d_y X_y, d_x X_y, d_y X_x)
-    C = O2.penalty(KAPPA, phi(x0), rho(x0), [dA[0], dA[1], 0, 0], [gu[0, 0], gu[1, 1], gu[0, 1], gu[1, 0]],
-                   [dD[0], dD[1], 0, 0], DTPHI)
+    gA = _full_gradient(d, x0, lambda p, r, v: r * v)
+    gD = _full_gradient(d, x0, lambda p, r, v: p * r * v)
+    # the oracle's penalty: dX = (d_x X_x, d_y X_y, d_x X_y, d_y X_x)
+    cross = lambda g: [g[0, 0], g[1, 1], g[0, 1], g[1, 0]]      # noqa: E731
+    C = O2.penalty(KAPPA, phi(x0), rho(x0), cross(gA), cross(gu), cross(gD), DTPHI, order=order)
     for k in stress:
         assert abs(ce[k] - C[k]) < 1e-11 + 1e-8 * abs(C[k]), (k, ce[k], C[k])
     assert abs(C[1]) > 1e-3      # the d_t phi term is exercised
