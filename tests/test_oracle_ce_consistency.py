@@ -12,7 +12,8 @@ O(|u|^2) terms the analysis neglects. This test evaluates the right-hand side at
 point from smooth analytic fields, with the oracle's equilibrium (f^eq, m^eq) and
 force moments as the only scheme ingredients and every derivative a central
 difference, and compares it with the oracle's penalty. On D2Q9 the same machinery
-must return the printed Eq. (20) (and, with App. B's equilibrium, the printed (B3));
+must return the printed Eq. (20) (with App. B's equilibrium the printed (B3), and
+model B's);
 on D3Q19 it checks the penalty derived for that lattice. Measured residuals are 1e-14 to 2e-12 against terms of 1e-7 to 2e-2 (the
 smallest, the shear term, is 3e-7), so a wrong coefficient or a dropped term in any
 of them fails by orders of magnitude.
@@ -44,7 +45,7 @@ def _grad(fn, x, d):
     return np.array([(fn(x + H * np.eye(d)[a]) - fn(x - H * np.eye(d)[a])) / (2 * H) for a in range(d)])
 
 
-def _ce_penalty(d, x0, e, M, meq, feq, force_moments, F_of, stress):
+def _ce_penalty(d, x0, e, M, meq, feq, force_moments, F_of, stress, phi_in_target=True):
     phi, rho, u = _fields(d)
     Q = len(e)
     # fluxes sum_i M_ki e_ia f^eq_i at x, and their divergence at x0
@@ -77,7 +78,7 @@ def _ce_penalty(d, x0, e, M, meq, feq, force_moments, F_of, stress):
     dt_meq = dm("phi", 1e-5) * DTPHI + dm("rho", 1e-5) * dt_rho + sum(dm(a, 1e-6) * dt_u[a] for a in range(d))
     S = force_moments(u0, F0)
     gu = np.array([_grad(lambda x, b=b: u(x)[b], x0, d) for b in range(d)]).T   # gu[a, b] = d_a u_b
-    T = p0 * r0 / 3 * (gu + gu.T)
+    T = (p0 if phi_in_target else 1.0) * r0 / 3 * (gu + gu.T)
     target = np.zeros(Q)
     for k, A in stress.items():
         target[k] = np.sum(A * T)
@@ -143,3 +144,25 @@ def test_d3q19_bookkeeping_returns_the_derived_penalty(x0):
     for k in stress:
         assert abs(ce[k] - C[k]) < 1e-11 + 1e-8 * abs(C[k]), (k, ce[k], C[k])
     assert abs(C[1]) > 1e-3
+
+
+@pytest.mark.parametrize("x0", [(0.3, -1.2), (2.0, 0.7)])
+def test_d2q9_bookkeeping_returns_model_b(x0):
+    """Model B (Sec. 2.3, VANSE set I): F^p = (kappa - 1) cs^2 grad rho and kappa - 1 in
+    Eq. (20); its target stress is cs^2 rho (grad u + grad u^T), without phi."""
+    d = 2
+    x0 = np.array(x0)
+    e, _ = O2.lattice()
+    phi, rho, u = _fields(d)
+    F_of = lambda x: (KAPPA - 1.0) / 3 * _grad(rho, x, d)      # noqa: E731
+    stress = {1: 3 * np.eye(2), 7: np.diag([1.0, -1.0]), 8: np.array([[0, 0.5], [0.5, 0]])}
+    ce, gu = _ce_penalty(d, x0, e.astype(float), O2.M(),
+                         lambda p, r, v: O2.meq(KAPPA, p, r, v[0], v[1]),
+                         lambda p, r, v: O2.feq(KAPPA, p, r, v[0], v[1]),
+                         lambda v, F: O2.force_moments(v[0], v[1], F[0], F[1]), F_of, stress, phi_in_target=False)
+    gA = _full_gradient(d, x0, lambda p, r, v: r * v)
+    gD = _full_gradient(d, x0, lambda p, r, v: p * r * v)
+    cross = lambda g: [g[0, 0], g[1, 1], g[0, 1], g[1, 0]]      # noqa: E731
+    C = O2.penalty(KAPPA, phi(x0), rho(x0), cross(gA), cross(gu), cross(gD), DTPHI, model_b=1)
+    for k in stress:
+        assert abs(ce[k] - C[k]) < 1e-11 + 1e-8 * abs(C[k]), (k, ce[k], C[k])
