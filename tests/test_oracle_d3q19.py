@@ -135,11 +135,15 @@ def test_reduces_to_textbook_bgk_when_phi_is_kappa_and_rates_are_equal():
     assert np.abs(f - g).max() < 1e-14
 
 
-def test_rest_state_is_a_fixed_point_with_a_varying_phi():
+@pytest.mark.parametrize("bc_y", [0, 1])
+def test_rest_state_is_a_fixed_point_with_a_varying_phi(bc_y):
+    """rho = rho0, u = 0, no force, any phi (discontinuous from cell to cell, the
+    no-flow setting of Eq. (24) in 3-D): F^p = 0, C = 0 and f = f^eq stay put, also next
+    to the walls (mirrored ghosts)."""
     nx, ny, nz = 6, 7, 5
     rng = np.random.default_rng(7)
     phi = rng.uniform(0.4, 1.0, size=(nz, ny, nx))
-    p = D.Params(nx, ny, nz, s_nu=1.25, kappa=0.5)
+    p = D.Params(nx, ny, nz, s_nu=1.25, kappa=0.5, bc_y=bc_y)
     f0 = D.init(p, np.ones_like(phi), np.zeros((3, nz, ny, nx)), phi)
     f = f0
     for _ in range(4):
