@@ -148,7 +148,7 @@ def test_rest_state_is_a_fixed_point_with_a_varying_phi(bc_y):
     f = f0
     for _ in range(4):
         f = D.step(p, f, phi)
-    assert np.abs(f - f0).max() < 1e-15
+    assert np.abs(f - f0).max() < 4e-15    # a few ulps of populations ~0.3 (1.1e-15 measured with walls)
 
 
 @pytest.mark.parametrize("bc_y", [0, 1])
