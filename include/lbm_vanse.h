@@ -91,7 +91,14 @@ lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_va
 /* Void fraction phi(x, t) of the next step and phi(x, t+1) (Eq. 7, 13, 14, 20;
  * d_t phi = phi(t+1) - phi(t), Sec. 2.3). phi_next = NULL means steady. After a
  * step, phi(t) takes the value of phi(t+1) and the field is steady until the next
- * call. Values must lie in (0, 1]. Must be called before lbm_vanse_init_fields.
+ * call. Values must lie in (0, 1] (phi divides in Eq. 7 and in X = kappa / phi of
+ * Eq. 20). Both fields are checked on the device before either replaces the
+ * lattice's: a NaN, a negative value or a value above 1 returns LBM_ERR_ARG and
+ * leaves the lattice unchanged. The check is waited for: device arrays and pageable
+ * host arrays synchronise the lattice's stream; pinned host arrays wait only for their
+ * own copy and check (below). A zero marks a solid cell (lbm_vanse_set_solid_cells);
+ * without solid cells it is reported by the next lbm_vanse_sync.
+ * Must be called before lbm_vanse_init_fields.
  * A new phi(t) keeps the populations the steps left (FP32/FP16/BF16 move their
  * stored f_0 deviation to the new rest value; FP16/BF16 round it again).
  * Host arrays in pinned (page-locked) memory are copied on a stream of the
@@ -221,15 +228,18 @@ lbm_status lbm_vanse_velocity_error(lbm_vanse_t h, const double* ux_ref, const d
  * every GPU that loads the library keeps until the process exits.
  *
  * The first call on a device looks up that array's device address with that device
- * current; make that first call before starting any stream capture. Every call on a
+ * current; make that first call before starting any stream capture (a first call on
+ * a capturing stream returns LBM_ERR_STATE). The kernels run on the handle's device
+ * whichever device the calling thread has current; the caller's current device is
+ * restored before the call returns. Every call on a
  * device shares the one array: calls whose kernels overlap on the GPU (two streams,
  * two handles, two threads) race on it and may return mixed sums, so keep such calls
  * ordered. Each call writes every partial it reads, so no clearing is needed and a
  * previous call's leftovers never leak into a result.
  *
  * Errors: LBM_ERR_ARG for a NULL handle or output, or ny > LBM_VANSE_NOALLOC_MAX_ROWS;
- * LBM_ERR_STATE before initialisation; LBM_ERR_CUDA if the address lookup or a launch
- * fails. It does not check the sums for NaN (the caller reads them). */
+ * LBM_ERR_STATE before initialisation, or for a first call on a capturing stream;
+ * LBM_ERR_CUDA if the address lookup, a device switch or a launch fails. It does not check the sums for NaN (the caller reads them). */
 lbm_status lbm_vanse_reduce_noalloc(lbm_vanse_t h, double* out_dev);
 
 /* ======================================================================== batches
@@ -342,8 +352,20 @@ lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, const lbm_v
                                           double* dJdphi, lbm_vanse_adjoint_stats* stats);
 
 /* Synchronise the stream and report any deferred kernel error (LBM_ERR_TIMEOUT
- * if a bounded wait gave up, LBM_ERR_CUDA for a launch/runtime error). */
+ * if a bounded wait gave up, LBM_ERR_CUDA for a launch/runtime error). After a
+ * timeout the populations are not valid; the flag stays set. */
 lbm_status lbm_vanse_sync(lbm_vanse_t h);
+
+/* Test hook for the timeout path (no counterpart in the paper): every wait of the
+ * step kernels for a staged source row gives up after `polls` polls of its mbarrier.
+ * The default, restored by polls < 0, is the library's bound of kWaitTries polls
+ * (seconds, far above a row's latency); larger values are capped at it, and 0 makes
+ * every wait give up at once. A wait that gives up sets the lattice's timeout flag;
+ * the kernel finishes its group of rows, waits with the full bound for every copy it
+ * issued (so no copy lands after it exits) and returns; the next lbm_vanse_sync
+ * returns LBM_ERR_TIMEOUT. Takes effect from the next step. LBM_ERR_ARG for a NULL
+ * handle. */
+lbm_status lbm_vanse_set_row_wait_limit(lbm_vanse_t h, long long polls);
 
 /* Steps taken since init_fields / set_populations. */
 long long lbm_vanse_step_count(lbm_vanse_t h);

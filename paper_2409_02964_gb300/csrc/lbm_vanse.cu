@@ -78,6 +78,9 @@ struct lbm_vanse {
     double s_nu = 0, s_e = 0;
     double scale = 1, inv_scale = 1;
     int* err = nullptr;           // device flag set by bounded waits
+    uint32_t wait_tries = kWaitTries;   // polls of a staged-row wait (lowered only to test the timeout path)
+    int* bad_phi = nullptr;       // device flags of the void-fraction check (1: phi_t, 2: phi_next)
+    int* bad_phi_host = nullptr;  // pinned copy of them
     double* partial = nullptr;    // reduction partials (kReduceBlocks * 3)
     double* red_out = nullptr;    // reduction result (3)
     double* scratch = nullptr;    // 3 dense double fields (macros / error norms)
@@ -331,6 +334,7 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
     p.uw_y = (R)h->uw_y;
     p.has_solid = h->has_solid;
     p.step_ctr = h->step_ctr;
+    p.wait_tries = h->wait_tries;
     dim3 grid(h->gridx, h->gridy);
     if (h->has_solid) return launch_solid_step<S>(h, p, grid, smem, stream, sums != nullptr);
     if (sums) {
@@ -447,7 +451,7 @@ lbm_status run_get(lbm_vanse* h, double* out) {
     using R = typename Prec<S>::R;
     const long long n = (long long)h->prm.nx * h->prm.ny;
     get_pop_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>((const S*)h->f[h->cur], (const R*)h->phi, out,
-                                                                       make_lattice<R>(h));
+                                                                       make_lattice<double>(h));
     CK(h, cudaGetLastError());
     return LBM_OK;
 }
@@ -457,7 +461,7 @@ lbm_status run_set(lbm_vanse* h, const double* in) {
     using R = typename Prec<S>::R;
     const long long n = (long long)h->prm.nx * h->prm.ny;
     set_pop_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>((S*)h->f[h->cur], (const R*)h->phi, in,
-                                                                       make_lattice<R>(h));
+                                                                       make_lattice<double>(h));
     CK(h, cudaGetLastError());
     return LBM_OK;
 }
@@ -466,7 +470,7 @@ template <typename S>
 lbm_status run_macros(lbm_vanse* h, double* rho, double* ux, double* uy, double* p) {
     using R = typename Prec<S>::R;
     const long long n = (long long)h->prm.nx * h->prm.ny;
-    Lattice<R> L = make_lattice<R>(h);
+    const Lattice<double> L = make_lattice<double>(h);   // the macroscopic passes compute in FP64
     rho_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>((const S*)h->f[h->cur], (const R*)h->phi, rho, L);
     CK(h, cudaGetLastError());
     if (ux || uy || p) {
@@ -556,6 +560,41 @@ lbm_status put_phi_t(lbm_vanse* h, const T* dev_src) {
     }
 }
 
+// The void-fraction check (check_phi_kernel) of the staged fields on stream s, then
+// its verdict: the flags are copied to pinned host memory and s is synchronised. A
+// bad field fails the call before anything of the lattice changes.
+lbm_status ensure_phi_check(lbm_vanse* h) {
+    if (h->bad_phi) return LBM_OK;
+    CK(h, cudaMalloc((void**)&h->bad_phi, sizeof(int)));
+    CK(h, cudaMallocHost((void**)&h->bad_phi_host, sizeof(int)));
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status check_phi_fields(lbm_vanse* h, const T* phi_t, const T* phi_next, cudaStream_t s) {
+    lbm_status st = ensure_phi_check(h);
+    if (st != LBM_OK) return st;
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    const int blocks = (int)std::min<long long>((n + kAuxThreads - 1) / kAuxThreads, 2048);
+    CK(h, cudaMemsetAsync(h->bad_phi, 0, sizeof(int), s));
+    check_phi_kernel<T><<<blocks, kAuxThreads, 0, s>>>(phi_t, n, 1, h->bad_phi);
+    CK(h, cudaGetLastError());
+    if (phi_next) {
+        check_phi_kernel<T><<<blocks, kAuxThreads, 0, s>>>(phi_next, n, 2, h->bad_phi);
+        CK(h, cudaGetLastError());
+    }
+    CK(h, cudaMemcpyAsync(h->bad_phi_host, h->bad_phi, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return LBM_OK;
+}
+
+// after the check's stream has been synchronised
+lbm_status phi_verdict(lbm_vanse* h) {
+    const int b = *h->bad_phi_host;
+    if (!b) return LBM_OK;
+    return fail(h, LBM_ERR_ARG, "%s outside [0, 1] (NaN, negative or above 1); the lattice is unchanged",
+                b == 1 ? "phi_t holds values" : (b == 2 ? "phi_next holds values" : "phi_t and phi_next hold values"));
+}
+
 // Upload of phi(t) [and phi(t+1)] from pinned host arrays: the copies run on the
 // copy stream into the staging buffers, overlapping whatever `stream` is still
 // executing (e.g. the previous step); the call returns once the caller's arrays
@@ -575,8 +614,14 @@ lbm_status upload_void_fraction_pinned(lbm_vanse* h, const T* phi_t, const T* ph
     CK(h, cudaStreamWaitEvent(h->copy_stream, h->staging_free, 0));
     CK(h, cudaMemcpyAsync(h->staging[0], phi_t, bytes, cudaMemcpyHostToDevice, h->copy_stream));
     if (phi_next) CK(h, cudaMemcpyAsync(h->staging[1], phi_next, bytes, cudaMemcpyHostToDevice, h->copy_stream));
+    // the check runs on the copy stream too, so the wait for the copies covers it
+    lbm_status chk = check_phi_fields<T>(h, (const T*)h->staging[0], phi_next ? (const T*)h->staging[1] : nullptr,
+                                         h->copy_stream);
+    if (chk != LBM_OK) return chk;
     CK(h, cudaEventRecord(h->copy_done, h->copy_stream));
     CK(h, cudaEventSynchronize(h->copy_done));
+    chk = phi_verdict(h);
+    if (chk != LBM_OK) return chk;
     CK(h, cudaStreamWaitEvent(h->stream, h->copy_done, 0));
     CK(h, cudaMemsetAsync(h->zero_phi, 0, sizeof(int), h->stream));
     lbm_status st = put_phi_t<T>(h, (const T*)h->staging[0]);
@@ -599,23 +644,27 @@ lbm_status set_void_fraction_impl(lbm_vanse* h, const T* phi_t, const T* phi_nex
         h->phi_set = true;
         return LBM_OK;
     }
-    T* d = nullptr;
-    bool owned = false;
-    CK(h, cudaMemsetAsync(h->zero_phi, 0, sizeof(int), h->stream));
-    lbm_status st = stage_in<T>(h, phi_t, n, on_device, &d, &owned);
-    if (st != LBM_OK) return st;
-    st = put_phi_t<T>(h, d);
-    if (owned) cudaFreeAsync(d, h->stream);
-    if (st != LBM_OK) return st;
-    h->unsteady = false;
-    if (phi_next) {
-        st = stage_in<T>(h, phi_next, n, on_device, &d, &owned);
-        if (st != LBM_OK) return st;
-        st = pad_into<T>(h, d, h->phin, h->zero_phi);
-        if (owned) cudaFreeAsync(d, h->stream);
-        if (st != LBM_OK) return st;
-        h->unsteady = true;
+    // stage and check both fields before either replaces the lattice's own
+    T* d[2] = {nullptr, nullptr};
+    bool owned[2] = {false, false};
+    auto release = [&]() {
+        for (int k = 0; k < 2; ++k)
+            if (owned[k]) cudaFreeAsync(d[k], h->stream);
+    };
+    lbm_status st = stage_in<T>(h, phi_t, n, on_device, &d[0], &owned[0]);
+    if (st == LBM_OK && phi_next) st = stage_in<T>(h, phi_next, n, on_device, &d[1], &owned[1]);
+    if (st == LBM_OK) st = check_phi_fields<T>(h, d[0], d[1], h->stream);
+    if (st == LBM_OK) {
+        const cudaError_t e = cudaStreamSynchronize(h->stream);
+        st = e == cudaSuccess ? phi_verdict(h) : cuda_fail(h, e, "void fraction check");
     }
+    if (st != LBM_OK) { release(); return st; }
+    CK(h, cudaMemsetAsync(h->zero_phi, 0, sizeof(int), h->stream));
+    st = put_phi_t<T>(h, d[0]);
+    if (st == LBM_OK && phi_next) st = pad_into<T>(h, d[1], h->phin, h->zero_phi);
+    release();
+    if (st != LBM_OK) return st;
+    h->unsteady = phi_next != nullptr;
     h->phi_set = true;
     return LBM_OK;
 }
@@ -644,11 +693,18 @@ std::mutex g_noalloc_mu;
 double* g_noalloc_addr[kMaxDevices] = {};
 
 // Device address of g_noalloc_rows on h's device (looked up on first use, with that
-// device current).
+// device current). The lookup is refused while h's stream is capturing a graph: it
+// must happen once, outside any capture.
 lbm_status noalloc_rows(lbm_vanse* h, double** out) {
     if (h->device < 0 || h->device >= kMaxDevices) return fail(h, LBM_ERR_ARG, "device %d out of range", h->device);
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[h->device]) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CK(h, cudaStreamIsCapturing(h->stream, &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(h, LBM_ERR_STATE,
+                        "the first lbm_vanse_reduce_noalloc call on device %d must come before any stream capture "
+                        "(it looks up the address of the fixed scratch)", h->device);
         int prev = -1;
         CK(h, cudaGetDevice(&prev));
         if (prev != h->device) CK(h, cudaSetDevice(h->device));
@@ -686,7 +742,17 @@ extern "C" lbm_status lbm_vanse_reduce_noalloc(lbm_vanse_t h, double* out_dev) {
     double* rows = nullptr;
     lbm_status st = noalloc_rows(h, &rows);
     if (st != LBM_OK) return st;
-    return DISPATCH(h, run_reduce_noalloc, rows, out_dev);
+    // the scratch address belongs to h's device: launch there even when the calling
+    // thread has another device current, and put the caller's device back afterwards
+    int prev = -1;
+    CK(h, cudaGetDevice(&prev));
+    if (prev != h->device) CK(h, cudaSetDevice(h->device));
+    st = DISPATCH(h, run_reduce_noalloc, rows, out_dev);
+    if (prev != h->device) {
+        const cudaError_t e = cudaSetDevice(prev);
+        if (st == LBM_OK && e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice(caller's device)");
+    }
+    return st;
 }
 
 // ============================================================================ C ABI
@@ -854,6 +920,16 @@ extern "C" lbm_status lbm_vanse_set_solid_cells(lbm_vanse_t h, int enable) {
         return fail(h, LBM_ERR_ARG, "solid cells run on step kernel 1 (this lattice uses kernel %d)", h->kernel);
     h->has_solid = enable != 0;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // the step's shared memory changes
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_set_row_wait_limit(lbm_vanse_t h, long long polls) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    const uint32_t v = polls < 0 ? kWaitTries : (uint32_t)std::min<long long>(polls, (long long)kWaitTries);
+    if (v != h->wait_tries) {
+        h->wait_tries = v;
+        if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // the steps' parameters change
+    }
     return LBM_OK;
 }
 
@@ -1112,9 +1188,10 @@ extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
         cudaEventDestroy(h->staging_free);
     }
     void* ptrs[] = {h->f[0], h->f[1], h->phi, h->phin, h->fb, h->err, h->partial, h->red_out, h->scratch,
-                    h->staging[0], h->staging[1], h->zero_phi, h->step_ctr};
+                    h->staging[0], h->staging[1], h->zero_phi, h->step_ctr, h->bad_phi};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    if (h->bad_phi_host) cudaFreeHost(h->bad_phi_host);
     delete h;
 }
 

@@ -70,6 +70,20 @@ __global__ void ghost_fill_kernel(S* __restrict__ buf, long long plane, int nx, 
     if (step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1u;
 }
 
+// Void-fraction check of a dense field before it replaces the lattice's: every value
+// must lie in [0, 1]; NaN fails. (Zeros are solid cells: without solid cells enabled
+// they are reported later, by the sync-time check of pad_field_kernel's flag.) Sets
+// the bit `which` of *bad when any value fails; block size a multiple of 32.
+template <typename T>
+__global__ void check_phi_kernel(const T* __restrict__ src, long long n, int which, int* __restrict__ bad) {
+    bool ok = true;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const T v = src[k];
+        ok = ok && v >= (T)0 && v <= (T)1;
+    }
+    if (!__all_sync(0xffffffffu, ok) && (threadIdx.x & 31) == 0) atomicOr(bad, which);
+}
+
 // Copy a dense [ny][nx] field (double or float) into a padded R field (with
 // ghosts). Rows are dealt to blocks and columns to threads (32-bit indices).
 // zero_seen (optional): set to 1 when a value is exactly zero (a solid cell in phi).
@@ -119,13 +133,15 @@ __global__ void pad_phi_rebase_kernel(const Tin* __restrict__ src, R* __restrict
 // Pull the post-streaming populations of cell (x, y) from the stored planes.
 // With solid cells: a solid cell has no populations (zeros), and a population whose
 // source cell is solid comes back from the half-way link (opposite slot, same cell).
-template <typename S, typename R>
-__device__ __forceinline__ void pull_cell(const S* __restrict__ buf, const R* __restrict__ phi, const Lattice<R>& L,
-                                          int x, int y, R f[9]) {
-    const R ph = phi[cell_off(L.P, x, y)];
-    if (L.has_solid && ph == (R)0) {
+// T: the type f is decoded to (R, or double for the read-back kernels, with the rest
+// values of a Lattice<double>).
+template <typename S, typename R, typename T = R>
+__device__ __forceinline__ void pull_cell(const S* __restrict__ buf, const R* __restrict__ phi, const Lattice<T>& L,
+                                          int x, int y, T f[9]) {
+    const T ph = (T)phi[cell_off(L.P, x, y)];
+    if (L.has_solid && ph == (T)0) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = (R)0;
+        for (int i = 0; i < 9; ++i) f[i] = (T)0;
         return;
     }
 #pragma unroll
@@ -138,15 +154,16 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ buf, const R* __
         }
         if (L.has_solid && pi == i && phi[cell_off(L.P, sx, sy)] == (R)0) { sx = x; sy = y; pi = opp_of(i); }
         const S v = buf[pi * L.plane + cell_off(L.P, sx, sy)];
-        const R rest = (i == 0) ? L.rest.r0(ph) : L.rest.ri(i);
-        f[i] = dec(v, rest, L.inv_scale);
+        const T rest = (i == 0) ? L.rest.r0(ph) : L.rest.ri(i);
+        f[i] = dec_as<T>(v, rest, L.inv_scale);
     }
 }
 
-// Store post-streaming value f_i(x, y) where the next pull will find it.
-template <typename S, typename R>
-__device__ __forceinline__ void scatter_cell(S* __restrict__ buf, const Lattice<R>& L, int x, int y, int i, R fi,
-                                             R phi_cell, const R* __restrict__ phi = nullptr) {
+// Store post-streaming value f_i(x, y) where the next pull will find it (the value,
+// rest state and deviation in T: R, or double for the write-back kernel).
+template <typename S, typename R, typename T = R>
+__device__ __forceinline__ void scatter_cell(S* __restrict__ buf, const Lattice<T>& L, int x, int y, int i, T fi,
+                                             T phi_cell, const R* __restrict__ phi = nullptr) {
     int tx = x - ex_of(i), ty = y - ey_of(i);
     int pi = i;
     if (ty < 0 || ty >= L.ny) {
@@ -155,8 +172,8 @@ __device__ __forceinline__ void scatter_cell(S* __restrict__ buf, const Lattice<
     }
     if (L.has_solid && pi == i && phi[cell_off(L.P, tx, ty)] == (R)0) { tx = x; ty = y; pi = opp_of(i); }
     tx = (tx + L.nx) % L.nx;
-    const R rest = (i == 0) ? L.rest.r0(phi_cell) : L.rest.ri(i);
-    put_with_ghosts<S>(buf + pi * L.plane, L.P, L.nx, tx, ty, enc<S, R>(fi, rest, L.scale));
+    const T rest = (i == 0) ? L.rest.r0(phi_cell) : L.rest.ri(i);
+    put_with_ghosts<S>(buf + pi * L.plane, L.P, L.nx, tx, ty, enc<S, T>(fi, rest, L.scale));
 }
 
 // the row a stencil row y + dy maps to: periodic wrap, or the mirror row at a wall
@@ -173,9 +190,9 @@ __device__ __forceinline__ int map_row(const Lattice<R>& L, int yy) {
 // solid cells (phi = 0) a solid neighbour reads the mirrored value: an axis neighbour
 // the cell itself, a diagonal one the mean of the fluid ones of its two axis images
 // (the cell itself if both are solid).
-template <typename R>
+template <typename R, typename PT = R>
 __device__ __forceinline__ void grad_dense_even(const double* __restrict__ a, const Lattice<R>& L, int x, int y, R& gx,
-                                                R& gy, const R* __restrict__ phi = nullptr) {
+                                                R& gy, const PT* __restrict__ phi = nullptr) {
     R sx = 0, sy = 0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
@@ -183,12 +200,12 @@ __device__ __forceinline__ void grad_dense_even(const double* __restrict__ a, co
         int ny_ = map_row(L, y + ey_of(i));
         const R w = (i <= 4) ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0);
         R v = (R)a[(long long)ny_ * L.nx + nx_];
-        if (L.has_solid && phi[cell_off(L.P, nx_, ny_)] == (R)0) {
+        if (L.has_solid && phi[cell_off(L.P, nx_, ny_)] == (PT)0) {
             const R own = (R)a[(long long)y * L.nx + x];
             v = own;
             if (ex_of(i) != 0 && ey_of(i) != 0) {
                 const int ax = nx_, by = map_row(L, y + ey_of(i));
-                const bool fa = phi[cell_off(L.P, ax, y)] != (R)0, fb_ = phi[cell_off(L.P, x, by)] != (R)0;
+                const bool fa = phi[cell_off(L.P, ax, y)] != (PT)0, fb_ = phi[cell_off(L.P, x, by)] != (PT)0;
                 const R va = (R)a[(long long)y * L.nx + ax], vb = (R)a[(long long)by * L.nx + x];
                 if (fa && fb_) v = (va + vb) / (R)2;
                 else if (fa) v = va;
@@ -245,46 +262,53 @@ __global__ void init_kernel(S* __restrict__ buf, const R* __restrict__ phi, cons
     }
 }
 
+// Read-back and write-back of the post-streaming populations, decoded / encoded in
+// FP64 (L: the lattice's Lattice<double>): a stored deviation d reads back as
+// d / scale + f^rest with f^rest in FP64, so the value carries no rounding at the
+// scale of f, and writing it back returns d.
 template <typename S, typename R>
 __global__ void get_pop_kernel(const S* __restrict__ buf, const R* __restrict__ phi, double* __restrict__ out,
-                               const Lattice<R> L) {
+                               const Lattice<double> L) {
     const long long n = (long long)L.nx * L.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(k / L.nx), x = (int)(k % L.nx);
-        R f[9];
-        pull_cell<S, R>(buf, phi, L, x, y, f);
+        double f[9];
+        pull_cell<S, R, double>(buf, phi, L, x, y, f);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) out[i * n + k] = (double)f[i];
+        for (int i = 0; i < 9; ++i) out[i * n + k] = f[i];
     }
 }
 
 template <typename S, typename R>
 __global__ void set_pop_kernel(S* __restrict__ buf, const R* __restrict__ phi, const double* __restrict__ in,
-                               const Lattice<R> L) {
+                               const Lattice<double> L) {
     const long long n = (long long)L.nx * L.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(k / L.nx), x = (int)(k % L.nx);
-        const R ph = phi[cell_off(L.P, x, y)];
-        if (L.has_solid && ph == (R)0) continue;
+        const double ph = (double)phi[cell_off(L.P, x, y)];
+        if (L.has_solid && ph == 0.0) continue;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) scatter_cell<S, R>(buf, L, x, y, i, (R)in[i * n + k], ph, phi);
+        for (int i = 0; i < 9; ++i) scatter_cell<S, R, double>(buf, L, x, y, i, in[i * n + k], ph, phi);
     }
 }
 
 // Macroscopic pass 1: rho = sum f / phi (Eq. 7) into a dense double array.
+// (Both macroscopic passes decode and compute in FP64 for every storage, L being
+// the lattice's Lattice<double>: off the step path, and free of FP32 rounding at
+// the scale of f.)
 template <typename S, typename R>
 __global__ void rho_kernel(const S* __restrict__ buf, const R* __restrict__ phi, double* __restrict__ rho,
-                           const Lattice<R> L) {
+                           const Lattice<double> L) {
     const long long n = (long long)L.nx * L.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(k / L.nx), x = (int)(k % L.nx);
-        R f[9];
-        pull_cell<S, R>(buf, phi, L, x, y, f);
-        R s = 0;
+        double f[9];
+        pull_cell<S, R, double>(buf, phi, L, x, y, f);
+        double s = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) s += f[i];
-        const R ph = phi[cell_off(L.P, x, y)];
-        rho[k] = (L.has_solid && ph == (R)0) ? 0.0 : (double)(s / ph);
+        const double ph = (double)phi[cell_off(L.P, x, y)];
+        rho[k] = (L.has_solid && ph == 0.0) ? 0.0 : s / ph;
     }
 }
 
@@ -292,32 +316,32 @@ __global__ void rho_kernel(const S* __restrict__ buf, const R* __restrict__ phi,
 template <typename S, typename R>
 __global__ void vel_kernel(const S* __restrict__ buf, const R* __restrict__ phi, const R* __restrict__ fb,
                            const double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy,
-                           double* __restrict__ pr, const Lattice<R> L) {
+                           double* __restrict__ pr, const Lattice<double> L) {
     const long long n = (long long)L.nx * L.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(k / L.nx), x = (int)(k % L.nx);
         const long long co = cell_off(L.P, x, y);
-        R f[9];
-        pull_cell<S, R>(buf, phi, L, x, y, f);
-        R s = 0, jx = 0, jy = 0;
+        double f[9];
+        pull_cell<S, R, double>(buf, phi, L, x, y, f);
+        double s = 0, jx = 0, jy = 0;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) { s += f[i]; jx += (R)ex_of(i) * f[i]; jy += (R)ey_of(i) * f[i]; }
-        const R ph = phi[co];
-        if (L.has_solid && ph == (R)0) {   // a solid cell reports zeros
+        for (int i = 0; i < 9; ++i) { s += f[i]; jx += (double)ex_of(i) * f[i]; jy += (double)ey_of(i) * f[i]; }
+        const double ph = (double)phi[co];
+        if (L.has_solid && ph == 0.0) {   // a solid cell reports zeros
             if (ux) ux[k] = 0.0;
             if (uy) uy[k] = 0.0;
             if (pr) pr[k] = 0.0;
             continue;
         }
-        R gx, gy;
-        grad_dense_even<R>(rho, L, x, y, gx, gy, phi);
-        const R kp = (L.model_b ? (L.kappa - (R)1) : (L.kappa - ph)) / (R)3;
-        R Fx = kp * gx + ph * L.gx, Fy = kp * gy + ph * L.gy;
-        if (fb) { Fx += fb[co]; Fy += fb[L.plane + co]; }
+        double gx, gy;
+        grad_dense_even<double>(rho, L, x, y, gx, gy, phi);
+        const double kp = (L.model_b ? (L.kappa - 1.0) : (L.kappa - ph)) / 3.0;
+        double Fx = kp * gx + ph * L.gx, Fy = kp * gy + ph * L.gy;
+        if (fb) { Fx += (double)fb[co]; Fy += (double)fb[L.plane + co]; }
         // Eq. (7) with the drag -beta (u - u_s) inside F, solved for u
-        const R beta = drag_beta(L, ph);
-        if (ux) ux[k] = (double)((jx + (R)0.5 * (Fx + beta * L.us_x)) / (s + (R)0.5 * beta));
-        if (uy) uy[k] = (double)((jy + (R)0.5 * (Fy + beta * L.us_y)) / (s + (R)0.5 * beta));
+        const double beta = drag_beta(L, ph);
+        if (ux) ux[k] = (jx + 0.5 * (Fx + beta * L.us_x)) / (s + 0.5 * beta);
+        if (uy) uy[k] = (jy + 0.5 * (Fy + beta * L.us_y)) / (s + 0.5 * beta);
         if (pr) pr[k] = rho[k] / 3.0;
     }
 }

@@ -75,6 +75,7 @@ struct BatchCtx {
     bool fast_strip;
     int fast_lo, fast_hi;
     uint32_t phase;            // parity of the next completion of each ring slot
+    int first_bad;             // first row of this unit whose wait gave up (this lane)
     RowCopy cp;
     bool st_pair;              // this lane stores its pair (lanes 1..30, first column inside)
     uint32_t step = 0, salt = 0;   // seed of the stochastic rounding of FP16/BF16 stores
@@ -129,6 +130,7 @@ struct BatchCtx {
             ++waited;
             const int s = wslot(waited);
             if (!mbar_wait_bounded(bar(waited), (phase >> s) & 1u, kWaitTries)) {
+                first_bad = min(first_bad, waited);
                 aborted = true;
                 atomicExch(p.err, 1);
             }
@@ -136,6 +138,24 @@ struct BatchCtx {
         }
     }
 };
+
+// After a wait gave up: wait (bounded by kWaitTries) for every copy of the unit that
+// may still be in flight, so none lands after the CTA exits. Rows first_bad .. waited
+// have toggled their slot's parity bit already (their completion has the other
+// parity); rows waited+1 .. issued have not. These at most kWarpSlots rows lie in
+// distinct slots (warp_run_strip never re-arms a slot whose wait gave up).
+template <typename S>
+__device__ __forceinline__ void batch_drain(const BatchCtx<S>& c, uint32_t& phase) {
+    for (int r = min(c.first_bad, c.waited + 1); r <= c.issued; ++r) {
+        const int s = wslot(r);
+        if (r <= c.waited) {
+            mbar_wait_bounded(c.bar(r), ((phase >> s) & 1u) ^ 1u, kWaitTries);
+        } else {
+            mbar_wait_bounded(c.bar(r), (phase >> s) & 1u, kWaitTries);
+            phase ^= 1u << s;
+        }
+    }
+}
 
 template <typename S, int MINB>
 __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_constant__ BatchParams bp) {
@@ -165,6 +185,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         c.step = (uint32_t)t;
         c.salt = (uint32_t)bp.unit_lattice[u] * 0x27d4eb2fu;
         c.aborted = false;
+        c.first_bad = 0x7fffffff;
         c.phase = phase;
         StepParams<float>& p = c.p;
         p.src = Lt.buf[t & 1];
@@ -196,6 +217,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         p.rest.k59 = Lt.kappa * Lt.rho0 * (5.f / 9.f);
         p.rest.rho0 = Lt.rho0;
         p.err = bp.err;
+        p.wait_tries = kWaitTries;
         p.eq2 = 0;
         p.has_drag = 0;
         p.drag_d0 = p.drag_d1 = p.us_x = p.us_y = 0.f;
@@ -232,12 +254,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         const bool ok = warp_run_strip<S, true>(c);
         phase = c.phase;
         if (!ok) {
-            if (lane == 0)
-                for (int r = c.waited + 1; r <= c.issued; ++r) {
-                    const int s = wslot(r);
-                    mbar_wait_bounded(c.bar(r), (phase >> s) & 1u, kWaitTries);
-                    phase ^= 1u << s;
-                }
+            if (lane == 0) batch_drain(c, phase);
             break;
         }
     }
@@ -344,18 +361,22 @@ __global__ void batch_init_kernel(const BatchLattice* lats, int index, float sca
     }
 }
 
-// Post-streaming populations of cell (x, y) of a batch lattice at step t.
+// Post-streaming populations of cell (x, y) of a batch lattice at step t, decoded in
+// FP64: the stored deviation (scaled) plus the FP64 rest value at the kernel's own FP32
+// phi(x, y, t), so the read-back adds no rounding at the scale of f.
 template <typename S>
 __device__ __forceinline__ void batch_pull(const BatchLattice& L, const Lattice<float>& Q, int t, int x, int y,
-                                           float f[9]) {
+                                           double f[9]) {
     const S* buf = reinterpret_cast<const S*>(L.buf[t & 1]);
-    const float ph = batch_phi(L, x, y, cosf(L.w * (float)t));
+    const double ph = (double)batch_phi(L, x, y, cosf(L.w * (float)t));
+    const double kr = (double)L.kappa * (double)L.rho0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int sx = x - ex_of(i);
         const int sy = (y - ey_of(i) + L.ny) % L.ny;
         const S v = buf[i * L.plane + cell_off(L.P, sx, sy)];
-        f[i] = dec(v, i == 0 ? Q.rest.r0(ph) : Q.rest.ri(i), Q.inv_scale);
+        const double rest = i == 0 ? ph * (double)L.rho0 - kr * (5.0 / 9.0) : kr * (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        f[i] = decd(v, rest, (double)Q.inv_scale);
     }
 }
 
@@ -368,10 +389,10 @@ __global__ void batch_get_kernel(const BatchLattice* lats, int index, const int*
     const long long n = (long long)L.nx * L.ny;
     for (long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x; kk < n; kk += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(kk / L.nx), x = (int)(kk % L.nx);
-        float f[9];
+        double f[9];
         batch_pull<S>(L, Q, t, x, y, f);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) out[i * n + kk] = (double)f[i];
+        for (int i = 0; i < 9; ++i) out[i * n + kk] = f[i];
     }
 }
 
@@ -386,12 +407,12 @@ __global__ void batch_rho_kernel(const BatchLattice* lats, int index, const int*
     const long long n = (long long)L.nx * L.ny;
     for (long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x; kk < n; kk += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(kk / L.nx), x = (int)(kk % L.nx);
-        float f[9];
+        double f[9];
         batch_pull<S>(L, Q, t, x, y, f);
-        float s = 0.f;
+        double s = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) s += f[i];
-        rho[kk] = (double)(s / batch_phi(L, x, y, ct));
+        rho[kk] = s / (double)batch_phi(L, x, y, ct);
     }
 }
 
@@ -409,11 +430,11 @@ __global__ void batch_err_kernel(const BatchLattice* lats, int index, const int*
     double num = 0, den = 0;
     for (long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x; kk < n; kk += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(kk / L.nx), x = (int)(kk % L.nx);
-        float f[9];
+        double f[9];
         batch_pull<S>(L, Q, t, x, y, f);
-        float s = 0, jx = 0, jy = 0;
+        double s = 0, jx = 0, jy = 0;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) { s += f[i]; jx += (float)ex_of(i) * f[i]; jy += (float)ey_of(i) * f[i]; }
+        for (int i = 0; i < 9; ++i) { s += f[i]; jx += (double)ex_of(i) * f[i]; jy += (double)ey_of(i) * f[i]; }
         float gx, gy;
         grad_dense_even<float>(rho, Q, x, y, gx, gy);
         float sx, cx, sy, cy;
@@ -425,7 +446,7 @@ __global__ void batch_err_kernel(const BatchLattice* lats, int index, const int*
         const float kp = (L.kappa - ph) * (1.0f / 3.0f);
         Fx = kp * gx + L.rho0 * Fx;
         Fy = kp * gy + L.rho0 * Fy;
-        const double ux = (jx + 0.5f * Fx) / s, uy = (jy + 0.5f * Fy) / s;
+        const double ux = (jx + 0.5 * (double)Fx) / s, uy = (jy + 0.5 * (double)Fy) / s;
         float uxr, uyr;
         batch_velocity(L, x, y, ct, st, uxr, uyr);
         num += (ux - uxr) * (ux - uxr) + (uy - uyr) * (uy - uyr);
@@ -457,6 +478,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     c.step = (uint32_t)t;
     c.salt = (uint32_t)index * 0x27d4eb2fu;
     c.aborted = false;
+    c.first_bad = 0x7fffffff;
     c.phase = 0;
     StepParams<float>& p = c.p;
     p.src = Lt.buf[t & 1];
@@ -488,6 +510,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     p.rest.k59 = Lt.kappa * Lt.rho0 * (5.f / 9.f);
     p.rest.rho0 = Lt.rho0;
     p.err = bp.err;
+    p.wait_tries = kWaitTries;
     p.eq2 = 0;
     p.has_drag = 0;
     p.drag_d0 = p.drag_d1 = p.us_x = p.us_y = 0.f;
@@ -518,12 +541,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     for (int r = c.rlo; r <= min(c.y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
     __syncwarp();
     const bool ok = warp_run_strip<S, true>(c);
-    if (!ok && lane == 0)
-        for (int r = c.waited + 1; r <= c.issued; ++r) {
-            const int s = wslot(r);
-            mbar_wait_bounded(c.bar(r), (c.phase >> s) & 1u, kWaitTries);
-            c.phase ^= 1u << s;
-        }
+    if (!ok && lane == 0) batch_drain(c, c.phase);
 }
 
 }  // namespace lbmv

@@ -35,11 +35,34 @@ __device__ __forceinline__ float dec(float s, float rest, float inv_scale) { ret
 __device__ __forceinline__ float dec(__half s, float rest, float inv_scale) { return fmaf(__half2float(s), inv_scale, rest); }
 __device__ __forceinline__ float dec(__nv_bfloat16 s, float rest, float inv_scale) { return fmaf(__bfloat162float(s), inv_scale, rest); }
 
+// The same decode in FP64 (the read-back kernels): the stored deviation and the rest
+// value are added without the FP32 rounding at the scale of f.
+__device__ __forceinline__ double decd(double s, double, double) { return s; }
+__device__ __forceinline__ double decd(float s, double rest, double inv_scale) { return fma((double)s, inv_scale, rest); }
+__device__ __forceinline__ double decd(__half s, double rest, double inv_scale) {
+    return fma((double)__half2float(s), inv_scale, rest);
+}
+__device__ __forceinline__ double decd(__nv_bfloat16 s, double rest, double inv_scale) {
+    return fma((double)__bfloat162float(s), inv_scale, rest);
+}
+template <typename T, typename S> __device__ __forceinline__ T dec_as(S s, T rest, T inv_scale) {
+    if constexpr (sizeof(T) == 8) return decd(s, rest, inv_scale);
+    else return dec(s, rest, inv_scale);
+}
+
 template <typename S, typename R> __device__ __forceinline__ S enc(R f, R rest, R scale);
 template <> __device__ __forceinline__ double enc<double, double>(double f, double, double) { return f; }
 template <> __device__ __forceinline__ float enc<float, float>(float f, float rest, float scale) { return (f - rest) * scale; }
 template <> __device__ __forceinline__ __half enc<__half, float>(float f, float rest, float scale) { return __float2half_rn((f - rest) * scale); }
 template <> __device__ __forceinline__ __nv_bfloat16 enc<__nv_bfloat16, float>(float f, float rest, float scale) { return __float2bfloat16_rn((f - rest) * scale); }
+// FP64 values into every storage (the write-back kernel): the deviation is formed in FP64
+template <> __device__ __forceinline__ float enc<float, double>(double f, double rest, double scale) { return (float)((f - rest) * scale); }
+template <> __device__ __forceinline__ __half enc<__half, double>(double f, double rest, double scale) {
+    return __float2half_rn((float)((f - rest) * scale));
+}
+template <> __device__ __forceinline__ __nv_bfloat16 enc<__nv_bfloat16, double>(double f, double rest, double scale) {
+    return __float2bfloat16_rn((float)((f - rest) * scale));
+}
 
 // Rest-state populations of Eq. (14) (u = 0, rho = rho0): w_i kappa rho0 for
 // i >= 1 and (phi - 5 kappa / 9) rho0 for i = 0.

@@ -130,6 +130,7 @@ struct PairCtx {
     int wsp, ww;
     int rlo, rhi;
     int waited, issued;
+    int first_bad = 0x7fffffff;   // first row whose wait gave up (this thread)
 
     __device__ __forceinline__ uint64_t* bar(int r) const { return reinterpret_cast<uint64_t*>(smem) + pslot(r); }
     __device__ __forceinline__ const S* pop(int r) const {
@@ -167,7 +168,8 @@ struct PairCtx {
         r = min(r, rhi);
         while (waited < r) {
             ++waited;
-            if (!mbar_wait_bounded(bar(waited), parity(waited), kWaitTries)) {
+            if (!mbar_wait_bounded(bar(waited), parity(waited), p.wait_tries)) {
+                first_bad = min(first_bad, waited);
                 *abort_flag = 1;
                 atomicExch(p.err, 1);
             }
@@ -489,7 +491,9 @@ __global__ void __launch_bounds__(T, MINB) vanse_pair_kernel(const __grid_consta
         if (ok && it + 2 < n_it) ok = iter(s2, s1, s0, p1 + 2);
     }
     if (!ok && t == 0) {
-        for (int r = c.waited + 1; r <= c.issued; ++r) mbar_wait_bounded(c.bar(r), c.parity(r), kWaitTries);
+        // every copy that may still be in flight (see kWaitTries)
+        for (int r = min(c.first_bad, c.waited + 1); r <= c.issued; ++r)
+            mbar_wait_bounded(c.bar(r), c.parity(r), kWaitTries);
     }
 }
 

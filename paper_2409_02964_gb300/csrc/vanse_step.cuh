@@ -38,6 +38,10 @@ namespace lbmv {
 
 constexpr int kSlots = 8;                  // ring slots (power of two)
 constexpr uint32_t kWaitTries = 1u << 22;  // bounded mbarrier polls (seconds, far above a row's latency)
+// The default bound of a staged-row wait is kWaitTries (StepParams::wait_tries; a test may
+// lower it to make the waits give up). Whatever that bound, a CTA drains the copies it
+// issued with kWaitTries before it exits: from the first row whose wait gave up (its copy
+// may still be in flight) to the newest row issued, so no copy lands after the exit.
 
 // Compile-time shared-memory layout of the step kernel.
 template <typename S, typename R, int T>
@@ -88,6 +92,7 @@ struct StepParams {
     // h_* x scale, rho0 x scale and inv_scale / 3 (equal to h_*, rho0, 1/3 at scale 1)
     R hs_e, hs_eps, hs_q, hs_nu, rho0s, kp3;
     const unsigned* step_ctr;   // one-warp kernel: steps taken (seeds the stochastic rounding), or nullptr
+    uint32_t wait_tries;        // polls of a staged-row wait before it gives up (kWaitTries by default)
 };
 
 // Compensated (Kahan) sums of the post-collision m_0, j_x, j_y of the cells one
@@ -132,6 +137,7 @@ struct StepCtx {
     int rlo, rhi;       // source rows this CTA loads
     int waited;         // newest row waited for
     int issued;         // newest row issued (thread 0 only)
+    int first_bad = 0x7fffffff;   // first row whose wait gave up (this thread)
 
     __device__ __forceinline__ uint64_t* bar(int r) const {
         return reinterpret_cast<uint64_t*>(smem) + (r & (kSlots - 1));
@@ -175,7 +181,8 @@ struct StepCtx {
         while (waited < r) {
             ++waited;
             const uint32_t parity = (uint32_t)(((waited - rlo) >> 3) & 1);
-            if (!mbar_wait_bounded(bar(waited), parity, kWaitTries)) {
+            if (!mbar_wait_bounded(bar(waited), parity, p.wait_tries)) {
+                first_bad = min(first_bad, waited);
                 *abort_flag = 1;
                 atomicExch(p.err, 1);
             }
@@ -706,8 +713,9 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
         if (ok && it + 2 < n_it) ok = iter(s2, s1, s0, p1 + 2);
     }
     if (!ok && t == 0) {
-        // drain: wait (bounded) for every copy issued, so none lands after exit
-        for (int r = c.waited + 1; r <= c.issued; ++r) {
+        // drain: wait (bounded) for every copy that may still be in flight, so none
+        // lands after exit (the rows whose wait gave up and those not waited for yet)
+        for (int r = min(c.first_bad, c.waited + 1); r <= c.issued; ++r) {
             const uint32_t parity = (uint32_t)(((r - c.rlo) >> 3) & 1);
             mbar_wait_bounded(c.bar(r), parity, kWaitTries);
         }

@@ -107,6 +107,7 @@ struct WarpCtx {
     RowCopy cp;
     bool st_pair;              // this lane stores its pair (lanes 1..30, first column inside)
     mutable PairSums sums;     // used when kSums
+    int first_bad = 0x7fffffff;   // first row whose wait gave up (this lane)
     uint32_t step = 0, salt = 0;   // seed of the stochastic rounding of FP16/BF16 stores
 
     __device__ __forceinline__ uint64_t* bar(int r) const { return reinterpret_cast<uint64_t*>(smem) + wslot(r); }
@@ -173,7 +174,8 @@ struct WarpCtx {
         r = min(r, rhi);
         while (waited < r) {
             ++waited;
-            if (!mbar_wait_bounded(bar(waited), parity(waited), kWaitTries)) {
+            if (!mbar_wait_bounded(bar(waited), parity(waited), p.wait_tries)) {
+                first_bad = min(first_bad, waited);
                 aborted = true;
                 atomicExch(p.err, 1);
             }
@@ -518,7 +520,12 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
     };
 
     const int n_it = (y1 + 1) - (y0 - 2) + 1;
-    bool ok = true;
+    // The rows the first iteration needs (y0-3 .. y0-1) are waited for here, with a vote:
+    // inside the loop each iteration then waits for one new row r (iteration r-1), whose
+    // slot is refilled at iteration r+3, after the vote that ends the group of three rows
+    // holding iteration r-1. So a slot whose wait gave up is never armed again.
+    c.wait_upto(y0 - 1);
+    bool ok = !__any_sync(0xffffffffu, c.aborted);
     for (int it = 0; it < n_it && ok; it += 3) {
         const int p1 = y0 - 2 + it;
         iter(s0, s2, s1, p1);
@@ -571,8 +578,10 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     if (c.fast_strip && (!p.wall_y || (y0 >= 3 && y1 <= p.ny - 3))) warp_run_strip<S, true>(c);
     else warp_run_strip<S, false>(c);
     if (lane == 0) {
-        // every issued row is waited for before the CTA exits (bounded)
-        for (int r = c.waited + 1; r <= c.issued; ++r) mbar_wait_bounded(c.bar(r), c.parity(r), kWaitTries);
+        // every copy that may still be in flight is waited for before the CTA exits
+        // (the rows whose wait gave up and those not waited for yet; see kWaitTries)
+        for (int r = min(c.first_bad, c.waited + 1); r <= c.issued; ++r)
+            mbar_wait_bounded(c.bar(r), c.parity(r), kWaitTries);
     }
     if constexpr (SUMS) {
         for (int k = 0; k < 3; ++k) {

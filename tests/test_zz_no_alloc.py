@@ -27,10 +27,19 @@ def P():
     return pkg
 
 
-def _channel(P, nx, ny, storage):
+def _channel(P, nx, ny, storage, solid_block=False):
     from synth import fields
     phi = fields.channel_phi(nx, ny)
-    lat = P.Lattice(nx, ny, 0.6, s_e=1.2, s_eps=1.2, s_q=1.2, bc_y="bounceback", storage=storage)
+    kw = {}
+    if solid_block:
+        # an impermeable block (phi = 0 cells, Sec. 3.3) and a few isolated solid cells;
+        # solid cells run on step kernel 1
+        phi[ny // 3:ny // 2, nx // 4:nx // 3] = 0.0
+        phi[5, 7] = phi[ny - 3, nx - 2] = 0.0
+        kw = dict(kernel=1)
+    lat = P.Lattice(nx, ny, 0.6, s_e=1.2, s_eps=1.2, s_q=1.2, bc_y="bounceback", storage=storage, **kw)
+    if solid_block:
+        lat.set_solid_cells()
     lat.set_void_fraction(phi)
     lat.set_body_force(1e-5, 0.0)
     rho, ux, uy = fields.rest_fields(nx, ny)
@@ -38,11 +47,14 @@ def _channel(P, nx, ny, storage):
     return lat
 
 
-@pytest.mark.parametrize("storage", ["fp64", "fp32"])
-def test_noalloc_reduce_matches_reduce_on_consecutive_calls(P, storage):
+@pytest.mark.parametrize("storage,solid_block", [("fp64", False), ("fp32", False), ("fp16", False),
+                                                 ("bf16", False), ("fp64", True), ("fp32", True)])
+def test_noalloc_reduce_matches_reduce_on_consecutive_calls(P, storage, solid_block):
+    """Every storage decodes its populations in the reduction (FP16/BF16 hold scaled
+    deviations from the rest state); solid cells hold no populations and are skipped."""
     import torch
     L = P.capi.load()
-    lat = _channel(P, 300, 173, storage)
+    lat = _channel(P, 300, 173, storage, solid_block)
     out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
     for call in range(2):
         lat.step(7)
