@@ -40,6 +40,15 @@ DTYPE = {"fp32": "f32", "fp16": "f32", "bf16": "f32", "fp64": "f64"}
 SBYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}
 
 
+def _config(n: int, storage: str, gpus: int) -> dict:
+    """The workload as both arms name it (identical keys and values): the lattice, and
+    how the timed steps relate to L2 (inputs larger than L2, no flush needed)."""
+    pop_gb = 2 * 9 * n * n * SBYTES[storage] / 1e9
+    return {"workload": WORKLOAD, "nx": n, "ny": n, "storage": storage,
+            "l2": f"inputs larger than L2: two population buffers of {pop_gb:.2f} GB against the 129 MB L2",
+            "parallelism": "replicas" if gpus > 1 else "single"}
+
+
 def _kernel_traffic(cells: int):
     """DRAM bytes per launch of the step kernel from the committed ncu capture (a
     smaller channel, scaled by cells), or None when a source the kernel is built
@@ -205,31 +214,54 @@ def mms_errors(steps: int = 1000):
     return out
 
 
+def _channel512_golden():
+    """The FP64 oracle's u and p after 10 000 steps of the channel recipe at 512 x 512
+    (tests/golden/channel512_oracle.txt, written by tests/golden/make_channel512.py
+    from the oracle alone): full-field sums and the values at 2048 seeded cells."""
+    path = os.path.join(ROOT, "tests", "golden", "channel512_oracle.txt")
+    head, rows = {}, []
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if len(parts) == 2:
+                head[parts[0]] = float(parts[1])
+            else:
+                rows.append([float(v) for v in parts])
+    a = np.array(rows)
+    return head, a[:, 0].astype(int), a[:, 1].astype(int), a[:, 2], a[:, 3], a[:, 4]
+
+
 def channel_precision(n: int = 512, steps: int = 10000):
-    """The channel recipe regenerated at n x n, `steps` steps from rest per storage;
-    relative L2 error of u, and RMS error of p = rho/3, against the FP64 path (which
-    matches the FP64 oracle to 1e-12)."""
+    """The channel recipe regenerated at n x n, `steps` steps from rest per storage,
+    against the FP64 oracle's run of the same recipe (a committed golden: its
+    velocity and pressure at 2048 seeded cells and its full-field sum of |u|^2).
+    E_u: relative L2 velocity error (Eq. 26) over the sampled cells; p_rms_err: RMS
+    error of p = rho / 3 there; max_rel_u: largest |u - u_oracle| relative to the
+    largest |u_oracle| of the sample."""
     import paper_2409_02964_gb300 as P
     from synth import fields
+    head, xs, ys, ux_o, uy_o, p_o = _channel512_golden()
     phi = fields.channel_phi(n, n)
     rho, ux, uy = fields.rest_fields(n, n)
-    res = {}
+    out = {"workload": f"channel recipe at {n}x{n}, {steps} steps from rest, each storage against the FP64 "
+                       f"oracle (golden tests/golden/channel512_oracle.txt: {len(xs)} seeded cells)",
+           "u_max_oracle": head["u_max"]}
+    den = np.sum(ux_o ** 2 + uy_o ** 2)
+    umax = float(np.max(np.sqrt(ux_o ** 2 + uy_o ** 2)))
     for st in ("fp64", "fp32", "fp16", "bf16"):
         lat = P.Lattice(n, n, TAU, bc_y="bounceback", storage=st, **RATES)
         lat.set_void_fraction(phi)
         lat.set_body_force(G, 0.0)
         lat.init_fields(rho, ux, uy)
         lat.step(steps)
-        res[st] = {k: v.cpu().numpy() for k, v in lat.macros().items()}
+        m = {k: v.cpu().numpy()[ys, xs] for k, v in lat.macros().items()}
         lat.close()
-    r = res["fp64"]
-    den = np.sum(r["ux"] ** 2 + r["uy"] ** 2)
-    out = {"workload": f"channel recipe at {n}x{n}, {steps} steps from rest, vs the FP64 path",
-           "u_max_fp64": float(np.abs(r["ux"]).max())}
-    for st in ("fp32", "fp16", "bf16"):
-        m = res[st]
-        out[st] = {"E_u": float(np.sqrt(np.sum((m["ux"] - r["ux"]) ** 2 + (m["uy"] - r["uy"]) ** 2) / den)),
-                   "p_rms_err": float(np.sqrt(np.mean((m["p"] - r["p"]) ** 2)))}
+        du2 = (m["ux"] - ux_o) ** 2 + (m["uy"] - uy_o) ** 2
+        out[st] = {"E_u": float(np.sqrt(np.sum(du2) / den)),
+                   "p_rms_err": float(np.sqrt(np.mean((m["p"] - p_o) ** 2))),
+                   "max_rel_u": float(np.sqrt(du2.max()) / umax)}
     return out
 
 
@@ -409,7 +441,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": nx, "ny": args.n, "storage": "fp64 (oracle)"},
+        "config": _config(args.n, args.storage, args.gpus),
+        "arithmetic": "FP64 oracle on the host cores",
         "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -493,10 +526,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.storage], "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "storage": args.storage,
-                       "bytes_per_cell": bpc, "l2": "inputs larger than L2 (two population buffers of "
-                       f"{2 * 9 * cells * SBYTES[args.storage] / 1e9:.2f} GB, L2 129 MB)",
-                       "parallelism": "replicas" if world > 1 else "single", "launch": shape},
+            "config": _config(args.n, args.storage, world),
+            "bytes_per_cell": bpc, "launch": shape,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
                          "traffic": _kernel_traffic(cells) if (args.storage == "fp32" and shape["threads"] == 32) else None,

@@ -3,11 +3,18 @@ FP64 oracle: every lattice of a batch runs the spatiotemporal manufactured
 solution with its own size, relaxation time, amplitude, period and U0; the
 oracle runs each lattice alone from the same manufactured fields (synth.mms).
 
-Tolerances follow the single-lattice parity tests: FP32 compute rounds each
-population by a few tens of units of 2^-24 |f| per step (the in-kernel FP32
-evaluation of phi and of the Eq. (25) force adds errors of the same order), so
-the bound is 32 * 2^-24 * max|f| per step; FP16 / BF16 storage add 2 * 2^-11 /
-2 * 2^-8 of max|f - f_rest| per step."""
+Tolerances. The batch kernel stores and collides deviations from the rest state
+like the single-lattice kernel 5, so its own arithmetic rounds at the scale of the
+deviations: K5 * 2^-24 D per step, D = max|f - f_rest| (see test_gpu_parity). It
+also evaluates phi(x, t) and the Eq. (25) force in FP32 inside the kernel (sin and
+cos of k x, k y, w t): its phi differs from the oracle's FP64 phi by a few units of
+2^-24 phi, and f_0's rest value rho0 (phi(t) - phi(t+1)) and rho = sum f / phi carry
+that difference: KPHI * 2^-24 rho0 max(phi) per step (measured: at most 1.5 units
+of 2^-24 max(phi) per step; the deviation part, K5 = 8 as for kernel 5, is far
+smaller on these lattices). The oracle starts from the
+device's initial populations (read back exactly; the initial state is computed in
+FP32, at the scale of f, and checked on its own against the oracle's). FP16 / BF16
+storage add 2 * 2^-11 / 2 * 2^-8 of D per step."""
 import numpy as np
 import pytest
 
@@ -18,6 +25,7 @@ from gpu_cases import rest_populations
 pytestmark = pytest.mark.gpu
 
 EPS32 = 2.0 ** -24
+K5, KPHI = 8, 4
 
 # n, tau, A, T, U0: ragged tails against the 60-column units (32, 75, 130),
 # a lattice narrower than the 3-cell ghost band's reach (7), several units per lattice
@@ -54,26 +62,34 @@ def _oracle_params(O, n, tau, s_e=1.2, s_eps=1.2, s_q=1.2):
     return O.Params(nx=n, ny=n, **kw, kappa=0.5)
 
 
-def _oracle_run(O, lat, steps, phi0=0.7, s_e=1.2):
+def _oracle_run(O, lat, steps, phi0=0.7, s_e=1.2, f_start=None):
+    """The oracle on one batch lattice: from its own initial state (Eq. 6, 14), or
+    from f_start (the device's initial populations)."""
     n, tau, A, T, U0 = lat
     M = mms.Config1(n=n, T=T, A=A, phi0=phi0, U0=U0)
     nu = (tau - 0.5) / 3.0
     prm = _oracle_params(O, n, tau, s_e)
     ux, uy = M.velocity(0)
-    f = O.init(prm, np.ones((n, n)), ux, uy, M.phi(0), M.force(0, nu))
+    f = O.init(prm, np.ones((n, n)), ux, uy, M.phi(0), M.force(0, nu)) if f_start is None else f_start.copy()
     for t in range(steps):
         f = O.step(prm, f, M.phi(t), M.phi(t + 1), M.force(t, nu))
     return f, M, prm
 
 
-def _check(fg, fo, phi, steps, storage):
+def _check(fg, fo, phi, steps, storage, init=False):
+    """init: the initial state (FP32 arithmetic at the scale of f: 8 * 2^-24 max|f|)."""
     dev = np.abs(fo - rest_populations(phi)).max()
-    tol = steps * 32 * EPS32 * np.abs(fo).max()
+    if init:
+        tol = 8 * EPS32 * np.abs(fo).max()
+    else:
+        tol = steps * (K5 * EPS32 * dev + KPHI * EPS32 * float(phi.max()))
     if storage == "fp16":
         tol += steps * 2 * 2.0 ** -11 * dev
     elif storage == "bf16":
         tol += steps * 2 * 2.0 ** -8 * dev
     err = np.abs(fg - fo).max()
+    print(f"batch {storage} n={fo.shape[-1]}: error {err / (EPS32 * dev):.1f} x 2^-24 D "
+          f"(bound {tol / (EPS32 * dev):.1f})")
     assert err <= tol, (err, tol)
 
 
@@ -82,10 +98,11 @@ def test_batch_matches_oracle(P, O, storage):
     steps = 5
     b = P.Batch(LATTICES, storage=storage, strip_rows=16, eager=True)
     b.init()
+    f0 = [b.populations(i).cpu().numpy() for i in range(len(LATTICES))]
     b.step(steps)
     assert b.step_count == steps
     for i, lat in enumerate(LATTICES):
-        fo, M, _ = _oracle_run(O, lat, steps)
+        fo, M, _ = _oracle_run(O, lat, steps, f_start=f0[i])
         _check(b.populations(i).cpu().numpy(), fo, M.phi(steps), steps, storage)
     b.close()
 
@@ -95,9 +112,10 @@ def test_batch_derived_energy_rate_matches_oracle(P, O):
     steps = 4
     b = P.Batch(LATTICES, s_e=0.0, eager=True)
     b.init()
+    f0 = [b.populations(i).cpu().numpy() for i in range(len(LATTICES))]
     b.step(steps)
     for i, lat in enumerate(LATTICES):
-        fo, M, _ = _oracle_run(O, lat, steps, s_e=0.0)
+        fo, M, _ = _oracle_run(O, lat, steps, s_e=0.0, f_start=f0[i])
         _check(b.populations(i).cpu().numpy(), fo, M.phi(steps), steps, "fp32")
     b.close()
 
@@ -107,8 +125,14 @@ def test_batch_initial_populations(P, O):
     b.init()
     for i, lat in enumerate(LATTICES):
         fo, M, _ = _oracle_run(O, lat, 0)
-        _check(b.populations(i).cpu().numpy(), fo, M.phi(0), 1, "fp32")
+        _check(b.populations(i).cpu().numpy(), fo, M.phi(0), 1, "fp32", init=True)
     b.close()
+
+
+def _dev(i, steps, f):
+    """Largest deviation from rest of batch lattice i's populations f after `steps` steps."""
+    n, tau, A, T, U0 = LATTICES[i]
+    return np.abs(f - rest_populations(mms.Config1(n=n, T=T, A=A, U0=U0).phi(steps))).max()
 
 
 @pytest.mark.parametrize("rows", [1, 5, 16, 200])
@@ -125,7 +149,7 @@ def test_batch_unit_height_invariance(P, rows):
     b.step(steps)
     for i in range(len(LATTICES)):
         a, c = ref.populations(i).cpu().numpy(), b.populations(i).cpu().numpy()
-        assert np.abs(a - c).max() <= 64 * EPS32 * np.abs(a).max()
+        assert np.abs(a - c).max() <= steps * K5 * EPS32 * _dev(i, steps, a)
     ref.close()
     b.close()
 
@@ -140,7 +164,7 @@ def test_persistent_equals_one_launch_per_lattice(P):
     b.step_each(steps)
     for i in range(len(LATTICES)):
         x, y = a.populations(i).cpu().numpy(), b.populations(i).cpu().numpy()
-        assert np.abs(x - y).max() <= 64 * EPS32 * np.abs(x).max()
+        assert np.abs(x - y).max() <= steps * K5 * EPS32 * _dev(i, steps, x)
     a.close()
     b.close()
 
@@ -209,8 +233,9 @@ def test_autotune_picks_a_candidate_and_resets(P, O):
     rows = b.autotune(trial_steps=4)
     assert rows in (16, 24, 32, 48, 64, 96, 128, 192, 256)
     assert b.step_count == 0
+    f0 = b.populations(2).cpu().numpy()
     b.step(3)
-    fo, M, _ = _oracle_run(O, LATTICES[2], 3)
+    fo, M, _ = _oracle_run(O, LATTICES[2], 3, f_start=f0)
     _check(b.populations(2).cpu().numpy(), fo, M.phi(3), 3, "fp32")
     b.close()
 
@@ -251,17 +276,18 @@ def test_full_batch_sampled_lattices_match_oracle(P, O):
     b = P.Batch(lats)
     b.autotune(trial_steps=2)
     steps = 3
-    b.step(steps)
     order = sorted(range(len(lats)), key=lambda i: lats[i][0])
-    for i in (order[0], order[len(order) // 2], order[-1]):
+    picks = (order[0], order[len(order) // 2], order[-1])
+    f0 = {i: b.populations(i).cpu().numpy() for i in picks}   # the device's initial state
+    b.step(steps)
+    for i in picks:
         n, tau, A, T, U0 = lats[i]
         M = mms.Config1(n=n, T=T, A=A, U0=U0)
         nu = (tau - 0.5) / 3.0
         kw = O.rates_from_tau(tau, s_eps=1.2, s_q=1.2)
         kw["s_e"] = 1.2
         prm = O.Params(nx=n, ny=n, **kw, kappa=0.5, nthreads=0)
-        ux, uy = M.velocity(0)
-        f = O.init(prm, np.ones((n, n)), ux, uy, M.phi(0), M.force(0, nu))
+        f = f0[i]
         for t in range(steps):
             f = O.step(prm, f, M.phi(t), M.phi(t + 1), M.force(t, nu))
         _check(b.populations(i).cpu().numpy(), f, M.phi(steps), steps, "fp32")
