@@ -108,6 +108,7 @@ struct lbm_vanse {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_done = nullptr, staging_free = nullptr;
     void* staging[2] = {nullptr, nullptr};
+    CUtensorMap pop_map[2];       // kernel 5: each population buffer as a tensor [9][ny][P] (tma_load_3d)
     int kernel = 1;               // step-kernel variant (see kNumKernels)
     bool pair = false;            // two columns per thread (packed FP32) step kernel
     std::string msg;
@@ -335,6 +336,7 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
     p.has_solid = h->has_solid;
     p.step_ctr = h->step_ctr;
     p.wait_tries = h->wait_tries;
+    if (h->kernel == 5) p.pop_map = h->pop_map[src];
     dim3 grid(h->gridx, h->gridy);
     if (h->has_solid) return launch_solid_step<S>(h, p, grid, smem, stream, sums != nullptr);
     if (sums) {
@@ -678,6 +680,59 @@ lbm_status ensure_scratch(lbm_vanse* h) {
 
 bool rate_ok(double s) { return s > 0.0 && s < 2.0; }
 
+// The tensor map of one population buffer for the one-warp kernel: a 3-D tensor
+// [9 planes][ny rows][P columns] of the storage type (row and plane strides are
+// multiples of 16 bytes: P is a multiple of 32), box = the staged width WW x 1 row x 9
+// planes. cuTensorMapEncodeTiled comes from the driver through the runtime's entry
+// point, so the library links no driver library of its own.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+template <typename S>
+lbm_status encode_pop_map(lbm_vanse* h, void* buf, CUtensorMap* out) {
+    static EncodeTiledFn enc = nullptr;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!enc) {
+            cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+            void* fn = nullptr;
+            const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                                   cudaEnableDefault, &q);
+            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+                return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+            enc = (EncodeTiledFn)fn;
+        }
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)h->P, (cuuint64_t)h->prm.ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)h->P * sizeof(S), (cuuint64_t)h->plane * sizeof(S)};
+    const cuuint32_t box[3] = {(cuuint32_t)WarpLayout<S>::WW, 1, 9};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (std::is_same<S, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    const CUresult r = enc(out, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return LBM_OK;
+}
+
+template <typename S>
+lbm_status encode_pop_maps(lbm_vanse* h) {
+    if constexpr (std::is_same<S, double>::value) {
+        return LBM_OK;
+    } else {
+        if (h->kernel != 5) return LBM_OK;
+        for (int b = 0; b < 2; ++b) {
+            const lbm_status st = encode_pop_map<S>(h, h->f[b], &h->pop_map[b]);
+            if (st != LBM_OK) return st;
+        }
+        return LBM_OK;
+    }
+}
+
 }  // namespace
 
 // ================================================== allocation-free reduction
@@ -854,6 +909,7 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
               alloc((void**)&h->partial, kReduceBlocks * 3 * sizeof(double)) &&
               alloc((void**)&h->red_out, 4 * sizeof(double));
     if (ok) st = DISPATCH(h, configure);
+    if (ok && st == LBM_OK) st = DISPATCH(h, encode_pop_maps);
     if (!ok || st != LBM_OK) {
         g_create_error = h->msg;
         lbm_vanse_destroy(h);

@@ -2,6 +2,7 @@
 // wrappers (mbarrier, bulk async copy) shared by the MRTLB-VANSE kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -122,6 +123,17 @@ __device__ __forceinline__ void bulk_g2s_at(uint32_t dst, const void* src, uint3
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst), "l"(src),
         "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// 3-D tiled tensor copy global -> shared: the box of the tensor map at coordinates
+// (x, y, z), completing on an mbarrier. The map lives in the kernel's parameters; x
+// times the element size must be a multiple of 16 bytes, the destination 128-byte
+// aligned.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
 

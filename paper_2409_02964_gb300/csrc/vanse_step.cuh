@@ -93,6 +93,9 @@ struct StepParams {
     R hs_e, hs_eps, hs_q, hs_nu, rho0s, kp3;
     const unsigned* step_ctr;   // one-warp kernel: steps taken (seeds the stochastic rounding), or nullptr
     uint32_t wait_tries;        // polls of a staged-row wait before it gives up (kWaitTries by default)
+    // one-warp kernel: the source buffer as a tensor [9][ny][P] whose box (the staged
+    // width x 1 row x 9 planes) stages a row's nine population rows in one copy
+    CUtensorMap pop_map;
 };
 
 // Compensated (Kahan) sums of the post-collision m_0, j_x, j_y of the cells one

@@ -8,8 +8,10 @@
 //     rows, no CTA barriers), so every warp runs its row pipeline independently and
 //     a stalled warp never holds the others up;
 //   * arithmetic on the packed FP32 pairs of vanse_pair.cuh (FFMA2 / FADD2 / FMUL2);
-//   * the source-row ring (cp.async.bulk + mbarriers, 8 slots) is per warp; the
-//     slot of row p - 3 is refilled with row p + 5 at the start of iteration p;
+//   * the source-row ring (8 slots, mbarriers) is per warp; the slot of row p - 3 is
+//     refilled with row p + 5 at the start of iteration p: the nine population rows
+//     by one 3-D tensor copy (cp.async.bulk.tensor, lane 0), the phi / phi(t+1) /
+//     force rows by 1-D bulk copies (lanes 1..4);
 //   * interior rows of steady, field-free strips run one branch-free block (no
 //     wall / validity / field tests), so the collision of one row can overlap the
 //     pulls and shuffles of the next two.
@@ -40,7 +42,7 @@ struct WarpLayout {
     static constexpr int WW = 64 + 2 * A;           // staged row width (elements)
     static constexpr int kPop = 128;                // after the mbarriers
     static constexpr int kPopRow = WW * (int)sizeof(S);
-    static constexpr int kPopSlot = 9 * kPopRow;
+    static constexpr int kPopSlot = (9 * kPopRow + 127) / 128 * 128;   // tensor-copy destinations: 128-byte aligned
     static constexpr int kAux = kPop + kWarpSlots * kPopSlot;
     static constexpr int kAuxRow = WW * 4;
     static constexpr size_t bytes(int nR) { return (size_t)kAux + (size_t)kWarpSlots * nR * kAuxRow; }
@@ -52,10 +54,12 @@ __device__ __forceinline__ int wslot(int r) {
     else return ((r % kWarpSlots) + kWarpSlots) % kWarpSlots;
 }
 
-// One source row of a strip is staged by up to 13 one-dimensional bulk copies (the 9
-// population rows, then phi, phi(t+1), F^B_x, F^B_y where the step reads them). Lane
-// i issues copy i, so a row costs the warp a handful of instructions; lane 0 first
-// arms the slot's mbarrier with the row's total byte count.
+// One source row of a strip is staged by a few copies into one ring slot, each issued
+// by one lane; lane 0 first arms the slot's mbarrier with the row's total byte count.
+// The one-warp step kernel stages the nine population rows with one 3-D tensor copy
+// (lane 0; a copy costs its warp hundreds of cycles to issue, so one request instead
+// of nine took the step from 67.7 to 73.8 GLUPS) and phi, phi(t+1), F^B_x, F^B_y with
+// 1-D bulk copies; the batch kernels issue one 1-D bulk copy per population row.
 struct RowCopy {
     const char* src = nullptr;   // this lane's source at row 0
     uint32_t pitch = 0;          // bytes per source row
@@ -64,13 +68,16 @@ struct RowCopy {
     uint32_t bytes = 0;          // bytes of this lane's copy (0: none)
     uint32_t tx = 0;             // bytes of the whole row (every lane)
     uint32_t bar0 = 0;           // shared address of the slot-0 mbarrier
+    const CUtensorMap* map = nullptr;   // this lane copies a tensor box: the map, its first column
+    int xcol = 0;
 
     // all lanes: stage global row gr into ring slot s
     __device__ __forceinline__ void issue(int lane, int s, int gr) const {
         const uint32_t b = bar0 + 8u * (uint32_t)s;
         if (lane == 0) mbar_expect_tx_at(b, tx);
         __syncwarp();
-        if (bytes) bulk_g2s_at(dst + (uint32_t)s * stride, src + (long long)gr * (long long)pitch, bytes, b);
+        if (map) tma_load_3d(dst + (uint32_t)s * stride, map, xcol, gr, 0, b);
+        else if (bytes) bulk_g2s_at(dst + (uint32_t)s * stride, src + (long long)gr * (long long)pitch, bytes, b);
     }
 };
 
@@ -139,20 +146,22 @@ struct WarpCtx {
         }
     }
 
-    // this lane's part of staging a source row (see RowCopy)
+    // this lane's part of staging a source row (see RowCopy): lane 0 the nine
+    // population rows, a box of the whole staged width WW (wsp is a multiple of 16
+    // bytes, so the box starts on a 16-byte boundary, and wsp + WW stays inside the
+    // padded row); lanes 1..nR the aux rows
     __device__ __forceinline__ void setup_copies() {
         const uint32_t base = smem_u32(smem);
         cp.bar0 = base;
-        cp.tx = 9u * (uint32_t)(ww * (int)sizeof(S)) + (uint32_t)p.nR * (uint32_t)(ww * 4);
-        if (lane < 9) {
-            cp.src = reinterpret_cast<const char*>(reinterpret_cast<const S*>(p.src) + lane * p.plane + wsp);
-            cp.pitch = (uint32_t)(p.P * (int)sizeof(S));
-            cp.dst = base + (uint32_t)(L::kPop + lane * L::kPopRow);
+        cp.tx = 9u * (uint32_t)(L::WW * (int)sizeof(S)) + (uint32_t)p.nR * (uint32_t)(ww * 4);
+        if (lane == 0) {
+            cp.map = &p.pop_map;
+            cp.xcol = wsp;
+            cp.dst = base + (uint32_t)L::kPop;
             cp.stride = (uint32_t)L::kPopSlot;
-            cp.bytes = (uint32_t)(ww * (int)sizeof(S));
-        } else if (lane < 9 + p.nR) {
+        } else if (lane <= p.nR) {
             // aux rows in the order phi, phi(t+1) (unsteady), F^B_x, F^B_y (force field)
-            const int k = lane - 9;
+            const int k = lane - 1;
             const float* a = p.phi;
             if (k == 1 && p.unsteady) a = p.phin;
             else if (k >= 1) a = p.fb + (k - (p.unsteady ? 2 : 1)) * p.plane;
