@@ -689,8 +689,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-template <typename S>
-lbm_status encode_pop_map(lbm_vanse* h, void* buf, CUtensorMap* out) {
+// Encodes the map of one population buffer (P columns per row, ny rows, planes of
+// `plane` elements, storage `storage`); returns an empty string or the failure.
+std::string encode_pop_map_raw(void* buf, int P, int ny, long long plane, int storage, CUtensorMap* out) {
     static EncodeTiledFn enc = nullptr;
     static std::mutex mu;
     {
@@ -701,21 +702,31 @@ lbm_status encode_pop_map(lbm_vanse* h, void* buf, CUtensorMap* out) {
             const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                                                    cudaEnableDefault, &q);
             if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-                return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+                return "cuTensorMapEncodeTiled is not available from the driver";
             enc = (EncodeTiledFn)fn;
         }
     }
-    const cuuint64_t dims[3] = {(cuuint64_t)h->P, (cuuint64_t)h->prm.ny, 9};
-    const cuuint64_t strides[2] = {(cuuint64_t)h->P * sizeof(S), (cuuint64_t)h->plane * sizeof(S)};
-    const cuuint32_t box[3] = {(cuuint32_t)WarpLayout<S>::WW, 1, 9};
+    const int sb = storage_bytes(storage);
+    const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)P * sb, (cuuint64_t)plane * sb};
+    // the staged width WarpLayout<S>::WW: 64 columns plus 16 bytes on each side
+    const cuuint32_t box[3] = {(cuuint32_t)(64 + 2 * (16 / sb)), 1, 9};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUtensorMapDataType dt = sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                   : (std::is_same<S, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    const CUtensorMapDataType dt = storage == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (storage == LBM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
     const CUresult r = enc(out, dt, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return std::string();
+}
+
+template <typename S>
+lbm_status encode_pop_map(lbm_vanse* h, void* buf, CUtensorMap* out) {
+    static_assert(WarpLayout<S>::WW == 64 + 2 * (16 / (int)sizeof(S)), "box width of encode_pop_map_raw");
+    const std::string e = encode_pop_map_raw(buf, h->P, h->prm.ny, h->plane, h->prm.storage, out);
+    if (!e.empty()) return fail(h, LBM_ERR_CUDA, "%s", e.c_str());
     return LBM_OK;
 }
 
@@ -1561,6 +1572,11 @@ extern "C" lbm_status lbm_vanse_batch_create(const lbm_vanse_batch_lattice* latt
             const size_t bytes = ((size_t)9 * b->desc[i].plane * b->sbytes + 255) / 256 * 256;
             b->desc[i].buf[0] = (char*)b->pool + b->offsets[i];
             b->desc[i].buf[1] = (char*)b->pool + b->offsets[i] + bytes;
+            for (int k = 0; k < 2 && st == LBM_OK; ++k) {
+                const std::string err = encode_pop_map_raw(b->desc[i].buf[k], b->desc[i].P, b->desc[i].ny,
+                                                           b->desc[i].plane, p->storage, &b->desc[i].map[k]);
+                if (!err.empty()) st = bfail(nullptr, LBM_ERR_CUDA, "batch tensor maps: %s", err.c_str());
+            }
         }
         e = cudaMalloc((void**)&b->d_desc, count * sizeof(BatchLattice));
         if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_clock, 4 * sizeof(int));

@@ -25,6 +25,7 @@
 namespace lbmv {
 
 struct BatchLattice {
+    CUtensorMap map[2];        // each buffer as a tensor [9][ny][P] (box: staged width x 1 x 9)
     void* buf[2];              // population buffers (ping-pong by the parity of t)
     long long plane;           // elements per population plane
     int nx, ny, P;
@@ -103,18 +104,20 @@ struct BatchCtx {
         Fy = fma2(rho0, f.fy, Fy);
     }
 
-    // this lane's part of staging a source row: lanes 0..8 copy the population rows
-    __device__ __forceinline__ void setup_copies() {
+    // this lane's part of staging a source row: lane 0 copies the nine population rows
+    // with one 3-D tensor copy of the lattice's buffer (map: its tensor map in the
+    // lattice descriptor, in global memory; a box of the whole staged width, starting
+    // on the 16-byte aligned column wsp)
+    __device__ __forceinline__ void setup_copies(const CUtensorMap* map) {
         const uint32_t base = smem_u32(smem);
         cp = RowCopy{};
         cp.bar0 = base;
-        cp.tx = 9u * (uint32_t)(ww * (int)sizeof(S));
-        if (lane < 9) {
-            cp.src = reinterpret_cast<const char*>(reinterpret_cast<const S*>(p.src) + lane * p.plane + wsp);
-            cp.pitch = (uint32_t)(p.P * (int)sizeof(S));
-            cp.dst = base + (uint32_t)(L::kPop + lane * L::kPopRow);
+        cp.tx = 9u * (uint32_t)(L::WW * (int)sizeof(S));
+        if (lane == 0) {
+            cp.map = map;
+            cp.xcol = wsp;
+            cp.dst = base + (uint32_t)L::kPop;
             cp.stride = (uint32_t)L::kPopSlot;
-            cp.bytes = (uint32_t)(ww * (int)sizeof(S));
         }
     }
     // all lanes: load source row r (periodic) into its slot
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_kernel(const __grid_cons
         c.fast_lo = c.y0;
         c.fast_hi = c.y1 + 1;
 
-        c.setup_copies();
+        c.setup_copies(&Lt.map[t & 1]);
         __syncwarp();
         fence_proxy_async();
         for (int r = c.rlo; r <= min(c.y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
@@ -326,7 +329,7 @@ __device__ __forceinline__ Lattice<float> batch_as_lattice(const BatchLattice& L
 // written where the first pull finds it (buffer 0).
 template <typename S>
 __global__ void batch_init_kernel(const BatchLattice* lats, int index, float scale, float inv_scale) {
-    const BatchLattice L = lats[index];
+    const BatchLattice& L = lats[index];
     const Lattice<float> Q = batch_as_lattice(L, scale, inv_scale);
     const long long n = (long long)L.nx * L.ny;
     for (long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x; kk < n; kk += (long long)gridDim.x * blockDim.x) {
@@ -383,7 +386,7 @@ __device__ __forceinline__ void batch_pull(const BatchLattice& L, const Lattice<
 template <typename S>
 __global__ void batch_get_kernel(const BatchLattice* lats, int index, const int* clock, double* out, float scale,
                                  float inv_scale) {
-    const BatchLattice L = lats[index];
+    const BatchLattice& L = lats[index];
     const Lattice<float> Q = batch_as_lattice(L, scale, inv_scale);
     const int t = *clock;
     const long long n = (long long)L.nx * L.ny;
@@ -400,7 +403,7 @@ __global__ void batch_get_kernel(const BatchLattice* lats, int index, const int*
 template <typename S>
 __global__ void batch_rho_kernel(const BatchLattice* lats, int index, const int* clock, double* rho, float scale,
                                  float inv_scale) {
-    const BatchLattice L = lats[index];
+    const BatchLattice& L = lats[index];
     const Lattice<float> Q = batch_as_lattice(L, scale, inv_scale);
     const int t = *clock;
     const float ct = cosf(L.w * (float)t);
@@ -421,7 +424,7 @@ __global__ void batch_rho_kernel(const BatchLattice* lats, int index, const int*
 template <typename S>
 __global__ void batch_err_kernel(const BatchLattice* lats, int index, const int* clock, const double* rho,
                                  double* partial, float scale, float inv_scale) {
-    const BatchLattice L = lats[index];
+    const BatchLattice& L = lats[index];
     const Lattice<float> Q = batch_as_lattice(L, scale, inv_scale);
     const int t = *clock;
     float st, ct;
@@ -537,7 +540,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_batch_one_kernel(const __grid_
     c.fast_strip = true;
     c.fast_lo = c.y0;
     c.fast_hi = c.y1 + 1;
-    c.setup_copies();
+    c.setup_copies(&Lt.map[t & 1]);
     for (int r = c.rlo; r <= min(c.y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
     __syncwarp();
     const bool ok = warp_run_strip<S, true>(c);
