@@ -361,29 +361,62 @@ def d3q19_run(n: int = 256, steps: int = 200, warmup: int = 5):
 
 
 def adjoint_run(n: int = 1024, nsteps: int = 4000, avg: int = 100, ckpt: int = 200):
-    """The differentiation workload: J and dJ/dphi through the C ABI; forward and
-    backward device time from CUDA events inside the call."""
+    """The differentiation workload: J and dJ/dphi through the C ABI, with the two-level
+    host checkpoints (the default: sub-segments of ceil(sqrt(K)) states on the device)
+    and with whole segments on the device; forward and backward device time from CUDA
+    events inside the call, device and pinned host memory held."""
     import paper_2409_02964_gb300 as P
     from synth import fields
-    ch = P.Channel(nx=n, ny=n, nsteps=nsteps, avg_steps=avg, checkpoint_every=ckpt)
     phi = fields.channel_phi(n, n)
     P.outlet_momentum(phi[:64, :64], P.Channel(nx=64, ny=64, nsteps=4, avg_steps=2, checkpoint_every=2))  # warm-up
-    J, g, st = P.outlet_momentum(phi, ch)
-    fwd_s, bwd_s = st["forward_ms"] / 1e3, st["backward_ms"] / 1e3
     lups = n * n * nsteps
-    ga = g.abs()
-    # FP64 flops per cell of one forward step (598) and of one backward step with its
-    # segment recompute (1614), from the ncu instruction counts of the adjoint kernels
-    flops = 598.0 + 1614.0
-    achieved = flops * lups / (fwd_s + bwd_s) / 1e12
-    return {"workload": ADJOINT_WORKLOAD, "J": J, "max_abs_grad": float(ga.max()),
-            "roofline": {"bound": "alu", "unit": "FP64 TFLOP/s", "achieved": round(achieved, 3), "peak": 1.25,
-                         "frac": round(achieved / 1.25, 3), "flops_per_cell_step": flops,
-                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)"},
-            "forward_s": round(fwd_s, 3), "backward_s": round(bwd_s, 3),
-            "forward_MLUPS": round(lups / fwd_s / 1e6, 1),
-            "forward_backward_MLUPS": round(lups / (fwd_s + bwd_s) / 1e6, 1),
-            "device_bytes": st["device_bytes"], "dtype": "f64"}
+    out = {"workload": ADJOINT_WORKLOAD}
+    for name, dense in (("two_level", False), ("dense_segments", True)):
+        ch = P.Channel(nx=n, ny=n, nsteps=nsteps, avg_steps=avg, checkpoint_every=ckpt, dense_segments=dense)
+        J, g, st = P.outlet_momentum(phi, ch)
+        fwd_s, bwd_s = st["forward_ms"] / 1e3, st["backward_ms"] / 1e3
+        # FP64 flops per cell: a forward step 598; a backward step with its segment
+        # recompute 1614 (ncu instruction counts of the adjoint kernels); the two-level
+        # scheme recomputes every step once more (598)
+        flops = 598.0 + 1614.0 + (0.0 if dense else 598.0)
+        achieved = flops * lups / (fwd_s + bwd_s) / 1e12
+        out[name] = {"J": J, "max_abs_grad": float(g.abs().max()),
+                     "forward_s": round(fwd_s, 3), "backward_s": round(bwd_s, 3),
+                     "forward_MLUPS": round(lups / fwd_s / 1e6, 1),
+                     "forward_backward_MLUPS": round(lups / (fwd_s + bwd_s) / 1e6, 1),
+                     "device_bytes": st["device_bytes"], "host_bytes": st["host_bytes"],
+                     "roofline": {"bound": "alu", "unit": "FP64 TFLOP/s", "achieved": round(achieved, 3),
+                                  "peak": 1.25, "frac": round(achieved / 1.25, 3), "flops_per_cell_step": flops,
+                                  "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)"}}
+        del g
+    out["bit_identical"] = out["two_level"]["J"] == out["dense_segments"]["J"]
+    out["dtype"] = "f64"
+    return out
+
+
+def adjoint_fd_check(n: int = 1024, nsteps: int = 4000, avg: int = 100, ckpt: int = 200, cells: int = 64,
+                     h: float = 1e-4):
+    """Central differences (h = 1e-4) of the device's own J at `cells` seeded cells of
+    the full differentiation workload against its dJ/dphi (2 * cells forward runs)."""
+    import paper_2409_02964_gb300 as P
+    from synth import fields
+    phi = fields.channel_phi(n, n)
+    ch = P.Channel(nx=n, ny=n, nsteps=nsteps, avg_steps=avg, checkpoint_every=ckpt)
+    J, g, _ = P.outlet_momentum(phi, ch)
+    g = g.cpu().numpy()
+    rng = np.random.default_rng(2409)
+    pts = [(int(rng.integers(n)), int(rng.integers(n))) for _ in range(cells)]
+    gmax = float(np.abs(g).max())
+    worst, rows = 0.0, []
+    for y, x in pts:
+        pp, pm = phi.copy(), phi.copy()
+        pp[y, x] += h
+        pm[y, x] -= h
+        fd = (P.outlet_momentum(pp, ch, grad=False)[0] - P.outlet_momentum(pm, ch, grad=False)[0]) / (2 * h)
+        worst = max(worst, abs(fd - g[y, x]) / gmax)
+        rows.append([y, x, fd, float(g[y, x])])
+    return {"workload": ADJOINT_WORKLOAD, "cells": cells, "h": h, "J": J, "max_abs_grad": gmax,
+            "largest_difference_over_max_grad": worst, "samples": rows}
 
 
 def oracle_rate(n_rows: int, nx: int, steps: int, threads: int):
@@ -468,6 +501,8 @@ def main():
     ap.add_argument("--adjoint-only", action="store_true", help="run only the differentiation workload")
     ap.add_argument("--adjoint-n", type=int, default=1024)
     ap.add_argument("--adjoint-steps", type=int, default=4000)
+    ap.add_argument("--adjoint-fd", action="store_true",
+                    help="central differences at 64 seeded cells of the differentiation workload (slow)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--no-3d", action="store_true", help="skip the 3-D (D3Q19) workload")
@@ -478,6 +513,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint_fd:
+        print(json.dumps({"adjoint_fd": adjoint_fd_check(args.adjoint_n, args.adjoint_steps)}), flush=True)
+        return 0
     if args.adjoint_only:
         print(json.dumps({"adjoint": adjoint_run(args.adjoint_n, args.adjoint_steps, min(100, args.adjoint_steps),
                                                   min(200, args.adjoint_steps))}), flush=True)

@@ -323,22 +323,30 @@ void lbm_vanse_batch_destroy(lbm_vanse_batch_t b);
  * dJ/dphi(x) is the exact derivative of this discrete J (every path by which phi
  * enters: Eq. 7 rho, Eq. 13 F^p, X = kappa / phi in Eq. 18 and Eq. 20, F^B and
  * f(0)), computed by a hand-written adjoint of the step run backwards in time. The
- * forward pass stores a checkpoint every checkpoint_every steps; the backward pass
- * recomputes one segment at a time, holding its states. Everything runs in FP64 on
- * the stream given, whatever p->storage says. The paper has no adjoint; this is the
- * differentiable-design use of its method. */
+ * forward pass stores a checkpoint every K = checkpoint_every steps; the backward
+ * pass recomputes one segment of K steps at a time. With dense_segments = 0 (the
+ * default) the checkpoints live in pinned host memory, and inside a segment the
+ * states every K2 = ceil(sqrt(K)) steps are recomputed and also kept on the host;
+ * the device holds one sub-segment of K2 states (about 2 + K2 population arrays and
+ * a few fields in all; every step is recomputed twice in the backward pass). With
+ * dense_segments = 1 the checkpoints and a whole segment of K states stay on the
+ * device (one recomputation, K + T/K population arrays). Both give bit-identical
+ * results. Everything runs in FP64 on the stream given, whatever p->storage says.
+ * The paper has no adjoint; this is the differentiable-design use of its method. */
 typedef struct {
     int nsteps;            /* >= 1 */
     int avg_steps;         /* 1 .. nsteps */
     int checkpoint_every;  /* >= 1 */
     int x_out;             /* outlet column, 0 .. nx - 1 */
     double gx, gy;         /* F^B = phi (gx, gy) */
+    int dense_segments;    /* 0: checkpoints on the host, K2-state sub-segments; 1: all on the device */
 } lbm_vanse_adjoint_params;
 
 typedef struct {
     double forward_ms;     /* device time of the forward pass (with checkpoints) */
     double backward_ms;    /* device time of the backward pass (with recomputation) */
     long long device_bytes;  /* device memory the call held at its peak */
+    long long host_bytes;    /* pinned host memory it held for checkpoints */
 } lbm_vanse_adjoint_stats;
 
 /* phi: [ny][nx] doubles, on the device (on_device = 1) or host; read only. J

@@ -36,6 +36,7 @@ class Channel:
     avg_steps: int = 100
     checkpoint_every: int = 200
     x_out: int = -1          # -1: the last column
+    dense_segments: bool = False   # True: checkpoints and whole segments on the device
 
 
 def _params(ch: Channel):
@@ -51,6 +52,7 @@ def _params(ch: Channel):
     a.nsteps, a.avg_steps, a.checkpoint_every = ch.nsteps, ch.avg_steps, ch.checkpoint_every
     a.x_out = ch.x_out if ch.x_out >= 0 else ch.nx - 1
     a.gx, a.gy = ch.gx, ch.gy
+    a.dense_segments = int(ch.dense_segments)
     return p, a
 
 
@@ -73,7 +75,8 @@ def outlet_momentum(phi, ch: Channel, grad: bool = True, stream=None):
     if rc != capi.LBM_OK:
         msg = L.lbm_vanse_last_error(None)
         raise LbmError(rc, msg.decode() if msg else "")
-    stats = {"forward_ms": st.forward_ms, "backward_ms": st.backward_ms, "device_bytes": st.device_bytes}
+    stats = {"forward_ms": st.forward_ms, "backward_ms": st.backward_ms, "device_bytes": st.device_bytes,
+             "host_bytes": st.host_bytes}
     return J.value, out, stats
 
 

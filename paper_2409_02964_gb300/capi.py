@@ -88,12 +88,13 @@ class lbm_vanse_adjoint_params(ctypes.Structure):
     _fields_ = [
         ("nsteps", ctypes.c_int), ("avg_steps", ctypes.c_int), ("checkpoint_every", ctypes.c_int),
         ("x_out", ctypes.c_int), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+        ("dense_segments", ctypes.c_int),
     ]
 
 
 class lbm_vanse_adjoint_stats(ctypes.Structure):
     _fields_ = [("forward_ms", ctypes.c_double), ("backward_ms", ctypes.c_double),
-                ("device_bytes", ctypes.c_longlong)]
+                ("device_bytes", ctypes.c_longlong), ("host_bytes", ctypes.c_longlong)]
 
 
 _lib = None

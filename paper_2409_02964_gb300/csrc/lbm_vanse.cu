@@ -1701,6 +1701,8 @@ namespace {
 struct AdjBuffers {
     std::vector<void*> held;
     long long bytes = 0;
+    void* host = nullptr;         // pinned host checkpoints
+    long long host_bytes = 0;
     cudaStream_t st = nullptr;
     cudaError_t err = cudaSuccess;
     double* get(long long n) {
@@ -1711,9 +1713,16 @@ struct AdjBuffers {
         bytes += n * (long long)sizeof(double);
         return (double*)q;
     }
+    double* get_host(long long n) {
+        if (err == cudaSuccess) err = cudaMallocHost(&host, (size_t)n * sizeof(double));
+        if (err != cudaSuccess) { host = nullptr; return nullptr; }
+        host_bytes = n * (long long)sizeof(double);
+        return (double*)host;
+    }
     ~AdjBuffers() {
         for (void* q : held) cudaFreeAsync(q, st);
         cudaStreamSynchronize(st);
+        if (host) cudaFreeHost(host);
     }
 };
 
@@ -1760,13 +1769,21 @@ extern "C" lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, 
     const int T = a->nsteps, M = a->avg_steps, K = a->checkpoint_every;
     const int nck = (T - 1) / K + 1;
     const bool want_grad = dJdphi != nullptr;
+    // Two levels (dense_segments = 0): the checkpoints every K steps and, while a
+    // segment is processed backwards, its states every K2 steps are kept in pinned host
+    // memory; the device holds one sub-segment of K2 states. One level: checkpoints and
+    // a whole segment of K states on the device.
+    const bool dense = a->dense_segments != 0;
+    const int K2 = dense ? std::min(K, T) : std::max(1, (int)std::ceil(std::sqrt((double)std::min(K, T))));
+    const int nsub = (std::min(K, T) - 1) / K2 + 1;   // sub-checkpoints per segment
 
     AdjBuffers B;
     B.st = st;
     double* d_phi = B.get(N);
     double* fa = B.get(N9);
     double* fb = B.get(N9);
-    double* ck = B.get((long long)nck * N9);
+    double* ck = dense ? B.get((long long)nck * N9) : B.get_host((long long)(nck + (want_grad ? nsub : 0)) * N9);
+    double* ck1 = dense ? nullptr : ck + (long long)nck * N9;   // host: a segment's sub-checkpoints
     adj::Fields F;
     F.s = B.get(N); F.rho = B.get(N); F.ux = B.get(N); F.uy = B.get(N); F.Fx = B.get(N); F.Fy = B.get(N);
     F.drx = B.get(N); F.dry = B.get(N); F.fld = B.get(6 * N);
@@ -1774,7 +1791,7 @@ extern "C" lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, 
     double *seg = nullptr, *lam = nullptr, *lam2 = nullptr, *gphi = nullptr;
     adj::Adj A;
     if (want_grad) {
-        seg = B.get((long long)std::min(K, T) * N9);
+        seg = B.get((long long)K2 * N9);
         lam = B.get(N9);
         lam2 = B.get(N9);
         gphi = B.get(N);
@@ -1784,8 +1801,9 @@ extern "C" lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, 
         A.ldrx = B.get(N); A.ldry = B.get(N);
     }
     if (B.err != cudaSuccess)
-        return fail(nullptr, B.err == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "adjoint buffers (%lld bytes): %s",
-                    B.bytes, cudaGetErrorString(B.err));
+        return fail(nullptr, B.err == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                    "adjoint buffers (%lld device bytes, %lld host bytes): %s", B.bytes, B.host_bytes,
+                    cudaGetErrorString(B.err));
 #define ACK(call)                                                                                              \
     do {                                                                                                       \
         cudaError_t e_ = (call);                                                                               \
@@ -1809,8 +1827,10 @@ extern "C" lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, 
     // forward: f(0), checkpoints every K steps, objective over the last M steps
     adj::adj_init_kernel<<<nb, nt, 0, st>>>(P, d_phi, fa);
     double *cur = fa, *nxt = fb;
+    const cudaMemcpyKind to_ck = dense ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const cudaMemcpyKind from_ck = dense ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     for (int n = 0; n < T; ++n) {
-        if (n % K == 0) ACK(cudaMemcpyAsync(ck + (long long)(n / K) * N9, cur, N9 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (n % K == 0) ACK(cudaMemcpyAsync(ck + (long long)(n / K) * N9, cur, N9 * sizeof(double), to_ck, st));
         fwd_step(cur, nxt);
         std::swap(cur, nxt);
         if (n + 1 > T - M) {
@@ -1830,17 +1850,39 @@ extern "C" lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, 
         adj::adj_bwd_collide<<<nb, nt, 0, st>>>(P, cur, d_phi, F, nullptr, A, gphi);
         adj::adj_bwd_u<<<nb, nt, 0, st>>>(P, cur, d_phi, F, A, wgt, gphi);
         adj::adj_bwd_rho<<<nb, nt, 0, st>>>(P, d_phi, F, A, lam, gphi);
-        for (int k = nck - 1; k >= 0; --k) {
-            const int n0 = k * K, n1 = std::min(n0 + K, T);
-            ACK(cudaMemcpyAsync(seg, ck + (long long)k * N9, N9 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            for (int j = 1; j < n1 - n0; ++j) fwd_step(seg + (long long)(j - 1) * N9, seg + (long long)j * N9);
-            for (int n = n1 - 1; n >= n0; --n) {
-                const double* fn = seg + (long long)(n - n0) * N9;
+        // backward over the steps m1 - 1 .. m0, whose states are seg[0 .. m1 - m0 - 1]
+        auto backward = [&](int m0, int m1) {
+            for (int n = m1 - 1; n >= m0; --n) {
+                const double* fn = seg + (long long)(n - m0) * N9;
                 fwd_fields(fn);
                 adj::adj_bwd_collide<<<nb, nt, 0, st>>>(P, fn, d_phi, F, lam, A, gphi);
                 adj::adj_bwd_u<<<nb, nt, 0, st>>>(P, fn, d_phi, F, A, n > T - M ? wgt : 0.0, gphi);
                 adj::adj_bwd_rho<<<nb, nt, 0, st>>>(P, d_phi, F, A, lam2, gphi);
                 std::swap(lam, lam2);
+            }
+        };
+        for (int k = nck - 1; k >= 0; --k) {
+            const int n0 = k * K, n1 = std::min(n0 + K, T);
+            if (dense) {
+                ACK(cudaMemcpyAsync(seg, ck + (long long)k * N9, N9 * sizeof(double), from_ck, st));
+                for (int j = 1; j < n1 - n0; ++j) fwd_step(seg + (long long)(j - 1) * N9, seg + (long long)j * N9);
+                backward(n0, n1);
+                continue;
+            }
+            // the segment's states every K2 steps to the host (fa, fb: the running state)
+            const int ns = (n1 - n0 - 1) / K2 + 1;
+            ACK(cudaMemcpyAsync(fa, ck + (long long)k * N9, N9 * sizeof(double), from_ck, st));
+            double *c0 = fa, *c1 = fb;
+            for (int j = 0; j < ns; ++j) {
+                ACK(cudaMemcpyAsync(ck1 + (long long)j * N9, c0, N9 * sizeof(double), cudaMemcpyDeviceToHost, st));
+                if (j + 1 < ns)
+                    for (int i = 0; i < K2; ++i) { fwd_step(c0, c1); std::swap(c0, c1); }
+            }
+            for (int j = ns - 1; j >= 0; --j) {
+                const int m0 = n0 + j * K2, m1 = std::min(m0 + K2, n1);
+                ACK(cudaMemcpyAsync(seg, ck1 + (long long)j * N9, N9 * sizeof(double), cudaMemcpyHostToDevice, st));
+                for (int i = 1; i < m1 - m0; ++i) fwd_step(seg + (long long)(i - 1) * N9, seg + (long long)i * N9);
+                backward(m0, m1);
             }
         }
         adj::adj_bwd_init<<<nb, nt, 0, st>>>(P, lam, gphi);
@@ -1857,6 +1899,7 @@ extern "C" lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, 
         stats->forward_ms = f_ms;
         stats->backward_ms = want_grad ? b_ms : 0.0;
         stats->device_bytes = B.bytes;
+        stats->host_bytes = B.host_bytes;
     }
 #undef ACK
     return LBM_OK;

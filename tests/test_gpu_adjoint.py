@@ -67,12 +67,18 @@ def test_channel_crop_128_matches_autograd_oracle(P):
 
 
 def test_checkpoint_spacing_does_not_change_the_result(P):
+    """Any checkpoint spacing, with the two-level host checkpoints (sub-segments of
+    ceil(sqrt(K)) states on the device) or with whole segments on the device: the
+    recomputed states are the same kernels' results, so J and dJ/dphi are
+    bit-identical."""
     base = dict(nx=31, ny=17, nsteps=25, avg_steps=6)
     phi = _phi(31, 17, 2)
     outs = []
-    for K in (1, 4, 25, 100):
-        J, g, _ = P.outlet_momentum(phi, P.Channel(**base, checkpoint_every=K))
-        outs.append((J, g.cpu().numpy()))
+    for K in (1, 4, 7, 25, 100):
+        for dense in (False, True):
+            J, g, st = P.outlet_momentum(phi, P.Channel(**base, checkpoint_every=K, dense_segments=dense))
+            outs.append((J, g.cpu().numpy()))
+            assert (st["host_bytes"] == 0) == dense
     for J, g in outs[1:]:
         assert J == outs[0][0]
         assert np.array_equal(g, outs[0][1])
@@ -147,8 +153,18 @@ def test_full_size_workload_central_differences(P):
     n = 1024
     ch = P.Channel(nx=n, ny=n, nsteps=4000, avg_steps=100, checkpoint_every=200)
     phi = fields.channel_phi(n, n)
-    J, g, _ = P.outlet_momentum(phi, ch)
+    J, g, st = P.outlet_momentum(phi, ch)
     g = g.cpu().numpy()
+    # two-level checkpoints: 15-state sub-segments on the device (under 2 GB), the 20
+    # checkpoints and 14 sub-checkpoints on the host; whole segments on the device
+    # (17 GB) give the same bits
+    print(f"device {st['device_bytes'] / 1e9:.2f} GB, host {st['host_bytes'] / 1e9:.2f} GB, "
+          f"forward {st['forward_ms']:.0f} ms, backward {st['backward_ms']:.0f} ms")
+    assert st["device_bytes"] <= 2e9
+    Jd, gd, std = P.outlet_momentum(phi, P.Channel(nx=n, ny=n, nsteps=4000, avg_steps=100, checkpoint_every=200,
+                                                   dense_segments=True))
+    assert Jd == J and np.array_equal(gd.cpu().numpy(), g)
+    assert std["device_bytes"] > 10e9 and std["host_bytes"] == 0
     rng = np.random.default_rng(2409)
     cells = [tuple(int(v) for v in np.unravel_index(np.argmax(np.abs(g)), g.shape)), (n // 2, n - 1),
              (int(rng.integers(n)), int(rng.integers(n)))]
