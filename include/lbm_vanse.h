@@ -72,7 +72,7 @@ typedef struct {
                                     pairs with 64 / 96 / 128-thread CTAs; 5 = one warp per CTA,
                                     two columns per lane (2..5: not FP64) */
     int eq_order;                /* 3 (or 0): the 3rd-order equilibrium of Eq. (14) with Eq. (18), (20);
-                                    2: App. B, Eq. (B1)-(B3) (kernel 1 only) */
+                                    2: App. B, Eq. (B1)-(B3) (kernels 1 and 5) */
 } lbm_vanse_params;
 
 typedef struct lbm_vanse* lbm_vanse_t;

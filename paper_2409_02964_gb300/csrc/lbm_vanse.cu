@@ -212,7 +212,9 @@ const void* step_kernel_ptr(const lbm_vanse* h) {
             case 2: return (const void*)vanse_pair_kernel<S, 64, 6>;
             case 3: return (const void*)vanse_pair_kernel<S, 96, 4>;
             case 4: return (const void*)vanse_pair_kernel<S, 128, 3>;
-            case 5: return (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB>;
+            case 5:
+                return h->prm.eq_order == 2 ? (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB, false, true>
+                                            : (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB>;
             default: break;
         }
     }
@@ -252,7 +254,9 @@ template <typename S>
 const void* step_sums_kernel_ptr(const lbm_vanse* h) {
     using R = typename Prec<S>::R;
     if constexpr (!std::is_same<S, double>::value) {
-        if (h->kernel == 5) return (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB, true>;
+        if (h->kernel == 5)
+            return h->prm.eq_order == 2 ? (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB, true, true>
+                                        : (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB, true>;
         if (h->kernel != 1) return nullptr;
     }
     return (const void*)vanse_step_kernel<S, R, kThreads, true>;   // (solid cells: launch_solid_step)
@@ -351,7 +355,8 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
         }
         if constexpr (!std::is_same<S, double>::value) {
             if (h->kernel == 5) {
-                vanse_warp_kernel<S, LBMV_WARP_MINB, true><<<grid, 32, smem, stream>>>(p);
+                if (p.eq2) vanse_warp_kernel<S, LBMV_WARP_MINB, true, true><<<grid, 32, smem, stream>>>(p);
+                else vanse_warp_kernel<S, LBMV_WARP_MINB, true><<<grid, 32, smem, stream>>>(p);
                 CK(h, cudaGetLastError());
                 const long long ng = 9LL * h->prm.ny * 2 * kGhost;
                 ghost_fill_kernel<S><<<(int)std::min<long long>((ng + 255) / 256, 4096), 256, 0, stream>>>(
@@ -370,7 +375,8 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
             case 3: vanse_pair_kernel<S, 96, 4><<<grid, 96, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
             case 4: vanse_pair_kernel<S, 128, 3><<<grid, 128, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
             case 5: {
-                vanse_warp_kernel<S, LBMV_WARP_MINB><<<grid, 32, smem, stream>>>(p);
+                if (p.eq2) vanse_warp_kernel<S, LBMV_WARP_MINB, false, true><<<grid, 32, smem, stream>>>(p);
+                else vanse_warp_kernel<S, LBMV_WARP_MINB><<<grid, 32, smem, stream>>>(p);
                 CK(h, cudaGetLastError());
                 // the one-warp kernel writes columns 0 .. nx-1 only
                 const long long ng = 9LL * h->prm.ny * 2 * kGhost;
@@ -892,12 +898,12 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
         delete h;
         return fail(nullptr, LBM_ERR_ARG, "eq_order must be 2 (App. B) or 3 (Eq. 14; 0 = 3)");
     }
-    if (p->eq_order == 2 && p->kernel >= 2) {
+    if (p->eq_order == 2 && p->kernel >= 2 && p->kernel <= 4) {
         delete h;
-        return fail(nullptr, LBM_ERR_ARG, "the App. B equilibrium runs on kernel 1 only");
+        return fail(nullptr, LBM_ERR_ARG, "the App. B equilibrium runs on kernels 1 and 5");
     }
     if (h->prm.eq_order == 0) h->prm.eq_order = 3;
-    h->kernel = p->kernel ? p->kernel : ((p->storage == LBM_FP64 || p->eq_order == 2) ? 1 : kDefaultKernel);
+    h->kernel = p->kernel ? p->kernel : (p->storage == LBM_FP64 ? 1 : kDefaultKernel);
     h->pair = h->kernel >= 2;
     h->W = h->kernel == 5 ? 60 : (h->pair ? 2 * kPairT[h->kernel - 2] - 4 : kThreads - 4);
     h->gridx = (p->nx + h->W - 1) / h->W;

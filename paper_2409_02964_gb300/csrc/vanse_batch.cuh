@@ -65,6 +65,7 @@ struct BatchCtx {
     using L = WarpLayout<S>;
     static constexpr bool kUnsteady = true;
     static constexpr bool kSums = false;
+    static constexpr bool kEq2 = false;
     StepParams<float> p;       // this lattice's scalars (pointers and sizes included)
     unsigned char* smem;
     int lane, xa, sa;

@@ -115,6 +115,7 @@ struct PRow {
     V2 Fx, Fy, ux, uy;
     V2 dAx, dBx, dBy, dDx;
     V2 wAy, wBy, wBx, wDy;
+    V2 dGy, wGx;       // one-warp kernel with App. B: G = phi rho u - kappa rho u (the (B3) cross terms)
 };
 
 __device__ __forceinline__ int pslot(int r) { return ((r % kPairSlots) + kPairSlots) % kPairSlots; }

@@ -96,11 +96,12 @@ struct PairSums {
     }
 };
 
-template <typename S, bool SUMS = false>
+template <typename S, bool SUMS = false, bool EQ2 = false>
 struct WarpCtx {
     using L = WarpLayout<S>;
     static constexpr bool kUnsteady = false;   // the fast path runs only on steady strips
     static constexpr bool kSums = SUMS;        // accumulate the written cells' m_0+, j+ (PairSums)
+    static constexpr bool kEq2 = EQ2;          // App. B: (B2) energy-flux equilibria, (B3) penalty
     const StepParams<float>& p;
     unsigned char* smem;
     int lane, xa, sa;
@@ -327,6 +328,16 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
     Bs.wBy = fma2(4.f, uy, rpair(uy, Byr) + lpair(uy, Byl));
     Bs.wBx = fma2(4.f, ux, rpair(ux, Bxr) + lpair(ux, Bxl));
     Bs.wDy = fma2(4.f, Dy, rpair(Dy, Dyr) + lpair(Dy, Dyl));
+    if constexpr (Ctx::kEq2) {
+        // (B3) needs the cross derivatives d_x(rho u_y), d_y(rho u_x), d_x(phi rho u_y),
+        // d_y(phi rho u_x) only as -kappa (d_x A_y + d_y A_x) + (d_x D_y + d_y D_x), the
+        // cross derivatives of G = D - kappa A
+        const V2 Gx = fma2(-p.kappa, Ax, Dx), Gy = fma2(-p.kappa, Ay, Dy);
+        const float Gyl = left_of(Gy), Gyr = right_of(Gy);
+        const float Gxl = left_of(Gx), Gxr = right_of(Gx);
+        Bs.dGy = rpair(Gy, Gyr) - lpair(Gy, Gyl);
+        Bs.wGx = fma2(4.f, Gx, rpair(Gx, Gxr) + lpair(Gx, Gxl));
+    }
 }
 
 template <typename S, bool FAST, typename Ctx>
@@ -369,10 +380,26 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     const V2 kp = p.model_b ? bc(p.kappa - 1.f) : bc(p.kappa) - phi;
     const V2 kr = kp * rho;
     const V2 divD = xDx + yDy, difD = xDx - yDy;
-    V2 Ca = fma2(tw, fma2(-p.kappa, xAx + yAy, fma2(2.f * kr, xBx + yBy, fma2(-2.f, X, bc(3.f)) * divD)), bc(0.f));
+    V2 Ca, Cb, Cc;
+    if constexpr (Ctx::kEq2) {
+        // Eq. (B3)
+        V2 xGy = fma2(4.f, Cs.dGy, An.dGy + Bs.dGy);
+        V2 yGx = Bs.wGx - An.wGx;
+        if (!FAST && p.wall_y && (p3 == 0 || p3 == p.ny - 1)) {
+            const bool lo = (p3 == 0), hi = (p3 == p.ny - 1);
+            xGy = fma2(4.f, Cs.dGy, (lo ? -Cs.dGy : An.dGy) + (hi ? -Cs.dGy : Bs.dGy));
+            yGx = (hi ? -Cs.wGx : Bs.wGx) - (lo ? -Cs.wGx : An.wGx);
+        }
+        Ca = tw * fma2(-2.f * p.kappa, xAx + yAy, fma2(2.f * kr, xBx + yBy, fma2(-2.f, X, bc(4.f)) * divD));
+        Cb = (tw * (2.f / 3.f)) * fma2(-p.kappa, xAx - yAy, fma2(kr, xBx - yBy, difD));
+        Cc = (1.f / 36.f) * fma2(kr, xBy + yBx, xGy + yGx);
+    } else {
+        // Eq. (20)
+        Ca = fma2(tw, fma2(-p.kappa, xAx + yAy, fma2(2.f * kr, xBx + yBy, fma2(-2.f, X, bc(3.f)) * divD)), bc(0.f));
+        Cb = tw * fma2(-p.kappa, xAx - yAy, fma2((2.f / 3.f) * kr, xBx - yBy, difD));
+        Cc = (1.f / 36.f) * (kr * (xBy + yBx));
+    }
     if (!FAST || Ctx::kUnsteady) Ca = fma2(-2.f, (X * rho) * (phin - phi), Ca);
-    const V2 Cb = tw * fma2(-p.kappa, xAx - yAy, fma2((2.f / 3.f) * kr, xBx - yBy, difD));
-    const V2 Cc = (1.f / 36.f) * (kr * (xBy + yBx));
     // Eq. (18), (19), (16) on the deviations from the rest state: the rest state's
     // moments (phi rho0, rho0 (2 kappa - 4 phi), rho0 (4 phi - 3 kappa), 0, ...) leave
     // m_0, e and eps; the equilibria of e and eps then differ from them by
@@ -384,7 +411,7 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     // equilibrium and source terms in the storage's scaled units
     const V2 m0s = sizeof(S) == 4 ? m0 : p.scale * m0;
     const V2 jxe = m0s * ux, jye = m0s * uy;
-    const V2 q = X - bc(2.f);
+    const V2 q = Ctx::kEq2 ? bc(-1.f) : X - bc(2.f);   // Eq. (18) / (B2) energy-flux equilibria
     const V2 m0uu3 = m0s * (3.f * uu);
     V2 a[9];
     a[0] = dm0;
@@ -548,7 +575,7 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
     return ok;
 }
 
-template <typename S, int MINB, bool SUMS = false>
+template <typename S, int MINB, bool SUMS = false, bool EQ2 = false>
 __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_constant__ StepParams<float> p) {
     using L = WarpLayout<S>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -558,7 +585,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     const int y0 = blockIdx.y * p.H;
     const int y1 = min(y0 + p.H, p.ny);
 
-    WarpCtx<S, SUMS> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
+    WarpCtx<S, SUMS, EQ2> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
     if constexpr (sizeof(S) == 2) c.step = p.step_ctr ? *p.step_ctr : 0u;
     c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
     c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
@@ -571,7 +598,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     c.waited = c.rlo - 1;
     c.issued = c.rlo - 1;
     // rows whose three phases need no wall, validity or field handling
-    c.fast_strip = !p.unsteady && !p.has_fb && !p.has_drag;
+    c.fast_strip = !p.unsteady && !p.has_fb && !p.has_drag;   // (the EQ2 instance's fast path evaluates B3)
     c.fast_lo = p.wall_y ? max(y0, 1) : y0;                 // lowest phase-3 row
     c.fast_hi = p.wall_y ? min(y1 + 1, p.ny - 2) : y1 + 1;  // highest phase-1 row
 

@@ -1,10 +1,12 @@
 """Physics variants on the GPU against the FP64 oracle: the linear drag with the
 implicit velocity (lbm_vanse_set_drag; kernels 1 and 5) and the App. B equilibrium
-(eq_order = 2; kernel 1), on walled and periodic lattices with moving phi and force
-fields; and the analytic Darcy-Brinkman channel (Eq. 22 I) on the device.
+(eq_order = 2; kernels 1 and 5), on walled and periodic lattices with moving phi and
+force fields; and the analytic Darcy-Brinkman channel (Eq. 22 I) on the device.
 
-Tolerances as in test_gpu_parity: FP64 1e-12 of the deviation from rest; FP32
-compute 32 * 2^-24 * max|f| per step."""
+Tolerances as in test_gpu_parity, D = max |f - f_rest|: FP64 1e-12 D; FP32 on kernel
+1 (full populations) 32 * 2^-24 * max|f| per step; kernel 5 (deviations from rest)
+K5 = 8 units of 2^-24 D per step, from the device's initial populations with the
+inputs rounded to FP32, plus 2 * 2^-11 D per step for FP16 storage."""
 import numpy as np
 import pytest
 
@@ -13,7 +15,26 @@ from gpu_cases import random_case, rest_populations, total_force
 pytestmark = pytest.mark.gpu
 
 EPS32 = 2.0 ** -24
+K5 = 8
 DRAG = dict(d0=0.03, d1=0.4, us_x=2e-3, us_y=-1e-3)
+
+
+def _f32(case):
+    r = lambda a: None if a is None else a.astype(np.float32).astype(np.float64)  # noqa: E731
+    return dict(case, phi=r(case["phi"]), phin=r(case["phin"]), fb=r(case["fb"]))
+
+
+def _check(fg, fo, case, steps, storage, kernel):
+    D = np.abs(fo - rest_populations(case["phi"])).max()
+    err = np.abs(fg - fo).max()
+    if storage == "fp64":
+        assert err / D <= 1e-12
+    elif kernel == 5:
+        tol = steps * K5 * EPS32 * D + (2 * steps * 2.0 ** -11 * D if storage == "fp16" else 0.0)
+        print(f"kernel 5 {storage}: {err / (steps * EPS32 * D):.2f} x 2^-24 D per step")
+        assert err <= tol, (err, tol)
+    else:
+        assert err <= steps * 32 * EPS32 * np.abs(fo).max()
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +47,7 @@ def P():
     return pkg
 
 
-def _run(P, O, nx, ny, case, steps, storage, kernel, wall_y, drag=None, eq_order=3, tau=0.8):
+def _run(P, O, nx, ny, case, steps, storage, kernel, wall_y, drag=None, eq_order=3, tau=0.8, from_device=False):
     lat = P.Lattice(nx, ny, tau, s_eps=1.2, s_q=1.4, bc_y="bounceback" if wall_y else "periodic", storage=storage,
                     kernel=kernel, eq_order=eq_order)
     if drag:
@@ -41,6 +62,8 @@ def _run(P, O, nx, ny, case, steps, storage, kernel, wall_y, drag=None, eq_order
     f = O.init(prm, case["rho"], case["ux"], case["uy"], case["phi"], fb)
     f0g = lat.get_populations().cpu().numpy()
     init_err = np.abs(f0g - f).max() / max(np.abs(f).max(), 1e-30)
+    if from_device:
+        f = f0g.copy()
     for k in range(steps):
         phin = case["phin"] if k == 0 else None
         if k == 1 and case["phin"] is not None:
@@ -69,34 +92,40 @@ CASES = [
 def test_drag_matches_oracle(P, oracle_mod, nx, ny, wall_y, unsteady, field, g, storage, kernel):
     steps = 5
     case = random_case(nx, ny, seed=nx + 7 * ny, wall_y=wall_y, unsteady=unsteady, field=field, g=g)
-    init_err, fg, fo, case, m, mo = _run(P, oracle_mod, nx, ny, case, steps, storage, kernel, wall_y, DRAG)
+    if kernel == 5:
+        case = _f32(case)
+    init_err, fg, fo, case, m, mo = _run(P, oracle_mod, nx, ny, case, steps, storage, kernel, wall_y, DRAG,
+                                         from_device=kernel == 5)
     if storage == "fp64":
         assert init_err < 1e-14
-        assert np.abs(fg - fo).max() / np.abs(fo - rest_populations(case["phi"])).max() <= 1e-12
         for k in ("ux", "uy", "rho"):
             assert np.abs(m[k] - mo[k]).max() <= 1e-14 * max(1.0, np.abs(mo[k]).max()), k
-    else:
-        assert np.abs(fg - fo).max() <= steps * 32 * EPS32 * np.abs(fo).max()
+    _check(fg, fo, case, steps, storage, kernel)
 
 
 @pytest.mark.parametrize("nx,ny,wall_y,unsteady,field,g", CASES)
-@pytest.mark.parametrize("storage", ["fp64", "fp32"])
-def test_appb_matches_oracle(P, oracle_mod, nx, ny, wall_y, unsteady, field, g, storage):
+@pytest.mark.parametrize("storage,kernel", [("fp64", 1), ("fp32", 1), ("fp32", 5), ("fp16", 5)])
+def test_appb_matches_oracle(P, oracle_mod, nx, ny, wall_y, unsteady, field, g, storage, kernel):
     steps = 5
     case = random_case(nx, ny, seed=3 * nx + ny, wall_y=wall_y, unsteady=unsteady, field=field, g=g)
-    init_err, fg, fo, case, _, _ = _run(P, oracle_mod, nx, ny, case, steps, storage, 0, wall_y, eq_order=2)
+    if kernel == 5:
+        case = _f32(case)
+    init_err, fg, fo, case, _, _ = _run(P, oracle_mod, nx, ny, case, steps, storage, kernel, wall_y, eq_order=2,
+                                        from_device=kernel == 5)
     if storage == "fp64":
         assert init_err < 1e-14
-        assert np.abs(fg - fo).max() / np.abs(fo - rest_populations(case["phi"])).max() <= 1e-12
-    else:
-        assert np.abs(fg - fo).max() <= steps * 32 * EPS32 * np.abs(fo).max()
+    _check(fg, fo, case, steps, storage, kernel)
 
 
-def test_appb_with_drag_matches_oracle(P, oracle_mod):
+@pytest.mark.parametrize("storage,kernel", [("fp64", 1), ("fp32", 5)])
+def test_appb_with_drag_matches_oracle(P, oracle_mod, storage, kernel):
     nx, ny = 50, 23
     case = random_case(nx, ny, seed=99, wall_y=True, unsteady=True, field=True, g=(1e-5, 0.0))
-    _, fg, fo, case, _, _ = _run(P, oracle_mod, nx, ny, case, 6, "fp64", 1, True, DRAG, eq_order=2)
-    assert np.abs(fg - fo).max() / np.abs(fo - rest_populations(case["phi"])).max() <= 1e-12
+    if kernel == 5:
+        case = _f32(case)
+    _, fg, fo, case, _, _ = _run(P, oracle_mod, nx, ny, case, 6, storage, kernel, True, DRAG, eq_order=2,
+                                 from_device=kernel == 5)
+    _check(fg, fo, case, 6, storage, kernel)
 
 
 @pytest.mark.parametrize("storage,G", [("fp64", 1e-6), ("fp32", 1e-5)])
@@ -136,12 +165,14 @@ def test_variant_argument_errors(P):
     with pytest.raises(P.LbmError):
         lat.set_drag(-1.0, 0.0)
     lat.close()
-    for k in (2, 5):
+    for k in (2, 3, 4):
         with pytest.raises(P.LbmError):
             P.Lattice(16, 8, 0.8, kernel=k, eq_order=2)
     with pytest.raises(P.LbmError):
         P.Lattice(16, 8, 0.8, eq_order=4)
-    assert P.Lattice(16, 8, 0.8, eq_order=2).launch_shape()["threads"] == 128
+    # App. B runs on the one-warp kernel by default (FP32 storage), on kernel 1 in FP64
+    assert P.Lattice(16, 8, 0.8, eq_order=2).launch_shape()["threads"] == 32
+    assert P.Lattice(16, 8, 0.8, eq_order=2, storage="fp64").launch_shape()["threads"] == 128
 
 
 def _run_wall(P, O, nx, ny, case, steps, storage, uw, drag=None, eq_order=3, model_b=False, tau=0.8):
