@@ -85,7 +85,11 @@ void lbm_vanse_default_params(lbm_vanse_params* p);
 /* Create a lattice on the current device. cuda_stream is a cudaStream_t (NULL =
  * legacy default stream). Allocates the two population buffers, the void-fraction
  * and body-force buffers. Errors: LBM_ERR_ARG (sizes < 1, tau_nu <= 1/2, rates
- * outside (0, 2), kappa outside [0, 1], bc_x = bounce-back), LBM_ERR_OOM. */
+ * outside (0, 2), kappa outside [0, 1], bc_x = bounce-back with kernels 2-5),
+ * LBM_ERR_OOM. Walls in x (bc_x = bounce-back, step kernel 1, chosen by default for
+ * them) follow the rule of the y walls: half-way bounce-back links, and in the
+ * Eq. (10) stencil the ghost cell past a wall mirrors the cell next to it, vector
+ * components negated once even past two walls (a corner). */
 lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_vanse_t* out);
 
 /* Void fraction phi(x, t) of the next step and phi(x, t+1) (Eq. 7, 13, 14, 20;

@@ -155,6 +155,7 @@ Lattice<R> make_lattice(const lbm_vanse* h) {
     L.ny = h->prm.ny;
     L.P = h->P;
     L.wall_y = h->prm.bc_y == LBM_BC_BOUNCEBACK;
+    L.wall_x = h->prm.bc_x == LBM_BC_BOUNCEBACK;
     L.model_b = h->prm.model_b;
     L.kappa = (R)h->prm.kappa;
     L.gx = (R)h->gx;
@@ -300,6 +301,7 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
     p.W = h->W;
     p.H = h->H;
     p.wall_y = h->prm.bc_y == LBM_BC_BOUNCEBACK;
+    p.wall_x = h->prm.bc_x == LBM_BC_BOUNCEBACK;
     p.unsteady = h->unsteady;
     p.has_fb = h->has_fb;
     p.model_b = h->prm.model_b;
@@ -860,7 +862,9 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
     if (!(p->rho0 > 0.0)) return fail(nullptr, LBM_ERR_ARG, "rho0 must be positive");
     if (!rate_ok(p->s_eps) || !rate_ok(p->s_q) || !rate_ok(p->s_c) || (p->s_e > 0 && !rate_ok(p->s_e)))
         return fail(nullptr, LBM_ERR_ARG, "relaxation rates must lie in (0, 2)");
-    if (p->bc_x != LBM_BC_PERIODIC) return fail(nullptr, LBM_ERR_ARG, "only periodic x boundaries are supported");
+    if (p->bc_x != LBM_BC_PERIODIC && p->bc_x != LBM_BC_BOUNCEBACK) return fail(nullptr, LBM_ERR_ARG, "bad bc_x");
+    if (p->bc_x == LBM_BC_BOUNCEBACK && p->kernel >= 2)
+        return fail(nullptr, LBM_ERR_ARG, "x walls run on step kernel 1");
     if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_BOUNCEBACK) return fail(nullptr, LBM_ERR_ARG, "bad bc_y");
     if (p->storage < LBM_FP64 || p->storage > LBM_BF16) return fail(nullptr, LBM_ERR_ARG, "bad storage");
     if (p->strip_rows < 0) return fail(nullptr, LBM_ERR_ARG, "strip_rows must be >= 0");
@@ -903,7 +907,8 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
         return fail(nullptr, LBM_ERR_ARG, "the App. B equilibrium runs on kernels 1 and 5");
     }
     if (h->prm.eq_order == 0) h->prm.eq_order = 3;
-    h->kernel = p->kernel ? p->kernel : (p->storage == LBM_FP64 ? 1 : kDefaultKernel);
+    h->kernel = p->kernel ? p->kernel
+                          : ((p->storage == LBM_FP64 || p->bc_x == LBM_BC_BOUNCEBACK) ? 1 : kDefaultKernel);
     h->pair = h->kernel >= 2;
     h->W = h->kernel == 5 ? 60 : (h->pair ? 2 * kPairT[h->kernel - 2] - 4 : kThreads - 4);
     h->gridx = (p->nx + h->W - 1) / h->W;
@@ -991,6 +996,8 @@ extern "C" lbm_status lbm_vanse_set_solid_cells(lbm_vanse_t h, int enable) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (enable && h->kernel != 1)
         return fail(h, LBM_ERR_ARG, "solid cells run on step kernel 1 (this lattice uses kernel %d)", h->kernel);
+    if (enable && h->prm.bc_x == LBM_BC_BOUNCEBACK)
+        return fail(h, LBM_ERR_ARG, "solid cells and x walls together are not supported (use a solid frame)");
     h->has_solid = enable != 0;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // the step's shared memory changes
     return LBM_OK;
@@ -1012,6 +1019,7 @@ extern "C" lbm_status lbm_vanse_set_moving_wall(lbm_vanse_t h, int enable, doubl
     if (!std::isfinite(uw_x) || !std::isfinite(uw_y)) return fail(h, LBM_ERR_ARG, "wall velocity must be finite");
     if (h->prm.bc_y != LBM_BC_BOUNCEBACK) return fail(h, LBM_ERR_ARG, "the moving wall needs bc_y = bounce-back");
     if (h->prm.ny < 3) return fail(h, LBM_ERR_ARG, "the moving wall needs ny >= 3");
+    if (h->prm.bc_x == LBM_BC_BOUNCEBACK) return fail(h, LBM_ERR_ARG, "the moving wall needs periodic x");
     if (h->kernel != 1)
         return fail(h, LBM_ERR_ARG, "the moving wall runs on step kernel 1 (this lattice uses kernel %d)", h->kernel);
     h->nee_top = true;

@@ -17,6 +17,7 @@ struct Lattice {
     long long plane;   // elements per padded plane
     int nx, ny, P;
     int wall_y, model_b;
+    int wall_x = 0;                    // half-way bounce-back walls at x = -1/2, nx - 1/2
     R kappa, gx, gy;
     R scale, inv_scale;
     Rest<R> rest;
@@ -148,6 +149,7 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ buf, const R* __
     for (int i = 0; i < 9; ++i) {
         int sx = x - ex_of(i), sy = y - ey_of(i);
         int pi = i;
+        if (L.wall_x && (sx < 0 || sx >= L.nx)) { sx = x; sy = y; pi = opp_of(i); }
         if (sy < 0 || sy >= L.ny) {
             if (L.wall_y) { sx = x; sy = y; pi = opp_of(i); }
             else sy = (sy + L.ny) % L.ny;
@@ -166,6 +168,7 @@ __device__ __forceinline__ void scatter_cell(S* __restrict__ buf, const Lattice<
                                              T phi_cell, const R* __restrict__ phi = nullptr) {
     int tx = x - ex_of(i), ty = y - ey_of(i);
     int pi = i;
+    if (L.wall_x && (tx < 0 || tx >= L.nx)) { tx = x; ty = y; pi = opp_of(i); }
     if (ty < 0 || ty >= L.ny) {
         if (L.wall_y) { tx = x; ty = y; pi = opp_of(i); }
         else ty = (ty + L.ny) % L.ny;
@@ -196,7 +199,8 @@ __device__ __forceinline__ void grad_dense_even(const double* __restrict__ a, co
     R sx = 0, sy = 0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        int nx_ = (x + ex_of(i) + L.nx) % L.nx;
+        int nx_ = x + ex_of(i);
+        if (nx_ < 0 || nx_ >= L.nx) nx_ = L.wall_x ? (nx_ < 0 ? -1 - nx_ : 2 * L.nx - 1 - nx_) : (nx_ + L.nx) % L.nx;
         int ny_ = map_row(L, y + ey_of(i));
         const R w = (i <= 4) ? (R)(1.0 / 9.0) : (R)(1.0 / 36.0);
         R v = (R)a[(long long)ny_ * L.nx + nx_];

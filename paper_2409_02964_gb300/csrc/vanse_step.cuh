@@ -74,6 +74,7 @@ struct StepParams {
     int nx, ny, P;        // lattice size, row pitch (elements)
     int W, H;             // output columns per CTA, rows per strip
     int wall_y, unsteady, has_fb, model_b;
+    int wall_x;           // half-way bounce-back walls at x = -1/2 and x = nx - 1/2 (kernel 1)
     int nR;               // staged aux rows per slot (phi, [phi(t+1)], [F^B x, y])
     R kappa, gx, gy;
     R s_e, s_eps, s_q, s_nu;      // relaxation rates (Gamma)
@@ -226,6 +227,18 @@ __device__ __forceinline__ void phase1(const StepCtx<S, R, T>& c, RowState<R>& s
         f4 = dec(hi[4 * RW], rs.ax, ia);
         f7 = dec(hi[7 * RW + 1], rs.dg, ia);
         f8 = dec(hi[8 * RW - 1], rs.dg, ia);
+    }
+    if (p.wall_x) {   // links from x = -1 or x = nx come back from the wall: opposite slot, same cell
+        if (c.xc == 0) {
+            f1 = dec(cur[3 * RW], rs.ax, ia);
+            f5 = dec(cur[7 * RW], rs.dg, ia);
+            f8 = dec(cur[6 * RW], rs.dg, ia);
+        }
+        if (c.xc == p.nx - 1) {
+            f3 = dec(cur[1 * RW], rs.ax, ia);
+            f6 = dec(cur[8 * RW], rs.dg, ia);
+            f7 = dec(cur[5 * RW], rs.dg, ia);
+        }
     }
     if constexpr (SOLID) {
         // a solid cell (phi = 0) has no populations; a link from a solid cell is a
@@ -444,6 +457,27 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
         yBy = wByh - wByl;
         yBx = wBxh - wBxl;
         yDy = wDh - wDl;
+        if (p.wall_x && (c.xc == 0 || c.xc == p.nx - 1)) {
+            // Corner cell: the ghost row's diagonal ghost lies past both walls and holds the
+            // negated cell value once (-psi), while the negated mirror row carries the
+            // x-wall ghost negated twice (+psi); the ghost row's x-difference and smoothed
+            // sum of a field component psi move by cd psi and cw psi.
+            const R cd = (c.xc == 0 ? (R)2 : (R)0) - (c.xc == p.nx - 1 ? (R)2 : (R)0);
+            const R cw = (c.xc == 0 ? (R)-2 : (R)0) + (c.xc == p.nx - 1 ? (R)-2 : (R)0);
+            const R ng = (R)((p3 == 0 ? 1 : 0) + (p3 == p.ny - 1 ? 1 : 0));   // ghost rows at this row
+            const R Ax = Cs.rho * Cs.ux, Ay = Cs.rho * Cs.uy, Dx = Cs.m[0] * Cs.ux, Dy = Cs.m[0] * Cs.uy;
+            // x-derivatives take each ghost row's d with weight 1; y-derivatives take the
+            // upper ghost's w with +1 and the lower's with -1
+            const R sy = (R)((p3 == p.ny - 1 ? 1 : 0) - (p3 == 0 ? 1 : 0));
+            xAx += ng * cd * Ax;
+            xBx += ng * cd * Cs.ux;
+            xBy += ng * cd * Cs.uy;
+            xDx += ng * cd * Dx;
+            yAy += sy * cw * Ay;
+            yBy += sy * cw * Cs.uy;
+            yBx += sy * cw * Cs.ux;
+            yDy += sy * cw * Dy;
+        }
     }
 
     // App. B cross derivatives, replaced below next to solid cells
@@ -492,6 +526,16 @@ __device__ __forceinline__ void phase3(const StepCtx<S, R, T>& c, const RowState
             xDy = (lo ? -Cs.dDy : An.dDy) + (R)4 * Cs.dDy + ghi(Cs.dDy, An.dDy, Bs.dDy);
             yAx = ghi(Cs.wAx, An.wAx, Bs.wAx) - (lo ? -Cs.wAx : An.wAx);
             yDx = ghi(Cs.wDx, An.wDx, Bs.wDx) - (lo ? -Cs.wDx : An.wDx);
+            if (p.wall_x && (c.xc == 0 || c.xc == p.nx - 1)) {   // corner cell, as above
+                const R cd = (c.xc == 0 ? (R)2 : (R)0) - (c.xc == p.nx - 1 ? (R)2 : (R)0);
+                const R cw = (c.xc == 0 ? (R)-2 : (R)0) + (c.xc == p.nx - 1 ? (R)-2 : (R)0);
+                const R ng = (R)((p3 == 0 ? 1 : 0) + (p3 == p.ny - 1 ? 1 : 0));
+                const R sy = (R)((p3 == p.ny - 1 ? 1 : 0) - (p3 == 0 ? 1 : 0));
+                xAy += ng * cd * (Cs.rho * Cs.uy);
+                xDy += ng * cd * (Cs.m[0] * Cs.uy);
+                yAx += sy * cw * (Cs.rho * Cs.ux);
+                yDx += sy * cw * (Cs.m[0] * Cs.ux);
+            }
         }
         if (solid_nb) { xAy = xAy_s; yAx = yAx_s; xDy = xDy_s; yDx = yDx_s; }
         const R t3 = (R)2 / (R)3;
@@ -665,7 +709,9 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
         }
         const bool ph2 = (p2 >= y0 - 1) && (p2 <= y1) && c.row_valid(p2);
         if (ph1 && ph2_thread) {
-            const R l = rbuf[t - 1], r = rbuf[t + 1];
+            // past an x wall rho's ghost is the cell itself (the mirror about the wall)
+            const R l = (p.wall_x && c.xc == 0) ? An.rho : rbuf[t - 1];
+            const R r = (p.wall_x && c.xc == p.nx - 1) ? An.rho : rbuf[t + 1];
             An.dr = r - l;
             An.wr = (R)4 * An.rho + (r + l);
         }
@@ -681,12 +727,15 @@ __global__ void __launch_bounds__(T) vanse_step_kernel(const __grid_constant__ S
         __syncthreads();  // B: field row p2 visible
         if (ph2 && ph3_thread) {
             const R* F0 = fbuf + t;
-            const R Axl = F0[-1], Axr = F0[1];
-            const R Ayl = F0[T - 1], Ayr = F0[T + 1];
-            const R Bxl = F0[2 * T - 1], Bxr = F0[2 * T + 1];
-            const R Byl = F0[3 * T - 1], Byr = F0[3 * T + 1];
-            const R Dxl = F0[4 * T - 1], Dxr = F0[4 * T + 1];
-            const R Dyl = F0[5 * T - 1], Dyr = F0[5 * T + 1];
+            // past an x wall every field component's ghost is the negated cell value (no-slip)
+            const bool xl = p.wall_x && c.xc == 0, xr = p.wall_x && c.xc == p.nx - 1;
+            auto nb = [&](int k, int dx) { return ((dx < 0 && xl) || (dx > 0 && xr)) ? -F0[k * T] : F0[k * T + dx]; };
+            const R Axl = nb(0, -1), Axr = nb(0, 1);
+            const R Ayl = nb(1, -1), Ayr = nb(1, 1);
+            const R Bxl = nb(2, -1), Bxr = nb(2, 1);
+            const R Byl = nb(3, -1), Byr = nb(3, 1);
+            const R Dxl = nb(4, -1), Dxr = nb(4, 1);
+            const R Dyl = nb(5, -1), Dyr = nb(5, 1);
             Bs.dAx = Axr - Axl;
             Bs.dBx = Bxr - Bxl;
             Bs.dBy = Byr - Byl;

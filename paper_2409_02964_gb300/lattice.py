@@ -81,7 +81,7 @@ class Lattice:
 
     def __init__(self, nx: int, ny: int, tau: float = 0.8, *, s_e: float = 0.0, s_eps: float = 1.2,
                  s_q: float = 1.4, s_c: float = 1.0, kappa: float = 0.5, rho0: float = 1.0,
-                 bc_y: str = "periodic", storage: str = "fp32", model_b: bool = False,
+                 bc_y: str = "periodic", bc_x: str = "periodic", storage: str = "fp32", model_b: bool = False,
                  scale_log2: int | None = None, strip_rows: int = 0, eager: bool = False, kernel: int = 0,
                  eq_order: int = 3, stream=None):
         L = capi.load()
@@ -89,7 +89,7 @@ class Lattice:
         p.nx, p.ny, p.tau_nu = int(nx), int(ny), float(tau)
         p.s_e, p.s_eps, p.s_q, p.s_c = float(s_e), float(s_eps), float(s_q), float(s_c)
         p.kappa, p.rho0 = float(kappa), float(rho0)
-        p.bc_x, p.bc_y = capi.LBM_BC_PERIODIC, _BC[bc_y]
+        p.bc_x, p.bc_y = _BC[bc_x], _BC[bc_y]
         p.storage, p.model_b = _STORAGE[storage], int(bool(model_b))
         if scale_log2 is not None:
             p.storage_scale_log2 = int(scale_log2)

@@ -45,8 +45,11 @@ def test_default_params_and_create_errors_without_gpu():
     assert b"nx" in L.lbm_vanse_last_error(None)
     p.nx, p.ny, p.tau_nu = 4, 4, 0.5
     assert L.lbm_vanse_create(ctypes.byref(p), None, ctypes.byref(h)) == capi.LBM_ERR_ARG
-    p.tau_nu, p.bc_x = 0.8, capi.LBM_BC_BOUNCEBACK
+    p.tau_nu, p.bc_x, p.kernel = 0.8, capi.LBM_BC_BOUNCEBACK, 5      # x walls run on kernel 1 only
     assert L.lbm_vanse_create(ctypes.byref(p), None, ctypes.byref(h)) == capi.LBM_ERR_ARG
+    p.bc_x, p.kernel = 7, 0
+    assert L.lbm_vanse_create(ctypes.byref(p), None, ctypes.byref(h)) == capi.LBM_ERR_ARG
+    p.bc_x = capi.LBM_BC_PERIODIC
     assert L.lbm_vanse_step(None, 1) == capi.LBM_ERR_ARG
     L.lbm_vanse_destroy(None)
 
