@@ -363,6 +363,26 @@ lbm_status lbm_vanse_outlet_momentum_grad(const lbm_vanse_params* p, const lbm_v
                                           const double* phi, int on_device, void* cuda_stream, double* J,
                                           double* dJdphi, lbm_vanse_adjoint_stats* stats);
 
+/* Checkpoint and resume (no counterpart in the paper; a service of this library).
+ * A state is everything a later step depends on: the stored populations as they are
+ * (the current buffer with its padding and ghost columns; FP16/BF16 deviations
+ * bit for bit), phi(x, t), a pending phi(x, t+1), the body force (constant and
+ * field), the drag and moving-wall settings, the step count and the device step
+ * counter that seeds the stochastic rounding of FP16/BF16 stores. Loading it into a
+ * lattice created with the same nx, ny, storage and solid-cell setting continues the
+ * run bit for bit. Layout: a 512-byte header, then the raw device contents.
+ *
+ * lbm_vanse_state_bytes: the size of the state now (it depends on a pending
+ * phi(t+1) and on a force field), or -1 before initialisation.
+ * lbm_vanse_save_state: writes it to buf (host memory, or device memory with
+ * on_device = 1; at least lbm_vanse_state_bytes bytes); synchronises the stream.
+ * lbm_vanse_load_state: reads it back; synchronises the stream. Errors: LBM_ERR_ARG
+ * for a NULL argument, a buffer that is not a state, or a state of another lattice;
+ * LBM_ERR_STATE (save) before initialisation; LBM_ERR_CUDA for a failed copy. */
+long long lbm_vanse_state_bytes(lbm_vanse_t h);
+lbm_status lbm_vanse_save_state(lbm_vanse_t h, void* buf, int on_device);
+lbm_status lbm_vanse_load_state(lbm_vanse_t h, const void* buf, int on_device);
+
 /* Synchronise the stream and report any deferred kernel error (LBM_ERR_TIMEOUT
  * if a bounded wait gave up, LBM_ERR_CUDA for a launch/runtime error). After a
  * timeout the populations are not valid; the flag stays set. */

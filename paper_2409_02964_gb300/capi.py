@@ -23,7 +23,7 @@ EXPORTS = [
     "lbm_vanse_default_params", "lbm_vanse_create", "lbm_vanse_set_void_fraction",
     "lbm_vanse_set_void_fraction_f32", "lbm_vanse_reduce_async", "lbm_vanse_step_sums",
     "lbm_vanse_set_body_force", "lbm_vanse_set_drag", "lbm_vanse_set_moving_wall", "lbm_vanse_set_solid_cells",
-    "lbm_vanse_set_row_wait_limit",
+    "lbm_vanse_set_row_wait_limit", "lbm_vanse_state_bytes", "lbm_vanse_save_state", "lbm_vanse_load_state",
     "lbm_vanse_init_fields",
     "lbm_vanse_step", "lbm_vanse_macros",
     "lbm_vanse_get_populations", "lbm_vanse_set_populations", "lbm_vanse_reduce",
@@ -128,6 +128,9 @@ def load(path: str | None = None):
         "lbm_vanse_set_moving_wall": (i, [vp, i, d, d]),
         "lbm_vanse_set_solid_cells": (i, [vp, i]),
         "lbm_vanse_set_row_wait_limit": (i, [vp, ctypes.c_longlong]),
+        "lbm_vanse_state_bytes": (ctypes.c_longlong, [vp]),
+        "lbm_vanse_save_state": (i, [vp, vp, i]),
+        "lbm_vanse_load_state": (i, [vp, vp, i]),
         "lbm_vanse_init_fields": (i, [vp, vp, vp, vp, i]),
         "lbm_vanse_step": (i, [vp, i]),
         "lbm_vanse_macros": (i, [vp, vp, vp, vp, vp, i]),

@@ -1138,6 +1138,108 @@ extern "C" lbm_status lbm_vanse_set_populations(lbm_vanse_t h, const double* f, 
     return LBM_OK;
 }
 
+// ============================================================ checkpoint / resume
+namespace {
+
+// A snapshot: this header (512 bytes) and then the raw device contents, in order: the
+// current population buffer (9 planes with their padding and ghost columns, as
+// stored), phi(t), phi(t+1) if pending, the force field if set.
+struct StateHeader {
+    char magic[8];
+    int version, nx, ny, P, storage, kernel, has_solid;
+    int unsteady, has_fb, has_drag, nee_top;
+    long long plane, steps;
+    unsigned step_ctr, pad0;
+    double gx, gy, drag[4], uw[2];
+};
+static_assert(sizeof(StateHeader) <= 512, "state header");
+constexpr size_t kStateHeader = 512;
+constexpr char kStateMagic[8] = {'L', 'B', 'M', 'V', 'S', 'N', 'A', 'P'};
+
+size_t state_bytes(const lbm_vanse* h) {
+    const size_t pop = (size_t)9 * h->plane * h->sbytes, fld = (size_t)h->plane * h->rbytes;
+    return kStateHeader + pop + fld * (1 + (h->unsteady ? 1 : 0) + (h->has_fb ? 2 : 0));
+}
+
+}  // namespace
+
+extern "C" long long lbm_vanse_state_bytes(lbm_vanse_t h) { return h && h->initialised ? (long long)state_bytes(h) : -1; }
+
+extern "C" lbm_status lbm_vanse_save_state(lbm_vanse_t h, void* buf, int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!buf) return fail(h, LBM_ERR_ARG, "buf is NULL");
+    if (!h->initialised) return fail(h, LBM_ERR_STATE, "lattice not initialised");
+    StateHeader hd{};
+    std::memcpy(hd.magic, kStateMagic, 8);
+    hd.version = 1;
+    hd.nx = h->prm.nx; hd.ny = h->prm.ny; hd.P = h->P; hd.storage = h->prm.storage;
+    hd.kernel = h->kernel; hd.has_solid = h->has_solid;
+    hd.unsteady = h->unsteady; hd.has_fb = h->has_fb; hd.has_drag = h->has_drag; hd.nee_top = h->nee_top;
+    hd.plane = h->plane; hd.steps = h->steps;
+    hd.gx = h->gx; hd.gy = h->gy;
+    hd.drag[0] = h->drag_d0; hd.drag[1] = h->drag_d1; hd.drag[2] = h->us_x; hd.drag[3] = h->us_y;
+    hd.uw[0] = h->uw_x; hd.uw[1] = h->uw_y;
+    CK(h, cudaMemcpyAsync(&hd.step_ctr, h->step_ctr, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    char* out = static_cast<char*>(buf);
+    const cudaMemcpyKind hk = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    const cudaMemcpyKind dk = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    char header[kStateHeader] = {};
+    std::memcpy(header, &hd, sizeof(hd));
+    CK(h, cudaMemcpyAsync(out, header, kStateHeader, hk, h->stream));
+    size_t off = kStateHeader;
+    const size_t pop = (size_t)9 * h->plane * h->sbytes, fld = (size_t)h->plane * h->rbytes;
+    CK(h, cudaMemcpyAsync(out + off, h->f[h->cur], pop, dk, h->stream));
+    off += pop;
+    CK(h, cudaMemcpyAsync(out + off, h->phi, fld, dk, h->stream));
+    off += fld;
+    if (h->unsteady) { CK(h, cudaMemcpyAsync(out + off, h->phin, fld, dk, h->stream)); off += fld; }
+    if (h->has_fb) CK(h, cudaMemcpyAsync(out + off, h->fb, 2 * fld, dk, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_vanse_load_state(lbm_vanse_t h, const void* buf, int on_device) {
+    if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
+    if (!buf) return fail(h, LBM_ERR_ARG, "buf is NULL");
+    const char* in = static_cast<const char*>(buf);
+    StateHeader hd{};
+    CK(h, cudaMemcpy(&hd, in, sizeof(hd), on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    if (std::memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != 1)
+        return fail(h, LBM_ERR_ARG, "not a lattice state (bad magic or version)");
+    if (hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.P != h->P || hd.storage != h->prm.storage ||
+        hd.plane != h->plane || hd.has_solid != (int)h->has_solid)
+        return fail(h, LBM_ERR_ARG, "the state is of another lattice (size %dx%d, storage %d, solid cells %d)", hd.nx,
+                    hd.ny, hd.storage, hd.has_solid);
+    if (hd.nee_top && h->kernel != 1) return fail(h, LBM_ERR_ARG, "the state has a moving wall: kernel 1 needed");
+    if (hd.has_fb && !h->fb) {
+        CK(h, cudaMallocAsync(&h->fb, (size_t)2 * h->plane * h->rbytes, h->stream));
+    }
+    const cudaMemcpyKind dk = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t off = kStateHeader;
+    const size_t pop = (size_t)9 * h->plane * h->sbytes, fld = (size_t)h->plane * h->rbytes;
+    CK(h, cudaMemcpyAsync(h->f[h->cur], in + off, pop, dk, h->stream));
+    off += pop;
+    CK(h, cudaMemcpyAsync(h->phi, in + off, fld, dk, h->stream));
+    off += fld;
+    if (hd.unsteady) { CK(h, cudaMemcpyAsync(h->phin, in + off, fld, dk, h->stream)); off += fld; }
+    if (hd.has_fb) CK(h, cudaMemcpyAsync(h->fb, in + off, 2 * fld, dk, h->stream));
+    CK(h, cudaMemcpyAsync(h->step_ctr, &hd.step_ctr, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->unsteady = hd.unsteady != 0;
+    h->has_fb = hd.has_fb != 0;
+    h->gx = hd.gx; h->gy = hd.gy;
+    h->has_drag = hd.has_drag != 0;
+    h->drag_d0 = hd.drag[0]; h->drag_d1 = hd.drag[1]; h->us_x = hd.drag[2]; h->us_y = hd.drag[3];
+    h->nee_top = hd.nee_top != 0;
+    h->uw_x = hd.uw[0]; h->uw_y = hd.uw[1];
+    h->steps = hd.steps;
+    h->phi_set = true;
+    h->initialised = true;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_vanse_reduce(lbm_vanse_t h, double* mass, double* momx, double* momy) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
     if (!h->initialised) return fail(h, LBM_ERR_STATE, "lattice not initialised");

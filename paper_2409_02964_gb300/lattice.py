@@ -206,6 +206,24 @@ class Lattice:
         a = _Arg(f, 9 * self.n, self.device)
         _check(self._L.lbm_vanse_set_populations(self._h, a.ptr, a.on_device), self._h)
 
+    def save_state(self) -> np.ndarray:
+        """A checkpoint of the whole lattice state (lbm_vanse_save_state) as a uint8
+        array in host memory; load_state resumes from it bit for bit."""
+        n = int(self._L.lbm_vanse_state_bytes(self._h))
+        if n < 0:
+            raise LbmError(capi.LBM_ERR_STATE, "lattice not initialised")
+        buf = np.empty(n, dtype=np.uint8)
+        _check(self._L.lbm_vanse_save_state(self._h, buf.ctypes.data, 0), self._h)
+        return buf
+
+    def load_state(self, state) -> None:
+        """Resume from a state saved by save_state (a uint8 host array or CUDA tensor)."""
+        if isinstance(state, torch.Tensor) and state.is_cuda:
+            _check(self._L.lbm_vanse_load_state(self._h, state.data_ptr(), 1), self._h)
+        else:
+            arr = np.ascontiguousarray(state, dtype=np.uint8)
+            _check(self._L.lbm_vanse_load_state(self._h, arr.ctypes.data, 0), self._h)
+
     def reduce(self):
         m, jx, jy = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(self._L.lbm_vanse_reduce(self._h, ctypes.byref(m), ctypes.byref(jx), ctypes.byref(jy)), self._h)
