@@ -142,8 +142,9 @@ lbm_status lbm_vanse_set_drag(lbm_vanse_t h, double d0, double d1, double us_x, 
  * (F^p there uses rho_b = rho_f), f^eq of Eq. (14) (B1 with eq_order 2). The wall
  * row's Eq. (10) stencil reads a ghost row extrapolated linearly from rows ny-1 and
  * ny-2. The bottom stays a half-way bounce-back wall, so the channel height is
- * ny - 1/2. Needs bc_y = LBM_BC_BOUNCEBACK, ny >= 3 and step kernel 1 (LBM_ERR_ARG
- * otherwise); enable = 0 restores the half-way wall. lbm_vanse_macros reports the
+ * ny - 1/2. Needs bc_y = LBM_BC_BOUNCEBACK, periodic x, ny >= 3 and step kernel 1
+ * or 5 (LBM_ERR_ARG otherwise; on kernel 5 the rows next to the wall take the row
+ * loop's general path); enable = 0 restores the half-way wall. lbm_vanse_macros reports the
  * wall row from its populations before the replacement. */
 lbm_status lbm_vanse_set_moving_wall(lbm_vanse_t h, int enable, double uw_x, double uw_y);
 

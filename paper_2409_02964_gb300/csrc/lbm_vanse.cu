@@ -1020,8 +1020,9 @@ extern "C" lbm_status lbm_vanse_set_moving_wall(lbm_vanse_t h, int enable, doubl
     if (h->prm.bc_y != LBM_BC_BOUNCEBACK) return fail(h, LBM_ERR_ARG, "the moving wall needs bc_y = bounce-back");
     if (h->prm.ny < 3) return fail(h, LBM_ERR_ARG, "the moving wall needs ny >= 3");
     if (h->prm.bc_x == LBM_BC_BOUNCEBACK) return fail(h, LBM_ERR_ARG, "the moving wall needs periodic x");
-    if (h->kernel != 1)
-        return fail(h, LBM_ERR_ARG, "the moving wall runs on step kernel 1 (this lattice uses kernel %d)", h->kernel);
+    if (h->kernel != 1 && h->kernel != 5)
+        return fail(h, LBM_ERR_ARG, "the moving wall runs on step kernels 1 and 5 (this lattice uses kernel %d)",
+                    h->kernel);
     h->nee_top = true;
     h->uw_x = uw_x;
     h->uw_y = uw_y;
@@ -1211,7 +1212,8 @@ extern "C" lbm_status lbm_vanse_load_state(lbm_vanse_t h, const void* buf, int o
         hd.plane != h->plane || hd.has_solid != (int)h->has_solid)
         return fail(h, LBM_ERR_ARG, "the state is of another lattice (size %dx%d, storage %d, solid cells %d)", hd.nx,
                     hd.ny, hd.storage, hd.has_solid);
-    if (hd.nee_top && h->kernel != 1) return fail(h, LBM_ERR_ARG, "the state has a moving wall: kernel 1 needed");
+    if (hd.nee_top && h->kernel != 1 && h->kernel != 5)
+        return fail(h, LBM_ERR_ARG, "the state has a moving wall: kernel 1 or 5 needed");
     if (hd.has_fb && !h->fb) {
         CK(h, cudaMallocAsync(&h->fb, (size_t)2 * h->plane * h->rbytes, h->stream));
     }

@@ -282,7 +282,12 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
     V2 dlo = Cs.dr, wlo = Cs.wr, dhi = An.dr, whi = An.wr;
     if (!FAST && p.wall_y && (p2 == 0 || p2 == p.ny - 1)) {
         if (p2 == 0) { dlo = Bs.dr; wlo = Bs.wr; }
-        if (p2 == p.ny - 1) { dhi = Bs.dr; whi = Bs.wr; }
+        if (p2 == p.ny - 1) {
+            // rho's ghost past a half-way wall is the mirror row (the row itself); past
+            // the moving wall row it extrapolates linearly, 2 (row ny-1) - (row ny-2)
+            if (p.nee_top) { dhi = fma2(2.f, Bs.dr, -Cs.dr); whi = fma2(2.f, Bs.wr, -Cs.wr); }
+            else { dhi = Bs.dr; whi = Bs.wr; }
+        }
     }
     const V2 gx = tw * fma2(4.f, Bs.dr, dlo + dhi);
     const V2 gy = tw * (whi - wlo);
@@ -340,6 +345,53 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
     }
 }
 
+// Moving wall by non-equilibrium extrapolation (Sec. 3.1) on the top row ny-1 (Wa),
+// next to the fluid row ny-2 (Fl, its Eq. 7 velocity done by phase 2): the wall
+// node's moments become M f^eq(rho_f, u_w, phi_b) + m_f - M f^eq(rho_f, u_f, phi_f),
+// rho_b = rho_f (Wa.rho and Wa.rf already hold rho_f). On the stored deviations:
+// with E(phi, u) = M f^eq(rho_f, u, phi) - m^rest(phi), whose parts are
+// (phi drho, drho (2 kappa - 4 phi) + 3 phi rho |u|^2, drho (4 phi - 3 kappa) - 3 phi
+// rho |u|^2, phi rho u_x, q phi rho u_x, phi rho u_y, q phi rho u_y, phi rho (u_x^2 -
+// u_y^2), phi rho u_x u_y) with drho = rho_f - rho0 and q phi = kappa - 2 phi (Eq. 18)
+// or -phi (B2), the wall's deviations are Fl.m + E(phi_b, u_w) - E(phi_f, u_f), in
+// the storage's scaled units.
+template <typename S, typename Ctx>
+__device__ __forceinline__ void warp_nee_moments(const Ctx& c, PRow& Wa, const PRow& Fl, int pw) {
+    const auto& p = c.p;
+    const V2 pb = c.phi2(pw, Wa), pf = c.phi2(pw - 1, Fl);
+    const V2 drs = Fl.rho;                                         // scale x (rho_f - rho0)
+    const V2 sr = sizeof(S) == 4 ? Fl.rf : p.scale * Fl.rf;        // scale x rho_f
+    const V2 bw = pb * sr, bf = pf * sr;                           // scale x phi rho_f
+    const float wx = p.uw_x, wy = p.uw_y;
+    const V2 fx = Fl.ux, fy = Fl.uy;
+    const V2 ufu = fma2(fx, fx, fy * fy);
+    const V2 uu3 = fma2(3.f * (wx * wx + wy * wy), bw, -(3.f * (bf * ufu)));   // 3 (phi_b rho uw^2 - phi_f rho uf^2)
+    const V2 dp4 = 4.f * (drs * (pf - pb));                                   // 4 drho (phi_f - phi_b)
+    const V2 jx = fma2(wx, bw, -(bf * fx)), jy = fma2(wy, bw, -(bf * fy));
+    // q phi rho u: (kappa - 2 phi) rho u, or -phi rho u with (B2)
+    V2 qx, qy;
+    if constexpr (Ctx::kEq2) {
+        qx = -jx;
+        qy = -jy;
+    } else {
+        const V2 qb = fma2(-2.f, pb, bc(p.kappa)) * sr, qf = fma2(-2.f, pf, bc(p.kappa)) * sr;
+        qx = fma2(wx, qb, -(qf * fx));
+        qy = fma2(wy, qb, -(qf * fy));
+    }
+    Wa.m[0] = fma2(pb - pf, drs, Fl.m[0]);
+    Wa.m[1] = Fl.m[1] + (dp4 + uu3);
+    Wa.m[2] = Fl.m[2] - (dp4 + uu3);
+    Wa.m[3] = Fl.m[3] + jx;
+    Wa.m[4] = Fl.m[4] + qx;
+    Wa.m[5] = Fl.m[5] + jy;
+    Wa.m[6] = Fl.m[6] + qy;
+    Wa.m[7] = Fl.m[7] + fma2(wx * wx - wy * wy, bw, -(bf * fma2(fx, fx, -(fy * fy))));
+    Wa.m[8] = Fl.m[8] + fma2(wx * wy, bw, -(bf * (fx * fy)));
+    // the full sum f of the wall node, as phase 1 keeps it
+    if constexpr (sizeof(S) == 4) Wa.mf = fma2(p.rest.rho0, pb, Wa.m[0]);
+    else Wa.mf = fma2(p.rest.rho0, pb, p.inv_scale * Wa.m[0]);
+}
+
 template <typename S, bool FAST, typename Ctx>
 __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const PRow& Bs, const PRow& Cs,
                                             int p3, bool lane_ok) {
@@ -354,16 +406,21 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     V2 yBy = Bs.wBy - An.wBy;
     V2 yBx = Bs.wBx - An.wBx;
     V2 yDy = Bs.wDy - An.wDy;
+    // the rows around row p3: An holds row p3-1, Bs row p3+1. Past a half-way wall the
+    // ghost row is the negated mirror row (no-slip); past the moving wall row (the
+    // top row with nee_top) the linear extrapolation 2 (row ny-1) - (row ny-2)
+    const bool nee_hi = !FAST && p.nee_top && p3 == p.ny - 1;
+    auto ghi = [&](V2 cs, V2 an, V2 bs) { return nee_hi ? fma2(2.f, cs, -an) : (p3 == p.ny - 1 ? -cs : bs); };
     if (!FAST && p.wall_y && (p3 == 0 || p3 == p.ny - 1)) {
-        const bool lo = (p3 == 0), hi = (p3 == p.ny - 1);
-        const V2 dAl = lo ? -Cs.dAx : An.dAx, dAh = hi ? -Cs.dAx : Bs.dAx;
-        const V2 dBxl = lo ? -Cs.dBx : An.dBx, dBxh = hi ? -Cs.dBx : Bs.dBx;
-        const V2 dByl = lo ? -Cs.dBy : An.dBy, dByh = hi ? -Cs.dBy : Bs.dBy;
-        const V2 dDl = lo ? -Cs.dDx : An.dDx, dDh = hi ? -Cs.dDx : Bs.dDx;
-        const V2 wAl = lo ? -Cs.wAy : An.wAy, wAh = hi ? -Cs.wAy : Bs.wAy;
-        const V2 wByl = lo ? -Cs.wBy : An.wBy, wByh = hi ? -Cs.wBy : Bs.wBy;
-        const V2 wBxl = lo ? -Cs.wBx : An.wBx, wBxh = hi ? -Cs.wBx : Bs.wBx;
-        const V2 wDl = lo ? -Cs.wDy : An.wDy, wDh = hi ? -Cs.wDy : Bs.wDy;
+        const bool lo = (p3 == 0);
+        const V2 dAl = lo ? -Cs.dAx : An.dAx, dAh = ghi(Cs.dAx, An.dAx, Bs.dAx);
+        const V2 dBxl = lo ? -Cs.dBx : An.dBx, dBxh = ghi(Cs.dBx, An.dBx, Bs.dBx);
+        const V2 dByl = lo ? -Cs.dBy : An.dBy, dByh = ghi(Cs.dBy, An.dBy, Bs.dBy);
+        const V2 dDl = lo ? -Cs.dDx : An.dDx, dDh = ghi(Cs.dDx, An.dDx, Bs.dDx);
+        const V2 wAl = lo ? -Cs.wAy : An.wAy, wAh = ghi(Cs.wAy, An.wAy, Bs.wAy);
+        const V2 wByl = lo ? -Cs.wBy : An.wBy, wByh = ghi(Cs.wBy, An.wBy, Bs.wBy);
+        const V2 wBxl = lo ? -Cs.wBx : An.wBx, wBxh = ghi(Cs.wBx, An.wBx, Bs.wBx);
+        const V2 wDl = lo ? -Cs.wDy : An.wDy, wDh = ghi(Cs.wDy, An.wDy, Bs.wDy);
         xAx = fma2(4.f, Cs.dAx, dAl + dAh);
         xBx = fma2(4.f, Cs.dBx, dBxl + dBxh);
         xBy = fma2(4.f, Cs.dBy, dByl + dByh);
@@ -386,9 +443,9 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
         V2 xGy = fma2(4.f, Cs.dGy, An.dGy + Bs.dGy);
         V2 yGx = Bs.wGx - An.wGx;
         if (!FAST && p.wall_y && (p3 == 0 || p3 == p.ny - 1)) {
-            const bool lo = (p3 == 0), hi = (p3 == p.ny - 1);
-            xGy = fma2(4.f, Cs.dGy, (lo ? -Cs.dGy : An.dGy) + (hi ? -Cs.dGy : Bs.dGy));
-            yGx = (hi ? -Cs.wGx : Bs.wGx) - (lo ? -Cs.wGx : An.wGx);
+            const bool lo = (p3 == 0);
+            xGy = fma2(4.f, Cs.dGy, (lo ? -Cs.dGy : An.dGy) + ghi(Cs.dGy, An.dGy, Bs.dGy));
+            yGx = ghi(Cs.wGx, An.wGx, Bs.wGx) - (lo ? -Cs.wGx : An.wGx);
         }
         Ca = tw * fma2(-2.f * p.kappa, xAx + yAy, fma2(2.f * kr, xBx + yBy, fma2(-2.f, X, bc(4.f)) * divD));
         Cb = (tw * (2.f / 3.f)) * fma2(-p.kappa, xAx - yAy, fma2(kr, xBx - yBy, difD));
@@ -543,14 +600,18 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
             return;
         }
         const bool ph1 = (p1 <= y1 + 1) && c.row_valid(p1);
+        // the moving wall row (its moments follow once row ny-2 has its velocity)
+        const bool nee_row = c.p.nee_top && p1 == c.p.ny - 1;
         if (ph1) {
             warp_phase1<S, false>(c, An, p1);
+            if (nee_row) { An.rho = Bs.rho; An.rf = Bs.rf; }   // rho_b = rho_f
             const float l = left_of(An.rho), r = right_of(An.rho);
             An.dr = rpair(An.rho, r) - lpair(An.rho, l);
             An.wr = fma2(4.f, An.rho, rpair(An.rho, r) + lpair(An.rho, l));
         }
         const bool ph2 = (p2 >= y0 - 1) && (p2 <= y1) && c.row_valid(p2);
         if (ph2) warp_phase2<S, false>(c, An, Bs, Cs, p2);
+        if (ph1 && nee_row) warp_nee_moments<S>(c, An, Bs, p1);
         const bool ph3 = (p3 >= y0) && (p3 < y1);
         if (ph3) warp_phase3<S, false>(c, An, Bs, Cs, p3, lane_ok);
     };

@@ -160,7 +160,7 @@ class Lattice:
 
     def set_moving_wall(self, uw_x: float = 0.0, uw_y: float = 0.0, enable: bool = True) -> None:
         """Row ny-1 as a wall moving at (uw_x, uw_y) by non-equilibrium extrapolation
-        (lbm_vanse_set_moving_wall; bounce-back walls, kernel 1)."""
+        (lbm_vanse_set_moving_wall; bounce-back walls, kernels 1 and 5)."""
         _check(self._L.lbm_vanse_set_moving_wall(self._h, int(enable), float(uw_x), float(uw_y)), self._h)
 
     def init_fields(self, rho, ux, uy) -> None:

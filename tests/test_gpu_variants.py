@@ -3,6 +3,9 @@ implicit velocity (lbm_vanse_set_drag; kernels 1 and 5) and the App. B equilibri
 (eq_order = 2; kernels 1 and 5), on walled and periodic lattices with moving phi and
 force fields; and the analytic Darcy-Brinkman channel (Eq. 22 I) on the device.
 
+The moving wall (non-equilibrium extrapolation, Sec. 3.1; kernels 1 and 5) alone
+and with each variant, and the Couette profile of Eq. (22 II).
+
 Tolerances as in test_gpu_parity, D = max |f - f_rest|: FP64 1e-12 D; FP32 on kernel
 1 (full populations) 32 * 2^-24 * max|f| per step; kernel 5 (deviations from rest)
 K5 = 8 units of 2^-24 D per step, from the device's initial populations with the
@@ -175,9 +178,14 @@ def test_variant_argument_errors(P):
     assert P.Lattice(16, 8, 0.8, eq_order=2, storage="fp64").launch_shape()["threads"] == 128
 
 
-def _run_wall(P, O, nx, ny, case, steps, storage, uw, drag=None, eq_order=3, model_b=False, tau=0.8):
-    lat = P.Lattice(nx, ny, tau, s_eps=1.2, s_q=1.4, bc_y="bounceback", storage=storage, kernel=1,
-                    eq_order=eq_order, model_b=model_b)
+def _run_wall(P, O, nx, ny, case, steps, storage, uw, drag=None, eq_order=3, model_b=False, tau=0.8, kernel=1,
+              strip_rows=0):
+    """Kernel 5 (FP32 arithmetic on deviations from rest): the inputs rounded to FP32
+    and the oracle started from the device's initial populations, as in _run."""
+    if kernel == 5:
+        case = _f32(case)
+    lat = P.Lattice(nx, ny, tau, s_eps=1.2, s_q=1.4, bc_y="bounceback", storage=storage, kernel=kernel,
+                    eq_order=eq_order, model_b=model_b, strip_rows=strip_rows)
     lat.set_moving_wall(*uw)
     if drag:
         lat.set_drag(drag["d0"], drag["d1"], drag["us_x"], drag["us_y"])
@@ -189,6 +197,8 @@ def _run_wall(P, O, nx, ny, case, steps, storage, uw, drag=None, eq_order=3, mod
                    eq_order=eq_order, model_b=int(model_b), nee_top=1, uw_x=uw[0], uw_y=uw[1], **kw)
     fb = total_force(case)
     f = O.init(prm, case["rho"], case["ux"], case["uy"], case["phi"], fb)
+    if kernel == 5:
+        f = lat.get_populations().cpu().numpy().astype(np.float64)
     for k in range(steps):
         phin = case["phin"] if k == 0 else None
         if k == 1 and case["phin"] is not None:
@@ -210,39 +220,64 @@ WALL_CASES = [
 ]
 
 
-@pytest.mark.parametrize("nx,ny,unsteady,field,g,uw", WALL_CASES)
-@pytest.mark.parametrize("storage", ["fp64", "fp32"])
-def test_moving_wall_matches_oracle(P, oracle_mod, nx, ny, unsteady, field, g, uw, storage):
-    """The non-equilibrium-extrapolation wall on row ny-1 (kernel 1) against the
-    oracle, 6 steps, with moving phi, force fields and a tangential and a normal
-    wall velocity; every population, the wall row's included."""
+# taller lattices: several strips of rows below the wall row's
+WALL_CASES_K5 = WALL_CASES + [
+    (61, 130, True, True, (1e-5, 0.0), (1e-3, 0.0)),
+    (200, 67, False, False, (0.0, 0.0), (2e-3, -5e-4)),
+]
+
+
+@pytest.mark.parametrize("nx,ny,unsteady,field,g,uw", WALL_CASES_K5)
+@pytest.mark.parametrize("storage,kernel", [("fp64", 1), ("fp32", 1), ("fp32", 5), ("fp16", 5)])
+def test_moving_wall_matches_oracle(P, oracle_mod, nx, ny, unsteady, field, g, uw, storage, kernel):
+    """The non-equilibrium-extrapolation wall on row ny-1 against the oracle, 6
+    steps, with moving phi, force fields and a tangential and a normal wall velocity;
+    every population, the wall row's included."""
     steps = 6
     case = random_case(nx, ny, seed=5 * nx + ny, wall_y=True, unsteady=unsteady, field=field, g=g)
-    fg, fo, case = _run_wall(P, oracle_mod, nx, ny, case, steps, storage, uw)
-    if storage == "fp64":
-        assert np.abs(fg - fo).max() / np.abs(fo - rest_populations(case["phi"])).max() <= 1e-12
+    fg, fo, case = _run_wall(P, oracle_mod, nx, ny, case, steps, storage, uw, kernel=kernel)
+    if storage == "fp64" or kernel == 5:
+        _check(fg, fo, case, steps, storage, kernel)
     else:
         assert np.abs(fg - fo).max() <= steps * 32 * EPS32 * np.abs(fo).max()
 
 
+@pytest.mark.parametrize("ny", [17, 18, 19, 20, 35])
+def test_moving_wall_at_strip_boundaries_kernel5(P, oracle_mod, ny):
+    """Strips of 16 rows: the wall row alone in the last strip (ny = 17), the row
+    below it alone (18), and the wall row 1 .. 3 rows past a strip boundary; the
+    phase-1 replacement of rho at the wall row then happens in the strip below as well."""
+    nx, steps = 70, 6
+    case = random_case(nx, ny, seed=ny, wall_y=True, unsteady=True, field=True, g=(1e-5, 0.0))
+    fg, fo, case = _run_wall(P, oracle_mod, nx, ny, case, steps, "fp32", (1e-3, 2e-4), kernel=5, strip_rows=16)
+    _check(fg, fo, case, steps, "fp32", 5)
+
+
 @pytest.mark.parametrize("variant", ["drag", "appb", "model_b"])
-def test_moving_wall_with_variants_matches_oracle(P, oracle_mod, variant):
+@pytest.mark.parametrize("storage,kernel", [("fp64", 1), ("fp32", 5)])
+def test_moving_wall_with_variants_matches_oracle(P, oracle_mod, variant, storage, kernel):
     nx, ny = 50, 23
     case = random_case(nx, ny, seed=77, wall_y=True, unsteady=True, field=True, g=(1e-5, 0.0))
     kw = {"drag": dict(drag=DRAG), "appb": dict(eq_order=2), "model_b": dict(model_b=True)}[variant]
-    fg, fo, case = _run_wall(P, oracle_mod, nx, ny, case, 6, "fp64", (1.5e-3, 0.0), **kw)
-    assert np.abs(fg - fo).max() / np.abs(fo - rest_populations(case["phi"])).max() <= 1e-12
+    fg, fo, case = _run_wall(P, oracle_mod, nx, ny, case, 6, storage, (1.5e-3, 0.0), kernel=kernel, **kw)
+    _check(fg, fo, case, 6, storage, kernel)
 
 
 @pytest.mark.parametrize("da,bound", [(None, 1e-9), (1e-2, 8e-3)])
-def test_couette_on_device(P, da, bound):
-    """Eq. (22 II) on the device (FP64, ny = 32, phi = 0.5, u_H = 1e-3): the linear
+@pytest.mark.parametrize("storage,kernel", [("fp64", 1), ("fp32", 5)])
+def test_couette_on_device(P, da, bound, storage, kernel):
+    """Eq. (22 II) on the device (ny = 32, phi = 0.5, u_H = 1e-3): the linear
     Couette profile without the Darcy term, and u_H sinh(r y) / sinh(r H) with
-    Da = 1e-2 within the oracle's own error at this resolution (7.5e-3)."""
+    Da = 1e-2 within the oracle's own error at this resolution (7.5e-3). FP32 on
+    kernel 5: the steady state of the rounded iteration carries a small quantisation
+    bias (round-to-nearest repeats the same rounding every step once the flow is
+    steady); measured 2.6e-5 on the linear profile (bound 1e-4)."""
+    if storage == "fp32" and da is None:
+        bound = 1e-4
     ny, nx, tau, phi0, uh = 32, 4, 0.8, 0.5, 1e-3
     nu = (tau - 0.5) / 3
     H = ny - 0.5
-    lat = P.Lattice(nx, ny, tau, s_eps=1.2, s_q=1.2, bc_y="bounceback", storage="fp64", kernel=1)
+    lat = P.Lattice(nx, ny, tau, s_eps=1.2, s_q=1.2, bc_y="bounceback", storage=storage, kernel=kernel)
     lat.set_moving_wall(uh, 0.0)
     if da:
         k0 = da * H * H
@@ -258,12 +293,16 @@ def test_couette_on_device(P, da, bound):
     lat.close()
     y = np.arange(ny - 1) + 0.5
     ua = uh * (np.sinh(np.sqrt(phi0 / k0) * y) / np.sinh(np.sqrt(phi0 / k0) * H) if da else y / H)
+    print(f"{storage} kernel {kernel} Da {da}: {np.sqrt(np.sum((u - ua) ** 2) / np.sum(ua ** 2)):.3e}")
     assert np.sqrt(np.sum((u - ua) ** 2) / np.sum(ua ** 2)) < bound
 
 
 def test_moving_wall_argument_errors(P):
+    for k in (2, 3, 4):
+        with pytest.raises(P.LbmError):
+            P.Lattice(16, 8, 0.8, bc_y="bounceback", kernel=k).set_moving_wall(1e-3)
     with pytest.raises(P.LbmError):
-        P.Lattice(16, 8, 0.8, bc_y="bounceback", kernel=5).set_moving_wall(1e-3)
+        P.Lattice(16, 8, 0.8, bc_y="bounceback", bc_x="bounceback").set_moving_wall(1e-3)
     with pytest.raises(P.LbmError):
         P.Lattice(16, 8, 0.8, bc_y="periodic", kernel=1).set_moving_wall(1e-3)
     with pytest.raises(P.LbmError):
