@@ -155,8 +155,10 @@ lbm_status lbm_vanse_set_moving_wall(lbm_vanse_t h, int enable, double uw_x, dou
  * stencil of a fluid cell it reads a ghost value mirrored about the solid surface: an
  * axis neighbour the cell itself, a diagonal neighbour the mean of the fluid ones of
  * its two axis images (the cell itself if both are solid), vector components negated.
- * Solid cells must stay solid (phi(t+1) = 0 where phi(t) = 0). Step kernel 1 only
- * (LBM_ERR_ARG otherwise); call before lbm_vanse_init_fields. Without it a zero in
+ * Solid cells must stay solid (phi(t+1) = 0 where phi(t) = 0). Step kernels 1 and 5
+ * (LBM_ERR_ARG otherwise; kernel 5 then runs every row on its general path and leaves
+ * the stored values of solid cells as they are, since no link reads them); call
+ * before lbm_vanse_init_fields. Without it a zero in
  * phi is an error, reported by the next lbm_vanse_sync. */
 lbm_status lbm_vanse_set_solid_cells(lbm_vanse_t h, int enable);
 

@@ -72,7 +72,7 @@ struct lbm_vanse {
     double drag_d0 = 0, drag_d1 = 0, us_x = 0, us_y = 0;
     bool nee_top = false;         // row ny-1: moving wall by non-equilibrium extrapolation
     double uw_x = 0, uw_y = 0;
-    bool has_solid = false;       // phi = 0 marks solid cells (kernel 1)
+    bool has_solid = false;       // phi = 0 marks solid cells (kernels 1 and 5)
     int* zero_phi = nullptr;      // device flag: the last phi upload held a zero
     unsigned* step_ctr = nullptr; // device step count of the one-warp kernel (seeds stochastic rounding)
     double s_nu = 0, s_e = 0;
@@ -270,6 +270,21 @@ template <typename S>
 lbm_status launch_solid_step(lbm_vanse* h, const StepParams<typename Prec<S>::R>& p, dim3 grid, size_t smem,
                              cudaStream_t stream, bool sums) {
     using R = typename Prec<S>::R;
+    if constexpr (!std::is_same<S, double>::value) {
+        if (h->kernel == 5) {
+            if (!h->solid_configured) {
+                CK(h, warp_solid_configure<S>(step_smem_max<S>(h)));
+                h->solid_configured = true;
+            }
+            CK(h, warp_solid_launch<S>(p, grid, smem, stream, sums, p.eq2 != 0));
+            // the one-warp kernel writes columns 0 .. nx-1 only
+            const long long ng = 9LL * h->prm.ny * 2 * kGhost;
+            ghost_fill_kernel<S><<<(int)std::min<long long>((ng + 255) / 256, 4096), 256, 0, stream>>>(
+                (S*)p.dst, h->plane, h->prm.nx, h->prm.ny, h->P, h->step_ctr);
+            CK(h, cudaGetLastError());
+            return LBM_OK;
+        }
+    }
     if (!h->solid_configured) {
         for (const void* k : {(const void*)vanse_step_kernel<S, R, kThreads, true, true>,
                               (const void*)vanse_step_kernel<S, R, kThreads, false, true>}) {
@@ -994,8 +1009,9 @@ extern "C" lbm_status lbm_vanse_set_drag(lbm_vanse_t h, double d0, double d1, do
 
 extern "C" lbm_status lbm_vanse_set_solid_cells(lbm_vanse_t h, int enable) {
     if (!h) return fail(nullptr, LBM_ERR_ARG, "handle is NULL");
-    if (enable && h->kernel != 1)
-        return fail(h, LBM_ERR_ARG, "solid cells run on step kernel 1 (this lattice uses kernel %d)", h->kernel);
+    if (enable && h->kernel != 1 && h->kernel != 5)
+        return fail(h, LBM_ERR_ARG, "solid cells run on step kernels 1 and 5 (this lattice uses kernel %d)",
+                    h->kernel);
     if (enable && h->prm.bc_x == LBM_BC_BOUNCEBACK)
         return fail(h, LBM_ERR_ARG, "solid cells and x walls together are not supported (use a solid frame)");
     h->has_solid = enable != 0;
@@ -1322,7 +1338,7 @@ extern "C" lbm_status lbm_vanse_sync(lbm_vanse_t h) {
     if (flag) return fail(h, LBM_ERR_TIMEOUT, "a step kernel gave up waiting for its staged rows");
     if (!h->has_solid) {
         CK(h, cudaMemcpy(&flag, h->zero_phi, sizeof(int), cudaMemcpyDeviceToHost));
-        if (flag) return fail(h, LBM_ERR_ARG, "phi holds zeros: solid cells need lbm_vanse_set_solid_cells (kernel 1)");
+        if (flag) return fail(h, LBM_ERR_ARG, "phi holds zeros: solid cells need lbm_vanse_set_solid_cells (kernels 1 and 5)");
     }
     return LBM_OK;
 }

@@ -66,6 +66,7 @@ struct BatchCtx {
     static constexpr bool kUnsteady = true;
     static constexpr bool kSums = false;
     static constexpr bool kEq2 = false;
+    static constexpr bool kSolid = false;
     StepParams<float> p;       // this lattice's scalars (pointers and sizes included)
     unsigned char* smem;
     int lane, xa, sa;

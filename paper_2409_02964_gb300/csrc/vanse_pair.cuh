@@ -116,6 +116,12 @@ struct PRow {
     V2 dAx, dBx, dBy, dDx;
     V2 wAy, wBy, wBx, wDy;
     V2 dGy, wGx;       // one-warp kernel with App. B: G = phi rho u - kappa rho u (the (B3) cross terms)
+    // one-warp kernel with solid cells: rho and the full sum f of the row whose velocity
+    // ux, uy hold (phase 1 of a later row overwrites rf, mf first), and the pair's
+    // solid-neighbour mask (bit 9 c + 3 (dy + 1) + dx + 1 for column c of the pair,
+    // the rows past a wall mapped as the stencil maps them; bit 9 c + 4: the cell itself)
+    V2 rfu, mfu;
+    uint32_t sm;
 };
 
 __device__ __forceinline__ int pslot(int r) { return ((r % kPairSlots) + kPairSlots) % kPairSlots; }

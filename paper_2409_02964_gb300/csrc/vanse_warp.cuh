@@ -96,12 +96,13 @@ struct PairSums {
     }
 };
 
-template <typename S, bool SUMS = false, bool EQ2 = false>
+template <typename S, bool SUMS = false, bool EQ2 = false, bool SOLID = false>
 struct WarpCtx {
     using L = WarpLayout<S>;
     static constexpr bool kUnsteady = false;   // the fast path runs only on steady strips
     static constexpr bool kSums = SUMS;        // accumulate the written cells' m_0+, j+ (PairSums)
     static constexpr bool kEq2 = EQ2;          // App. B: (B2) energy-flux equilibria, (B3) penalty
+    static constexpr bool kSolid = SOLID;      // phi = 0 marks solid cells (general path only)
     const StepParams<float>& p;
     unsigned char* smem;
     int lane, xa, sa;
@@ -208,6 +209,86 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 __device__ __forceinline__ float left_of(V2 v) { return __shfl_up_sync(0xffffffffu, v.v.y, 1); }
 __device__ __forceinline__ float right_of(V2 v) { return __shfl_down_sync(0xffffffffu, v.v.x, 1); }
 
+// ------------------------------------------------------------------ solid cells
+// The Eq. (10) stencil next to solid cells (phi = 0), neighbour by neighbour. w is the
+// 3 x 4 window of a field around the lane's pair: rows 0, 1, 2 = below, the row, above
+// (the rows past a wall already mapped: the mirror row, negated for a vector
+// component, or the moving wall's extrapolated row), columns 0..3 = xa-1, xa, xb, xb+1.
+// m9: the solid bits of column C's 3 x 3 neighbourhood (bit 3 (dy + 1) + dx + 1). A
+// solid neighbour reads the value mirrored about the solid surface: an axis neighbour
+// the cell itself; a diagonal one the mean of its two axis images (x+dx, y), (x, y+dy)
+// when both are fluid, the fluid one when one is, the cell itself when neither is;
+// negated for a vector component (odd). Returns 12 x the gradient.
+template <int C>
+__device__ __forceinline__ void solid_stencil(const float (&w)[3][4], uint32_t m9, bool odd, float& gx12,
+                                              float& gy12) {
+    constexpr int j = 1 + C;
+    const float own = w[1][j];
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            if (dx == 0 && dy == 0) continue;
+            float v = w[dy + 1][j + dx];
+            if ((m9 >> (3 * (dy + 1) + dx + 1)) & 1u) {
+                v = own;
+                if (dx != 0 && dy != 0) {
+                    const bool fa = !((m9 >> (3 + dx + 1)) & 1u), fb = !((m9 >> (3 * (dy + 1) + 1)) & 1u);
+                    const float va = w[1][j + dx], vb = w[dy + 1][j];
+                    if (fa && fb) v = 0.5f * (va + vb);
+                    else if (fa) v = va;
+                    else if (fb) v = vb;
+                }
+                if (odd) v = -v;
+            }
+            const float k = (dx != 0 && dy != 0) ? 1.f : 4.f;   // 36 w_i
+            sx = fmaf(k * (float)dx, v, sx);
+            sy = fmaf(k * (float)dy, v, sy);
+        }
+    gx12 = sx;
+    gy12 = sy;
+}
+
+// the 4-wide row window of a pair field: xa-1 (from the lane below), xa, xb, xb+1
+__device__ __forceinline__ void win_row(float (&w)[4], V2 v) {
+    w[0] = __shfl_up_sync(0xffffffffu, v.v.y, 1);
+    w[1] = v.v.x;
+    w[2] = v.v.y;
+    w[3] = __shfl_down_sync(0xffffffffu, v.v.x, 1);
+}
+
+// Solid bits of the pair's neighbourhoods at row y (bit layout of PRow::sm), from the
+// staged phi rows y-1 .. y+1: past a half-way y wall the mirror row (the row itself),
+// past the moving wall the extrapolated row, which is never solid.
+template <typename Ctx>
+__device__ __forceinline__ uint32_t solid_mask(const Ctx& c, int y) {
+    const auto& p = c.p;
+    const float* q0 = c.aux(y, 0);
+    const bool lo_m = p.wall_y && y == 0;
+    const bool hi_m = p.wall_y && y == p.ny - 1;
+    const float* ql = lo_m ? q0 : c.aux(y - 1, 0);
+    const float* qh = hi_m ? q0 : c.aux(y + 1, 0);
+    const bool hi_fluid = hi_m && p.nee_top;
+    uint32_t m = 0;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        const uint32_t bl = ql[jj - 1] == 0.f, bm = q0[jj - 1] == 0.f, bh = !hi_fluid && qh[jj - 1] == 0.f;
+#pragma unroll
+        for (int col = 0; col < 2; ++col) {
+            const int dx = jj - 1 - col;
+            if (dx < -1 || dx > 1) continue;
+            m |= (bl << (9 * col + dx + 1)) | (bm << (9 * col + 3 + dx + 1)) | (bh << (9 * col + 6 + dx + 1));
+        }
+    }
+    return m;
+}
+__device__ __forceinline__ bool solid_own(uint32_t m, int col) { return (m >> (9 * col + 4)) & 1u; }
+// a fluid cell with at least one solid neighbour
+__device__ __forceinline__ bool solid_next(uint32_t m, int col) {
+    return !solid_own(m, col) && ((m >> (9 * col)) & 0x1EFu) != 0;
+}
+
 template <typename S, bool FAST, typename Ctx>
 __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
     using IO = PairIO<S>;
@@ -246,6 +327,34 @@ __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
         f7 = IO::dev(IO::un(hi + 7 * RW + 1), ia);
         f8 = IO::dev(IO::un(hi + 8 * RW - 1), ia);
     }
+    bool sol_a = false, sol_b = false;
+    if constexpr (Ctx::kSolid) {
+        // a link whose source cell is solid (phi = 0) is a half-way bounce-back link:
+        // the population comes from the opposite slot of this cell (the rows past a
+        // y wall were handled above)
+        auto pick = [](V2 f, const S* own, bool ka, bool kb) {
+            if (!(ka || kb)) return f;
+            const V2 o = IO::dev(IO::al(own), 1.f);
+            return mk(ka ? o.v.x : f.v.x, kb ? o.v.y : f.v.y);
+        };
+        const float* q0 = c.aux(r, 0);
+        sol_a = q0[0] == 0.f;
+        sol_b = q0[1] == 0.f;
+        f1 = pick(f1, cur + 3 * RW, q0[-1] == 0.f, sol_a);
+        f3 = pick(f3, cur + 1 * RW, sol_b, q0[2] == 0.f);
+        if (!(p.wall_y && r == 0)) {
+            const float* ql = c.aux(r - 1, 0);
+            f2 = pick(f2, cur + 4 * RW, ql[0] == 0.f, ql[1] == 0.f);
+            f5 = pick(f5, cur + 7 * RW, ql[-1] == 0.f, ql[0] == 0.f);
+            f6 = pick(f6, cur + 8 * RW, ql[1] == 0.f, ql[2] == 0.f);
+        }
+        if (!(p.wall_y && r == p.ny - 1)) {
+            const float* qh = c.aux(r + 1, 0);
+            f4 = pick(f4, cur + 2 * RW, qh[0] == 0.f, qh[1] == 0.f);
+            f7 = pick(f7, cur + 5 * RW, qh[1] == 0.f, qh[2] == 0.f);
+            f8 = pick(f8, cur + 6 * RW, qh[-1] == 0.f, qh[0] == 0.f);
+        }
+    }
     const V2 a13 = f1 + f3, a24 = f2 + f4, b57 = f5 + f7, b68 = f6 + f8;
     const V2 sax = a13 + a24, sdg = b57 + b68;
     const V2 d13 = f1 - f3, d24 = f2 - f4, d57 = f5 - f7;
@@ -273,6 +382,19 @@ __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
         st.mf = fma2(p.rest.rho0, phi, ia * st.m[0]);
         st.rf = fma2(ia, st.rho, bc(p.rest.rho0));
     }
+    if constexpr (Ctx::kSolid) {
+        // a solid cell holds no populations: a finite zero state (its neighbours read it
+        // through the mirrored ghost values of the solid stencil, never directly)
+        if (sol_a || sol_b) {
+            auto z = [&](V2 v) { return mk(sol_a ? 0.f : v.v.x, sol_b ? 0.f : v.v.y); };
+#pragma unroll
+            for (int k = 0; k < 9; ++k) st.m[k] = z(st.m[k]);
+            st.iphi = z(st.iphi);
+            st.rho = z(st.rho);
+            st.mf = z(st.mf);
+            st.rf = z(st.rf);
+        }
+    }
 }
 
 template <typename S, bool FAST, typename Ctx>
@@ -289,8 +411,32 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
             else { dhi = Bs.dr; whi = Bs.wr; }
         }
     }
-    const V2 gx = tw * fma2(4.f, Bs.dr, dlo + dhi);
-    const V2 gy = tw * (whi - wlo);
+    V2 gx = tw * fma2(4.f, Bs.dr, dlo + dhi);
+    V2 gy = tw * (whi - wlo);
+    bool sol_a = false, sol_b = false;
+    if constexpr (Ctx::kSolid) {
+        const uint32_t sm = solid_mask(c, p2);
+        Bs.sm = sm;
+        sol_a = solid_own(sm, 0);
+        sol_b = solid_own(sm, 1);
+        const bool na = solid_next(sm, 0), nb = solid_next(sm, 1);
+        if (__any_sync(0xffffffffu, na || nb)) {
+            // rho of the rows below and above: past a wall the row itself, past the
+            // moving wall 2 (row ny-1) - (row ny-2)
+            V2 lo = Cs.rho, hi = An.rho;
+            if (p.wall_y && p2 == 0) lo = Bs.rho;
+            if (p.wall_y && p2 == p.ny - 1) hi = p.nee_top ? fma2(2.f, Bs.rho, -Cs.rho) : Bs.rho;
+            float w[3][4];
+            win_row(w[0], lo);
+            win_row(w[1], Bs.rho);
+            win_row(w[2], hi);
+            float gxa, gya, gxb, gyb;
+            solid_stencil<0>(w, sm & 0x1FFu, false, gxa, gya);
+            solid_stencil<1>(w, (sm >> 9) & 0x1FFu, false, gxb, gyb);
+            if (na) { gx.v.x = tw * gxa; gy.v.x = tw * gya; }
+            if (nb) { gx.v.y = tw * gxb; gy.v.y = tw * gyb; }
+        }
+    }
     const V2 phi = c.phi2(p2, Bs);
     // (kappa - phi) / 3 times 1/scale: the rho differences are in scaled units
     const float k3 = sizeof(S) == 4 ? 1.f / 3.f : p.kp3;
@@ -314,6 +460,15 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
         const V2 inv = rcp2(m0);
         ux = fma2(0.5f, Fx, jx) * inv;
         uy = fma2(0.5f, Fy, jy) * inv;
+    }
+    if constexpr (Ctx::kSolid) {
+        // a solid cell: no velocity, no force, zero fields
+        if (sol_a || sol_b) {
+            auto z = [&](V2 v) { return mk(sol_a ? 0.f : v.v.x, sol_b ? 0.f : v.v.y); };
+            ux = z(ux); uy = z(uy); Fx = z(Fx); Fy = z(Fy);
+        }
+        Bs.rfu = Bs.rf;
+        Bs.mfu = Bs.mf;
     }
     Bs.Fx = Fx; Bs.Fy = Fy; Bs.ux = ux; Bs.uy = uy;
     // the Eq. (10) x-differences / smoothed sums of rho u, u, phi rho u on row p2
@@ -430,6 +585,57 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
         yBx = wBxh - wBxl;
         yDy = wDh - wDl;
     }
+    // next to solid cells: 12 x the gradients of the six fields (rho u_x, rho u_y, u_x,
+    // u_y, phi rho u_x, phi rho u_y) neighbour by neighbour, from the velocities of rows
+    // p3-1 (An), p3 (Cs), p3+1 (Bs) and their rho, sum f kept by phase 2
+    bool sna = false, snb = false;
+    float sGy[2] = {0.f, 0.f}, sGx[2] = {0.f, 0.f};   // (B3): x-derivative of G_y, y-derivative of G_x
+    if constexpr (Ctx::kSolid) {
+        sna = solid_next(Cs.sm, 0);
+        snb = solid_next(Cs.sm, 1);
+        if (__any_sync(0xffffffffu, sna || snb)) {
+            const bool lo_w = p.wall_y && p3 == 0, hi_w = p.wall_y && p3 == p.ny - 1;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                auto fld = [&](const PRow& R) {
+                    const V2 u = (k & 1) ? R.uy : R.ux;
+                    return k < 2 ? R.rfu * u : (k < 4 ? u : R.mfu * u);
+                };
+                const V2 l0 = fld(An), m = fld(Cs), h0 = fld(Bs);
+                // past a half-way wall the negated mirror row (no-slip); past the
+                // moving wall row 2 (row ny-1) - (row ny-2)
+                const V2 l = lo_w ? -m : l0;
+                const V2 h = hi_w ? (p.nee_top ? fma2(2.f, m, -l0) : -m) : h0;
+                float w[3][4];
+                win_row(w[0], l);
+                win_row(w[1], m);
+                win_row(w[2], h);
+                float g[2][2];   // column, x / y
+                solid_stencil<0>(w, Cs.sm & 0x1FFu, true, g[0][0], g[0][1]);
+                solid_stencil<1>(w, (Cs.sm >> 9) & 0x1FFu, true, g[1][0], g[1][1]);
+                auto put = [&](V2& d, int xy) {
+                    if (sna) d.v.x = g[0][xy];
+                    if (snb) d.v.y = g[1][xy];
+                };
+                if (k == 0) put(xAx, 0);
+                if (k == 1) put(yAy, 1);
+                if (k == 2) { put(xBx, 0); put(yBx, 1); }
+                if (k == 3) { put(yBy, 1); put(xBy, 0); }
+                if (k == 4) put(xDx, 0);
+                if (k == 5) put(yDy, 1);
+                if constexpr (Ctx::kEq2) {
+                    // G = D - kappa A
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        if (k == 0) sGx[cc] = -p.kappa * g[cc][1];
+                        if (k == 1) sGy[cc] = -p.kappa * g[cc][0];
+                        if (k == 4) sGx[cc] += g[cc][1];
+                        if (k == 5) sGy[cc] += g[cc][0];
+                    }
+                }
+            }
+        }
+    }
     const V2 phi = c.phi2(p3, Cs);
     const V2 phin = c.template phin2<FAST>(p3, Cs);
     const V2 rho = Cs.rf;
@@ -446,6 +652,10 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
             const bool lo = (p3 == 0);
             xGy = fma2(4.f, Cs.dGy, (lo ? -Cs.dGy : An.dGy) + ghi(Cs.dGy, An.dGy, Bs.dGy));
             yGx = ghi(Cs.wGx, An.wGx, Bs.wGx) - (lo ? -Cs.wGx : An.wGx);
+        }
+        if constexpr (Ctx::kSolid) {
+            if (sna) { xGy.v.x = sGy[0]; yGx.v.x = sGx[0]; }
+            if (snb) { xGy.v.y = sGy[1]; yGx.v.y = sGx[1]; }
         }
         Ca = tw * fma2(-2.f * p.kappa, xAx + yAy, fma2(2.f * kr, xBx + yBy, fma2(-2.f, X, bc(4.f)) * divD));
         Cb = (tw * (2.f / 3.f)) * fma2(-p.kappa, xAx - yAy, fma2(kr, xBx - yBy, difD));
@@ -588,16 +798,18 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
             warp_phase3<S, true>(c, An, Bs, Cs, p3, lane_ok && p3 >= y0);
             return;
         }
-        if (c.fast_strip && p3 >= c.fast_lo && p1 <= c.fast_hi) {
-            // interior row: one branch-free block, so the collision of row p3 overlaps
-            // the pulls and shuffles of rows p1, p2
-            warp_phase1<S, true>(c, An, p1);
-            const float l = left_of(An.rho), r = right_of(An.rho);
-            An.dr = rpair(An.rho, r) - lpair(An.rho, l);
-            An.wr = fma2(4.f, An.rho, rpair(An.rho, r) + lpair(An.rho, l));
-            warp_phase2<S, true>(c, An, Bs, Cs, p2);
-            warp_phase3<S, true>(c, An, Bs, Cs, p3, lane_ok);
-            return;
+        if constexpr (!Ctx::kSolid) {
+            if (c.fast_strip && p3 >= c.fast_lo && p1 <= c.fast_hi) {
+                // interior row: one branch-free block, so the collision of row p3 overlaps
+                // the pulls and shuffles of rows p1, p2
+                warp_phase1<S, true>(c, An, p1);
+                const float l = left_of(An.rho), r = right_of(An.rho);
+                An.dr = rpair(An.rho, r) - lpair(An.rho, l);
+                An.wr = fma2(4.f, An.rho, rpair(An.rho, r) + lpair(An.rho, l));
+                warp_phase2<S, true>(c, An, Bs, Cs, p2);
+                warp_phase3<S, true>(c, An, Bs, Cs, p3, lane_ok);
+                return;
+            }
         }
         const bool ph1 = (p1 <= y1 + 1) && c.row_valid(p1);
         // the moving wall row (its moments follow once row ny-2 has its velocity)
@@ -636,7 +848,7 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
     return ok;
 }
 
-template <typename S, int MINB, bool SUMS = false, bool EQ2 = false>
+template <typename S, int MINB, bool SUMS = false, bool EQ2 = false, bool SOLID = false>
 __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_constant__ StepParams<float> p) {
     using L = WarpLayout<S>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -646,7 +858,7 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     const int y0 = blockIdx.y * p.H;
     const int y1 = min(y0 + p.H, p.ny);
 
-    WarpCtx<S, SUMS, EQ2> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
+    WarpCtx<S, SUMS, EQ2, SOLID> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
     if constexpr (sizeof(S) == 2) c.step = p.step_ctr ? *p.step_ctr : 0u;
     c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
     c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
@@ -659,7 +871,8 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     c.waited = c.rlo - 1;
     c.issued = c.rlo - 1;
     // rows whose three phases need no wall, validity or field handling
-    c.fast_strip = !p.unsteady && !p.has_fb && !p.has_drag;   // (the EQ2 instance's fast path evaluates B3)
+    // (the EQ2 instance's fast path evaluates B3; the SOLID instance has none)
+    c.fast_strip = !SOLID && !p.unsteady && !p.has_fb && !p.has_drag;
     c.fast_lo = p.wall_y ? max(y0, 1) : y0;                 // lowest phase-3 row
     c.fast_hi = p.wall_y ? min(y1 + 1, p.ny - 2) : y1 + 1;  // highest phase-1 row
 
@@ -672,8 +885,12 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     for (int r = c.rlo; r <= min(y0 + kWarpSlots - 6, c.rhi); ++r) c.issue(r);
     __syncwarp();
     // strips that stage no wall row run the loop that holds only the branch-free path
-    if (c.fast_strip && (!p.wall_y || (y0 >= 3 && y1 <= p.ny - 3))) warp_run_strip<S, true>(c);
-    else warp_run_strip<S, false>(c);
+    if constexpr (SOLID) {
+        warp_run_strip<S, false>(c);
+    } else {
+        if (c.fast_strip && (!p.wall_y || (y0 >= 3 && y1 <= p.ny - 3))) warp_run_strip<S, true>(c);
+        else warp_run_strip<S, false>(c);
+    }
     if (lane == 0) {
         // every copy that may still be in flight is waited for before the CTA exits
         // (the rows whose wait gave up and those not waited for yet; see kWaitTries)
@@ -689,5 +906,18 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
         }
     }
 }
+
+}  // namespace lbmv
+
+namespace lbmv {
+
+// The one-warp kernel's instances with solid cells (the SOLID template argument),
+// compiled in vanse_warp_solid.cu. configure sets their shared-memory attributes;
+// launch starts the step-sum (sums) or plain instance, with App. B (eq2) or Eq. (18).
+template <typename S>
+cudaError_t warp_solid_configure(size_t smem_max);
+template <typename S>
+cudaError_t warp_solid_launch(const StepParams<float>& p, dim3 grid, size_t smem, cudaStream_t stream, bool sums,
+                              bool eq2);
 
 }  // namespace lbmv

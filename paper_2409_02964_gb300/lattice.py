@@ -154,8 +154,8 @@ class Lattice:
         _check(self._L.lbm_vanse_set_drag(self._h, float(d0), float(d1), float(us_x), float(us_y)), self._h)
 
     def set_solid_cells(self, enable: bool = True) -> None:
-        """Cells with phi = 0 are solid (lbm_vanse_set_solid_cells; kernel 1, before
-        init_fields)."""
+        """Cells with phi = 0 are solid (lbm_vanse_set_solid_cells; kernels 1 and 5,
+        before init_fields)."""
         _check(self._L.lbm_vanse_set_solid_cells(self._h, int(enable)), self._h)
 
     def set_moving_wall(self, uw_x: float = 0.0, uw_y: float = 0.0, enable: bool = True) -> None:
