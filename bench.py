@@ -129,14 +129,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def build_channel(n: int, storage: str, strip_rows: int = 0, kernel: int = 0, eq_order: int = 3, drag=None):
+def build_channel(n: int, storage: str, strip_rows: int = 0, kernel: int = 0, eq_order: int = 3, drag=None,
+                  moving_wall=None, solid_block: bool = False, dev_base: str = "rest"):
+    """The channel lattice; variants: a drag, App. B (eq_order 2), the top wall moving
+    at moving_wall = (u_x, u_y), or the block's interior (inside its two-cell ramp)
+    made solid (phi = 0)."""
     import paper_2409_02964_gb300 as P
     from synth import fields
     phi = fields.channel_phi(n, n)
     lat = P.Lattice(n, n, TAU, bc_y="bounceback", storage=storage, strip_rows=strip_rows, kernel=kernel,
-                    eq_order=eq_order, **RATES)
+                    eq_order=eq_order, dev_base=dev_base, **RATES)
     if drag:
         lat.set_drag(*drag)
+    if moving_wall:
+        lat.set_moving_wall(*moving_wall)
+    if solid_block:
+        x0, x1, y0, y1 = (int(round(f * n)) for f in (0.4, 0.6, 0.4, 0.6))
+        phi = phi.copy()
+        phi[y0 + 2:y1 - 2, x0 + 2:x1 - 2] = 0.0
+        lat.set_solid_cells()
     lat.set_void_fraction(phi)
     lat.set_body_force(G, 0.0)
     rho, ux, uy = fields.rest_fields(n, n)
@@ -211,6 +222,38 @@ def mms_errors(steps: int = 1000):
         b.step(steps)
         out[st] = b.relative_error(0)
         b.close()
+    return out
+
+
+def mms_errors_lattice(forms, steps: int = 1000):
+    """E_u (Eq. 26) of the same 64 x 64 manufactured solution through the single-lattice
+    step (phi(t), phi(t+1) and the Eq. (25) force uploaded every step), for storage
+    forms the batch kernel does not take: "fp64" (the discretisation error on this
+    path) and the momentum-base forms "fp16_momentum", "bf16_momentum"."""
+    import paper_2409_02964_gb300 as P
+    from synth import mms
+    n, nu = 64, 0.1
+    M = mms.Config1(n=n, T=1000.0)
+    phis = [M.phi(t) for t in range(steps + 1)]
+    forces = [M.force(t, nu) for t in range(steps + 1)]
+    out = {}
+    for form in forms:
+        base = "momentum" if form.endswith("_momentum") else "rest"
+        lat = P.Lattice(n, n, 0.8, s_eps=1.2, s_q=1.2, storage=form.split("_")[0], dev_base=base)
+        ux0, uy0 = M.velocity(0)
+        lat.set_void_fraction(phis[0], phis[1])
+        lat.set_body_force(0.0, 0.0, forces[0])
+        lat.init_fields(np.ones((n, n)), ux0, uy0)
+        for t in range(steps):
+            lat.set_void_fraction(phis[t], phis[t + 1])
+            lat.set_body_force(0.0, 0.0, forces[t])
+            lat.step(1)
+        lat.set_void_fraction(phis[steps])
+        lat.set_body_force(0.0, 0.0, forces[steps])
+        uxr, uyr = M.velocity(steps)
+        num, den = lat.velocity_error(uxr, uyr)
+        out[form] = float(np.sqrt(num / den))
+        lat.close()
     return out
 
 
@@ -589,30 +632,39 @@ def main():
     lat.close()
     if not args.quick and rank == 0:
         variants = {}
-        for st in ("fp16", "bf16", "fp64"):
+        for st in ("fp16", "bf16", "fp64", "fp16_momentum", "bf16_momentum"):
             if st == args.storage:
                 continue
-            lv, _ = build_channel(args.n, st)
+            lv, _ = build_channel(args.n, st.split("_")[0], dev_base="momentum" if st.endswith("_momentum") else "rest")
             ns = 2000 if st != "fp64" else 200
             s = time_steps(lv, ns, 5)
             variants[st] = {"MLUPS": round(cells * ns / s / 1e6, 1),
                             "GB_s": round(lv.bytes_per_cell * cells * ns / s / 1e9, 1),
                             "bytes_per_cell": lv.bytes_per_cell, "steps": ns}
             lv.close()
-        # physics variants on the same channel: a Darcy drag (Sec. 3.1, Da = k0 / H^2 = 1e-2;
-        # the one-warp kernel's general row path) and the App. B equilibrium (kernel 1)
+        # physics variants on the same channel, all on the one-warp kernel: a Darcy drag
+        # (Sec. 3.1, Da = k0 / H^2 = 1e-2) and the moving top wall (Sec. 3.1) take its
+        # general row path on every row / the rows next to the wall, App. B its
+        # branch-free path, solid cells (the block's interior, Sec. 3.3) the general
+        # path with the neighbour-by-neighbour stencil next to the solid
         nu = (TAU - 0.5) / 3
         for name, kw in (("fp32_darcy_drag", dict(drag=(nu / (1e-2 * args.n * args.n), 0.0, 0.0, 0.0))),
-                         ("fp32_appB_eq2", dict(eq_order=2))):
+                         ("fp32_appB_eq2", dict(eq_order=2)),
+                         ("fp32_moving_wall", dict(moving_wall=(0.01, 0.0))),
+                         ("fp32_solid_block", dict(solid_block=True))):
             lv, _ = build_channel(args.n, "fp32", **kw)
             s = time_steps(lv, 1000, 5)
-            variants[name] = {"MLUPS": round(cells * 1000 / s / 1e6, 1), "steps": 1000,
-                              "kernel": lv.launch_shape()["threads"]}
+            mlups = cells * 1000 / s / 1e6
+            variants[name] = {"MLUPS": round(mlups, 1), "steps": 1000, "kernel": lv.launch_shape()["threads"],
+                              "of_plain_fp32": round(mlups * world / value, 3) if args.storage == "fp32" else None}
             lv.close()
         out["precision_channel_512"] = channel_precision()
         errs = mms_errors()
+        errs.update(mms_errors_lattice(("fp16_momentum", "bf16_momentum")))
         for st, e in errs.items():
             variants.setdefault(st, {})["mms64_E_u"] = e
+        # the discretisation error on the per-step-upload path (equals the batch's FP32 value)
+        variants["fp64"]["mms64_E_u"] = mms_errors_lattice(("fp64",))["fp64"]
         out["variants"] = variants
         if not args.no_batch:
             out["batch"] = batch_run(args.batch_steps, args.batch_count)

@@ -41,6 +41,17 @@ typedef enum {
  * i >= 1 and (phi - 5 kappa / 9) rho0 for i = 0 (the rest equilibrium of Eq. 14). */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3 } lbm_storage;
 
+/* The base FP16 / BF16 deviations are taken from. LBM_BASE_REST: f_i^rest as above.
+ * LBM_BASE_MOMENTUM: f_i^rest + 3 w_i e_i . J, the linear (momentum) term of the
+ * Eq. (14) equilibrium, with J the post-collision momentum m_3+, m_5+ of the cell
+ * that holds the slot (the slot of population i at cell c holds f_i+(c)); J, rounded
+ * to the storage type and scaled like the deviations, is stored in two more planes of
+ * each population buffer (2 more values per cell read and written). The remainders
+ * are an order smaller than the deviations from rest, so their rounding is too: with
+ * BF16 the manufactured-solution error of Eq. (26) stays within a few per cent of
+ * FP64's instead of doubling. Step kernel 5 only; not with solid cells. */
+typedef enum { LBM_BASE_REST = 0, LBM_BASE_MOMENTUM = 1 } lbm_dev_base;
+
 /* Boundary type of an axis pair: periodic (Sec. 3, default) or half-way
  * bounce-back no-slip walls at both ends (Sec. 3.1). Walls are supported on y. */
 typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 } lbm_bc;
@@ -73,6 +84,7 @@ typedef struct {
                                     two columns per lane (2..5: not FP64) */
     int eq_order;                /* 3 (or 0): the 3rd-order equilibrium of Eq. (14) with Eq. (18), (20);
                                     2: App. B, Eq. (B1)-(B3) (kernels 1 and 5) */
+    int dev_base;                /* lbm_dev_base of FP16 / BF16 storage (default LBM_BASE_REST) */
 } lbm_vanse_params;
 
 typedef struct lbm_vanse* lbm_vanse_t;

@@ -12,6 +12,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_STATE,
     0, -1, -2, -3, -4, -5, -6)
 LBM_FP64, LBM_FP32, LBM_FP16, LBM_BF16 = 0, 1, 2, 3
 LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = 0, 1
+LBM_BASE_REST, LBM_BASE_MOMENTUM = 0, 1
 
 NOALLOC_MAX_ROWS = 8192  # LBM_VANSE_NOALLOC_MAX_ROWS
 
@@ -54,6 +55,7 @@ class lbm_vanse_params(ctypes.Structure):
         ("storage", ctypes.c_int), ("model_b", ctypes.c_int),
         ("storage_scale_log2", ctypes.c_int), ("strip_rows", ctypes.c_int),
         ("eager", ctypes.c_int), ("kernel", ctypes.c_int), ("eq_order", ctypes.c_int),
+        ("dev_base", ctypes.c_int),
     ]
 
 

@@ -73,6 +73,10 @@ struct lbm_vanse {
     bool nee_top = false;         // row ny-1: moving wall by non-equilibrium extrapolation
     double uw_x = 0, uw_y = 0;
     bool has_solid = false;       // phi = 0 marks solid cells (kernels 1 and 5)
+    bool jbase = false;           // FP16/BF16 deviations from the momentum base (kernel 5)
+    unsigned char* solid_tiles = nullptr;   // kernel 5 with solid cells: CTAs whose staged region holds one
+    int* tile_order = nullptr;              // ... their launch order (those tiles first), and 2 counters
+    int npl = 9;                  // planes per population buffer (11 with the momentum base)
     int* zero_phi = nullptr;      // device flag: the last phi upload held a zero
     unsigned* step_ctr = nullptr; // device step count of the one-warp kernel (seeds stochastic rounding)
     double s_nu = 0, s_e = 0;
@@ -170,6 +174,7 @@ Lattice<R> make_lattice(const lbm_vanse* h) {
     L.us_x = (R)h->us_x;
     L.us_y = (R)h->us_y;
     L.has_solid = h->has_solid;
+    L.jbase = h->jbase;
     return L;
 }
 
@@ -185,7 +190,7 @@ size_t step_smem_bytes(const lbm_vanse* h, int nR) {
         case 2: return PairLayout<S, 64>::bytes(nR);
         case 3: return PairLayout<S, 96>::bytes(nR);
         case 4: return PairLayout<S, 128>::bytes(nR);
-        case 5: return WarpLayout<S>::bytes(nR);
+        case 5: return h->jbase ? WarpLayout<S, 11>::bytes(nR) : WarpLayout<S>::bytes(nR);
         default:
             return StepLayout<S, R, kThreads>::bytes(nR) +
                    (h->has_solid ? StepLayout<S, R, kThreads>::solid_bytes() : 0);
@@ -214,6 +219,9 @@ const void* step_kernel_ptr(const lbm_vanse* h) {
             case 3: return (const void*)vanse_pair_kernel<S, 96, 4>;
             case 4: return (const void*)vanse_pair_kernel<S, 128, 3>;
             case 5:
+                if constexpr (sizeof(S) == 2) {
+                    if (h->jbase) return warp_jb_kernel<S>();
+                }
                 return h->prm.eq_order == 2 ? (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB, false, true>
                                             : (const void*)vanse_warp_kernel<S, LBMV_WARP_MINB>;
             default: break;
@@ -231,6 +239,9 @@ lbm_status configure(lbm_vanse* h) {
     const size_t smax = step_smem_max<S>(h);
     CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+    if constexpr (sizeof(S) == 2) {
+        if (h->jbase) CK(h, warp_jb_configure<S>(smax));
+    }
     const size_t s1 = step_smem_bytes<S>(h, 1);
     int per_sm = 0, nsm = 0;
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, s1));
@@ -278,9 +289,9 @@ lbm_status launch_solid_step(lbm_vanse* h, const StepParams<typename Prec<S>::R>
             }
             CK(h, warp_solid_launch<S>(p, grid, smem, stream, sums, p.eq2 != 0));
             // the one-warp kernel writes columns 0 .. nx-1 only
-            const long long ng = 9LL * h->prm.ny * 2 * kGhost;
+            const long long ng = (long long)h->npl * h->prm.ny * 2 * kGhost;
             ghost_fill_kernel<S><<<(int)std::min<long long>((ng + 255) / 256, 4096), 256, 0, stream>>>(
-                (S*)p.dst, h->plane, h->prm.nx, h->prm.ny, h->P, h->step_ctr);
+                (S*)p.dst, h->plane, h->prm.nx, h->prm.ny, h->P, h->step_ctr, h->npl);
             CK(h, cudaGetLastError());
             return LBM_OK;
         }
@@ -355,6 +366,8 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
     p.uw_x = (R)h->uw_x;
     p.uw_y = (R)h->uw_y;
     p.has_solid = h->has_solid;
+    p.solid_tiles = (h->has_solid && h->kernel == 5) ? h->solid_tiles : nullptr;
+    p.tile_order = p.solid_tiles ? h->tile_order : nullptr;
     p.step_ctr = h->step_ctr;
     p.wait_tries = h->wait_tries;
     if (h->kernel == 5) p.pop_map = h->pop_map[src];
@@ -372,12 +385,17 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
         }
         if constexpr (!std::is_same<S, double>::value) {
             if (h->kernel == 5) {
-                if (p.eq2) vanse_warp_kernel<S, LBMV_WARP_MINB, true, true><<<grid, 32, smem, stream>>>(p);
-                else vanse_warp_kernel<S, LBMV_WARP_MINB, true><<<grid, 32, smem, stream>>>(p);
+                if constexpr (sizeof(S) == 2) {
+                    if (h->jbase) CK(h, warp_jb_launch<S>(p, grid, smem, stream, true, p.eq2 != 0));
+                }
+                if (!h->jbase) {
+                    if (p.eq2) vanse_warp_kernel<S, LBMV_WARP_MINB, true, true><<<grid, 32, smem, stream>>>(p);
+                    else vanse_warp_kernel<S, LBMV_WARP_MINB, true><<<grid, 32, smem, stream>>>(p);
+                }
                 CK(h, cudaGetLastError());
-                const long long ng = 9LL * h->prm.ny * 2 * kGhost;
+                const long long ng = (long long)h->npl * h->prm.ny * 2 * kGhost;
                 ghost_fill_kernel<S><<<(int)std::min<long long>((ng + 255) / 256, 4096), 256, 0, stream>>>(
-                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P, h->step_ctr);
+                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P, h->step_ctr, h->npl);
                 CK(h, cudaGetLastError());
                 return LBM_OK;
             }
@@ -392,13 +410,18 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
             case 3: vanse_pair_kernel<S, 96, 4><<<grid, 96, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
             case 4: vanse_pair_kernel<S, 128, 3><<<grid, 128, smem, stream>>>(p); CK(h, cudaGetLastError()); return LBM_OK;
             case 5: {
-                if (p.eq2) vanse_warp_kernel<S, LBMV_WARP_MINB, false, true><<<grid, 32, smem, stream>>>(p);
-                else vanse_warp_kernel<S, LBMV_WARP_MINB><<<grid, 32, smem, stream>>>(p);
+                if constexpr (sizeof(S) == 2) {
+                    if (h->jbase) CK(h, warp_jb_launch<S>(p, grid, smem, stream, false, p.eq2 != 0));
+                }
+                if (!h->jbase) {
+                    if (p.eq2) vanse_warp_kernel<S, LBMV_WARP_MINB, false, true><<<grid, 32, smem, stream>>>(p);
+                    else vanse_warp_kernel<S, LBMV_WARP_MINB><<<grid, 32, smem, stream>>>(p);
+                }
                 CK(h, cudaGetLastError());
                 // the one-warp kernel writes columns 0 .. nx-1 only
-                const long long ng = 9LL * h->prm.ny * 2 * kGhost;
+                const long long ng = (long long)h->npl * h->prm.ny * 2 * kGhost;
                 ghost_fill_kernel<S><<<(int)std::min<long long>((ng + 255) / 256, 4096), 256, 0, stream>>>(
-                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P, h->step_ctr);
+                    (S*)h->f[1 - src], h->plane, h->prm.nx, h->prm.ny, h->P, h->step_ctr, h->npl);
                 CK(h, cudaGetLastError());
                 return LBM_OK;
             }
@@ -460,11 +483,19 @@ lbm_status replay_graph(lbm_vanse* h) {
     return LBM_OK;
 }
 
+// The momentum base's J planes of buffer b set to zero: the auxiliary writers encode
+// every slot against f^rest alone (J = 0 is a valid base; the next step stores its own).
+cudaError_t zero_j_planes(lbm_vanse* h, int b) {
+    return cudaMemsetAsync((char*)h->f[b] + (size_t)9 * h->plane * h->sbytes, 0, (size_t)2 * h->plane * h->sbytes,
+                           h->stream);
+}
+
 template <typename S>
 lbm_status run_init(lbm_vanse* h, const double* rho, const double* ux, const double* uy) {
     using R = typename Prec<S>::R;
     const long long n = (long long)h->prm.nx * h->prm.ny;
     Lattice<R> L = make_lattice<R>(h);
+    if (h->jbase) CK(h, zero_j_planes(h, h->cur));
     init_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>(
         (S*)h->f[h->cur], (const R*)h->phi, h->has_fb ? (const R*)h->fb : nullptr, rho, ux, uy, L);
     CK(h, cudaGetLastError());
@@ -485,6 +516,7 @@ template <typename S>
 lbm_status run_set(lbm_vanse* h, const double* in) {
     using R = typename Prec<S>::R;
     const long long n = (long long)h->prm.nx * h->prm.ny;
+    if (h->jbase) CK(h, zero_j_planes(h, h->cur));
     set_pop_kernel<S, R><<<aux_blocks(n), kAuxThreads, 0, h->stream>>>((S*)h->f[h->cur], (const R*)h->phi, in,
                                                                        make_lattice<double>(h));
     CK(h, cudaGetLastError());
@@ -656,6 +688,25 @@ lbm_status upload_void_fraction_pinned(lbm_vanse* h, const T* phi_t, const T* ph
     return LBM_OK;
 }
 
+// Kernel 5 with solid cells: flag the CTAs whose staged region holds a solid cell of
+// phi(t) or phi(t+1) (solid_tiles_kernel), after every change of phi. The others run
+// the solid-free path. (Solid cells stay solid, so the flags of phi(t) and phi(t+1)
+// also cover the steady steps after phi(t+1) has become phi(t).)
+lbm_status update_solid_tiles(lbm_vanse* h) {
+    if (!h->has_solid || h->kernel != 5 || !h->phi_set) return LBM_OK;
+    const int nt = h->gridx * h->gridy;
+    if (!h->solid_tiles) CK(h, cudaMallocAsync((void**)&h->solid_tiles, (size_t)nt, h->stream));
+    if (!h->tile_order) CK(h, cudaMallocAsync((void**)&h->tile_order, (size_t)(nt + 2) * sizeof(int), h->stream));
+    solid_tiles_kernel<float><<<dim3(h->gridx, h->gridy), 256, 0, h->stream>>>(
+        (const float*)h->phi, h->unsteady ? (const float*)h->phin : nullptr, h->solid_tiles, h->prm.nx, h->prm.ny, h->P,
+        h->W, h->H, h->prm.bc_y == LBM_BC_BOUNCEBACK);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemsetAsync(h->tile_order + nt, 0, 2 * sizeof(int), h->stream));
+    solid_order_kernel<<<(nt + 255) / 256, 256, 0, h->stream>>>(h->solid_tiles, nt, h->tile_order, h->tile_order + nt);
+    CK(h, cudaGetLastError());
+    return LBM_OK;
+}
+
 // lbm_vanse_set_void_fraction for double or float caller arrays.
 template <typename T>
 lbm_status set_void_fraction_impl(lbm_vanse* h, const T* phi_t, const T* phi_next, int on_device) {
@@ -667,7 +718,7 @@ lbm_status set_void_fraction_impl(lbm_vanse* h, const T* phi_t, const T* phi_nex
         if (st != LBM_OK) return st;
         h->unsteady = phi_next != nullptr;
         h->phi_set = true;
-        return LBM_OK;
+        return update_solid_tiles(h);
     }
     // stage and check both fields before either replaces the lattice's own
     T* d[2] = {nullptr, nullptr};
@@ -691,7 +742,7 @@ lbm_status set_void_fraction_impl(lbm_vanse* h, const T* phi_t, const T* phi_nex
     if (st != LBM_OK) return st;
     h->unsteady = phi_next != nullptr;
     h->phi_set = true;
-    return LBM_OK;
+    return update_solid_tiles(h);
 }
 
 lbm_status ensure_scratch(lbm_vanse* h) {
@@ -714,7 +765,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 // Encodes the map of one population buffer (P columns per row, ny rows, planes of
 // `plane` elements, storage `storage`); returns an empty string or the failure.
-std::string encode_pop_map_raw(void* buf, int P, int ny, long long plane, int storage, CUtensorMap* out) {
+std::string encode_pop_map_raw(void* buf, int P, int ny, long long plane, int storage, CUtensorMap* out,
+                               int npl = 9) {
     static EncodeTiledFn enc = nullptr;
     static std::mutex mu;
     {
@@ -730,10 +782,10 @@ std::string encode_pop_map_raw(void* buf, int P, int ny, long long plane, int st
         }
     }
     const int sb = storage_bytes(storage);
-    const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)ny, 9};
+    const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)ny, (cuuint64_t)npl};
     const cuuint64_t strides[2] = {(cuuint64_t)P * sb, (cuuint64_t)plane * sb};
     // the staged width WarpLayout<S>::WW: 64 columns plus 16 bytes on each side
-    const cuuint32_t box[3] = {(cuuint32_t)(64 + 2 * (16 / sb)), 1, 9};
+    const cuuint32_t box[3] = {(cuuint32_t)(64 + 2 * (16 / sb)), 1, (cuuint32_t)npl};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = storage == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : (storage == LBM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -748,7 +800,7 @@ std::string encode_pop_map_raw(void* buf, int P, int ny, long long plane, int st
 template <typename S>
 lbm_status encode_pop_map(lbm_vanse* h, void* buf, CUtensorMap* out) {
     static_assert(WarpLayout<S>::WW == 64 + 2 * (16 / (int)sizeof(S)), "box width of encode_pop_map_raw");
-    const std::string e = encode_pop_map_raw(buf, h->P, h->prm.ny, h->plane, h->prm.storage, out);
+    const std::string e = encode_pop_map_raw(buf, h->P, h->prm.ny, h->plane, h->prm.storage, out, h->npl);
     if (!e.empty()) return fail(h, LBM_ERR_CUDA, "%s", e.c_str());
     return LBM_OK;
 }
@@ -864,6 +916,7 @@ extern "C" void lbm_vanse_default_params(lbm_vanse_params* p) {
     p->strip_rows = 0;
     p->eager = 0;
     p->eq_order = 3;
+    p->dev_base = LBM_BASE_REST;
 }
 
 extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_stream, lbm_vanse_t* out) {
@@ -924,6 +977,21 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
     if (h->prm.eq_order == 0) h->prm.eq_order = 3;
     h->kernel = p->kernel ? p->kernel
                           : ((p->storage == LBM_FP64 || p->bc_x == LBM_BC_BOUNCEBACK) ? 1 : kDefaultKernel);
+    if (p->dev_base != LBM_BASE_REST && p->dev_base != LBM_BASE_MOMENTUM) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "dev_base must be LBM_BASE_REST or LBM_BASE_MOMENTUM");
+    }
+    if (p->dev_base == LBM_BASE_MOMENTUM && (p->storage != LBM_FP16 && p->storage != LBM_BF16)) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "the momentum base is an FP16 / BF16 storage form");
+    }
+    if (p->dev_base == LBM_BASE_MOMENTUM && h->kernel != 5) {
+        delete h;
+        return fail(nullptr, LBM_ERR_ARG, "the momentum base runs on step kernel 5 (this lattice: kernel %d)",
+                    h->kernel);
+    }
+    h->jbase = p->dev_base == LBM_BASE_MOMENTUM;
+    h->npl = h->jbase ? 11 : 9;
     h->pair = h->kernel >= 2;
     h->W = h->kernel == 5 ? 60 : (h->pair ? 2 * kPairT[h->kernel - 2] - 4 : kThreads - 4);
     h->gridx = (p->nx + h->W - 1) / h->W;
@@ -938,7 +1006,7 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
         if (ee != cudaSuccess) { st = cuda_fail(h, ee, "cudaMemsetAsync"); return false; }
         return true;
     };
-    const size_t popb = (size_t)9 * h->plane * h->sbytes;
+    const size_t popb = (size_t)h->npl * h->plane * h->sbytes;
     const size_t fldb = (size_t)h->plane * h->rbytes;
     bool ok = alloc(&h->f[0], popb) && alloc(&h->f[1], popb) && alloc(&h->phi, fldb) && alloc(&h->phin, fldb) &&
               alloc((void**)&h->err, sizeof(int)) && alloc((void**)&h->zero_phi, sizeof(int)) &&
@@ -1014,9 +1082,11 @@ extern "C" lbm_status lbm_vanse_set_solid_cells(lbm_vanse_t h, int enable) {
                     h->kernel);
     if (enable && h->prm.bc_x == LBM_BC_BOUNCEBACK)
         return fail(h, LBM_ERR_ARG, "solid cells and x walls together are not supported (use a solid frame)");
+    if (enable && h->jbase)
+        return fail(h, LBM_ERR_ARG, "solid cells and the momentum base together are not supported");
     h->has_solid = enable != 0;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // the step's shared memory changes
-    return LBM_OK;
+    return update_solid_tiles(h);
 }
 
 extern "C" lbm_status lbm_vanse_set_row_wait_limit(lbm_vanse_t h, long long polls) {
@@ -1168,13 +1238,14 @@ struct StateHeader {
     long long plane, steps;
     unsigned step_ctr, pad0;
     double gx, gy, drag[4], uw[2];
+    int dev_base, pad1;
 };
 static_assert(sizeof(StateHeader) <= 512, "state header");
 constexpr size_t kStateHeader = 512;
 constexpr char kStateMagic[8] = {'L', 'B', 'M', 'V', 'S', 'N', 'A', 'P'};
 
 size_t state_bytes(const lbm_vanse* h) {
-    const size_t pop = (size_t)9 * h->plane * h->sbytes, fld = (size_t)h->plane * h->rbytes;
+    const size_t pop = (size_t)h->npl * h->plane * h->sbytes, fld = (size_t)h->plane * h->rbytes;
     return kStateHeader + pop + fld * (1 + (h->unsteady ? 1 : 0) + (h->has_fb ? 2 : 0));
 }
 
@@ -1196,6 +1267,7 @@ extern "C" lbm_status lbm_vanse_save_state(lbm_vanse_t h, void* buf, int on_devi
     hd.gx = h->gx; hd.gy = h->gy;
     hd.drag[0] = h->drag_d0; hd.drag[1] = h->drag_d1; hd.drag[2] = h->us_x; hd.drag[3] = h->us_y;
     hd.uw[0] = h->uw_x; hd.uw[1] = h->uw_y;
+    hd.dev_base = h->jbase ? 1 : 0;
     CK(h, cudaMemcpyAsync(&hd.step_ctr, h->step_ctr, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     char* out = static_cast<char*>(buf);
@@ -1205,7 +1277,7 @@ extern "C" lbm_status lbm_vanse_save_state(lbm_vanse_t h, void* buf, int on_devi
     std::memcpy(header, &hd, sizeof(hd));
     CK(h, cudaMemcpyAsync(out, header, kStateHeader, hk, h->stream));
     size_t off = kStateHeader;
-    const size_t pop = (size_t)9 * h->plane * h->sbytes, fld = (size_t)h->plane * h->rbytes;
+    const size_t pop = (size_t)h->npl * h->plane * h->sbytes, fld = (size_t)h->plane * h->rbytes;
     CK(h, cudaMemcpyAsync(out + off, h->f[h->cur], pop, dk, h->stream));
     off += pop;
     CK(h, cudaMemcpyAsync(out + off, h->phi, fld, dk, h->stream));
@@ -1225,9 +1297,10 @@ extern "C" lbm_status lbm_vanse_load_state(lbm_vanse_t h, const void* buf, int o
     if (std::memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != 1)
         return fail(h, LBM_ERR_ARG, "not a lattice state (bad magic or version)");
     if (hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.P != h->P || hd.storage != h->prm.storage ||
-        hd.plane != h->plane || hd.has_solid != (int)h->has_solid)
-        return fail(h, LBM_ERR_ARG, "the state is of another lattice (size %dx%d, storage %d, solid cells %d)", hd.nx,
-                    hd.ny, hd.storage, hd.has_solid);
+        hd.plane != h->plane || hd.has_solid != (int)h->has_solid || hd.dev_base != (h->jbase ? 1 : 0))
+        return fail(h, LBM_ERR_ARG,
+                    "the state is of another lattice (size %dx%d, storage %d, solid cells %d, deviation base %d)",
+                    hd.nx, hd.ny, hd.storage, hd.has_solid, hd.dev_base);
     if (hd.nee_top && h->kernel != 1 && h->kernel != 5)
         return fail(h, LBM_ERR_ARG, "the state has a moving wall: kernel 1 or 5 needed");
     if (hd.has_fb && !h->fb) {
@@ -1235,7 +1308,7 @@ extern "C" lbm_status lbm_vanse_load_state(lbm_vanse_t h, const void* buf, int o
     }
     const cudaMemcpyKind dk = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     size_t off = kStateHeader;
-    const size_t pop = (size_t)9 * h->plane * h->sbytes, fld = (size_t)h->plane * h->rbytes;
+    const size_t pop = (size_t)h->npl * h->plane * h->sbytes, fld = (size_t)h->plane * h->rbytes;
     CK(h, cudaMemcpyAsync(h->f[h->cur], in + off, pop, dk, h->stream));
     off += pop;
     CK(h, cudaMemcpyAsync(h->phi, in + off, fld, dk, h->stream));
@@ -1255,7 +1328,7 @@ extern "C" lbm_status lbm_vanse_load_state(lbm_vanse_t h, const void* buf, int o
     h->phi_set = true;
     h->initialised = true;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
-    return LBM_OK;
+    return update_solid_tiles(h);
 }
 
 extern "C" lbm_status lbm_vanse_reduce(lbm_vanse_t h, double* mass, double* momx, double* momy) {
@@ -1347,7 +1420,7 @@ extern "C" long long lbm_vanse_step_count(lbm_vanse_t h) { return h ? h->steps :
 
 extern "C" double lbm_vanse_bytes_per_cell(lbm_vanse_t h) {
     if (!h) return 0.0;
-    double b = 18.0 * h->sbytes + h->rbytes;  // 9 populations read + 9 written, phi(t)
+    double b = 2.0 * h->npl * h->sbytes + h->rbytes;  // 9 populations (+ J) read and written, phi(t)
     if (h->unsteady) b += h->rbytes;
     if (h->has_fb) b += 2.0 * h->rbytes;
     return b;
@@ -1389,7 +1462,8 @@ extern "C" void lbm_vanse_destroy(lbm_vanse_t h) {
         cudaEventDestroy(h->staging_free);
     }
     void* ptrs[] = {h->f[0], h->f[1], h->phi, h->phin, h->fb, h->err, h->partial, h->red_out, h->scratch,
-                    h->staging[0], h->staging[1], h->zero_phi, h->step_ctr, h->bad_phi};
+                    h->staging[0], h->staging[1], h->zero_phi, h->step_ctr, h->bad_phi, h->solid_tiles,
+                    h->tile_order};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (h->bad_phi_host) cudaFreeHost(h->bad_phi_host);

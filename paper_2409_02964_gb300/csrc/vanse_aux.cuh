@@ -25,6 +25,10 @@ struct Lattice {
     int has_drag = 0;                  // F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi))
     R drag_d0 = 0, drag_d1 = 0, us_x = 0, us_y = 0;
     int has_solid = 0;                 // cells with phi = 0 are solid (half-way bounce-back links)
+    // momentum base (FP16 / BF16 on the one-warp kernel): slot (i, c) holds the deviation
+    // from f_i^rest + 3 w_i e_i . J(c), J(c) the post-collision momentum of cell c stored
+    // (scaled like the deviations) in planes 9 (x) and 10 (y) of the same buffer
+    int jbase = 0;
 };
 
 // the linear drag coefficient beta(phi) of a lattice (0 without drag)
@@ -62,13 +66,52 @@ __device__ __forceinline__ void fill_ghosts(S* __restrict__ buf, long long plane
 
 // step_ctr (optional): the one-warp kernel's step count, advanced here once per step
 // (it seeds the stochastic rounding of FP16/BF16 stores).
+// npl: the planes of the buffer (9 populations, 11 with the momentum base's J planes).
 template <typename S>
 __global__ void ghost_fill_kernel(S* __restrict__ buf, long long plane, int nx, int ny, int P,
-                                  unsigned* __restrict__ step_ctr = nullptr) {
-    const long long n = 9LL * ny * 2 * kGhost;
+                                  unsigned* __restrict__ step_ctr = nullptr, int npl = 9) {
+    const long long n = (long long)npl * ny * 2 * kGhost;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
         fill_ghosts<S>(buf, plane, nx, ny, P, k);
     if (step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1u;
+}
+
+// Solid-cell tiles of the one-warp kernel: per CTA (its 60 columns x0 .., its strip's
+// rows y0 .. y1-1), 1 when the void fraction phi(t) or phi(t+1) is 0 anywhere in what
+// the CTA stages: rows y0-3 .. y1+2 (past a y wall none, periodic rows wrapped) and
+// columns x0-3 .. x0+63 that lie within the lattice or its ghost columns (the columns
+// beyond hold no value a written cell reads). One CTA per tile.
+template <typename R>
+__global__ void solid_tiles_kernel(const R* __restrict__ phi, const R* __restrict__ phin,
+                                   unsigned char* __restrict__ tiles, int nx, int ny, int P, int W, int H,
+                                   int wall_y) {
+    const int x0 = blockIdx.x * W, y0 = blockIdx.y * H, y1 = min(y0 + H, ny);
+    const int xlo = x0 - kGhost, xhi = min(x0 + 64, nx + kGhost);
+    const int ncol = xhi - xlo, nrow = (y1 + 2) - (y0 - 3) + 1;
+    int found = 0;
+    for (int k = threadIdx.x; k < nrow * ncol; k += blockDim.x) {
+        int y = y0 - 3 + k / ncol;
+        const int x = xlo + k % ncol;
+        if (y < 0 || y >= ny) {
+            if (wall_y) continue;
+            y = ((y % ny) + ny) % ny;
+        }
+        const long long o = (long long)y * P + kPadCols + x;
+        if (phi[o] == (R)0 || (phin && phin[o] == (R)0)) found = 1;
+    }
+    found = __syncthreads_or(found);
+    if (threadIdx.x == 0) tiles[blockIdx.y * gridDim.x + blockIdx.x] = (unsigned char)(found != 0);
+}
+
+// The launch order of the tiles: those with solid cells first (their CTAs take the
+// longer solid path, and started first they overlap the others instead of trailing
+// them), then the rest. cnt[0..1] must be zero on entry. One thread per tile.
+__global__ void solid_order_kernel(const unsigned char* __restrict__ tiles, int n, int* __restrict__ order,
+                                   int* __restrict__ cnt) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        if (tiles[t]) order[atomicAdd(cnt, 1)] = t;
+        else order[n - 1 - atomicAdd(cnt + 1, 1)] = t;
+    }
 }
 
 // Void-fraction check of a dense field before it replaces the lattice's: every value
@@ -155,9 +198,16 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ buf, const R* __
             else sy = (sy + L.ny) % L.ny;
         }
         if (L.has_solid && pi == i && phi[cell_off(L.P, sx, sy)] == (R)0) { sx = x; sy = y; pi = opp_of(i); }
-        const S v = buf[pi * L.plane + cell_off(L.P, sx, sy)];
+        const long long so = cell_off(L.P, sx, sy);
+        const S v = buf[pi * L.plane + so];
         const T rest = (i == 0) ? L.rest.r0(ph) : L.rest.ri(i);
         f[i] = dec_as<T>(v, rest, L.inv_scale);
+        if (L.jbase && pi != 0) {
+            // the slot's own base: 3 w_pi e_pi . J of the cell it sits in
+            const T jx = dec_as<T>(buf[9 * L.plane + so], (T)0, L.inv_scale);
+            const T jy = dec_as<T>(buf[10 * L.plane + so], (T)0, L.inv_scale);
+            f[i] += w3_of<T>(pi) * ((T)ex_of(pi) * jx + (T)ey_of(pi) * jy);
+        }
     }
 }
 

@@ -67,6 +67,7 @@ struct BatchCtx {
     static constexpr bool kSums = false;
     static constexpr bool kEq2 = false;
     static constexpr bool kSolid = false;
+    static constexpr bool kJB = false;
     StepParams<float> p;       // this lattice's scalars (pointers and sizes included)
     unsigned char* smem;
     int lane, xa, sa;

@@ -13,6 +13,10 @@ namespace lbmv {
 __host__ __device__ constexpr int ex_of(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
 __host__ __device__ constexpr int ey_of(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
 __host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
+// 3 w_i of Eq. (5): the weight of the linear (momentum) term 3 w_i e_i . j of f^eq_i
+template <typename T> __host__ __device__ constexpr T w3_of(int i) {
+    return i == 0 ? (T)0 : (i <= 4 ? (T)1 / (T)3 : (T)1 / (T)12);
+}
 
 // Ghost columns kept on each side of a periodic x axis (the pull at halo radius 2
 // reads 3 columns beyond a CTA's cells), and the column offset of cell x = 0 in a

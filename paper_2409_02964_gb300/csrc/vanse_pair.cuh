@@ -56,6 +56,7 @@ template <> struct PairIO<float> {
     __device__ static V2 dev(V2 d, float) { return d; }
     __device__ static void st(float* p, V2 v) { *reinterpret_cast<float2*>(p) = v.v; }
     __device__ static float enc1(float f, float rest, float) { return f - rest; }
+    __device__ static V2 round_rn(V2 v) { return v; }
 };
 template <> struct PairIO<__half> {
     __device__ static V2 al(const __half* p) { return V2{__half22float2(*reinterpret_cast<const __half2*>(p))}; }
@@ -70,6 +71,8 @@ template <> struct PairIO<__half> {
         *reinterpret_cast<uint32_t*>(p) = d;
     }
     __device__ static __half enc1(float f, float rest, float s) { return __float2half_rn((f - rest) * s); }
+    // a pair rounded to the storage type (to nearest) and back: stored as it is, exactly
+    __device__ static V2 round_rn(V2 v) { return V2{__half22float2(__float22half2_rn(v.v))}; }
 };
 template <> struct PairIO<__nv_bfloat16> {
     __device__ static V2 al(const __nv_bfloat16* p) {
@@ -87,6 +90,7 @@ template <> struct PairIO<__nv_bfloat16> {
         *reinterpret_cast<uint32_t*>(p) = d;
     }
     __device__ static __nv_bfloat16 enc1(float f, float rest, float s) { return __float2bfloat16_rn((f - rest) * s); }
+    __device__ static V2 round_rn(V2 v) { return V2{__bfloat1622float2(__float22bfloat162_rn(v.v))}; }
 };
 
 constexpr int kPairSlots = 6;   // ring slots: rows p-2 .. p+1 in use, two rows of prefetch

@@ -86,16 +86,21 @@ struct StepParams {
     int has_drag;         // F^B += -beta (u - u_s), beta = phi^2 (d0 + d1 (1 - phi)); u solved implicitly
     R drag_d0, drag_d1, us_x, us_y;
     double* sums;         // step-sum variants: FP64 sums of m_0+, j_x+, j_y+ over the cells written (added)
-    int nee_top;          // row ny-1 is a moving wall by non-equilibrium extrapolation (kernel 1 only)
+    int nee_top;          // row ny-1 is a moving wall by non-equilibrium extrapolation (kernels 1 and 5)
     R uw_x, uw_y;         // its velocity
-    int has_solid;        // cells with phi = 0 are solid (the SOLID variants of kernel 1; see solid_grad12)
+    int has_solid;        // cells with phi = 0 are solid (the SOLID variants of kernels 1 and 5)
+    // one-warp kernel with solid cells: per CTA (blockIdx.y * gridDim.x + blockIdx.x), 1
+    // when a solid cell lies in the rows and columns the CTA stages (else it runs the
+    // solid-free path), or nullptr (every CTA takes the solid path)
+    const unsigned char* solid_tiles;
+    const int* tile_order;   // with solid_tiles: the tile (y * gridDim.x + x) CTA number k runs
     // the one-warp kernel collides FP16/BF16 deviations in the storage's scaled units:
     // h_* x scale, rho0 x scale and inv_scale / 3 (equal to h_*, rho0, 1/3 at scale 1)
     R hs_e, hs_eps, hs_q, hs_nu, rho0s, kp3;
     const unsigned* step_ctr;   // one-warp kernel: steps taken (seeds the stochastic rounding), or nullptr
     uint32_t wait_tries;        // polls of a staged-row wait before it gives up (kWaitTries by default)
-    // one-warp kernel: the source buffer as a tensor [9][ny][P] whose box (the staged
-    // width x 1 row x 9 planes) stages a row's nine population rows in one copy
+    // one-warp kernel: the source buffer as a tensor [9 or 11][ny][P] whose box (the
+    // staged width x 1 row x all planes) stages a row's population rows in one copy
     CUtensorMap pop_map;
 };
 

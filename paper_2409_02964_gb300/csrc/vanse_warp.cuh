@@ -36,13 +36,15 @@ constexpr int kWarpSlots = LBMV_WARP_SLOTS;
 #define LBMV_WARP_MINB 8
 #endif
 
-template <typename S>
+// NPL: planes staged per source row (the 9 populations; 11 with the momentum base,
+// whose J planes follow them in the same buffer)
+template <typename S, int NPL = 9>
 struct WarpLayout {
     static constexpr int A = 16 / (int)sizeof(S);
     static constexpr int WW = 64 + 2 * A;           // staged row width (elements)
     static constexpr int kPop = 128;                // after the mbarriers
     static constexpr int kPopRow = WW * (int)sizeof(S);
-    static constexpr int kPopSlot = (9 * kPopRow + 127) / 128 * 128;   // tensor-copy destinations: 128-byte aligned
+    static constexpr int kPopSlot = (NPL * kPopRow + 127) / 128 * 128;   // tensor-copy destinations: 128-byte aligned
     static constexpr int kAux = kPop + kWarpSlots * kPopSlot;
     static constexpr int kAuxRow = WW * 4;
     static constexpr size_t bytes(int nR) { return (size_t)kAux + (size_t)kWarpSlots * nR * kAuxRow; }
@@ -96,13 +98,15 @@ struct PairSums {
     }
 };
 
-template <typename S, bool SUMS = false, bool EQ2 = false, bool SOLID = false>
+template <typename S, bool SUMS = false, bool EQ2 = false, bool SOLID = false, bool JB = false>
 struct WarpCtx {
-    using L = WarpLayout<S>;
+    static constexpr int kNPL = JB ? 11 : 9;   // planes per staged row
+    using L = WarpLayout<S, kNPL>;
     static constexpr bool kUnsteady = false;   // the fast path runs only on steady strips
     static constexpr bool kSums = SUMS;        // accumulate the written cells' m_0+, j+ (PairSums)
     static constexpr bool kEq2 = EQ2;          // App. B: (B2) energy-flux equilibria, (B3) penalty
     static constexpr bool kSolid = SOLID;      // phi = 0 marks solid cells (general path only)
+    static constexpr bool kJB = JB;            // FP16 / BF16 deviations from the momentum base
     const StepParams<float>& p;
     unsigned char* smem;
     int lane, xa, sa;
@@ -155,7 +159,7 @@ struct WarpCtx {
     __device__ __forceinline__ void setup_copies() {
         const uint32_t base = smem_u32(smem);
         cp.bar0 = base;
-        cp.tx = 9u * (uint32_t)(L::WW * (int)sizeof(S)) + (uint32_t)p.nR * (uint32_t)(ww * 4);
+        cp.tx = (uint32_t)kNPL * (uint32_t)(L::WW * (int)sizeof(S)) + (uint32_t)p.nR * (uint32_t)(ww * 4);
         if (lane == 0) {
             cp.map = &p.pop_map;
             cp.xcol = wsp;
@@ -327,32 +331,76 @@ __device__ __forceinline__ void warp_phase1(const Ctx& c, PRow& st, int r) {
         f7 = IO::dev(IO::un(hi + 7 * RW + 1), ia);
         f8 = IO::dev(IO::un(hi + 8 * RW - 1), ia);
     }
+    if constexpr (Ctx::kJB) {
+        // momentum base: the value in slot k of cell c is the deviation from f_k^rest +
+        // 3 w_k e_k . J(c), J(c) in the slot row's planes 9 and 10 (scaled units); add
+        // back each pulled slot's term at the cell it was read from
+        auto jx = [&](const S* row, int off, bool aligned) {
+            return aligned ? IO::dev(IO::al(row + 9 * RW + off), ia) : IO::dev(IO::un(row + 9 * RW + off), ia);
+        };
+        auto jy = [&](const S* row, int off, bool aligned) {
+            return aligned ? IO::dev(IO::al(row + 10 * RW + off), ia) : IO::dev(IO::un(row + 10 * RW + off), ia);
+        };
+        constexpr float t3 = 1.f / 3.f, t12 = 1.f / 12.f;
+        f1 = fma2(t3, jx(cur, -1, false), f1);     // slot 1 of (x-1, y): e = (1, 0)
+        f3 = fma2(-t3, jx(cur, 1, false), f3);     // slot 3 of (x+1, y): e = (-1, 0)
+        if (!FAST && p.wall_y && r == 0) {         // slots 4, 7, 8 of the cell itself
+            const V2 ox = jx(cur, 0, true), oy = jy(cur, 0, true);
+            f2 = fma2(-t3, oy, f2);
+            f5 = fma2(-t12, ox + oy, f5);
+            f6 = fma2(t12, ox - oy, f6);
+        } else {
+            const S* lo = c.pop(r - 1);
+            f2 = fma2(t3, jy(lo, 0, true), f2);                             // slot 2 of (x, y-1)
+            f5 = fma2(t12, jx(lo, -1, false) + jy(lo, -1, false), f5);      // slot 5 of (x-1, y-1)
+            f6 = fma2(t12, jy(lo, 1, false) - jx(lo, 1, false), f6);        // slot 6 of (x+1, y-1)
+        }
+        if (!FAST && p.wall_y && r == p.ny - 1) {  // slots 2, 5, 6 of the cell itself
+            const V2 ox = jx(cur, 0, true), oy = jy(cur, 0, true);
+            f4 = fma2(t3, oy, f4);
+            f7 = fma2(t12, ox + oy, f7);
+            f8 = fma2(t12, oy - ox, f8);
+        } else {
+            const S* hi = c.pop(r + 1);
+            f4 = fma2(-t3, jy(hi, 0, true), f4);                            // slot 4 of (x, y+1)
+            f7 = fma2(-t12, jx(hi, 1, false) + jy(hi, 1, false), f7);       // slot 7 of (x+1, y+1)
+            f8 = fma2(t12, jx(hi, -1, false) - jy(hi, -1, false), f8);      // slot 8 of (x-1, y+1)
+        }
+    }
     bool sol_a = false, sol_b = false;
     if constexpr (Ctx::kSolid) {
         // a link whose source cell is solid (phi = 0) is a half-way bounce-back link:
         // the population comes from the opposite slot of this cell (the rows past a
-        // y wall were handled above)
-        auto pick = [](V2 f, const S* own, bool ka, bool kb) {
-            if (!(ka || kb)) return f;
-            const V2 o = IO::dev(IO::al(own), 1.f);
-            return mk(ka ? o.v.x : f.v.x, kb ? o.v.y : f.v.y);
-        };
+        // y wall were handled above). The solid flags of the 3 x 4 window first; rows
+        // of warps with no solid cell in it keep the pulls as they are (one vote), the
+        // others select branch-free.
         const float* q0 = c.aux(r, 0);
-        sol_a = q0[0] == 0.f;
-        sol_b = q0[1] == 0.f;
-        f1 = pick(f1, cur + 3 * RW, q0[-1] == 0.f, sol_a);
-        f3 = pick(f3, cur + 1 * RW, sol_b, q0[2] == 0.f);
-        if (!(p.wall_y && r == 0)) {
-            const float* ql = c.aux(r - 1, 0);
-            f2 = pick(f2, cur + 4 * RW, ql[0] == 0.f, ql[1] == 0.f);
-            f5 = pick(f5, cur + 7 * RW, ql[-1] == 0.f, ql[0] == 0.f);
-            f6 = pick(f6, cur + 8 * RW, ql[1] == 0.f, ql[2] == 0.f);
+        const bool lo_in = !(p.wall_y && r == 0), hi_in = !(p.wall_y && r == p.ny - 1);
+        const float* ql = lo_in ? c.aux(r - 1, 0) : q0;
+        const float* qh = hi_in ? c.aux(r + 1, 0) : q0;
+        bool s0[4], sl[4], sh[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            s0[j] = q0[j - 1] == 0.f;
+            sl[j] = lo_in && ql[j - 1] == 0.f;
+            sh[j] = hi_in && qh[j - 1] == 0.f;
         }
-        if (!(p.wall_y && r == p.ny - 1)) {
-            const float* qh = c.aux(r + 1, 0);
-            f4 = pick(f4, cur + 2 * RW, qh[0] == 0.f, qh[1] == 0.f);
-            f7 = pick(f7, cur + 5 * RW, qh[1] == 0.f, qh[2] == 0.f);
-            f8 = pick(f8, cur + 6 * RW, qh[-1] == 0.f, qh[0] == 0.f);
+        sol_a = s0[1];
+        sol_b = s0[2];
+        const bool any = s0[0] | s0[1] | s0[2] | s0[3] | sl[0] | sl[1] | sl[2] | sl[3] | sh[0] | sh[1] | sh[2] | sh[3];
+        if (__any_sync(0xffffffffu, any)) {
+            auto pick = [&](V2 f, int slot, bool ka, bool kb) {
+                const V2 o = IO::dev(IO::al(cur + slot * RW), ia);
+                return mk(ka ? o.v.x : f.v.x, kb ? o.v.y : f.v.y);
+            };
+            f1 = pick(f1, 3, s0[0], s0[1]);
+            f3 = pick(f3, 1, s0[2], s0[3]);
+            f2 = pick(f2, 4, sl[1], sl[2]);
+            f5 = pick(f5, 7, sl[0], sl[1]);
+            f6 = pick(f6, 8, sl[2], sl[3]);
+            f4 = pick(f4, 2, sh[1], sh[2]);
+            f7 = pick(f7, 5, sh[2], sh[3]);
+            f8 = pick(f8, 6, sh[0], sh[1]);
         }
     }
     const V2 a13 = f1 + f3, a24 = f2 + f4, b57 = f5 + f7, b68 = f6 + f8;
@@ -595,7 +643,10 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
         snb = solid_next(Cs.sm, 1);
         if (__any_sync(0xffffffffu, sna || snb)) {
             const bool lo_w = p.wall_y && p3 == 0, hi_w = p.wall_y && p3 == p.ny - 1;
-#pragma unroll
+            // a rolled loop: this block runs only next to solid cells, and six unrolled
+            // copies (three times over in the unrolled row loop) crowd the instruction
+            // cache that the solid-free CTAs on the same SM share
+#pragma unroll 1
             for (int k = 0; k < 6; ++k) {
                 auto fld = [&](const PRow& R) {
                     const V2 u = (k & 1) ? R.uy : R.ux;
@@ -617,12 +668,14 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
                     if (sna) d.v.x = g[0][xy];
                     if (snb) d.v.y = g[1][xy];
                 };
-                if (k == 0) put(xAx, 0);
-                if (k == 1) put(yAy, 1);
-                if (k == 2) { put(xBx, 0); put(yBx, 1); }
-                if (k == 3) { put(yBy, 1); put(xBy, 0); }
-                if (k == 4) put(xDx, 0);
-                if (k == 5) put(yDy, 1);
+                switch (k) {
+                    case 0: put(xAx, 0); break;
+                    case 1: put(yAy, 1); break;
+                    case 2: put(xBx, 0); put(yBx, 1); break;
+                    case 3: put(yBy, 1); put(xBy, 0); break;
+                    case 4: put(xDx, 0); break;
+                    default: put(yDy, 1); break;
+                }
                 if constexpr (Ctx::kEq2) {
                     // G = D - kappa A
 #pragma unroll
@@ -730,6 +783,24 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
 
     // f_0's rest value follows phi to t+1 (it is stored against phi(t+1))
     if (!FAST || Ctx::kUnsteady) fo[0] = fma2(sizeof(S) == 4 ? p.rest.rho0 : p.rho0s, phi - phin, fo[0]);
+    // momentum base: this cell's post-collision momentum (m_3+, m_5+), rounded to the
+    // storage type, is stored with the slots and each slot keeps its deviation from
+    // 3 w_i e_i . J as well (these remainders carry no momentum)
+    V2 Jq{}, Jqy{};
+    if constexpr (Ctx::kJB) {
+        Jq = IO::round_rn(a[3]);
+        Jqy = IO::round_rn(a[5]);
+        constexpr float t3 = 1.f / 3.f, t12 = 1.f / 12.f;
+        const V2 sp = t12 * (Jq + Jqy), sm = t12 * (Jq - Jqy);
+        fo[1] = fma2(-t3, Jq, fo[1]);
+        fo[3] = fma2(t3, Jq, fo[3]);
+        fo[2] = fma2(-t3, Jqy, fo[2]);
+        fo[4] = fma2(t3, Jqy, fo[4]);
+        fo[5] = fo[5] - sp;
+        fo[7] = fo[7] + sp;
+        fo[6] = fo[6] + sm;
+        fo[8] = fo[8] - sm;
+    }
     // one 2-wide store per population for every lane whose first column is inside
     // the lattice; the second column may then be the first ghost column, which the
     // ghost refresh after the step overwrites (the one-warp kernels leave all ghost
@@ -761,6 +832,10 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
 #pragma unroll
             for (int i = 0; i < 9; ++i)
                 IO::st_sr(cell + i * p.plane, fo[i], h0 * (0x2545F491u + 0x9E3779B8u * (uint32_t)i));
+            if constexpr (Ctx::kJB) {
+                IO::st(cell + 9 * p.plane, Jq);     // exact: already rounded
+                IO::st(cell + 10 * p.plane, Jqy);
+            }
         }
     }
 }
@@ -848,17 +923,17 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
     return ok;
 }
 
-template <typename S, int MINB, bool SUMS = false, bool EQ2 = false, bool SOLID = false>
-__global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_constant__ StepParams<float> p) {
-    using L = WarpLayout<S>;
-    extern __shared__ __align__(128) unsigned char smem[];
+// One CTA of the one-warp step kernel (the kernel below picks the instance).
+template <typename S, bool SUMS, bool EQ2, bool SOLID, bool JB>
+__device__ __forceinline__ void warp_step_cta(const StepParams<float>& p, unsigned char* smem, int bx, int by) {
+    using L = WarpLayout<S, JB ? 11 : 9>;
     const int lane = threadIdx.x;
     constexpr int A = L::A;
-    const int x0 = blockIdx.x * p.W;
-    const int y0 = blockIdx.y * p.H;
+    const int x0 = bx * p.W;
+    const int y0 = by * p.H;
     const int y1 = min(y0 + p.H, p.ny);
 
-    WarpCtx<S, SUMS, EQ2, SOLID> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
+    WarpCtx<S, SUMS, EQ2, SOLID, JB> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
     if constexpr (sizeof(S) == 2) c.step = p.step_ctr ? *p.step_ctr : 0u;
     c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
     c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
@@ -907,6 +982,25 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
     }
 }
 
+template <typename S, int MINB, bool SUMS = false, bool EQ2 = false, bool SOLID = false, bool JB = false>
+__global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_constant__ StepParams<float> p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if constexpr (SOLID) {
+        // the tiles with solid cells run first (tile_order); a CTA whose staged rows and
+        // columns hold no solid cell runs the solid-free path (with its branch-free
+        // interior rows)
+        int t = blockIdx.y * gridDim.x + blockIdx.x;
+        if (p.solid_tiles && p.tile_order) t = p.tile_order[t];
+        const int bx = t % gridDim.x, by = t / gridDim.x;
+        if (p.solid_tiles && !p.solid_tiles[t])
+            warp_step_cta<S, SUMS, EQ2, false, JB>(p, smem, bx, by);
+        else
+            warp_step_cta<S, SUMS, EQ2, true, JB>(p, smem, bx, by);
+    } else {
+        warp_step_cta<S, SUMS, EQ2, false, JB>(p, smem, blockIdx.x, blockIdx.y);
+    }
+}
+
 }  // namespace lbmv
 
 namespace lbmv {
@@ -919,5 +1013,16 @@ cudaError_t warp_solid_configure(size_t smem_max);
 template <typename S>
 cudaError_t warp_solid_launch(const StepParams<float>& p, dim3 grid, size_t smem, cudaStream_t stream, bool sums,
                               bool eq2);
+
+// The FP16 / BF16 instances with the momentum base (the JB template argument),
+// compiled in vanse_warp_jb.cu; kernel returns the plain (sums = eq2 = false) instance
+// for occupancy queries.
+template <typename S>
+cudaError_t warp_jb_configure(size_t smem_max);
+template <typename S>
+cudaError_t warp_jb_launch(const StepParams<float>& p, dim3 grid, size_t smem, cudaStream_t stream, bool sums,
+                           bool eq2);
+template <typename S>
+const void* warp_jb_kernel();
 
 }  // namespace lbmv

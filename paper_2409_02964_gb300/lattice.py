@@ -77,13 +77,15 @@ class Lattice:
     is the relaxation time of the shear moments (nu = (tau - 1/2)/3); ``s_e <= 0``
     derives the energy rate from nu_e = nu/3 (Eq. A12); ``s_eps``, ``s_q``, ``s_c``
     are rates; ``kappa`` is the provisional equation-of-state constant.
+    ``dev_base="momentum"`` stores FP16 / BF16 deviations from f^rest plus the
+    momentum term of the equilibrium (lbm_dev_base; kernel 5).
     """
 
     def __init__(self, nx: int, ny: int, tau: float = 0.8, *, s_e: float = 0.0, s_eps: float = 1.2,
                  s_q: float = 1.4, s_c: float = 1.0, kappa: float = 0.5, rho0: float = 1.0,
                  bc_y: str = "periodic", bc_x: str = "periodic", storage: str = "fp32", model_b: bool = False,
                  scale_log2: int | None = None, strip_rows: int = 0, eager: bool = False, kernel: int = 0,
-                 eq_order: int = 3, stream=None):
+                 eq_order: int = 3, dev_base: str = "rest", stream=None):
         L = capi.load()
         p = capi.default_params()
         p.nx, p.ny, p.tau_nu = int(nx), int(ny), float(tau)
@@ -97,6 +99,7 @@ class Lattice:
         p.eager = int(bool(eager))
         p.kernel = int(kernel)
         p.eq_order = int(eq_order)
+        p.dev_base = {"rest": capi.LBM_BASE_REST, "momentum": capi.LBM_BASE_MOMENTUM}[dev_base]
         self.nx, self.ny, self.storage = int(nx), int(ny), storage
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
