@@ -91,6 +91,7 @@ struct lbm_vanse {
     long long steps = 0;
     // step-kernel launch shape
     int W = 0, H = 0, gridx = 0, gridy = 0;
+    int resident = 1;             // step-kernel CTAs resident on the device
     // replayed graph of kGraphSteps steady steps, valid while its key matches
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -230,6 +231,23 @@ const void* step_kernel_ptr(const lbm_vanse* h) {
     return (const void*)vanse_step_kernel<S, R, kThreads>;
 }
 
+// Rows per strip (CTA): strip_rows, or automatically about five waves of resident
+// CTAs (short strips cost halo rows, long ones leave SMs idle in the last wave); ten
+// on kernel 5 with solid cells, whose CTAs next to a solid take several times as long
+// as the others: shorter strips shorten the longest CTA (on the 4096^2 channel with
+// a solid block 56 GLUPS at 24 rows against 49 at 47).
+void pick_strip_height(lbm_vanse* h) {
+    int H = h->prm.strip_rows;
+    if (H <= 0) {
+        const int waves = (h->has_solid && h->kernel == 5) ? 10 : 5;
+        const int nstrips = std::max(1, (waves * h->resident + h->gridx - 1) / h->gridx);
+        H = (h->prm.ny + nstrips - 1) / nstrips;
+        H = std::max(H, 16);
+    }
+    h->H = std::min(H, h->prm.ny);
+    h->gridy = (h->prm.ny + h->H - 1) / h->H;
+}
+
 template <typename S>
 lbm_status configure(lbm_vanse* h) {
     using R = typename Prec<S>::R;
@@ -246,17 +264,8 @@ lbm_status configure(lbm_vanse* h) {
     int per_sm = 0, nsm = 0;
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, s1));
     CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    const int resident = std::max(1, per_sm * nsm);
-    int H = h->prm.strip_rows;
-    if (H <= 0) {
-        // about five waves of resident CTAs: short strips cost halo rows, long ones
-        // leave SMs idle in the last wave
-        const int nstrips = std::max(1, (5 * resident + h->gridx - 1) / h->gridx);
-        H = (h->prm.ny + nstrips - 1) / nstrips;
-        H = std::max(H, 16);
-    }
-    h->H = std::min(H, h->prm.ny);
-    h->gridy = (h->prm.ny + h->H - 1) / h->H;
+    h->resident = std::max(1, per_sm * nsm);
+    pick_strip_height(h);
     return LBM_OK;
 }
 
@@ -1086,6 +1095,15 @@ extern "C" lbm_status lbm_vanse_set_solid_cells(lbm_vanse_t h, int enable) {
         return fail(h, LBM_ERR_ARG, "solid cells and the momentum base together are not supported");
     h->has_solid = enable != 0;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }   // the step's shared memory changes
+    if (h->kernel == 5) {
+        // the strip height follows (pick_strip_height); the tile flags are re-sized
+        const int gy = h->gridy;
+        pick_strip_height(h);
+        if (h->gridy != gy) {
+            if (h->solid_tiles) { cudaFreeAsync(h->solid_tiles, h->stream); h->solid_tiles = nullptr; }
+            if (h->tile_order) { cudaFreeAsync(h->tile_order, h->stream); h->tile_order = nullptr; }
+        }
+    }
     return update_solid_tiles(h);
 }
 

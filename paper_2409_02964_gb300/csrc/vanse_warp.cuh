@@ -214,44 +214,61 @@ __device__ __forceinline__ float left_of(V2 v) { return __shfl_up_sync(0xfffffff
 __device__ __forceinline__ float right_of(V2 v) { return __shfl_down_sync(0xffffffffu, v.v.x, 1); }
 
 // ------------------------------------------------------------------ solid cells
-// The Eq. (10) stencil next to solid cells (phi = 0), neighbour by neighbour. w is the
-// 3 x 4 window of a field around the lane's pair: rows 0, 1, 2 = below, the row, above
-// (the rows past a wall already mapped: the mirror row, negated for a vector
-// component, or the moving wall's extrapolated row), columns 0..3 = xa-1, xa, xb, xb+1.
-// m9: the solid bits of column C's 3 x 3 neighbourhood (bit 3 (dy + 1) + dx + 1). A
-// solid neighbour reads the value mirrored about the solid surface: an axis neighbour
-// the cell itself; a diagonal one the mean of its two axis images (x+dx, y), (x, y+dy)
-// when both are fluid, the fluid one when one is, the cell itself when neither is;
-// negated for a vector component (odd). Returns 12 x the gradient.
-template <int C>
-__device__ __forceinline__ void solid_stencil(const float (&w)[3][4], uint32_t m9, bool odd, float& gx12,
-                                              float& gy12) {
-    constexpr int j = 1 + C;
-    const float own = w[1][j];
-    float sx = 0.f, sy = 0.f;
+// The Eq. (10) stencil next to solid cells (phi = 0). A solid neighbour reads the value
+// mirrored about the solid surface: an axis neighbour the cell itself; a diagonal one
+// the mean of its two axis images (x+dx, y), (x, y+dy) when both are fluid, the fluid
+// one when one is, the cell itself when neither is; negated for a vector component.
+// Being linear in the field, the rule is a set of 3 x 3 weights per cell, built once
+// from the solid mask (branch-free) and applied to every field with that parity.
+// m9: the solid bits of column C's neighbourhood (bit 3 (dy + 1) + dx + 1); sg = -1
+// for a vector component, +1 for a scalar. kx, ky: 12 x the d/dx, d/dy weights at
+// [dy + 1][dx + 1].
+__device__ __forceinline__ void solid_weights(uint32_t m9, float sg, float (&kx)[3][3], float (&ky)[3][3]) {
+    auto bit = [&](int dx, int dy) { return ((m9 >> (3 * (dy + 1) + dx + 1)) & 1u) != 0u; };
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const float cw = (dx != 0 && dy != 0) ? 1.f : 4.f;   // 36 w_i
+            kx[dy + 1][dx + 1] = (dx == 0 && dy == 0) ? 0.f : cw * (float)dx;
+            ky[dy + 1][dx + 1] = (dx == 0 && dy == 0) ? 0.f : cw * (float)dy;
+        }
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
             if (dx == 0 && dy == 0) continue;
-            float v = w[dy + 1][j + dx];
-            if ((m9 >> (3 * (dy + 1) + dx + 1)) & 1u) {
-                v = own;
-                if (dx != 0 && dy != 0) {
-                    const bool fa = !((m9 >> (3 + dx + 1)) & 1u), fb = !((m9 >> (3 * (dy + 1) + 1)) & 1u);
-                    const float va = w[1][j + dx], vb = w[dy + 1][j];
-                    if (fa && fb) v = 0.5f * (va + vb);
-                    else if (fa) v = va;
-                    else if (fb) v = vb;
-                }
-                if (odd) v = -v;
+            const float cw = (dx != 0 && dy != 0) ? 1.f : 4.f;
+            const bool sol = bit(dx, dy);
+            const float wx = sol ? cw * (float)dx : 0.f, wy = sol ? cw * (float)dy : 0.f;
+            kx[dy + 1][dx + 1] -= wx;
+            ky[dy + 1][dx + 1] -= wy;
+            if (dx == 0 || dy == 0) {
+                kx[1][1] = fmaf(sg, wx, kx[1][1]);
+                ky[1][1] = fmaf(sg, wy, ky[1][1]);
+            } else {
+                const bool fa = !bit(dx, 0), fb = !bit(0, dy);
+                const float ca = fa ? (fb ? 0.5f : 1.f) : 0.f, cb = fb ? (fa ? 0.5f : 1.f) : 0.f;
+                const float cc = (fa || fb) ? 0.f : 1.f;
+                kx[1][dx + 1] = fmaf(sg * ca, wx, kx[1][dx + 1]);
+                ky[1][dx + 1] = fmaf(sg * ca, wy, ky[1][dx + 1]);
+                kx[dy + 1][1] = fmaf(sg * cb, wx, kx[dy + 1][1]);
+                ky[dy + 1][1] = fmaf(sg * cb, wy, ky[dy + 1][1]);
+                kx[1][1] = fmaf(sg * cc, wx, kx[1][1]);
+                ky[1][1] = fmaf(sg * cc, wy, ky[1][1]);
             }
-            const float k = (dx != 0 && dy != 0) ? 1.f : 4.f;   // 36 w_i
-            sx = fmaf(k * (float)dx, v, sx);
-            sy = fmaf(k * (float)dy, v, sy);
         }
-    gx12 = sx;
-    gy12 = sy;
+}
+
+// sum_{dy, dx} k[dy + 1][dx + 1] w[dy + 1][1 + C + dx]: column C of the pair
+template <int C>
+__device__ __forceinline__ float solid_apply(const float (&w)[3][4], const float (&k)[3][3]) {
+    float a = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a = fmaf(k[r][c], w[r][C + c], a);
+    return a;
 }
 
 // the 4-wide row window of a pair field: xa-1 (from the lane below), xa, xb, xb+1
@@ -478,11 +495,11 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
             win_row(w[0], lo);
             win_row(w[1], Bs.rho);
             win_row(w[2], hi);
-            float gxa, gya, gxb, gyb;
-            solid_stencil<0>(w, sm & 0x1FFu, false, gxa, gya);
-            solid_stencil<1>(w, (sm >> 9) & 0x1FFu, false, gxb, gyb);
-            if (na) { gx.v.x = tw * gxa; gy.v.x = tw * gya; }
-            if (nb) { gx.v.y = tw * gxb; gy.v.y = tw * gyb; }
+            float kx[3][3], ky[3][3];
+            solid_weights(sm & 0x1FFu, 1.f, kx, ky);
+            if (na) { gx.v.x = tw * solid_apply<0>(w, kx); gy.v.x = tw * solid_apply<0>(w, ky); }
+            solid_weights((sm >> 9) & 0x1FFu, 1.f, kx, ky);
+            if (nb) { gx.v.y = tw * solid_apply<1>(w, kx); gy.v.y = tw * solid_apply<1>(w, ky); }
         }
     }
     const V2 phi = c.phi2(p2, Bs);
@@ -643,6 +660,10 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
         snb = solid_next(Cs.sm, 1);
         if (__any_sync(0xffffffffu, sna || snb)) {
             const bool lo_w = p.wall_y && p3 == 0, hi_w = p.wall_y && p3 == p.ny - 1;
+            // the weights of both columns (vector components), once for the six fields
+            float ka_x[3][3], ka_y[3][3], kb_x[3][3], kb_y[3][3];
+            solid_weights(Cs.sm & 0x1FFu, -1.f, ka_x, ka_y);
+            solid_weights((Cs.sm >> 9) & 0x1FFu, -1.f, kb_x, kb_y);
             // a rolled loop: this block runs only next to solid cells, and six unrolled
             // copies (three times over in the unrolled row loop) crowd the instruction
             // cache that the solid-free CTAs on the same SM share
@@ -662,8 +683,10 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
                 win_row(w[1], m);
                 win_row(w[2], h);
                 float g[2][2];   // column, x / y
-                solid_stencil<0>(w, Cs.sm & 0x1FFu, true, g[0][0], g[0][1]);
-                solid_stencil<1>(w, (Cs.sm >> 9) & 0x1FFu, true, g[1][0], g[1][1]);
+                g[0][0] = solid_apply<0>(w, ka_x);
+                g[0][1] = solid_apply<0>(w, ka_y);
+                g[1][0] = solid_apply<1>(w, kb_x);
+                g[1][1] = solid_apply<1>(w, kb_y);
                 auto put = [&](V2& d, int xy) {
                     if (sna) d.v.x = g[0][xy];
                     if (snb) d.v.y = g[1][xy];
