@@ -40,13 +40,17 @@ DTYPE = {"fp32": "f32", "fp16": "f32", "bf16": "f32", "fp64": "f64"}
 SBYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}
 
 
-def _config(n: int, storage: str, gpus: int) -> dict:
+def _config(n: int, storage: str, gpus: int, dev_base: str = "rest") -> dict:
     """The workload as both arms name it (identical keys and values): the lattice, and
-    how the timed steps relate to L2 (inputs larger than L2, no flush needed)."""
-    pop_gb = 2 * 9 * n * n * SBYTES[storage] / 1e9
-    return {"workload": WORKLOAD, "nx": n, "ny": n, "storage": storage,
-            "l2": f"inputs larger than L2: two population buffers of {pop_gb:.2f} GB against the 129 MB L2",
-            "parallelism": "replicas" if gpus > 1 else "single"}
+    how the timed steps relate to L2 (inputs larger than L2, no flush needed); the
+    FP16 / BF16 deviation base when it is not the rest state."""
+    pop_gb = 2 * (11 if dev_base == "momentum" else 9) * n * n * SBYTES[storage] / 1e9
+    cfg = {"workload": WORKLOAD, "nx": n, "ny": n, "storage": storage,
+           "l2": f"inputs larger than L2: two population buffers of {pop_gb:.2f} GB against the 129 MB L2",
+           "parallelism": "replicas" if gpus > 1 else "single"}
+    if dev_base != "rest":
+        cfg["dev_base"] = dev_base
+    return cfg
 
 
 def _kernel_traffic(cells: int):
@@ -517,7 +521,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(args.n, args.storage, args.gpus),
+        "config": _config(args.n, args.storage, args.gpus, args.dev_base),
         "arithmetic": "FP64 oracle on the host cores",
         "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
                          "sample": sample},
@@ -537,6 +541,8 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--strip-rows", type=int, default=0)
     ap.add_argument("--kernel", type=int, default=0, help="step-kernel variant (0 = the library's choice)")
+    ap.add_argument("--dev-base", choices=["rest", "momentum"], default="rest",
+                    help="FP16 / BF16 deviation base (momentum: lbm_dev_base LBM_BASE_MOMENTUM)")
     ap.add_argument("--quick", action="store_true", help="timed steps only (no e2e / variants / CPU baseline)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-lattice workload")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-lattice workload")
@@ -580,7 +586,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    lat, phi = build_channel(args.n, args.storage, args.strip_rows, args.kernel)
+    lat, phi = build_channel(args.n, args.storage, args.strip_rows, args.kernel, dev_base=args.dev_base)
     cells = args.n * args.n
     m0 = lat.reduce()[0]
     if dist:
@@ -607,7 +613,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.storage], "data": "synthetic",
-            "config": _config(args.n, args.storage, world),
+            "config": _config(args.n, args.storage, world, args.dev_base),
             "bytes_per_cell": bpc, "launch": shape,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
