@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_vanse.so")
-SOURCES = ["lbm_vanse.cu", "vanse_warp_solid.cu", "vanse_warp_jb.cu", "lbm_vanse3d.cu"]
+SOURCES = ["lbm_vanse.cu", "vanse_warp_solid.cu", "vanse_warp_jb.cu", "vanse_warp_nee.cu", "lbm_vanse3d.cu"]
 HEADERS = ["vanse_common.cuh", "vanse_step.cuh", "vanse_aux.cuh", "vanse_pair.cuh", "vanse_warp.cuh",
            "vanse_batch.cuh", "mms_force.cuh", "vanse_adjoint.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

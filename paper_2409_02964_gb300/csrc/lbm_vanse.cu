@@ -107,6 +107,7 @@ struct lbm_vanse {
     bool use_graphs = true;
     bool sums_configured = false; // shared-memory attributes set on the step-sum kernel variant
     bool solid_configured = false;  // ... and on the solid-cell variants
+    bool nee_configured = false;    // ... and on kernel 5's moving-wall instances
     // uploads from pinned host memory: copied on their own stream into device staging
     // buffers (phi(t), phi(t+1)), so the copy overlaps the work already queued on
     // `stream`; staging_free marks the last read of the staging buffers on `stream`
@@ -283,6 +284,18 @@ const void* step_sums_kernel_ptr(const lbm_vanse* h) {
     return (const void*)vanse_step_kernel<S, R, kThreads, true>;   // (solid cells: launch_solid_step)
 }
 
+// Kernel 5 with the moving wall: its instances' shared-memory attributes, on first use.
+template <typename S>
+lbm_status configure_nee(lbm_vanse* h) {
+    if constexpr (!std::is_same<S, double>::value) {
+        if (!h->nee_configured) {
+            CK(h, warp_nee_configure<S>(step_smem_max<S>(h)));
+            h->nee_configured = true;
+        }
+    }
+    return LBM_OK;
+}
+
 // Kernel 1 with solid cells: a variant of its own (the neighbour-by-neighbour stencil
 // and the 3-row rings stay out of the other kernels); shared-memory attributes set on
 // first use.
@@ -397,7 +410,11 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
                 if constexpr (sizeof(S) == 2) {
                     if (h->jbase) CK(h, warp_jb_launch<S>(p, grid, smem, stream, true, p.eq2 != 0));
                 }
-                if (!h->jbase) {
+                if (!h->jbase && h->nee_top) {
+                    lbm_status st = configure_nee<S>(h);
+                    if (st != LBM_OK) return st;
+                    CK(h, warp_nee_launch<S>(p, grid, smem, stream, true, p.eq2 != 0));
+                } else if (!h->jbase) {
                     if (p.eq2) vanse_warp_kernel<S, LBMV_WARP_MINB, true, true><<<grid, 32, smem, stream>>>(p);
                     else vanse_warp_kernel<S, LBMV_WARP_MINB, true><<<grid, 32, smem, stream>>>(p);
                 }
@@ -422,7 +439,11 @@ lbm_status enqueue_step(lbm_vanse* h, cudaStream_t stream, int src, double* sums
                 if constexpr (sizeof(S) == 2) {
                     if (h->jbase) CK(h, warp_jb_launch<S>(p, grid, smem, stream, false, p.eq2 != 0));
                 }
-                if (!h->jbase) {
+                if (!h->jbase && h->nee_top) {
+                    lbm_status st = configure_nee<S>(h);
+                    if (st != LBM_OK) return st;
+                    CK(h, warp_nee_launch<S>(p, grid, smem, stream, false, p.eq2 != 0));
+                } else if (!h->jbase) {
                     if (p.eq2) vanse_warp_kernel<S, LBMV_WARP_MINB, false, true><<<grid, 32, smem, stream>>>(p);
                     else vanse_warp_kernel<S, LBMV_WARP_MINB><<<grid, 32, smem, stream>>>(p);
                 }

@@ -68,6 +68,7 @@ struct BatchCtx {
     static constexpr bool kEq2 = false;
     static constexpr bool kSolid = false;
     static constexpr bool kJB = false;
+    static constexpr bool kNee = false;
     StepParams<float> p;       // this lattice's scalars (pointers and sizes included)
     unsigned char* smem;
     int lane, xa, sa;

@@ -98,7 +98,7 @@ struct PairSums {
     }
 };
 
-template <typename S, bool SUMS = false, bool EQ2 = false, bool SOLID = false, bool JB = false>
+template <typename S, bool SUMS = false, bool EQ2 = false, bool SOLID = false, bool JB = false, bool NEE = false>
 struct WarpCtx {
     static constexpr int kNPL = JB ? 11 : 9;   // planes per staged row
     using L = WarpLayout<S, kNPL>;
@@ -107,6 +107,10 @@ struct WarpCtx {
     static constexpr bool kEq2 = EQ2;          // App. B: (B2) energy-flux equilibria, (B3) penalty
     static constexpr bool kSolid = SOLID;      // phi = 0 marks solid cells (general path only)
     static constexpr bool kJB = JB;            // FP16 / BF16 deviations from the momentum base
+    // the moving wall's code (row ny-1 by non-equilibrium extrapolation): compiled only
+    // into the instances that may meet it, since even untaken it slows the general row
+    // path by about 7 % (instruction-cache footprint)
+    static constexpr bool kNee = NEE || SOLID || JB;
     const StepParams<float>& p;
     unsigned char* smem;
     int lane, xa, sa;
@@ -472,7 +476,7 @@ __device__ __forceinline__ void warp_phase2(const Ctx& c, const PRow& An, PRow& 
         if (p2 == p.ny - 1) {
             // rho's ghost past a half-way wall is the mirror row (the row itself); past
             // the moving wall row it extrapolates linearly, 2 (row ny-1) - (row ny-2)
-            if (p.nee_top) { dhi = fma2(2.f, Bs.dr, -Cs.dr); whi = fma2(2.f, Bs.wr, -Cs.wr); }
+            if (Ctx::kNee && p.nee_top) { dhi = fma2(2.f, Bs.dr, -Cs.dr); whi = fma2(2.f, Bs.wr, -Cs.wr); }
             else { dhi = Bs.dr; whi = Bs.wr; }
         }
     }
@@ -629,7 +633,7 @@ __device__ __forceinline__ void warp_phase3(const Ctx& c, const PRow& An, const 
     // the rows around row p3: An holds row p3-1, Bs row p3+1. Past a half-way wall the
     // ghost row is the negated mirror row (no-slip); past the moving wall row (the
     // top row with nee_top) the linear extrapolation 2 (row ny-1) - (row ny-2)
-    const bool nee_hi = !FAST && p.nee_top && p3 == p.ny - 1;
+    const bool nee_hi = !FAST && Ctx::kNee && p.nee_top && p3 == p.ny - 1;
     auto ghi = [&](V2 cs, V2 an, V2 bs) { return nee_hi ? fma2(2.f, cs, -an) : (p3 == p.ny - 1 ? -cs : bs); };
     if (!FAST && p.wall_y && (p3 == 0 || p3 == p.ny - 1)) {
         const bool lo = (p3 == 0);
@@ -911,7 +915,7 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
         }
         const bool ph1 = (p1 <= y1 + 1) && c.row_valid(p1);
         // the moving wall row (its moments follow once row ny-2 has its velocity)
-        const bool nee_row = c.p.nee_top && p1 == c.p.ny - 1;
+        const bool nee_row = Ctx::kNee && c.p.nee_top && p1 == c.p.ny - 1;
         if (ph1) {
             warp_phase1<S, false>(c, An, p1);
             if (nee_row) { An.rho = Bs.rho; An.rf = Bs.rf; }   // rho_b = rho_f
@@ -947,7 +951,7 @@ __device__ __forceinline__ bool warp_run_strip(Ctx& c) {
 }
 
 // One CTA of the one-warp step kernel (the kernel below picks the instance).
-template <typename S, bool SUMS, bool EQ2, bool SOLID, bool JB>
+template <typename S, bool SUMS, bool EQ2, bool SOLID, bool JB, bool NEE>
 __device__ __forceinline__ void warp_step_cta(const StepParams<float>& p, unsigned char* smem, int bx, int by) {
     using L = WarpLayout<S, JB ? 11 : 9>;
     const int lane = threadIdx.x;
@@ -956,7 +960,7 @@ __device__ __forceinline__ void warp_step_cta(const StepParams<float>& p, unsign
     const int y0 = by * p.H;
     const int y1 = min(y0 + p.H, p.ny);
 
-    WarpCtx<S, SUMS, EQ2, SOLID, JB> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
+    WarpCtx<S, SUMS, EQ2, SOLID, JB, NEE> c{p, smem, lane, 0, 0, y0, y1, 0, 0, 0, 0, 0, 0, false};
     if constexpr (sizeof(S) == 2) c.step = p.step_ctr ? *p.step_ctr : 0u;
     c.wsp = ((kPadCols + x0 - kGhost) / A) * A;
     c.ww = ((kPadCols + x0 + 63 + A - 1) / A) * A - c.wsp;
@@ -1005,7 +1009,8 @@ __device__ __forceinline__ void warp_step_cta(const StepParams<float>& p, unsign
     }
 }
 
-template <typename S, int MINB, bool SUMS = false, bool EQ2 = false, bool SOLID = false, bool JB = false>
+template <typename S, int MINB, bool SUMS = false, bool EQ2 = false, bool SOLID = false, bool JB = false,
+          bool NEE = false>
 __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_constant__ StepParams<float> p) {
     extern __shared__ __align__(128) unsigned char smem[];
     if constexpr (SOLID) {
@@ -1016,11 +1021,11 @@ __global__ void __launch_bounds__(32, MINB) vanse_warp_kernel(const __grid_const
         if (p.solid_tiles && p.tile_order) t = p.tile_order[t];
         const int bx = t % gridDim.x, by = t / gridDim.x;
         if (p.solid_tiles && !p.solid_tiles[t])
-            warp_step_cta<S, SUMS, EQ2, false, JB>(p, smem, bx, by);
+            warp_step_cta<S, SUMS, EQ2, false, JB, true>(p, smem, bx, by);
         else
-            warp_step_cta<S, SUMS, EQ2, true, JB>(p, smem, bx, by);
+            warp_step_cta<S, SUMS, EQ2, true, JB, true>(p, smem, bx, by);
     } else {
-        warp_step_cta<S, SUMS, EQ2, false, JB>(p, smem, blockIdx.x, blockIdx.y);
+        warp_step_cta<S, SUMS, EQ2, false, JB, NEE>(p, smem, blockIdx.x, blockIdx.y);
     }
 }
 
@@ -1047,5 +1052,13 @@ cudaError_t warp_jb_launch(const StepParams<float>& p, dim3 grid, size_t smem, c
                            bool eq2);
 template <typename S>
 const void* warp_jb_kernel();
+
+// The instances with the moving wall's code (the NEE template argument), compiled in
+// vanse_warp_nee.cu.
+template <typename S>
+cudaError_t warp_nee_configure(size_t smem_max);
+template <typename S>
+cudaError_t warp_nee_launch(const StepParams<float>& p, dim3 grid, size_t smem, cudaStream_t stream, bool sums,
+                            bool eq2);
 
 }  // namespace lbmv
