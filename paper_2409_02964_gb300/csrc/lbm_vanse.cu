@@ -966,6 +966,16 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
     if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_BOUNCEBACK) return fail(nullptr, LBM_ERR_ARG, "bad bc_y");
     if (p->storage < LBM_FP64 || p->storage > LBM_BF16) return fail(nullptr, LBM_ERR_ARG, "bad storage");
     if (p->strip_rows < 0) return fail(nullptr, LBM_ERR_ARG, "strip_rows must be >= 0");
+    if (p->dev_base != LBM_BASE_REST && p->dev_base != LBM_BASE_MOMENTUM)
+        return fail(nullptr, LBM_ERR_ARG, "dev_base must be LBM_BASE_REST or LBM_BASE_MOMENTUM");
+    if (p->dev_base == LBM_BASE_MOMENTUM) {
+        if (p->storage != LBM_FP16 && p->storage != LBM_BF16)
+            return fail(nullptr, LBM_ERR_ARG, "the momentum base is an FP16 / BF16 storage form");
+        // the kernel the lattice would run (the default rule below)
+        const int k = p->kernel ? p->kernel : (p->bc_x == LBM_BC_BOUNCEBACK ? 1 : kDefaultKernel);
+        if (k != 5)
+            return fail(nullptr, LBM_ERR_ARG, "the momentum base runs on step kernel 5 (this lattice: kernel %d)", k);
+    }
 
     lbm_vanse* h = new lbm_vanse();
     h->prm = *p;
@@ -1007,20 +1017,7 @@ extern "C" lbm_status lbm_vanse_create(const lbm_vanse_params* p, void* cuda_str
     if (h->prm.eq_order == 0) h->prm.eq_order = 3;
     h->kernel = p->kernel ? p->kernel
                           : ((p->storage == LBM_FP64 || p->bc_x == LBM_BC_BOUNCEBACK) ? 1 : kDefaultKernel);
-    if (p->dev_base != LBM_BASE_REST && p->dev_base != LBM_BASE_MOMENTUM) {
-        delete h;
-        return fail(nullptr, LBM_ERR_ARG, "dev_base must be LBM_BASE_REST or LBM_BASE_MOMENTUM");
-    }
-    if (p->dev_base == LBM_BASE_MOMENTUM && (p->storage != LBM_FP16 && p->storage != LBM_BF16)) {
-        delete h;
-        return fail(nullptr, LBM_ERR_ARG, "the momentum base is an FP16 / BF16 storage form");
-    }
-    if (p->dev_base == LBM_BASE_MOMENTUM && h->kernel != 5) {
-        delete h;
-        return fail(nullptr, LBM_ERR_ARG, "the momentum base runs on step kernel 5 (this lattice: kernel %d)",
-                    h->kernel);
-    }
-    h->jbase = p->dev_base == LBM_BASE_MOMENTUM;
+    h->jbase = p->dev_base == LBM_BASE_MOMENTUM;   // (checked above)
     h->npl = h->jbase ? 11 : 9;
     h->pair = h->kernel >= 2;
     h->W = h->kernel == 5 ? 60 : (h->pair ? 2 * kPairT[h->kernel - 2] - 4 : kThreads - 4);

@@ -77,3 +77,52 @@ def test_graft_entry_build_compiles_everything():
     g.build()
     from paper_2409_02964_gb300 import build
     assert os.path.exists(build.LIB)
+
+
+def _header_struct(name):
+    """(field, c type) of `typedef struct { ... } name;` in include/*.h, in order."""
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", h)).read(), flags=re.S)
+        m = re.search(r"typedef\s+struct\s*\{([^}]*)\}\s*" + name + r"\s*;", src)
+        if m:
+            out = []
+            for decl in m.group(1).split(";"):
+                decl = decl.strip()
+                if not decl:
+                    continue
+                m2 = re.match(r"((?:(?:unsigned|long|short)\s+)*\w+)\s+(.*)$", decl, flags=re.S)
+                ctype, names = " ".join(m2.group(1).split()), m2.group(2)
+                out += [(n.strip(), ctype) for n in names.split(",")]
+            return out
+    raise AssertionError(f"{name} not found")
+
+
+def test_ctypes_structs_match_the_header():
+    from paper_2409_02964_gb300 import capi
+    ct = {ctypes.c_int: "int", ctypes.c_double: "double", ctypes.c_longlong: "long long"}
+    for name in ("lbm_vanse_params", "lbm_vanse3d_params", "lbm_vanse_batch_lattice", "lbm_vanse_batch_params",
+                 "lbm_vanse_adjoint_params", "lbm_vanse_adjoint_stats"):
+        py = [(f, ct[t]) for f, t in getattr(capi, name)._fields_]
+        assert py == _header_struct(name), name
+
+
+def test_momentum_base_checks_without_gpu():
+    """lbm_dev_base: checked before any CUDA call, like the other arguments."""
+    from paper_2409_02964_gb300 import capi
+    L = capi.load()
+    h = ctypes.c_void_p()
+    p = capi.default_params()
+    assert p.dev_base == capi.LBM_BASE_REST
+    p.nx, p.ny = 16, 8
+    for storage, kernel, bc_x, dev_base, word in (
+            (capi.LBM_BF16, 0, capi.LBM_BC_PERIODIC, 7, b"dev_base"),
+            (capi.LBM_FP32, 0, capi.LBM_BC_PERIODIC, capi.LBM_BASE_MOMENTUM, b"FP16 / BF16"),
+            (capi.LBM_FP64, 0, capi.LBM_BC_PERIODIC, capi.LBM_BASE_MOMENTUM, b"FP16 / BF16"),
+            (capi.LBM_BF16, 1, capi.LBM_BC_PERIODIC, capi.LBM_BASE_MOMENTUM, b"kernel 5"),
+            (capi.LBM_FP16, 2, capi.LBM_BC_PERIODIC, capi.LBM_BASE_MOMENTUM, b"kernel 5"),
+            (capi.LBM_FP16, 0, capi.LBM_BC_BOUNCEBACK, capi.LBM_BASE_MOMENTUM, b"kernel 5")):
+        p.storage, p.kernel, p.bc_x, p.dev_base = storage, kernel, bc_x, dev_base
+        assert L.lbm_vanse_create(ctypes.byref(p), None, ctypes.byref(h)) == capi.LBM_ERR_ARG
+        assert word in L.lbm_vanse_last_error(None), L.lbm_vanse_last_error(None)
