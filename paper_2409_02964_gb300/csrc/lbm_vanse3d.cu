@@ -288,8 +288,21 @@ __device__ __forceinline__ void equilibrium_deviation(T kappa, T phi, T rho, T d
     m[2] = (T)12 * phi * drho - (T)9 * kappa * drho - (T)5.5 * m0u2;
 }
 
-// the collision's tile: 32 x 2 x 2 cells (one thread each) and a one-cell halo
-constexpr int TX = 32, TY = 2, TZ = 2, HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HN = HX * HY * HZ;
+// the collision's tile: 32 x 2 x 2 cells (one thread each) and a one-cell halo (larger
+// tiles, 32 x 4 x 2 to 32 x 4 x 4, stage fewer halo cells per cell but ran slower)
+#ifndef LBMV3_TY
+#define LBMV3_TY 2
+#endif
+#ifndef LBMV3_TZ
+#define LBMV3_TZ 2
+#endif
+// resident collision CTAs per SM the register allocation is sized for: 7 (72 registers,
+// about 150 bytes of L1-cached spills per thread) ran the 256^3 FP32 step 11 % faster
+// than the unbounded 96 registers (5 CTAs)
+#ifndef LBMV3_MINB
+#define LBMV3_MINB 7
+#endif
+constexpr int TX = 32, TY = LBMV3_TY, TZ = LBMV3_TZ, HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HN = HX * HY * HZ;
 
 __device__ __forceinline__ int modp(int v, int n) {
     v %= n;
@@ -297,7 +310,7 @@ __device__ __forceinline__ int modp(int v, int n) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TX * TY * TZ) v3_collide(const T* __restrict__ f, T* __restrict__ fo,
+__global__ void __launch_bounds__(TX * TY * TZ, LBMV3_MINB) v3_collide(const T* __restrict__ f, T* __restrict__ fo,
                                                            const T* __restrict__ rho, const T* __restrict__ u,
                                                            const T* __restrict__ F, const T* __restrict__ phi,
                                                            const T* __restrict__ phin, Rates<T> R, Geo g) {
