@@ -52,7 +52,7 @@ struct BatchParams {
 struct ForcePair {
     V2 fx, fy;
 };
-__device__ __noinline__ ForcePair mms_force_pair(V2 sx, V2 cx, float sy, float cy, float ct, float st, float k,
+__device__ __forceinline__ ForcePair mms_force_pair(V2 sx, V2 cx, float sy, float cy, float ct, float st, float k,
                                                  float w, float A, float U0, float phi0, float nu) {
     ForcePair r;
     mms_force<V2>(sx, cx, bc(sy), bc(cy), ct, st, k, w, A, U0, phi0, nu, r.fx, r.fy);
